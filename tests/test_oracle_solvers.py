@@ -1,0 +1,254 @@
+"""Pins for oracle.relax, oracle.tb and oracle.krylov (Sec. 3.1, Eqs. 2-3, App. C):
+library special cases, matrix splittings, invariants and brute force."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import scenes
+from oracle import assemble, krylov, relax, tb
+
+
+def _small(n=20, dim=2, k0=9.0, cells=4, seed=0, box=(8, 11)):
+    rng = np.random.default_rng(seed)
+    mask = (scenes.ring_mask(dim, n) | scenes.box_mask(dim, n, *box)).reshape(-1).astype(np.uint8)
+    k2 = assemble.k2_field(dim, n, k0, cells, 0.5)
+    A = assemble.assemble(dim, n, k2, mask)
+    N = n ** dim
+    src = np.where(mask == 0, rng.standard_normal(N) + 1j * rng.standard_normal(N), 0)
+    b = assemble.rhs(dim, n, mask, src, np.zeros(N, complex))
+    return A, b, mask, rng
+
+
+# ----------------------------------------------------------------- relaxation
+def test_jacobi_matches_splitting_form():
+    """Damped Jacobi written as x' = (1-w) x + w D^-1 (f - (L+U) x)."""
+    A, b, mask, rng = _small()
+    x0 = rng.standard_normal(b.size) + 1j * rng.standard_normal(b.size)
+    D = sp.diags(A.diagonal())
+    LU_ = A - D
+    x = x0.copy()
+    for _ in range(3):
+        x = (1 - 0.6) * x + 0.6 * (b - LU_ @ x) / A.diagonal()
+    y = relax.jacobi(A, b, x0, 0.6, 3)
+    assert np.linalg.norm(x - y) <= 1e-13 * np.linalg.norm(x)
+
+
+def test_rbgs_equals_lexicographic_gs_on_permuted_system():
+    """Red-black GS = forward GS on the red-first permuted matrix."""
+    A, b, mask, rng = _small(n=11, box=(4, 6))
+    n, dim = 11, 2
+    col = assemble.colour(dim, n)
+    perm = np.concatenate([np.flatnonzero(col == 0), np.flatnonzero(col == 1)])
+    P = A[perm][:, perm].tocsr()
+    bp = b[perm]
+    x0 = rng.standard_normal(b.size) + 1j * rng.standard_normal(b.size)
+    xp = x0[perm].copy()
+    L = sp.tril(P, 0).tocsr()
+    U = sp.triu(P, 1).tocsr()
+    for _ in range(2):
+        xp = spla.spsolve_triangular(L, bp - U @ xp, lower=True)
+    y = relax.rbgs(A, b, x0, col, 2)
+    assert np.linalg.norm(y[perm] - xp) <= 1e-12 * np.linalg.norm(xp)
+
+
+def test_colour_is_checkerboard():
+    c = assemble.colour(3, 4).reshape(4, 4, 4)
+    assert c[0, 0, 0] == 0 and c[0, 0, 1] == 1 and c[1, 1, 0] == 0 and c[1, 2, 3] == 0
+
+
+def test_relaxations_converge_on_poisson():
+    """k = 0 (negative-definite Laplacian): Jacobi and RBGS converge to the LU solution."""
+    n = 12
+    mask = scenes.ring_mask(2, n).reshape(-1).astype(np.uint8)
+    A = assemble.assemble(2, n, np.zeros(n * n, complex), mask)
+    rng = np.random.default_rng(0)
+    b = np.where(mask == 0, rng.standard_normal(n * n), 0).astype(complex)
+    u = spla.spsolve(A.tocsc(), b)
+    xj = relax.jacobi(A, b, np.zeros_like(b), 1.0, 2000)
+    xg = relax.rbgs(A, b, np.zeros_like(b), assemble.colour(2, n), 800)
+    assert np.linalg.norm(xj - u) <= 1e-9 * np.linalg.norm(u)
+    assert np.linalg.norm(xg - u) <= 1e-9 * np.linalg.norm(u)
+
+
+def test_plain_jacobi_diverges_with_scatterer():
+    """Sec. 4.1: plain relaxation diverges on the scattering problem."""
+    sc = scenes.square2d(0)
+    A, b, _ = assemble.problem(sc)
+    x, info = krylov.relaxation_metasolver(A, b, np.zeros_like(b), "jacobi", 20, None, max_cycles=200)
+    assert info["res"][-1] > 10 * info["res"][0]
+
+
+# ------------------------------------------------------------------ TB coarse
+def _tb_small(p=12):
+    A, b, mask, rng = _small()
+    X = scenes.node_coords(2, 20)
+    layers = scenes.glorot_mlp(rng, [2, 16, 16, p])
+    return A, b, mask, rng, X, layers
+
+
+def test_tb_orthonormal_and_zero_on_mask():
+    A, b, mask, rng, X, layers = _tb_small()
+    s = tb.tb_setup(A, layers, X, mask, 12)
+    assert np.max(np.abs(s.Q.T @ s.Q - np.eye(12))) < 1e-14
+    assert np.all(s.Q[mask == 1] == 0)
+
+
+def test_tb_galerkin_linear_and_basis_invariant():
+    A, b, mask, rng, X, layers = _tb_small()
+    s = tb.tb_setup(A, layers, X, mask, 12)
+    r1 = rng.standard_normal(b.size) + 1j * rng.standard_normal(b.size)
+    r2 = rng.standard_normal(b.size) + 1j * rng.standard_normal(b.size)
+    z = tb.tb_correct(s, r1)
+    # Galerkin: the corrected residual is orthogonal to span(Q)
+    assert np.linalg.norm(s.Q.T @ (r1 - A @ z)) <= 1e-12 * np.linalg.norm(s.Q.T @ r1)
+    # linear (App. C: M2 is linear, so it may precondition Krylov methods)
+    al, be = 0.3 - 1.2j, 2.5 + 0.1j
+    lhs = tb.tb_correct(s, al * r1 + be * r2)
+    assert np.linalg.norm(lhs - al * z - be * tb.tb_correct(s, r2)) <= 1e-12 * np.linalg.norm(lhs)
+    # depends only on span(T): any change of basis (incl. column signs) gives the same M2
+    T = tb.trunk_matrix(layers, X, mask, 12)
+    G = rng.standard_normal((12, 12)) * np.sign(rng.standard_normal(12))
+    Q2, _ = np.linalg.qr(T @ G)
+    s2 = tb.tb_setup(A, None, X, mask, 12, Q=Q2)
+    assert np.linalg.norm(tb.tb_correct(s2, r1) - z) <= 1e-10 * np.linalg.norm(z)
+
+
+def test_tb_full_space_is_exact_inverse():
+    """p = number of fluid nodes, Q spanning the fluid space: one correction solves A u = f."""
+    A, b, mask, rng = _small(n=9, box=(3, 4))
+    fluid = np.flatnonzero(mask == 0)
+    Q = np.zeros((b.size, fluid.size))
+    Q[fluid, np.arange(fluid.size)] = 1.0
+    s = tb.tb_setup(A, None, None, mask, fluid.size, Q=Q)
+    u = spla.spsolve(A.tocsc(), b)
+    z = tb.tb_correct(s, b)          # b = 0 on masked nodes, so u = 0 there too
+    assert np.linalg.norm(z - u) <= 1e-12 * np.linalg.norm(u)
+
+
+def test_hybrid_preconditioner_p0_is_plain_relaxation():
+    A, b, mask, rng = _small()
+    r = rng.standard_normal(b.size) + 0j
+    M = tb.hybrid_preconditioner(A, None, "jacobi", 3)
+    assert np.array_equal(M(r), relax.jacobi(A, r, np.zeros_like(r), 0.6, 3))
+
+
+def test_mlp_forward_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    layers = scenes.glorot_mlp(rng, [3, 10, 7, 5])
+    X = rng.random((13, 3))
+    net = []
+    for i, (W, bb) in enumerate(layers):
+        lin = torch.nn.Linear(W.shape[1], W.shape[0]).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(W)); lin.bias.copy_(torch.from_numpy(bb + 0.1 * i))
+        net += [lin, torch.nn.Tanh()]
+    seq = torch.nn.Sequential(*net[:-1])
+    layers_b = [(W, bb + 0.1 * i) for i, (W, bb) in enumerate(layers)]
+    ref = seq(torch.from_numpy(X)).detach().numpy()
+    assert np.max(np.abs(tb.mlp_forward(layers_b, X) - ref)) < 1e-14
+
+
+# --------------------------------------------------------------------- Krylov
+def test_givens_zeroes_second_component():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        a, bb = rng.standard_normal(2) @ [1, 1j], rng.standard_normal(2) @ [1, 1j]
+        c, s, r = krylov.givens(a, bb)
+        assert abs(c * a + s * bb - r) < 1e-14 and abs(-np.conj(s) * a + c * bb) < 1e-14
+        assert abs(c ** 2 + abs(s) ** 2 - 1) < 1e-14
+    assert krylov.givens(0.0, 2.0 + 0j)[2] == 2.0
+
+
+def test_fgmres_unpreconditioned_matches_scipy_gmres():
+    """Identity preconditioner: the per-step residual estimates equal scipy's GMRES."""
+    A, b, mask, rng = _small()
+    x, info = krylov.fgmres(A, b, np.zeros_like(b), None, tol=1e-10, m=20, maxit=20)
+    ref = []
+    spla.gmres(A, b, rtol=1e-14, restart=20, maxiter=1, callback=lambda pr: ref.append(pr),
+               callback_type="pr_norm")
+    ref = np.asarray(ref[: len(info["est"])])
+    assert np.allclose(info["est"], ref, rtol=1e-8, atol=0)
+
+
+def test_fgmres_flexible_arnoldi_relation_and_monotone():
+    A, b, mask, rng, X, layers = _tb_small()
+    s = tb.tb_setup(A, layers, X, mask, 12)
+    M = tb.hybrid_preconditioner(A, s, "jacobi", 1)
+    x, info = krylov.fgmres(A, b, np.zeros_like(b), M, tol=1e-14, m=15, maxit=15, keep_first=True)
+    f = info["first"]
+    k = f["k"]
+    V, Z, H = f["V"][: k + 1], f["Z"][:k], f["H"][: k + 1, :k]
+    AZ = np.stack([A @ z for z in Z])
+    assert np.linalg.norm(AZ.T - V.T @ H) <= 1e-12 * np.linalg.norm(AZ)
+    assert np.max(np.abs(V.conj() @ V.T - np.eye(k + 1))) < 1e-13     # CGS2 orthogonality
+    est = np.asarray(info["est"])
+    assert np.all(np.diff(est) <= 1e-15)
+    # the Givens estimate equals the true residual at the end of the cycle
+    assert abs(info["res"][-1] - est[-1]) <= 1e-9 * est[-1]
+
+
+def test_gmres_full_space_terminates():
+    """GMRES(m >= N) on a tiny system reaches 1e-12 in at most N steps."""
+    A, b, mask, rng = _small(n=6, box=(2, 3))
+    N = b.size
+    x, info = krylov.fgmres(A, b, np.zeros_like(b), None, tol=1e-12, m=N, maxit=N)
+    assert info["status"] == "converged" and info["iters"] <= N
+
+
+def test_bicgstab_unpreconditioned_matches_scipy():
+    """Identity preconditioner: the iterates equal scipy's BiCGStab step by step."""
+    A, b, mask, rng = _small()
+    xs = []
+    spla.bicgstab(A, b, x0=np.zeros_like(b), rtol=1e-30, maxiter=8, callback=lambda xk: xs.append(xk.copy()))
+    for k in (1, 3, 8):
+        x, info = krylov.bicgstab(A, b, np.zeros_like(b), None, tol=1e-30, maxit=k)
+        assert np.linalg.norm(x - xs[k - 1]) <= 1e-10 * np.linalg.norm(xs[k - 1])
+
+
+def test_krylov_metasolvers_reach_lu_solution():
+    A, b, mask, rng, X, layers = _tb_small()
+    s = tb.tb_setup(A, layers, X, mask, 12)
+    u = spla.spsolve(A.tocsc(), b)
+    for method in ("fgmres", "bicgstab"):
+        M = tb.hybrid_preconditioner(A, s, "jacobi" if method == "fgmres" else "rbgs", 1,
+                                     colours=assemble.colour(2, 20))
+        if method == "fgmres":
+            x, info = krylov.fgmres(A, b, np.zeros_like(b), M, tol=1e-11, m=30, maxit=500)
+        else:
+            x, info = krylov.bicgstab(A, b, np.zeros_like(b), M, tol=1e-11, maxit=500)
+        assert info["status"] == "converged"
+        assert np.linalg.norm(b - A @ x) <= 1e-11 * np.linalg.norm(b)
+        assert np.linalg.norm(x - u) <= 1e-8 * np.linalg.norm(u)
+
+
+def test_don_krylov_fewer_iterations_than_plain():
+    """Sec. 4.1 (qualitative): the DeepONet-Krylov method needs far fewer iterations."""
+    sc = scenes.square2d(0)
+    A, b, _ = assemble.problem(sc)
+    s = tb.tb_setup(A, sc.trunk, scenes.node_coords(2, sc.n), sc.mask, sc.p)
+    M = tb.hybrid_preconditioner(A, s, "jacobi", 1)
+    _, i1 = krylov.bicgstab(A, b, np.zeros_like(b), M, 1e-8, 2000)
+    _, i0 = krylov.bicgstab(A, b, np.zeros_like(b), None, 1e-8, 2000)
+    assert i1["status"] == "converged" and i1["iters"] * 2 < i0["iters"]
+
+
+def test_natural_order_select_matches_householder_span():
+    """tau = 0 and a well-conditioned T: same span as numpy's Householder QR;
+    dependent columns are dropped; kept columns are orthonormal."""
+    rng = np.random.default_rng(6)
+    T = rng.standard_normal((200, 8))
+    Q, kept = tb.natural_order_select(T, 0.0)
+    Qh, _ = np.linalg.qr(T)
+    assert kept == list(range(8))
+    assert np.linalg.norm(Q @ Q.T - Qh @ Qh.T) < 1e-13
+    # plant two dependent columns: a copy and a combination
+    T2 = np.column_stack([T[:, 0], T[:, 1], 2 * T[:, 0], T[:, 2], T[:, 1] - T[:, 2] + 1e-12 * T[:, 3]])
+    Q2, kept2 = tb.natural_order_select(T2, 1e-6)
+    assert kept2 == [0, 1, 3]
+    assert np.max(np.abs(Q2.T @ Q2 - np.eye(3))) < 1e-14
+    Qh3, _ = np.linalg.qr(T[:, :3])
+    assert np.linalg.norm(Q2 @ Q2.T - Qh3 @ Qh3.T) < 1e-13
+    # kmax stops early
+    assert tb.natural_order_select(T, 0.0, kmax=3)[1] == [0, 1, 2]
