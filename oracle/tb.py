@@ -107,14 +107,18 @@ def tb_correct(s: TBSetup, r):
 
 def hybrid_preconditioner(A, s: "TBSetup | None", kind: str, n_r: int, omega: float = 0.6,
                           colours=None):
-    """z = M(r): n_r relaxation sweeps from zero, then the TB correction."""
+    """z = M(r): n_r relaxation sweeps from zero, then the TB correction.
+    With neither sweeps nor a correction M is the identity (plain Krylov)."""
+    if (kind == "none" or n_r <= 0) and s is None:
+        return lambda r: np.array(r, dtype=np.complex128, copy=True)
+
     def M(r):
         z = np.zeros_like(r, dtype=np.complex128)
-        if kind == "jacobi":
+        if kind == "jacobi" and n_r > 0:
             z = relax.jacobi(A, r, z, omega, n_r)
-        elif kind == "rbgs":
+        elif kind == "rbgs" and n_r > 0:
             z = relax.rbgs(A, r, z, colours, n_r)
-        elif kind != "none":
+        elif kind not in ("none", "jacobi", "rbgs"):
             raise ValueError(kind)
         if s is not None:
             z = z + tb_correct(s, r - A @ z)

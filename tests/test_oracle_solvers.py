@@ -126,6 +126,13 @@ def test_tb_full_space_is_exact_inverse():
     assert np.linalg.norm(z - u) <= 1e-12 * np.linalg.norm(u)
 
 
+def test_hybrid_preconditioner_without_stages_is_identity():
+    A, b, mask, rng = _small()
+    r = rng.standard_normal(b.size) + 1j * rng.standard_normal(b.size)
+    assert np.array_equal(tb.hybrid_preconditioner(A, None, "none", 0)(r), r)
+    assert np.array_equal(tb.hybrid_preconditioner(A, None, "jacobi", 0)(r), r)
+
+
 def test_hybrid_preconditioner_p0_is_plain_relaxation():
     A, b, mask, rng = _small()
     r = rng.standard_normal(b.size) + 0j
@@ -252,3 +259,19 @@ def test_natural_order_select_matches_householder_span():
     assert np.linalg.norm(Q2 @ Q2.T - Qh3 @ Qh3.T) < 1e-13
     # kmax stops early
     assert tb.natural_order_select(T, 0.0, kmax=3)[1] == [0, 1, 2]
+
+
+def test_oracle_bicgstab_rounding_sensitivity():
+    """Documents why BiCGStab iterates are compared only over the first steps: a
+    relative perturbation of 1e-15 in f grows by many orders of magnitude within
+    ten iterations (while both runs still converge to the same solution)."""
+    A, b, mask, rng, X, layers = _tb_small()
+    s = tb.tb_setup(A, layers, X, mask, 12)
+    M = tb.hybrid_preconditioner(A, s, "rbgs", 1, colours=assemble.colour(2, 20))
+    bp = b * (1 + 1e-15 * rng.standard_normal(b.size))
+    x1, _ = krylov.bicgstab(A, b, np.zeros_like(b), M, 1e-30, 2)
+    x2, _ = krylov.bicgstab(A, bp, np.zeros_like(b), M, 1e-30, 2)
+    assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
+    y1, _ = krylov.bicgstab(A, b, np.zeros_like(b), M, 1e-12, 500)
+    y2, _ = krylov.bicgstab(A, bp, np.zeros_like(b), M, 1e-12, 500)
+    assert np.linalg.norm(y1 - y2) <= 1e-9 * np.linalg.norm(y1)
