@@ -1,0 +1,188 @@
+/*
+ * helm.h -- C ABI of libhelm: GB300 (sm_103a) meta-solvers for the discretised
+ * complex Helmholtz equation with an absorbing layer and a sound-soft scatterer
+ * (arXiv 2405.12380, "Fast meta-solvers for 3D complex-shape scatterers using
+ * neural operators trained on a non-scattering problem").
+ *
+ * Problem (Eq. 1, finite-difference reading): on n^d nodes of [0,1]^d,
+ * d in {2,3}, h = 1/(n-1), flat index l = i + n*(j + n*k) (x fastest),
+ *   fluid rows   (A x)_l = h^-2 sum_{fluid nbr m} x_m + (k_l^2 - 2d h^-2) x_l
+ *   masked rows  (A x)_l = x_l                  (Dirichlet: scatterer + outer ring)
+ *   k_l^2 = k0^2 (1 + i*s*eta_l^2), eta_l = max_a max(0, L - dist_a)/L,
+ *   dist_a = min(i_a, n-1-i_a)     (absorbing layer of L cells, strength s)
+ * unless a per-node complex k^2 field is supplied.  A is complex symmetric, so
+ * A^H = conj(A); every operator entry point takes a `conj` flag for the adjoint.
+ *
+ * Conventions
+ *  - Every call returns helm_status (0 = HELM_OK).  helm_last_error() gives a
+ *    message for the last failing call on a handle.  No call asserts or traps.
+ *  - Arrays marked [dev] are device pointers owned by the caller; [host] are
+ *    host pointers.  Complex data is interleaved (re, im): complex128 = 2 doubles,
+ *    complex64 = 2 floats.  Vectors have N = n^d entries.
+ *  - Calls are asynchronous on the handle's stream (helm_set_stream), except
+ *    don_load, helm_solve and helm_solve_host, which synchronise and return
+ *    statistics.
+ *  - The handle owns its workspace (trunk basis, coarse operator, Krylov
+ *    vectors) and frees it in helm_destroy.  It copies the mask and k^2 field.
+ *  - No CPU fallback: without an sm_103a device helm_create returns HELM_NO_DEVICE.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_handle helm_handle;
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_BAD_ARG = 1,          /* argument out of range, wrong dtype, null pointer */
+    HELM_NO_DEVICE = 2,        /* no sm_103a GPU visible */
+    HELM_CUDA_ERROR = 3,       /* a CUDA runtime call failed */
+    HELM_NOT_CONVERGED = 4,    /* maxit reached above tol */
+    HELM_DIVERGED = 5,         /* residual > 1e8 * initial, or NaN/Inf */
+    HELM_BREAKDOWN = 6,        /* BiCGStab rho or omega = 0, (t,t) = 0 */
+    HELM_SINGULAR_COARSE = 7,  /* zero pivot in the coarse operator A_c */
+    HELM_NOT_READY = 8,        /* correction requested before don_load */
+    HELM_OUT_OF_MEMORY = 9
+} helm_status;
+
+/* dtype of the vectors passed to a call */
+enum { HELM_C128 = 0, HELM_C64 = 1 };
+/* precision mode of a handle: FP64 everywhere, or complex64 preconditioner
+ * (stencil, relaxation, projection with a BF16-rounded Q) inside an FP64 outer
+ * FGMRES (Arnoldi, Hessenberg/Givens, true residual in FP64). */
+enum { HELM_FP64 = 0, HELM_MIXED = 1 };
+/* relaxation kinds (Sec. 3.1.1: M = diag(A) -> Jacobi, lower triangle -> GS) */
+enum { HELM_RELAX_NONE = 0, HELM_JACOBI = 1, HELM_RBGS = 2 };
+/* second-stage correction M2 (Eq. 3): none, trunk-basis Galerkin (App. C) */
+enum { HELM_CORR_NONE = 0, HELM_CORR_TB = 1 };
+/* outer methods */
+enum { HELM_METHOD_RELAX = 0, HELM_METHOD_FGMRES = 1, HELM_METHOD_BICGSTAB = 2 };
+/* trunk activations on hidden layers */
+enum { HELM_ACT_TANH = 0 };
+
+/* Options of one solve.  `relax`, `n_r`, `omega` and `correction` define the
+ * hybrid cycle M (Eq. 3): n_r relaxation sweeps from zero, then M2 on the new
+ * residual.  METHOD_RELAX runs that cycle as a Richardson iteration on A u = f
+ * (relaxation meta-solver); FGMRES/BICGSTAB use it as a right preconditioner
+ * (Krylov meta-solver).  Convergence: ||f - A x||_2 <= tol ||f||_2, true residual
+ * in FP64.  `restart` is m of FGMRES(m) (<= 256).  `maxit` counts Arnoldi
+ * steps / BiCGStab iterations / relaxation cycles.  conj = 1 solves with
+ * conj(A) = A^H (adjoint), using the conjugated preconditioner. */
+typedef struct {
+    int method;
+    int relax;
+    int n_r;
+    double omega;
+    int correction;
+    double tol;
+    int restart;
+    int maxit;
+    int conj;
+} helm_solve_opts;
+
+typedef struct {
+    int status;          /* helm_status of the solve */
+    int iters;           /* Arnoldi steps / BiCGStab iterations / cycles */
+    int cycles;          /* FGMRES restarts, BiCGStab restarts */
+    int precond_applies;
+    int matvecs;
+    double rel_res;      /* final true relative residual ||f - A x|| / ||f|| */
+    double ms;           /* device time of the solve (CUDA events) */
+    long long launches;  /* kernels launched by the solve */
+    int n_restrict;      /* trunk-basis restrictions (fused residual + Q^T r) */
+    int n_prolong;       /* trunk-basis prolongations (z += Q y) */
+    double restrict_ms;  /* summed CUDA-event time of the restriction kernels (profiling on) */
+    double prolong_ms;   /* summed CUDA-event time of the prolongation kernels (profiling on) */
+} helm_stats;
+
+/* Create a problem handle.  Eq. 1 on n^dim nodes (dim 2 or 3, 3 <= n <= 2048,
+ * n^dim < 2^31), wavenumber k0, absorbing layer of `layer_cells` cells with
+ * strength s (Im k^2 ramps to s*k0^2).  mask [dev] N bytes, 1 = Dirichlet node;
+ * the outer node ring must be masked (HELM_BAD_ARG otherwise, checked on device).
+ * k2 [dev] N complex128 or NULL: when given it is the full k^2 of every fluid
+ * node and the layer formula is not applied.  precision: HELM_FP64 or
+ * HELM_MIXED.  The handle keeps its own copies of mask and k2. */
+helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer_strength,
+                        const uint8_t* mask, const double* k2, int precision,
+                        helm_handle** out);
+helm_status helm_destroy(helm_handle* h);
+/* stream: a cudaStream_t (NULL = legacy default stream). */
+helm_status helm_set_stream(helm_handle* h, void* stream);
+const char* helm_last_error(const helm_handle* h);
+/* on = 1: bracket every trunk-basis restriction/prolongation kernel with CUDA
+ * events on the handle's stream and report their summed time in helm_stats. */
+helm_status helm_set_profiling(helm_handle* h, int on);
+/* Grid query: N, h. */
+helm_status helm_info(const helm_handle* h, long long* N, double* hstep);
+
+/* k2_out [dev] N complex128 = k0^2 * scale_l * (1 + i*s*eta_l^2) with the
+ * layer profile of the handle; scale [dev] N doubles or NULL (= 1). */
+helm_status helm_layer_k2(helm_handle* h, const double* scale, double* k2_out);
+
+/* Right-hand side with the Dirichlet data moved across (App. D): b_l = g_l on
+ * masked nodes, b_l = src_l - h^-2 sum_{masked nbr m} g_m on fluid nodes.
+ * src, g, b [dev] complex128. */
+helm_status helm_rhs(helm_handle* h, const double* src, const double* g, double* b);
+
+/* y = A x (conj = 0) or conj(A) x (conj = 1).  x, y [dev], dtype HELM_C128 or
+ * HELM_C64, must not overlap. */
+helm_status helm_apply(helm_handle* h, const void* x, void* y, int conj, int dtype);
+
+/* r = f - A x; if norm2 [dev] is not NULL, *norm2 = ||r||_2^2 (FP64). */
+helm_status helm_residual(helm_handle* h, const void* f, const void* x, void* r,
+                          double* norm2, int conj, int dtype);
+
+/* `sweeps` relaxation sweeps on A x = f in place (Eq. 2):
+ * HELM_JACOBI: x <- x + omega D^-1 (f - A x), D = diag(A) (1 on masked rows);
+ * HELM_RBGS:   red ((i+j+k) even) then black half-sweeps, x_l <- x_l + D_l^-1 (f - A x)_l
+ *              with the latest neighbours (omega unused). */
+helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const void* f,
+                       void* x, int conj, int dtype);
+
+/* Load the trunk network and build the trunk-basis coarse space (App. C):
+ * T_lj = trunk(x_l)_j (Eq. 6) for j < p, zero rows on masked nodes; natural-order
+ * selection keeps column j when its part orthogonal to the columns already kept
+ * exceeds tau * ||T_j|| (tau = 0 keeps every nonzero column); Q orthonormal with
+ * span(Q) = span(selected columns); A_c = Q^T A Q (complex, k x k); A_c^-1 by
+ * Gauss-Jordan with partial pivoting.
+ * weights [host] FP64: per layer W (row-major out x in) then bias; widths[0] = dim,
+ * widths[n_layers] >= p; activation on hidden layers only.  p <= 256.
+ * Synchronises.  Returns HELM_SINGULAR_COARSE on a zero pivot. */
+helm_status don_load(helm_handle* h, const double* weights, const int* widths, int n_layers,
+                     int act, int p, double tau);
+/* k = number of kept columns; kept_idx [host] (p ints) or NULL. */
+helm_status don_info(const helm_handle* h, int* k, int* kept_idx);
+/* Copy Q (N x k FP64, row-major: k contiguous per node) into q_out [dev]. */
+helm_status don_get_q(const helm_handle* h, double* q_out);
+/* Copy A_c^-1 (k x k complex128, row-major) into out [dev]. */
+helm_status don_get_ainv(const helm_handle* h, double* out);
+
+/* z += M2 r = Q A_c^-1 Q^T r (mode HELM_CORR_TB).  r, z [dev] HELM_C128. */
+helm_status don_correct(helm_handle* h, int mode, const void* r, void* z, int conj, int dtype);
+
+/* z = M(r), the hybrid cycle of `opts` (Eq. 3).  r, z [dev] HELM_C128. */
+helm_status helm_precond(helm_handle* h, const helm_solve_opts* opts, const void* r, void* z);
+
+/* Solve A x = f (conj(A) x = f if opts->conj).  f [dev] complex128, x [dev]
+ * complex128: initial guess in, solution out.  Masked entries of x are set to
+ * f on entry (x_l = g_l).  res_hist [host] or NULL: relative true residual
+ * after every restart/cycle, up to hist_len values (FGMRES: per Arnoldi step,
+ * Givens estimate).  Synchronises; stats [host] may be NULL. */
+helm_status helm_solve(helm_handle* h, const helm_solve_opts* opts, const void* f, void* x,
+                       helm_stats* stats, double* res_hist, int hist_len);
+
+/* As helm_solve with f and x in host memory [host] (pinned or pageable): the
+ * copies to and from the device are part of the call. */
+helm_status helm_solve_host(helm_handle* h, const helm_solve_opts* opts, const double* f,
+                            double* x, helm_stats* stats, double* res_hist, int hist_len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

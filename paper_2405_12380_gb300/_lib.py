@@ -1,0 +1,83 @@
+"""ctypes binding of libhelm.so (argument marshalling only).
+
+Every name here mirrors a declaration in include/helm.h.  Loading fails loudly
+when the in-tree library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhelm.so")
+
+HELM_OK, HELM_BAD_ARG, HELM_NO_DEVICE, HELM_CUDA_ERROR = 0, 1, 2, 3
+HELM_NOT_CONVERGED, HELM_DIVERGED, HELM_BREAKDOWN, HELM_SINGULAR_COARSE = 4, 5, 6, 7
+HELM_NOT_READY, HELM_OUT_OF_MEMORY = 8, 9
+STATUS_NAMES = {0: "ok", 1: "bad_arg", 2: "no_device", 3: "cuda_error", 4: "not_converged",
+                5: "diverged", 6: "breakdown", 7: "singular_coarse", 8: "not_ready", 9: "out_of_memory"}
+HELM_C128, HELM_C64 = 0, 1
+HELM_FP64, HELM_MIXED = 0, 1
+HELM_RELAX_NONE, HELM_JACOBI, HELM_RBGS = 0, 1, 2
+HELM_CORR_NONE, HELM_CORR_TB = 0, 1
+HELM_METHOD_RELAX, HELM_METHOD_FGMRES, HELM_METHOD_BICGSTAB = 0, 1, 2
+HELM_ACT_TANH = 0
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("method", C.c_int), ("relax", C.c_int), ("n_r", C.c_int), ("omega", C.c_double),
+                ("correction", C.c_int), ("tol", C.c_double), ("restart", C.c_int),
+                ("maxit", C.c_int), ("conj", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("cycles", C.c_int),
+                ("precond_applies", C.c_int), ("matvecs", C.c_int), ("rel_res", C.c_double),
+                ("ms", C.c_double), ("launches", C.c_longlong), ("n_restrict", C.c_int),
+                ("n_prolong", C.c_int), ("restrict_ms", C.c_double), ("prolong_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+vp, i32, f64, i64 = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+H = C.c_void_p
+
+SIGNATURES = {
+    "helm_create": (i32, [i32, i32, f64, i32, f64, vp, vp, i32, C.POINTER(H)]),
+    "helm_destroy": (i32, [H]),
+    "helm_set_stream": (i32, [H, vp]),
+    "helm_last_error": (C.c_char_p, [H]),
+    "helm_set_profiling": (i32, [H, i32]),
+    "helm_info": (i32, [H, C.POINTER(i64), C.POINTER(f64)]),
+    "helm_layer_k2": (i32, [H, vp, vp]),
+    "helm_rhs": (i32, [H, vp, vp, vp]),
+    "helm_apply": (i32, [H, vp, vp, i32, i32]),
+    "helm_residual": (i32, [H, vp, vp, vp, vp, i32, i32]),
+    "helm_relax": (i32, [H, i32, f64, i32, vp, vp, i32, i32]),
+    "don_load": (i32, [H, vp, C.POINTER(i32), i32, i32, i32, f64]),
+    "don_info": (i32, [H, C.POINTER(i32), C.POINTER(i32)]),
+    "don_get_q": (i32, [H, vp]),
+    "don_get_ainv": (i32, [H, vp]),
+    "don_correct": (i32, [H, i32, vp, vp, i32, i32]),
+    "helm_precond": (i32, [H, C.POINTER(SolveOpts), vp, vp]),
+    "helm_solve": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(Stats), vp, i32]),
+    "helm_solve_host": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(Stats), vp, i32]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libhelm (raises if the in-tree build is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libhelm.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib

@@ -1,0 +1,870 @@
+// C ABI of libhelm and the host drivers of the meta-solvers (Sec. 3.1).
+//
+// The drivers only launch kernels and read back a few status words from pinned
+// memory; every vector operation, reduction and scalar recurrence runs on the
+// device (stencil.cu, blas.cu, tb.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "helm_internal.cuh"
+
+using namespace helm;
+
+namespace {
+
+helm_status fail(helm_handle* h, helm_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(h, HELM_CUDA_ERROR, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                                        \
+    do {                                                                                             \
+        cudaError_t e_ = cudaGetLastError();                                                         \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(h, HELM_CUDA_ERROR, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(expr)                          \
+    do {                                   \
+        helm_status st_ = (expr);          \
+        if (st_ != HELM_OK) return st_;    \
+    } while (0)
+
+template <typename T>
+helm_status dalloc(helm_handle* h, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return HELM_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(h, HELM_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return HELM_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+int round32(int k) { return ((k + 31) / 32) * 32; }
+
+helm_status ensure_tmp(helm_handle* h, size_t count) {
+    while (h->tmp.size() < count) {
+        double2* p = nullptr;
+        TRY(dalloc(h, &p, (size_t)h->N));
+        h->tmp.push_back(p);
+    }
+    return HELM_OK;
+}
+
+helm_status ensure_tmp32(helm_handle* h, size_t count) {
+    while (h->tmp32.size() < count) {
+        float2* p = nullptr;
+        TRY(dalloc(h, &p, (size_t)h->N));
+        h->tmp32.push_back(p);
+    }
+    return HELM_OK;
+}
+
+double* scal(helm_handle* h, int slot) { return reinterpret_cast<double*>(h->sc + slot); }
+
+helm_status poll(helm_handle* h) {
+    CK(cudaMemcpyAsync(h->hpin, h->sc, S_NSLOTS * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return HELM_OK;
+}
+double hs(const helm_handle* h, int slot, int im = 0) { return h->hpin[2 * slot + im]; }
+
+// ||f - A x||^2 into slot (FP64)
+helm_status residual_norm(helm_handle* h, const double2* f, const double2* x, double2* r, int conj, int slot) {
+    launch_apply<double>(h->op64, x, f, r, h->red, conj, true, h->stream);
+    launch_sum_real(h->red, apply_grid_blocks(h->dim, h->n), scal(h, slot), h->stream);
+    h->launches += 2;
+    CKL();
+    return HELM_OK;
+}
+
+helm_status norm2_into(helm_handle* h, const double2* a, int slot) {
+    launch_norm2(a, h->N, h->red, h->stream);
+    launch_sum_real(h->red, kRedBlocks, scal(h, slot), h->stream);
+    h->launches += 2;
+    CKL();
+    return HELM_OK;
+}
+
+// z = n sweeps of the relaxation on A z = r from z = 0 (FP64)
+helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, const double2* r, double2* z,
+                            int conj) {
+    cudaStream_t s = h->stream;
+    if (kind == HELM_RELAX_NONE || sweeps <= 0) {
+        CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
+        return HELM_OK;
+    }
+    if (kind == HELM_JACOBI) {
+        TRY(ensure_tmp(h, 1));
+        // sweep 1 from zero writes z; later sweeps ping-pong so that the last lands in z
+        double2* a = (sweeps % 2 == 1) ? z : h->tmp[0];
+        double2* b = (sweeps % 2 == 1) ? h->tmp[0] : z;
+        launch_jacobi<double>(h->op64, omega, r, nullptr, a, conj, true, s);
+        for (int q = 1; q < sweeps; ++q) {
+            launch_jacobi<double>(h->op64, omega, r, a, b, conj, false, s);
+            std::swap(a, b);
+        }
+        h->launches += sweeps;
+        CKL();
+        return HELM_OK;
+    }
+    if (kind == HELM_RBGS) {
+        CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
+        for (int q = 0; q < sweeps; ++q) {
+            launch_rbgs_half<double>(h->op64, 0, r, z, conj, q == 0, s);
+            launch_rbgs_half<double>(h->op64, 1, r, z, conj, false, s);
+        }
+        h->launches += 2 * sweeps;
+        CKL();
+        return HELM_OK;
+    }
+    return fail(h, HELM_BAD_ARG, "unknown relaxation kind");
+}
+
+// event pair around one launch of phase ph (0 = restrict, 1 = prolong)
+void ev_mark(helm_handle* h, int ph, int end) {
+    if (!h->profile) return;
+    auto& pool = h->evpool[ph];
+    const size_t need = 2 * (size_t)h->evn[ph] + 2;
+    while (pool.size() < need) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        pool.push_back(e);
+    }
+    cudaEventRecord(pool[2 * h->evn[ph] + end], h->stream);
+    if (end) ++h->evn[ph];
+}
+
+double ev_sum(helm_handle* h, int ph) {
+    double t = 0;
+    for (int q = 0; q < h->evn[ph]; ++q) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->evpool[ph][2 * q], h->evpool[ph][2 * q + 1]);
+        t += ms;
+    }
+    return t;
+}
+
+// z += Q A_c^-1 Q^T (v - A zres)   (zres may be null: plain restriction of v)
+helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, double2* z, int conj) {
+    if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
+    const int nblk = restrict_blocks(h->N);
+    ev_mark(h, 0, 0);
+    launch_restrict(h->op64, h->Q, h->ldq, h->k, v, zres, conj, h->coarse_partials, nblk, h->stream);
+    ev_mark(h, 0, 1);
+    launch_coarse_apply(h->coarse_partials, nblk, h->k, h->ldq, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
+    ev_mark(h, 1, 0);
+    launch_prolong(h->Q, h->ldq, h->k, h->ybuf, z, h->N, h->stream);
+    ev_mark(h, 1, 1);
+    h->launches += 3;
+    CKL();
+    return HELM_OK;
+}
+
+helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
+    TRY(relax_from_zero(h, o->relax, o->omega, o->n_r, r, z, conj));
+    if (o->correction == HELM_CORR_TB) {
+        const bool zero = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
+        TRY(tb_correct(h, r, zero ? nullptr : z, z, conj));
+    }
+    return HELM_OK;
+}
+
+helm_status check_opts(helm_handle* h, const helm_solve_opts* o) {
+    if (!o) return fail(h, HELM_BAD_ARG, "opts is NULL");
+    if (o->method < 0 || o->method > 2) return fail(h, HELM_BAD_ARG, "unknown method");
+    if (o->relax < 0 || o->relax > 2) return fail(h, HELM_BAD_ARG, "unknown relaxation");
+    if (o->correction < 0 || o->correction > 1) return fail(h, HELM_BAD_ARG, "unknown correction");
+    if (o->correction == HELM_CORR_TB && !h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
+    if (o->method == HELM_METHOD_FGMRES && (o->restart < 1 || o->restart > kMaxRestart))
+        return fail(h, HELM_BAD_ARG, "restart must be in 1..64");
+    if (!(o->tol >= 0) || o->maxit < 0 || o->n_r < 0) return fail(h, HELM_BAD_ARG, "bad tol/maxit/n_r");
+    return HELM_OK;
+}
+
+struct Hist {
+    double* buf;
+    int len, n = 0;
+    void push(double v) {
+        if (buf && n < len) buf[n] = v;
+        ++n;
+    }
+};
+
+// ------------------------------------------------------------- relaxation
+helm_status solve_relax(helm_handle* h, const helm_solve_opts* o, const double2* f, double2* x, helm_stats* st,
+                        Hist& hist, double bnorm) {
+    TRY(ensure_tmp(h, 2));
+    double2* r = h->tmp[1];
+    int cycles = 0;
+    while (true) {
+        TRY(residual_norm(h, f, x, r, o->conj, S_RN2));
+        ++st->matvecs;
+        TRY(poll(h));
+        const double res = std::sqrt(hs(h, S_RN2)) / bnorm;
+        hist.push(res);
+        st->rel_res = res;
+        if (res <= o->tol) { st->status = HELM_OK; break; }
+        if (!std::isfinite(res) || res > 1e8) { st->status = HELM_DIVERGED; break; }
+        if (cycles >= o->maxit) { st->status = HELM_NOT_CONVERGED; break; }
+        if (o->relax == HELM_JACOBI) {
+            TRY(ensure_tmp(h, 1));
+            double2* a = x;
+            double2* b = h->tmp[0];
+            for (int q = 0; q < o->n_r; ++q) {
+                launch_jacobi<double>(h->op64, o->omega, f, a, b, o->conj, false, h->stream);
+                std::swap(a, b);
+            }
+            h->launches += o->n_r;
+            if (a != x) CK(cudaMemcpyAsync(x, a, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        } else if (o->relax == HELM_RBGS) {
+            for (int q = 0; q < o->n_r; ++q) {
+                launch_rbgs_half<double>(h->op64, 0, f, x, o->conj, false, h->stream);
+                launch_rbgs_half<double>(h->op64, 1, f, x, o->conj, false, h->stream);
+            }
+            h->launches += 2 * o->n_r;
+        }
+        CKL();
+        if (o->correction == HELM_CORR_TB) {
+            TRY(tb_correct(h, f, x, x, o->conj));
+            ++st->precond_applies;
+        }
+        ++cycles;
+    }
+    st->iters = cycles;
+    st->cycles = cycles;
+    return HELM_OK;
+}
+
+// ---------------------------------------------------------------- FGMRES(m)
+helm_status ensure_krylov(helm_handle* h, int m) {
+    if (h->m_alloc >= m) return HELM_OK;
+    dfree(h->V); dfree(h->Z); dfree(h->Hm); dfree(h->cs); dfree(h->sn); dfree(h->g); dfree(h->y); dfree(h->hpart);
+    h->m_alloc = 0;
+    TRY(dalloc(h, &h->V, (size_t)(m + 1) * h->N));
+    TRY(dalloc(h, &h->Z, (size_t)m * h->N));
+    TRY(dalloc(h, &h->Hm, (size_t)(m + 1) * m));
+    TRY(dalloc(h, &h->cs, (size_t)m));
+    TRY(dalloc(h, &h->sn, (size_t)m));
+    TRY(dalloc(h, &h->g, (size_t)(m + 1)));
+    TRY(dalloc(h, &h->y, (size_t)2 * (kMaxRestart + 1)));
+    TRY(dalloc(h, &h->hpart, (size_t)kRedBlocks * (m + 1)));
+    h->m_alloc = m;
+    return HELM_OK;
+}
+
+helm_status solve_fgmres(helm_handle* h, const helm_solve_opts* o, const double2* f, double2* x, helm_stats* st,
+                         Hist& hist, double bnorm) {
+    const int m = o->restart;
+    TRY(ensure_krylov(h, m));
+    const long long N = h->N;
+    cudaStream_t s = h->stream;
+    const int ldh = m + 1;
+    double2* h2 = h->y + (kMaxRestart + 1);
+    int iters = 0, cycles = 0;
+    while (true) {
+        double2* V0 = h->V;
+        TRY(residual_norm(h, f, x, V0, o->conj, S_BETA2));
+        ++st->matvecs;
+        TRY(poll(h));
+        const double beta = std::sqrt(hs(h, S_BETA2));
+        st->rel_res = beta / bnorm;
+        if (cycles == 0) hist.push(beta / bnorm);
+        if (beta <= o->tol * bnorm) { st->status = HELM_OK; break; }
+        if (!std::isfinite(beta)) { st->status = HELM_DIVERGED; break; }
+        if (iters >= o->maxit) { st->status = HELM_NOT_CONVERGED; break; }
+        ++cycles;
+        launch_init_g(h->g, m + 1, scal(h, S_BETA2), s);
+        launch_scale_vec(V0, V0, scal(h, S_BETA2), N, s);
+        h->launches += 2;
+        CK(cudaMemsetAsync(h->Hm, 0, sizeof(double2) * (m + 1) * m, s));
+        int kdim = 0;
+        for (int j = 0; j < m; ++j) {
+            double2* Vj = h->V + (long long)j * N;
+            double2* Zj = h->Z + (long long)j * N;
+            double2* w = h->V + (long long)(j + 1) * N;
+            double2* Hcol = h->Hm + (long long)j * ldh;
+            TRY(precond(h, o, Vj, Zj, o->conj));
+            ++st->precond_applies;
+            launch_apply<double>(h->op64, Zj, nullptr, w, nullptr, o->conj, false, s);
+            h->launches += 1;
+            ++st->matvecs;
+            // CGS2: h = V^H w, w -= V h, h2 = V^H w, w -= V h2, h += h2
+            launch_mdot(h->V, j + 1, w, N, h->hpart, s);
+            launch_mdot_finalize(h->hpart, kRedBlocks, j + 1, Hcol, 0, nullptr, s);
+            launch_mupdate(h->V, j + 1, Hcol, -1.0, w, N, nullptr, s);
+            launch_mdot(h->V, j + 1, w, N, h->hpart, s);
+            launch_mdot_finalize(h->hpart, kRedBlocks, j + 1, Hcol, 1, h2, s);
+            launch_mupdate(h->V, j + 1, h2, -1.0, w, N, h->red, s);
+            launch_sum_real(h->red, kRedBlocks, scal(h, S_WN2), s);
+            launch_givens(h->Hm, ldh, j, h->cs, h->sn, h->g, scal(h, S_WN2), scal(h, S_EST), s);
+            launch_scale_vec(w, w, scal(h, S_WN2), N, s);
+            h->launches += 10;
+            CKL();
+            ++iters;
+            kdim = j + 1;
+            TRY(poll(h));
+            const double est = hs(h, S_EST) / bnorm;
+            hist.push(est);
+            const double wn2 = hs(h, S_WN2);
+            if (!std::isfinite(est)) break;
+            if (wn2 == 0.0 || est <= o->tol || iters >= o->maxit) break;
+        }
+        launch_hsolve(h->Hm, ldh, kdim, h->g, h->y, s);
+        launch_mupdate(h->Z, kdim, h->y, 1.0, x, N, nullptr, s);
+        h->launches += 2;
+        CKL();
+    }
+    st->iters = iters;
+    st->cycles = cycles;
+    return HELM_OK;
+}
+
+// ---------------------------------------------------------------- BiCGStab
+helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const double2* f, double2* x,
+                           helm_stats* st, Hist& hist, double bnorm) {
+    TRY(ensure_tmp(h, 10));
+    const long long N = h->N;
+    cudaStream_t s = h->stream;
+    double2 *r = h->tmp[1], *rh = h->tmp[2], *p = h->tmp[3], *v = h->tmp[4], *sv = h->tmp[5], *t = h->tmp[6],
+            *ph = h->tmp[7], *sh = h->tmp[8];
+    const double tol_abs = o->tol * bnorm;
+    TRY(residual_norm(h, f, x, r, o->conj, S_RN2));
+    ++st->matvecs;
+    TRY(poll(h));
+    double res = std::sqrt(hs(h, S_RN2)) / bnorm;
+    hist.push(res);
+    st->rel_res = res;
+    int iters = 0, restarts = 0;
+    if (res <= o->tol) {
+        st->status = HELM_OK;
+        st->iters = 0;
+        return HELM_OK;
+    }
+    auto restart = [&]() -> helm_status {
+        CK(cudaMemcpyAsync(rh, r, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(p, 0, sizeof(double2) * N, s));
+        CK(cudaMemsetAsync(v, 0, sizeof(double2) * N, s));
+        launch_bicg_scalar(5, h->red, 0, h->sc, 0.0, s);
+        h->launches += 1;
+        CKL();
+        return HELM_OK;
+    };
+    TRY(restart());
+    st->status = HELM_NOT_CONVERGED;
+    while (iters < o->maxit) {
+        launch_dot(rh, r, N, reinterpret_cast<double2*>(h->red), s);
+        launch_bicg_scalar(0, h->red, kRedBlocks, h->sc, tol_abs, s);
+        launch_bicg_update_p(r, v, p, h->sc, N, s);
+        TRY(precond(h, o, p, ph, o->conj));
+        launch_apply<double>(h->op64, ph, nullptr, v, nullptr, o->conj, false, s);
+        launch_dot(rh, v, N, reinterpret_cast<double2*>(h->red), s);
+        launch_bicg_scalar(1, h->red, kRedBlocks, h->sc, tol_abs, s);
+        launch_bicg_s(r, v, sv, h->sc, N, h->red, s);
+        launch_bicg_scalar(2, h->red, kRedBlocks, h->sc, tol_abs, s);
+        TRY(precond(h, o, sv, sh, o->conj));
+        launch_apply<double>(h->op64, sh, nullptr, t, nullptr, o->conj, false, s);
+        launch_bicg_omega_dots(t, sv, N, h->red, s);
+        launch_bicg_scalar(3, h->red, kRedBlocks, h->sc, tol_abs, s);
+        launch_bicg_xr(x, r, ph, sh, sv, t, h->sc, N, h->red, s);
+        launch_bicg_scalar(4, h->red, kRedBlocks, h->sc, tol_abs, s);
+        h->launches += 13;
+        CKL();
+        st->precond_applies += 2;
+        st->matvecs += 2;
+        ++iters;
+        TRY(poll(h));
+        const double brk = hs(h, S_FLAGS, 1);
+        if (brk == 1.0) { st->status = HELM_BREAKDOWN; break; }
+        res = std::sqrt(hs(h, S_RN2)) / bnorm;
+        hist.push(res);
+        if (!std::isfinite(res)) { st->status = HELM_DIVERGED; break; }
+        if (res <= o->tol) {
+            TRY(residual_norm(h, f, x, r, o->conj, S_RN2));
+            ++st->matvecs;
+            TRY(poll(h));
+            const double rt = std::sqrt(hs(h, S_RN2)) / bnorm;
+            if (rt <= o->tol) {
+                st->status = HELM_OK;
+                res = rt;
+                break;
+            }
+            ++restarts;
+            TRY(restart());
+        } else if (brk == 2.0) {
+            st->status = HELM_BREAKDOWN;
+            break;
+        }
+    }
+    // final true residual
+    TRY(residual_norm(h, f, x, t, o->conj, S_RN2));
+    TRY(poll(h));
+    st->rel_res = std::sqrt(hs(h, S_RN2)) / bnorm;
+    st->iters = iters;
+    st->cycles = restarts;
+    return HELM_OK;
+}
+
+void fill_tables(helm_handle* h) {
+    Op<double>& o = h->op64;
+    Op<float>& f = h->op32;
+    o.dim = f.dim = h->dim;
+    o.n = f.n = h->n;
+    o.L = f.L = h->L;
+    o.N = f.N = h->N;
+    o.hinv2 = 1.0 / (h->h * h->h);
+    f.hinv2 = (float)o.hinv2;
+    o.dre = h->k0 * h->k0 - 2.0 * h->dim / (h->h * h->h);
+    f.dre = (float)o.dre;
+    o.mask = f.mask = h->mask;
+    for (int m = 0; m <= kMaxLayerCells; ++m) {
+        double eta = (h->L > 0 && m <= h->L) ? (double)m / (double)h->L : 0.0;
+        double im = h->k0 * h->k0 * ((h->strength * eta) * eta);
+        o.im[m] = im;
+        f.im[m] = (float)im;
+        double2 inv = cdiv(make_double2(1.0, 0.0), make_double2(o.dre, im));
+        o.invd_tab[m] = inv;
+        f.invd_tab[m] = make_float2((float)inv.x, (float)inv.y);
+    }
+    o.k2 = h->k2;
+    o.invd = h->invd;
+    f.k2 = h->k2f;
+    f.invd = h->invdf;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer_strength, const uint8_t* mask,
+                        const double* k2, int precision, helm_handle** out) {
+    helm_handle* h = nullptr;
+    if (!out) return HELM_BAD_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || n < 3 || layer_cells < 0 || layer_cells > kMaxLayerCells || !mask ||
+        (precision != HELM_FP64 && precision != HELM_MIXED) || !std::isfinite(k0) || !std::isfinite(layer_strength))
+        return HELM_BAD_ARG;
+    long long N = 1;
+    for (int a = 0; a < dim; ++a) N *= n;
+    if (N >= (1LL << 31) || n > 65535) return HELM_BAD_ARG;
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return HELM_NO_DEVICE;
+    }
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return HELM_NO_DEVICE;
+    if (prop.major * 10 + prop.minor != 103) return HELM_NO_DEVICE;
+    h = new helm_handle();
+    h->dim = dim;
+    h->n = n;
+    h->N = N;
+    h->L = layer_cells;
+    h->k0 = k0;
+    h->strength = layer_strength;
+    h->precision = precision;
+    h->h = 1.0 / (n - 1);
+    h->hinv2 = 1.0 / (h->h * h->h);
+    auto bail = [&](helm_status st) {
+        helm_destroy(h);
+        return st;
+    };
+    if (dalloc(h, &h->mask, (size_t)N) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (cudaMemcpy(h->mask, mask, (size_t)N, cudaMemcpyDefault) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    h->red_len = std::max<long long>(apply_grid_blocks(dim, n), 4LL * kRedBlocks) * 2;
+    if (dalloc(h, &h->red, (size_t)h->red_len) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (dalloc(h, &h->sc, (size_t)S_NSLOTS) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (dalloc(h, &h->dflag, 8) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (cudaMallocHost((void**)&h->hpin, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_OUT_OF_MEMORY);
+    if (cudaMemset(h->sc, 0, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    if (k2) {
+        if (dalloc(h, &h->k2, (size_t)N) != HELM_OK || dalloc(h, &h->invd, (size_t)N) != HELM_OK ||
+            dalloc(h, &h->k2f, (size_t)N) != HELM_OK || dalloc(h, &h->invdf, (size_t)N) != HELM_OK)
+            return bail(HELM_OUT_OF_MEMORY);
+        if (cudaMemcpy(h->k2, k2, sizeof(double2) * N, cudaMemcpyDefault) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    }
+    fill_tables(h);
+    if (k2) {
+        launch_invd_field(h->op64, h->invd, nullptr);
+        launch_cvt_f64_to_f32(h->k2, h->k2f, N, nullptr);
+        launch_cvt_f64_to_f32(h->invd, h->invdf, N, nullptr);
+    }
+    cudaMemset(h->dflag, 0, sizeof(int) * 8);
+    launch_check_ring(h->op64, h->dflag, nullptr);
+    int bad = 0;
+    if (cudaMemcpy(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    if (bad) return bail(HELM_BAD_ARG);
+    cudaEventCreate(&h->ev0);
+    cudaEventCreate(&h->ev1);
+    *out = h;
+    return HELM_OK;
+}
+
+helm_status helm_destroy(helm_handle* h) {
+    if (!h) return HELM_BAD_ARG;
+    dfree(h->mask); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
+    dfree(h->red); dfree(h->sc); dfree(h->dflag);
+    if (h->hpin) cudaFreeHost(h->hpin);
+    for (auto p : h->tmp) cudaFree(p);
+    for (auto p : h->tmp32) cudaFree(p);
+    dfree(h->Q); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
+    dfree(h->V); dfree(h->Z); dfree(h->Hm); dfree(h->cs); dfree(h->sn); dfree(h->g); dfree(h->y); dfree(h->hpart);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (auto& pool : h->evpool)
+        for (auto e : pool) cudaEventDestroy(e);
+    delete h;
+    return HELM_OK;
+}
+
+helm_status helm_set_stream(helm_handle* h, void* stream) {
+    if (!h) return HELM_BAD_ARG;
+    h->stream = (cudaStream_t)stream;
+    return HELM_OK;
+}
+
+const char* helm_last_error(const helm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+helm_status helm_set_profiling(helm_handle* h, int on) {
+    if (!h) return HELM_BAD_ARG;
+    h->profile = on ? 1 : 0;
+    return HELM_OK;
+}
+
+helm_status helm_info(const helm_handle* h, long long* N, double* hstep) {
+    if (!h) return HELM_BAD_ARG;
+    if (N) *N = h->N;
+    if (hstep) *hstep = h->h;
+    return HELM_OK;
+}
+
+helm_status helm_layer_k2(helm_handle* h, const double* scale, double* k2_out) {
+    if (!h || !k2_out) return fail(h, HELM_BAD_ARG, "null argument");
+    launch_layer_k2(h->op64, h->k0, h->strength, scale, reinterpret_cast<double2*>(k2_out), h->stream);
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_rhs(helm_handle* h, const double* src, const double* g, double* b) {
+    if (!h || !src || !g || !b) return fail(h, HELM_BAD_ARG, "null argument");
+    launch_rhs(h->op64, reinterpret_cast<const double2*>(src), reinterpret_cast<const double2*>(g),
+               reinterpret_cast<double2*>(b), h->stream);
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_apply(helm_handle* h, const void* x, void* y, int conj, int dtype) {
+    if (!h || !x || !y) return fail(h, HELM_BAD_ARG, "null argument");
+    if (dtype == HELM_C128)
+        launch_apply<double>(h->op64, (const double2*)x, nullptr, (double2*)y, nullptr, conj, false, h->stream);
+    else if (dtype == HELM_C64)
+        launch_apply<float>(h->op32, (const float2*)x, nullptr, (float2*)y, nullptr, conj, false, h->stream);
+    else
+        return fail(h, HELM_BAD_ARG, "dtype");
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_residual(helm_handle* h, const void* f, const void* x, void* r, double* norm2, int conj,
+                          int dtype) {
+    if (!h || !f || !x || !r) return fail(h, HELM_BAD_ARG, "null argument");
+    double* part = norm2 ? h->red : nullptr;
+    if (dtype == HELM_C128)
+        launch_apply<double>(h->op64, (const double2*)x, (const double2*)f, (double2*)r, part, conj, true, h->stream);
+    else if (dtype == HELM_C64)
+        launch_apply<float>(h->op32, (const float2*)x, (const float2*)f, (float2*)r, part, conj, true, h->stream);
+    else
+        return fail(h, HELM_BAD_ARG, "dtype");
+    if (norm2) launch_sum_real(h->red, apply_grid_blocks(h->dim, h->n), norm2, h->stream);
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const void* f, void* x, int conj,
+                       int dtype) {
+    if (!h || !f || !x || sweeps < 0) return fail(h, HELM_BAD_ARG, "bad argument");
+    if (kind != HELM_JACOBI && kind != HELM_RBGS) return fail(h, HELM_BAD_ARG, "kind");
+    cudaStream_t s = h->stream;
+    if (dtype == HELM_C128) {
+        if (kind == HELM_JACOBI) {
+            TRY(ensure_tmp(h, 1));
+            double2* a = (double2*)x;
+            double2* b = h->tmp[0];
+            for (int q = 0; q < sweeps; ++q) {
+                launch_jacobi<double>(h->op64, omega, (const double2*)f, a, b, conj, false, s);
+                std::swap(a, b);
+            }
+            if (a != x) CK(cudaMemcpyAsync(x, a, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, s));
+        } else {
+            for (int q = 0; q < sweeps; ++q) {
+                launch_rbgs_half<double>(h->op64, 0, (const double2*)f, (double2*)x, conj, false, s);
+                launch_rbgs_half<double>(h->op64, 1, (const double2*)f, (double2*)x, conj, false, s);
+            }
+        }
+    } else if (dtype == HELM_C64) {
+        if (kind == HELM_JACOBI) {
+            TRY(ensure_tmp32(h, 1));
+            float2* a = (float2*)x;
+            float2* b = h->tmp32[0];
+            for (int q = 0; q < sweeps; ++q) {
+                launch_jacobi<float>(h->op32, omega, (const float2*)f, a, b, conj, false, s);
+                std::swap(a, b);
+            }
+            if (a != x) CK(cudaMemcpyAsync(x, a, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, s));
+        } else {
+            for (int q = 0; q < sweeps; ++q) {
+                launch_rbgs_half<float>(h->op32, 0, (const float2*)f, (float2*)x, conj, false, s);
+                launch_rbgs_half<float>(h->op32, 1, (const float2*)f, (float2*)x, conj, false, s);
+            }
+        }
+    } else {
+        return fail(h, HELM_BAD_ARG, "dtype");
+    }
+    CKL();
+    return HELM_OK;
+}
+
+helm_status don_load(helm_handle* h, const double* weights, const int* widths, int n_layers, int act, int p,
+                     double tau) {
+    if (!h || !weights || !widths) return fail(h, HELM_BAD_ARG, "null argument");
+    if (act != HELM_ACT_TANH) return fail(h, HELM_BAD_ARG, "activation");
+    if (n_layers < 1 || n_layers > 7) return fail(h, HELM_BAD_ARG, "n_layers must be 1..7");
+    if (widths[0] != h->dim) return fail(h, HELM_BAD_ARG, "widths[0] must equal dim");
+    for (int i = 1; i <= n_layers; ++i)
+        if (widths[i] < 1 || widths[i] > 256) return fail(h, HELM_BAD_ARG, "layer widths must be 1..256");
+    if (p < 1 || p > kMaxP || widths[n_layers] < p) return fail(h, HELM_BAD_ARG, "p must be 1..min(256, out width)");
+    if (!(tau >= 0.0) || tau >= 1.0) return fail(h, HELM_BAD_ARG, "tau must be in [0, 1)");
+    cudaStream_t s = h->stream;
+    // weights: transpose each W to (in x out) for coalesced reads
+    std::vector<double> hw;
+    size_t off = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        const int win = widths[l], wout = widths[l + 1];
+        const double* W = weights + off;
+        const double* b = W + (size_t)win * wout;
+        for (int i = 0; i < win; ++i)
+            for (int o = 0; o < wout; ++o) hw.push_back(W[(size_t)o * win + i]);
+        for (int o = 0; o < wout; ++o) hw.push_back(b[o]);
+        off += (size_t)win * wout + wout;
+    }
+    dfree(h->Q); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
+    h->k = 0;
+    const long long N = h->N;
+    const int ldt = round32(p);
+    double *dW = nullptr, *T = nullptr, *G = nullptr, *Wk = nullptr, *R = nullptr, *Rinv = nullptr, *Q1 = nullptr,
+           *Wc = nullptr, *Cc = nullptr, *part = nullptr;
+    double2* gj = nullptr;
+    int* kept = nullptr;
+    helm_status st = HELM_OK;
+    auto cleanup = [&]() {
+        dfree(dW); dfree(T); dfree(G); dfree(Wk); dfree(R); dfree(Rinv); dfree(Q1); dfree(Wc); dfree(Cc);
+        dfree(part); dfree(gj); dfree(kept);
+    };
+#define STEP(expr)                \
+    do {                          \
+        st = (expr);              \
+        if (st != HELM_OK) {      \
+            cleanup();            \
+            return st;            \
+        }                         \
+    } while (0)
+#define STEPC(call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            cleanup();                                                                                \
+            return fail(h, HELM_CUDA_ERROR, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+        }                                                                                             \
+    } while (0)
+    STEP(dalloc(h, &dW, hw.size()));
+    STEPC(cudaMemcpy(dW, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    STEP(dalloc(h, &T, (size_t)N * ldt));
+    STEP(dalloc(h, &G, (size_t)p * p));
+    STEP(dalloc(h, &Wk, (size_t)p * p));
+    STEP(dalloc(h, &R, (size_t)p * p));
+    STEP(dalloc(h, &Rinv, (size_t)p * p));
+    STEP(dalloc(h, &kept, (size_t)p));
+    STEP(dalloc(h, &part, (size_t)2 * 152 * 64 * 64 * 4 + (size_t)p * 2 * p * 16));
+    launch_trunk_eval(h->op64, dW, widths, n_layers, p, T, ldt, s);
+    launch_gram(T, ldt, p, T, ldt, p, N, part, G, s);
+    STEPC(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s));
+    launch_select_chol(G, p, p, tau, Wk, R, kept, h->dflag + 1, h->dflag, s);
+    STEPC(cudaGetLastError());
+    int hk[2] = {0, 0};
+    STEPC(cudaMemcpyAsync(hk, h->dflag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    STEPC(cudaStreamSynchronize(s));
+    const int k = hk[1];
+    if (hk[0] != 0 || k == 0) {
+        cleanup();
+        return fail(h, HELM_SINGULAR_COARSE, "trunk basis is empty (no column kept)");
+    }
+    h->kept.assign(k, 0);
+    STEPC(cudaMemcpy(h->kept.data(), kept, sizeof(int) * k, cudaMemcpyDeviceToHost));
+    const int ldq = round32(k);
+    launch_tri_inverse(R, k, p, Rinv, s);
+    STEP(dalloc(h, &Q1, (size_t)N * ldq));
+    launch_gather_times_upper(T, ldt, kept, k, Rinv, p, Q1, ldq, N, s);
+    // CholeskyQR2 second pass: Q = Q1 R2^-1 with Q1^T Q1 = R2^T R2
+    launch_gram(Q1, ldq, k, Q1, ldq, k, N, part, G, s);
+    STEPC(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s));
+    launch_select_chol(G, k, k, 0.0, Wk, R, kept, h->dflag + 1, h->dflag, s);
+    STEPC(cudaMemcpyAsync(hk, h->dflag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    STEPC(cudaStreamSynchronize(s));
+    if (hk[1] != k) {
+        cleanup();
+        return fail(h, HELM_SINGULAR_COARSE, "second CholeskyQR pass lost rank");
+    }
+    launch_tri_inverse(R, k, k, Rinv, s);
+    STEP(dalloc(h, &h->Q, (size_t)N * ldq));
+    launch_gather_times_upper(Q1, ldq, nullptr, k, Rinv, k, h->Q, ldq, N, s);
+    dfree(T);
+    // A_c = Q^T (A Q)
+    STEP(dalloc(h, &Wc, (size_t)N * 2 * ldq));
+    launch_apply_columns(h->op64, h->Q, ldq, k, Wc, 2 * ldq, s);
+    STEP(dalloc(h, &Cc, (size_t)k * 2 * k));
+    launch_gram(h->Q, ldq, k, Wc, 2 * ldq, 2 * k, N, part, Cc, s);
+    STEP(dalloc(h, &gj, (size_t)k * 2 * k));
+    STEP(dalloc(h, &h->Ainv, (size_t)k * k));
+    STEPC(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s));
+    launch_gauss_jordan(Cc, 2 * k, k, h->Ainv, gj, h->dflag, s);
+    STEPC(cudaGetLastError());
+    STEPC(cudaMemcpyAsync(hk, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STEPC(cudaStreamSynchronize(s));
+    if (hk[0] != 0) {
+        cleanup();
+        dfree(h->Q); dfree(h->Ainv);
+        return fail(h, HELM_SINGULAR_COARSE, "coarse operator A_c is singular");
+    }
+    STEP(dalloc(h, &h->coarse_partials, (size_t)restrict_blocks(N) * ldq));
+    STEP(dalloc(h, &h->cbuf, (size_t)ldq));
+    STEP(dalloc(h, &h->ybuf, (size_t)ldq));
+    h->p = p;
+    h->k = k;
+    h->ldq = ldq;
+    cleanup();
+    STEPC(cudaStreamSynchronize(s));
+#undef STEP
+#undef STEPC
+    return HELM_OK;
+}
+
+helm_status don_info(const helm_handle* h, int* k, int* kept_idx) {
+    if (!h) return HELM_BAD_ARG;
+    if (k) *k = h->k;
+    if (kept_idx)
+        for (int i = 0; i < h->k; ++i) kept_idx[i] = h->kept[i];
+    return HELM_OK;
+}
+
+helm_status don_get_q(const helm_handle* hc, double* q_out) {
+    helm_handle* h = const_cast<helm_handle*>(hc);
+    if (!h || !q_out) return fail(h, HELM_BAD_ARG, "null argument");
+    if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
+    CK(cudaMemcpy2DAsync(q_out, sizeof(double) * h->k, h->Q, sizeof(double) * h->ldq, sizeof(double) * h->k, h->N,
+                         cudaMemcpyDeviceToDevice, h->stream));
+    return HELM_OK;
+}
+
+helm_status don_get_ainv(const helm_handle* hc, double* out) {
+    helm_handle* h = const_cast<helm_handle*>(hc);
+    if (!h || !out) return fail(h, HELM_BAD_ARG, "null argument");
+    if (!h->Ainv) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
+    CK(cudaMemcpyAsync(out, h->Ainv, sizeof(double2) * h->k * h->k, cudaMemcpyDeviceToDevice, h->stream));
+    return HELM_OK;
+}
+
+helm_status don_correct(helm_handle* h, int mode, const void* r, void* z, int conj, int dtype) {
+    if (!h || !r || !z) return fail(h, HELM_BAD_ARG, "null argument");
+    if (mode != HELM_CORR_TB) return fail(h, HELM_BAD_ARG, "mode");
+    if (dtype != HELM_C128) return fail(h, HELM_BAD_ARG, "dtype");
+    return tb_correct(h, (const double2*)r, nullptr, (double2*)z, conj);
+}
+
+helm_status helm_precond(helm_handle* h, const helm_solve_opts* opts, const void* r, void* z) {
+    if (!h || !r || !z) return fail(h, HELM_BAD_ARG, "null argument");
+    TRY(check_opts(h, opts));
+    return precond(h, opts, (const double2*)r, (double2*)z, opts->conj);
+}
+
+helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv, void* xv, helm_stats* stats,
+                       double* res_hist, int hist_len) {
+    if (!h || !fv || !xv) return fail(h, HELM_BAD_ARG, "null argument");
+    TRY(check_opts(h, o));
+    const double2* f = (const double2*)fv;
+    double2* x = (double2*)xv;
+    helm_stats st{};
+    st.status = HELM_NOT_CONVERGED;
+    Hist hist{res_hist, hist_len};
+    h->launches = 0;
+    h->evn[0] = h->evn[1] = 0;
+    CK(cudaEventRecord(h->ev0, h->stream));
+    launch_set_masked(x, f, h->mask, h->N, h->stream);
+    h->launches += 1;
+    TRY(norm2_into(h, f, S_BN2));
+    TRY(poll(h));
+    double bnorm = std::sqrt(hs(h, S_BN2));
+    if (bnorm == 0.0) {
+        CK(cudaMemsetAsync(x, 0, sizeof(double2) * h->N, h->stream));
+        st.status = HELM_OK;
+        st.rel_res = 0;
+    } else if (o->method == HELM_METHOD_RELAX) {
+        TRY(solve_relax(h, o, f, x, &st, hist, bnorm));
+    } else if (o->method == HELM_METHOD_FGMRES) {
+        TRY(solve_fgmres(h, o, f, x, &st, hist, bnorm));
+    } else {
+        TRY(solve_bicgstab(h, o, f, x, &st, hist, bnorm));
+    }
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    st.ms = ms;
+    st.launches = h->launches;
+    st.n_restrict = h->evn[0];
+    st.n_prolong = h->evn[1];
+    st.restrict_ms = h->profile ? ev_sum(h, 0) : 0.0;
+    st.prolong_ms = h->profile ? ev_sum(h, 1) : 0.0;
+    if (stats) *stats = st;
+    return (helm_status)st.status;
+}
+
+helm_status helm_solve_host(helm_handle* h, const helm_solve_opts* o, const double* f, double* x,
+                            helm_stats* stats, double* res_hist, int hist_len) {
+    if (!h || !f || !x) return fail(h, HELM_BAD_ARG, "null argument");
+    TRY(ensure_tmp(h, 12));
+    double2* df = h->tmp[10];
+    double2* dx = h->tmp[11];
+    CK(cudaMemcpyAsync(df, f, sizeof(double2) * h->N, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(dx, x, sizeof(double2) * h->N, cudaMemcpyHostToDevice, h->stream));
+    helm_status st = helm_solve(h, o, df, dx, stats, res_hist, hist_len);
+    CK(cudaMemcpyAsync(x, dx, sizeof(double2) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+}  // extern "C"

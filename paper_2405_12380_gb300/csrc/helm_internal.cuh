@@ -1,0 +1,203 @@
+// Internal declarations shared by the libhelm translation units.
+//
+// Data layout in HBM
+//   vectors       N complex, interleaved (double2 / float2), flat index i + n(j + n k)
+//   mask          N uint8 (1 = Dirichlet: outer ring + scatterer)
+//   Q             N x kcap doubles, node-major (the k basis values of a node are
+//                 contiguous, row stride kcap = k rounded up to a multiple of 32)
+//   A_c^-1        k x k complex128, row-major
+//   Krylov basis  V: (m+1) x N complex128, Z: m x N complex128, one vector after another
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+
+namespace helm {
+
+constexpr int kMaxLayerCells = 64;
+constexpr int kMaxP = 256;          // trunk basis functions
+constexpr int kMaxRestart = 64;     // FGMRES(m)
+constexpr int kRedBlocks = 304;     // blocks of the fixed-grid reductions (2 per SM)
+constexpr int kFinThreads = 1024;
+
+// ------------------------------------------------------------ complex helpers
+template <typename R> struct CT;
+template <> struct CT<double> { using T = double2; };
+template <> struct CT<float> { using T = float2; };
+
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// ------------------------------------------------------ operator description
+// Everything a stencil kernel needs, passed by value.  The absorbing layer is
+// tabulated by the layer index m = max_a max(0, L - dist_a) in 0..L, so k^2 and
+// the inverse diagonal of a fluid node are table lookups (no per-node FP64
+// division); with a stored k^2 field the per-node arrays are used instead.
+template <typename R>
+struct Op {
+    using C = typename CT<R>::T;
+    int dim, n, L;
+    long long N;
+    R hinv2;                 // h^-2
+    R dre;                   // k0^2 - 2 d h^-2 (real part of the diagonal, layer form)
+    const uint8_t* mask;
+    const C* k2;             // stored k^2 field or nullptr
+    const C* invd;           // per-node 1/diag for the stored field, or nullptr
+    R im[kMaxLayerCells + 1];        // Im k^2 by layer index
+    C invd_tab[kMaxLayerCells + 1];  // 1/(diag) by layer index (fluid nodes)
+};
+
+// device scalar slots of the Krylov drivers (double2 each, in helm_handle::sc)
+enum { S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_SN2, S_RN2, S_FLAGS, S_TS, S_TT,
+       S_BETA2, S_WN2, S_EST, S_BN2, S_NSLOTS };
+// S_FLAGS.x = 1: ||s|| met the tolerance this iteration; S_FLAGS.y = 1: breakdown
+
+// ------------------------------------------------------------ kernel launchers
+// stencil.cu
+template <typename R>
+void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f,
+                  typename CT<R>::T* y, double* partials, int conj, bool resid, cudaStream_t s);
+template <typename R>
+void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f,
+                   const typename CT<R>::T* xin, typename CT<R>::T* xout, int conj, bool xzero,
+                   cudaStream_t s);
+template <typename R>
+void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x,
+                      int conj, bool xzero, cudaStream_t s);
+int apply_grid_blocks(int dim, int n);
+void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s);
+void launch_layer_k2(const Op<double>& op, double k0, double strength, const double* scale,
+                     double2* k2, cudaStream_t s);
+void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s);
+void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s);
+
+// blas.cu
+// partial reductions over a fixed grid of kRedBlocks blocks
+void launch_dot(const double2* a, const double2* b, long long N, double2* partials, cudaStream_t s);
+void launch_norm2(const double2* a, long long N, double* partials, cudaStream_t s);
+void launch_sum_real(const double* partials, int nparts, double* out, cudaStream_t s);
+void launch_sum_cplx(const double2* partials, int nparts, double2* out, cudaStream_t s);
+// BiCGStab pieces (scalars live in device memory, see blas.cu)
+void launch_bicg_update_p(const double2* r, const double2* v, double2* p, const double2* sc, long long N,
+                          cudaStream_t s);
+void launch_bicg_s(const double2* r, const double2* v, double2* sv, const double2* sc, long long N,
+                   double* partials, cudaStream_t s);
+void launch_bicg_omega_dots(const double2* t, const double2* sv, long long N, double* partials,
+                            cudaStream_t s);
+void launch_bicg_xr(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
+                    const double2* t, const double2* sc, long long N, double* partials, cudaStream_t s);
+void launch_bicg_scalar(int recipe, const double* partials, int nparts, double2* sc, double tol_abs,
+                        cudaStream_t s);
+// FGMRES pieces
+void launch_mdot(const double2* V, int nv, const double2* w, long long N, double2* partials,
+                 cudaStream_t s);
+void launch_mupdate(const double2* V, int nv, const double2* coef, double sign, double2* w, long long N,
+                    double* norm_partials, cudaStream_t s);
+void launch_mdot_finalize(const double2* partials, int nparts, int nv, double2* out, int accumulate,
+                          double2* copy, cudaStream_t s);
+void launch_scale_vec(const double2* w, double2* v, const double* norm2, long long N, cudaStream_t s);
+void launch_givens(double2* H, int ldh, int j, double* cs, double2* sn, double2* g, const double* wnorm2,
+                   double* est, cudaStream_t s);
+void launch_hsolve(const double2* H, int ldh, int k, const double2* g, double2* y, cudaStream_t s);
+void launch_init_g(double2* g, int m1, const double* beta2, cudaStream_t s);
+void launch_axpy(double2* y, const double2* x, double2 a, long long N, cudaStream_t s);
+void launch_set_masked(double2* x, const double2* f, const uint8_t* mask, long long N, cudaStream_t s);
+void launch_cvt_f64_to_f32(const double2* a, float2* b, long long N, cudaStream_t s);
+void launch_cvt_f32_to_f64(const float2* a, double2* b, long long N, cudaStream_t s);
+
+// tb.cu
+void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p,
+                       double* T, int ldt, cudaStream_t s);
+void launch_gram(const double* A, int lda, int p, const double* B, int ldb, int q, long long N,
+                 double* partials, double* out, cudaStream_t s);
+void launch_select_chol(const double* G, int p, int ldg, double tau, double* W, double* R, int* kept,
+                        int* nkept, int* flag, cudaStream_t s);
+void launch_tri_inverse(const double* R, int k, int ldr, double* Rinv, cudaStream_t s);
+void launch_gather_times_upper(const double* T, int ldt, const int* kept, int k, const double* Rinv, int ldr,
+                               double* Q, int ldq, long long N, cudaStream_t s);
+void launch_apply_columns(const Op<double>& op, const double* Q, int ldq, int k, double* W, int ldw,
+                          cudaStream_t s);
+void launch_gauss_jordan(const double* C, int ldc, int k, double2* Ainv, double2* work, int* flag,
+                         cudaStream_t s);
+void launch_restrict(const Op<double>& op, const double* Q, int ldq, int k, const double2* v,
+                     const double2* z, int conj, double2* partials, int nblk, cudaStream_t s);
+void launch_coarse_apply(const double2* partials, int nblk, int k, int ldq, const double2* Ainv, int conj,
+                         double2* y, double2* cbuf, cudaStream_t s);
+void launch_prolong(const double* Q, int ldq, int k, const double2* y, double2* z, long long N,
+                    cudaStream_t s);
+int restrict_blocks(long long N);
+
+// ------------------------------------------------------------------- handle
+}  // namespace helm
+
+struct helm_handle {
+    int dim = 0, n = 0, L = 0, precision = 0;
+    long long N = 0;
+    double k0 = 0, strength = 0, h = 0, hinv2 = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    helm::Op<double> op64{};
+    helm::Op<float> op32{};
+    uint8_t* mask = nullptr;
+    double2* k2 = nullptr;
+    double2* invd = nullptr;
+    float2* k2f = nullptr;
+    float2* invdf = nullptr;
+    // scratch for reductions and device scalars
+    double* red = nullptr;          // partial sums (size max(apply blocks, kRedBlocks) * 8 doubles)
+    long long red_len = 0;
+    double2* sc = nullptr;          // device scalars (BiCGStab/FGMRES)
+    double* hpin = nullptr;         // pinned host mirror for status polling
+    int* dflag = nullptr;           // device int flags
+    // general temporaries (N complex128 each)
+    std::vector<double2*> tmp;
+    // trunk basis
+    int p = 0, k = 0, ldq = 0;
+    std::vector<int> kept;
+    double* Q = nullptr;
+    double2* Ainv = nullptr;
+    double2* coarse_partials = nullptr;
+    double2* cbuf = nullptr;
+    double2* ybuf = nullptr;
+    // Krylov workspace
+    int m_alloc = 0;
+    double2* V = nullptr;
+    double2* Z = nullptr;
+    double2* Hm = nullptr;
+    double* cs = nullptr;
+    double2* sn = nullptr;
+    double2* g = nullptr;
+    double2* y = nullptr;
+    double2* hpart = nullptr;
+    // mixed precision buffers
+    std::vector<float2*> tmp32;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // launch accounting and per-kernel event timing (helm_set_profiling)
+    int profile = 0;
+    long long launches = 0;
+    std::vector<cudaEvent_t> evpool[2];
+    int evn[2] = {0, 0};
+};

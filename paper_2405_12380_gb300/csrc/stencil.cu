@@ -1,0 +1,329 @@
+// Matrix-free Helmholtz operator, residual and relaxation sweeps (Eq. 1-2).
+//
+// One thread per node; blocks of 32 x 8 nodes in (x, y), one z-plane per
+// blockIdx.z.  The mask and the layer index are integers; k^2 and 1/diag come
+// from the tables in Op (or the stored field).  FP64 is the scarce pipe on
+// GB300, so per node the operator costs 2d complex adds, one scale and one
+// complex multiply-add, and the sweeps multiply by a tabulated reciprocal.
+#include "helm_internal.cuh"
+
+namespace helm {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+__device__ __forceinline__ int layer_index(int i, int n, int L) {
+    int d = min(i, n - 1 - i);
+    return max(0, L - d);
+}
+
+template <typename R>
+__device__ __forceinline__ int node_layer(const Op<R>& op, int i, int j, int k) {
+    int m = max(layer_index(i, op.n, op.L), layer_index(j, op.n, op.L));
+    if (op.dim == 3) m = max(m, layer_index(k, op.n, op.L));
+    return m;
+}
+
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T diag_of(const Op<R>& op, long long l, int m, int conj) {
+    typename CT<R>::T d;
+    if (op.k2) {
+        d = op.k2[l];
+        d.x -= (R)(2 * op.dim) * op.hinv2;
+    } else {
+        d.x = op.dre;
+        d.y = op.im[m];
+    }
+    if (conj) d.y = -d.y;
+    return d;
+}
+
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T invd_of(const Op<R>& op, long long l, int m, int conj) {
+    typename CT<R>::T d = op.k2 ? op.invd[l] : op.invd_tab[m];
+    if (conj) d.y = -d.y;
+    return d;
+}
+
+// sum of the fluid neighbours of an interior node
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T nbr_sum(const Op<R>& op, const typename CT<R>::T* __restrict__ x,
+                                                     long long l) {
+    using C = typename CT<R>::T;
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    C s;
+    s.x = 0; s.y = 0;
+    const uint8_t* mk = op.mask;
+    if (!mk[l - 1]) s = cadd(s, x[l - 1]);
+    if (!mk[l + 1]) s = cadd(s, x[l + 1]);
+    if (!mk[l - sy]) s = cadd(s, x[l - sy]);
+    if (!mk[l + sy]) s = cadd(s, x[l + sy]);
+    if (op.dim == 3) {
+        if (!mk[l - sz]) s = cadd(s, x[l - sz]);
+        if (!mk[l + sz]) s = cadd(s, x[l + sz]);
+    }
+    return s;
+}
+
+template <typename R>
+__device__ __forceinline__ void block_reduce_store(double v, double* out) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    int lane = tid & 31, w = tid >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    int nw = (blockDim.x * blockDim.y) >> 5;
+    if (w == 0) {
+        v = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) *out = v;
+    }
+}
+
+// y = A x, or y = f - A x (resid); optional per-block ||y||^2 partials.
+template <typename R, bool RESID, bool NORM>
+__global__ void __launch_bounds__(BX * BY) k_apply(Op<R> op, const typename CT<R>::T* __restrict__ x,
+                                                   const typename CT<R>::T* __restrict__ f,
+                                                   typename CT<R>::T* __restrict__ y, double* partials,
+                                                   int conj) {
+    using C = typename CT<R>::T;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    double acc = 0.0;
+    if (i < op.n && j < op.n) {
+        const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+        C xc = x[l];
+        C out;
+        if (op.mask[l]) {
+            out = xc;
+        } else {
+            C s = nbr_sum(op, x, l);
+            C d = diag_of(op, l, node_layer(op, i, j, k), conj);
+            out.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
+            out.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
+        }
+        if (RESID) out = csub(f[l], out);
+        y[l] = out;
+        if (NORM) acc = (double)out.x * out.x + (double)out.y * out.y;
+    }
+    if (NORM) {
+        block_reduce_store<R>(acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    }
+}
+
+// one damped-Jacobi sweep: xout = xin + omega D^-1 (f - A xin)
+template <typename R, bool XZERO>
+__global__ void __launch_bounds__(BX * BY) k_jacobi(Op<R> op, R omega, const typename CT<R>::T* __restrict__ f,
+                                                    const typename CT<R>::T* __restrict__ xin,
+                                                    typename CT<R>::T* __restrict__ xout, int conj) {
+    using C = typename CT<R>::T;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    C fl = f[l];
+    C out;
+    if (op.mask[l]) {
+        if (XZERO) {
+            out = cscale(omega, fl);
+        } else {
+            C xc = xin[l];
+            out = cadd(xc, cscale(omega, csub(fl, xc)));
+        }
+    } else {
+        const int m = node_layer(op, i, j, k);
+        C r;
+        C xc;
+        if (XZERO) {
+            xc.x = 0; xc.y = 0;
+            r = fl;
+        } else {
+            xc = xin[l];
+            C s = nbr_sum(op, xin, l);
+            C d = diag_of(op, l, m, conj);
+            C ax;
+            ax.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
+            ax.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
+            r = csub(fl, ax);
+        }
+        C id = invd_of(op, l, m, conj);
+        out = cadd(xc, cscale(omega, cmul(id, r)));
+    }
+    xout[l] = out;
+}
+
+// red-black Gauss-Seidel half-sweep on colour c, in place
+template <typename R, bool XZERO>
+__global__ void __launch_bounds__(BX * BY) k_rbgs(Op<R> op, int colour, const typename CT<R>::T* __restrict__ f,
+                                                  typename CT<R>::T* x, int conj) {
+    using C = typename CT<R>::T;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + colour) & 1);
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    C fl = f[l];
+    C out;
+    if (op.mask[l]) {
+        if (XZERO) {
+            out = fl;
+        } else {
+            C xc = x[l];
+            out = cadd(xc, csub(fl, xc));
+        }
+    } else {
+        const int m = node_layer(op, i, j, k);
+        C xc;
+        C r;
+        if (XZERO) {
+            xc.x = 0; xc.y = 0;
+            r = fl;
+        } else {
+            xc = x[l];
+            C s = nbr_sum(op, x, l);
+            C d = diag_of(op, l, m, conj);
+            C ax;
+            ax.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
+            ax.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
+            r = csub(fl, ax);
+        }
+        out = cadd(xc, cmul(invd_of(op, l, m, conj), r));
+    }
+    x[l] = out;
+}
+
+__global__ void k_rhs(Op<double> op, const double2* __restrict__ src, const double2* __restrict__ g,
+                      double2* __restrict__ b) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    if (op.mask[l]) {
+        b[l] = g[l];
+        return;
+    }
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    double2 v = src[l];
+    long long nb[6] = {l - 1, l + 1, l - sy, l + sy, l - sz, l + sz};
+    const int nn = 2 * op.dim;
+    for (int q = 0; q < nn; ++q) {
+        if (op.mask[nb[q]]) {
+            double2 gm = g[nb[q]];
+            v.x -= gm.x * op.hinv2;
+            v.y -= gm.y * op.hinv2;
+        }
+    }
+    b[l] = v;
+}
+
+__global__ void k_layer_k2(Op<double> op, double k0sq, double strength, const double* __restrict__ scale,
+                           double2* __restrict__ k2) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const int m = node_layer(op, i, j, k);
+    const double eta = (double)m / (double)op.L;
+    const double base = scale ? k0sq * scale[l] : k0sq;
+    k2[l] = make_double2(base, base * (strength * eta * eta));
+}
+
+__global__ void k_invd_field(Op<double> op, double2* __restrict__ invd) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    double2 d = op.k2[l];
+    d.x -= 2.0 * op.dim * op.hinv2;
+    invd[l] = op.mask[l] ? make_double2(1.0, 0.0) : cdiv(make_double2(1.0, 0.0), d);
+}
+
+__global__ void k_check_ring(Op<double> op, int* bad) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    bool ring = i == 0 || j == 0 || i == op.n - 1 || j == op.n - 1;
+    if (op.dim == 3) ring = ring || k == 0 || k == op.n - 1;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    if (ring && !op.mask[l]) atomicOr(bad, 1);
+}
+
+dim3 grid_for(int dim, int n, int xdiv = 1) {
+    int nx = (n + xdiv - 1) / xdiv;
+    return dim3((nx + BX - 1) / BX, (n + BY - 1) / BY, dim == 3 ? n : 1);
+}
+
+}  // namespace
+
+int apply_grid_blocks(int dim, int n) {
+    dim3 g = grid_for(dim, n);
+    return g.x * g.y * g.z;
+}
+
+template <typename R>
+void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f,
+                  typename CT<R>::T* y, double* partials, int conj, bool resid, cudaStream_t s) {
+    dim3 g = grid_for(op.dim, op.n), b(BX, BY);
+    if (resid) {
+        if (partials) k_apply<R, true, true><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
+        else k_apply<R, true, false><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
+    } else {
+        if (partials) k_apply<R, false, true><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
+        else k_apply<R, false, false><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
+    }
+}
+
+template <typename R>
+void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f, const typename CT<R>::T* xin,
+                   typename CT<R>::T* xout, int conj, bool xzero, cudaStream_t s) {
+    dim3 g = grid_for(op.dim, op.n), b(BX, BY);
+    if (xzero) k_jacobi<R, true><<<g, b, 0, s>>>(op, (R)omega, f, xin, xout, conj);
+    else k_jacobi<R, false><<<g, b, 0, s>>>(op, (R)omega, f, xin, xout, conj);
+}
+
+template <typename R>
+void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x, int conj,
+                      bool xzero, cudaStream_t s) {
+    dim3 g = grid_for(op.dim, op.n, 2), b(BX, BY);
+    if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj);
+    else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj);
+}
+
+template void launch_apply<double>(const Op<double>&, const double2*, const double2*, double2*, double*, int,
+                                   bool, cudaStream_t);
+template void launch_apply<float>(const Op<float>&, const float2*, const float2*, float2*, double*, int, bool,
+                                  cudaStream_t);
+template void launch_jacobi<double>(const Op<double>&, double, const double2*, const double2*, double2*, int,
+                                    bool, cudaStream_t);
+template void launch_jacobi<float>(const Op<float>&, double, const float2*, const float2*, float2*, int, bool,
+                                   cudaStream_t);
+template void launch_rbgs_half<double>(const Op<double>&, int, const double2*, double2*, int, bool,
+                                       cudaStream_t);
+template void launch_rbgs_half<float>(const Op<float>&, int, const float2*, float2*, int, bool, cudaStream_t);
+
+void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s) {
+    k_rhs<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, src, g, b);
+}
+
+void launch_layer_k2(const Op<double>& op, double k0, double strength, const double* scale, double2* k2,
+                     cudaStream_t s) {
+    k_layer_k2<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, k0 * k0, strength, scale, k2);
+}
+
+void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s) {
+    k_invd_field<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, invd);
+}
+
+void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s) {
+    k_check_ring<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, bad);
+}
+
+}  // namespace helm

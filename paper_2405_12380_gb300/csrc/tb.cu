@@ -1,0 +1,599 @@
+// Trunk-basis (TB) coarse space and correction (App. C, Eq. 6).
+//
+// Setup (once per don_load):
+//   T_lj = trunk(x_l)_j                     k_trunk      (FP64 SIMT, activations in smem)
+//   G = T^T T                               k_gram       (split-K tiles + fixed-order sum)
+//   natural-order selection + Cholesky      k_select_chol (one CTA, right-looking, drop test)
+//   Q1 = T_S R^-1, then CholQR2 pass        k_tri_inverse, k_gather_upper
+//   W = A Q (real columns -> complex)       k_apply_columns
+//   A_c = Q^T W, A_c^-1 by Gauss-Jordan     k_gram, k_gauss_jordan (one CTA, partial pivoting)
+// Per application (z += Q A_c^-1 Q^T (v - A z)):
+//   k_restrict   residual on the fly, 32 rows per warp step, lane-owned columns
+//   k_coarse     fixed-order sum of block partials, y = A_c^-1 c
+//   k_prolong    z_l += sum_j Q_lj y_j, one warp per row
+#include "helm_internal.cuh"
+
+namespace helm {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int layer_index(int i, int n, int L) {
+    int d = min(i, n - 1 - i);
+    return max(0, L - d);
+}
+
+// ------------------------------------------------------------ trunk network
+constexpr int TR_NB = 16;        // nodes per block
+constexpr int TR_T = 256;        // threads = max width
+
+// dW: per layer, W^T (in x out, row-major) then bias (out)
+__global__ void __launch_bounds__(TR_T) k_trunk(Op<double> op, const double* __restrict__ dW, int4 w03, int4 w47,
+                                                int n_layers, int p, double* __restrict__ T, int ldt) {
+    extern __shared__ double sm[];
+    double* a_in = sm;                       // [TR_NB][TR_T]
+    double* a_out = sm + TR_NB * TR_T;       // [TR_NB][TR_T]
+    const int widths[8] = {w03.x, w03.y, w03.z, w03.w, w47.x, w47.y, w47.z, w47.w};
+    const long long node0 = (long long)blockIdx.x * TR_NB;
+    const double h = 1.0 / (op.n - 1);
+    // coordinates of the block's nodes
+    for (int t = threadIdx.x; t < TR_NB * op.dim; t += TR_T) {
+        int nb = t / op.dim, ax = t % op.dim;
+        long long l = node0 + nb;
+        double c = 0;
+        if (l < op.N) {
+            long long q = l;
+            for (int a = 0; a < ax; ++a) q /= op.n;
+            c = (double)(q % op.n) * h;
+        }
+        a_in[nb * TR_T + ax] = c;
+    }
+    __syncthreads();
+    const double* W = dW;
+    for (int layer = 0; layer < n_layers; ++layer) {
+        const int win = widths[layer], wout = widths[layer + 1];
+        const double* Wt = W;                 // win x wout
+        const double* b = W + (long long)win * wout;
+        const int o = threadIdx.x;
+        if (o < wout) {
+            double acc[TR_NB];
+            const double bo = b[o];
+#pragma unroll
+            for (int nb = 0; nb < TR_NB; ++nb) acc[nb] = 0.0;
+            for (int i = 0; i < win; ++i) {
+                const double w = Wt[(long long)i * wout + o];
+#pragma unroll
+                for (int nb = 0; nb < TR_NB; ++nb) acc[nb] = fma(a_in[nb * TR_T + i], w, acc[nb]);
+            }
+            const bool last = layer == n_layers - 1;
+#pragma unroll
+            for (int nb = 0; nb < TR_NB; ++nb) {
+                double v = acc[nb] + bo;
+                a_out[nb * TR_T + o] = last ? v : tanh(v);
+            }
+        }
+        __syncthreads();
+        double* tmp = a_in;
+        a_in = a_out;
+        a_out = tmp;
+        W = b + wout;
+        __syncthreads();
+    }
+    // a_in holds the output layer
+    for (int t = threadIdx.x; t < TR_NB * ldt; t += TR_T) {
+        int nb = t / ldt, j = t % ldt;
+        long long l = node0 + nb;
+        if (l >= op.N) continue;
+        double v = (j < p && !op.mask[l]) ? a_in[nb * TR_T + j] : 0.0;
+        T[l * ldt + j] = v;
+    }
+}
+
+// ------------------------------------------------------------------- Gram
+// C = A^T B over N rows; A: N x p (lda), B: N x q (ldb); 64 x 64 output tile per
+// block, 4 x 4 per thread, split over row slices (blockIdx.z); partials then summed.
+constexpr int GT = 64, GR = 32;
+
+__global__ void __launch_bounds__(256) k_gram(const double* __restrict__ A, int lda, int p,
+                                              const double* __restrict__ B, int ldb, int q, long long N,
+                                              long long rows_per_split, double* __restrict__ partials) {
+    __shared__ double As[GR][GT + 1];
+    __shared__ double Bs[GR][GT + 1];
+    const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;   // 16 x 16 threads, 4 x 4 each
+    const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+    const long long r0 = (long long)blockIdx.z * rows_per_split;
+    const long long r1 = min(N, r0 + rows_per_split);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+    for (long long rb = r0; rb < r1; rb += GR) {
+        for (int t = threadIdx.x; t < GR * GT; t += 256) {
+            int rr = t / GT, cc = t % GT;
+            long long row = rb + rr;
+            bool ok = row < r1;
+            As[rr][cc] = (ok && i0 + cc < p) ? A[row * lda + i0 + cc] : 0.0;
+            Bs[rr][cc] = (ok && j0 + cc < q) ? B[row * ldb + j0 + cc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < GR; ++rr) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[rr][ti + 16 * a];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bv[c] = Bs[rr][tj + 16 * c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+        }
+        __syncthreads();
+    }
+    double* P = partials + (long long)blockIdx.z * p * q;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int i = i0 + ti + 16 * a, j = j0 + tj + 16 * c;
+            if (i < p && j < q) P[(long long)i * q + j] = acc[a][c];
+        }
+}
+
+__global__ void k_gram_sum(const double* __restrict__ partials, int nsplit, long long pq, double* __restrict__ out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pq; e += (long long)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int z = 0; z < nsplit; ++z) s += partials[(long long)z * pq + e];
+        out[e] = s;
+    }
+}
+
+// ------------------------------------------- natural-order Cholesky with drop
+// G (p x p, ldg) symmetric.  Right-looking: at step j the trailing block holds the
+// Schur complement of the kept columns.  Column j is kept when its Schur diagonal
+// d_j > tau^2 G_jj (and d_j > 0).  Output: compact upper R (k x k, ld p), kept[0..k).
+// flag = 1 when no column is kept.
+__global__ void __launch_bounds__(1024) k_select_chol(const double* __restrict__ G, int p, int ldg, double tau,
+                                                      double* __restrict__ W, double* __restrict__ R,
+                                                      int* __restrict__ kept, int* __restrict__ nkept, int* flag) {
+    __shared__ int s_keep;
+    __shared__ double s_rjj;
+    __shared__ int s_k;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) W[e] = G[(e / p) * (long long)ldg + e % p];
+    if (threadIdx.x == 0) s_k = 0;
+    __syncthreads();
+    for (int j = 0; j < p; ++j) {
+        if (threadIdx.x == 0) {
+            const double g = G[(long long)j * ldg + j];
+            const double d = W[j * p + j];
+            const int keep = (g > 0.0) && (d > 0.0) && (d > tau * tau * g);
+            s_keep = keep;
+            s_rjj = keep ? sqrt(d) : 0.0;
+        }
+        __syncthreads();
+        if (s_keep) {
+            const double rjj = s_rjj;
+            // row j of R (uncompacted) over the trailing columns b >= j
+            for (int b = j + threadIdx.x; b < p; b += blockDim.x) W[j * p + b] = (b == j) ? rjj : W[j * p + b] / rjj;
+            __syncthreads();
+            const int m = p - j - 1;
+            for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+                int a = j + 1 + (int)(e / m), b = j + 1 + (int)(e % m);
+                if (b < a) continue;
+                W[a * p + b] -= W[j * p + a] * W[j * p + b];
+            }
+            if (threadIdx.x == 0) {
+                kept[s_k] = j;
+                s_k = s_k + 1;
+            }
+        }
+        __syncthreads();
+    }
+    const int k = s_k;
+    // compact R: R[a][b] = W[kept[a]][kept[b]] for a <= b
+    for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
+        int a = (int)(e / k), b = (int)(e % k);
+        R[(long long)a * p + b] = (b >= a) ? W[kept[a] * p + kept[b]] : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        *nkept = k;
+        if (k == 0) *flag = 1;
+    }
+}
+
+// inverse of an upper-triangular k x k matrix (ld ldr); one thread per column
+__global__ void k_tri_inverse(const double* __restrict__ R, int k, int ldr, double* __restrict__ Rinv) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= k) return;
+    // solve R x = e_c by back substitution; x_a = 0 for a > c
+    for (int a = k - 1; a > c; --a) Rinv[(long long)a * ldr + c] = 0.0;
+    for (int a = c; a >= 0; --a) {
+        double s = (a == c) ? 1.0 : 0.0;
+        for (int b = a + 1; b <= c; ++b) s -= R[(long long)a * ldr + b] * Rinv[(long long)b * ldr + c];
+        Rinv[(long long)a * ldr + c] = s / R[(long long)a * ldr + a];
+    }
+}
+
+// Q[l][c] = sum_{a <= c} T[l][kept[a]] Rinv[a][c]  (kept == nullptr: identity)
+constexpr int GU_NB = 16;
+__global__ void __launch_bounds__(256) k_gather_upper(const double* __restrict__ T, int ldt,
+                                                      const int* __restrict__ kept, int k,
+                                                      const double* __restrict__ Rinv, int ldr,
+                                                      double* __restrict__ Q, int ldq, long long N) {
+    extern __shared__ double ts[];     // [GU_NB][k]
+    const long long l0 = (long long)blockIdx.x * GU_NB;
+    for (int t = threadIdx.x; t < GU_NB * k; t += blockDim.x) {
+        int nb = t / k, a = t % k;
+        long long l = l0 + nb;
+        ts[t] = l < N ? T[l * ldt + (kept ? kept[a] : a)] : 0.0;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ldq; c += blockDim.x) {
+        double acc[GU_NB];
+#pragma unroll
+        for (int nb = 0; nb < GU_NB; ++nb) acc[nb] = 0.0;
+        if (c < k) {
+            for (int a = 0; a <= c; ++a) {
+                const double r = Rinv[(long long)a * ldr + c];
+#pragma unroll
+                for (int nb = 0; nb < GU_NB; ++nb) acc[nb] = fma(ts[nb * k + a], r, acc[nb]);
+            }
+        }
+#pragma unroll
+        for (int nb = 0; nb < GU_NB; ++nb) {
+            long long l = l0 + nb;
+            if (l < N) Q[l * ldq + c] = acc[nb];
+        }
+    }
+}
+
+// W[l][2c], W[l][2c+1] = Re, Im of (A q_c)_l for the real columns q_c of Q
+__global__ void __launch_bounds__(256) k_apply_columns(Op<double> op, const double* __restrict__ Q, int ldq, int k,
+                                                       double* __restrict__ W, int ldw) {
+    const long long total = op.N * (long long)k;
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long l = e / k;
+        const int c = (int)(e % k);
+        double re = 0, im = 0;
+        if (!op.mask[l]) {
+            const int i = (int)(l % op.n), j = (int)((l / op.n) % op.n), kk = (int)(l / sz);
+            double s = 0;
+            if (!op.mask[l - 1]) s += Q[(l - 1) * ldq + c];
+            if (!op.mask[l + 1]) s += Q[(l + 1) * ldq + c];
+            if (!op.mask[l - sy]) s += Q[(l - sy) * ldq + c];
+            if (!op.mask[l + sy]) s += Q[(l + sy) * ldq + c];
+            if (op.dim == 3) {
+                if (!op.mask[l - sz]) s += Q[(l - sz) * ldq + c];
+                if (!op.mask[l + sz]) s += Q[(l + sz) * ldq + c];
+            }
+            double dre, dim_;
+            if (op.k2) {
+                double2 kk2 = op.k2[l];
+                dre = kk2.x - 2.0 * op.dim * op.hinv2;
+                dim_ = kk2.y;
+            } else {
+                int m = max(layer_index(i, op.n, op.L), layer_index(j, op.n, op.L));
+                if (op.dim == 3) m = max(m, layer_index(kk, op.n, op.L));
+                dre = op.dre;
+                dim_ = op.im[m];
+            }
+            const double qv = Q[l * ldq + c];
+            re = op.hinv2 * s + dre * qv;
+            im = dim_ * qv;
+        }
+        W[l * ldw + 2 * c] = re;
+        W[l * ldw + 2 * c + 1] = im;
+    }
+}
+
+// Gauss-Jordan with partial pivoting on the complex k x k matrix
+// A_c[i][c] = C[i][2c] + i C[i][2c+1]; one CTA; work: k x 2k complex.
+__global__ void __launch_bounds__(1024) k_gauss_jordan(const double* __restrict__ C, int ldc, int k,
+                                                       double2* __restrict__ Ainv, double2* __restrict__ Wk,
+                                                       int* flag) {
+    __shared__ int s_piv;
+    __shared__ double s_val[32];
+    __shared__ int s_idx[32];
+    const int w2 = 2 * k;
+    for (long long e = threadIdx.x; e < (long long)k * w2; e += blockDim.x) {
+        int i = (int)(e / w2), c = (int)(e % w2);
+        Wk[e] = c < k ? make_double2(C[(long long)i * ldc + 2 * c], C[(long long)i * ldc + 2 * c + 1])
+                      : make_double2(c - k == i ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < k; ++j) {
+        // pivot: largest |a_ij| for i >= j (ties -> smallest index)
+        double best = -1;
+        int bi = j;
+        for (int i = j + threadIdx.x; i < k; i += blockDim.x) {
+            double v = hypot(Wk[(long long)i * w2 + j].x, Wk[(long long)i * w2 + j].y);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bv = s_val[0];
+            int bix = s_idx[0];
+            for (int q = 1; q < nw; ++q)
+                if (s_val[q] > bv || (s_val[q] == bv && s_idx[q] < bix)) { bv = s_val[q]; bix = s_idx[q]; }
+            s_piv = bv > 0 ? bix : -1;
+            if (bv <= 0) *flag = 2;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        if (piv < 0) return;
+        if (piv != j) {
+            for (int c = threadIdx.x; c < w2; c += blockDim.x) {
+                double2 t = Wk[(long long)j * w2 + c];
+                Wk[(long long)j * w2 + c] = Wk[(long long)piv * w2 + c];
+                Wk[(long long)piv * w2 + c] = t;
+            }
+        }
+        __syncthreads();
+        const double2 pv = Wk[(long long)j * w2 + j];
+        const double2 ipv = cdiv(make_double2(1, 0), pv);
+        __syncthreads();
+        for (int c = threadIdx.x; c < w2; c += blockDim.x) Wk[(long long)j * w2 + c] = cmul(Wk[(long long)j * w2 + c], ipv);
+        __syncthreads();
+        for (long long e = threadIdx.x; e < (long long)k * w2; e += blockDim.x) {
+            int i = (int)(e / w2), c = (int)(e % w2);
+            if (i == j || c < j) continue;
+            double2 f = Wk[(long long)i * w2 + j];
+            if (c == j) continue;
+            Wk[e] = csub(Wk[e], cmul(f, Wk[(long long)j * w2 + c]));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x)
+            if (i != j) Wk[(long long)i * w2 + j] = make_double2(0, 0);
+        __syncthreads();
+    }
+    for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
+        int i = (int)(e / k), c = (int)(e % k);
+        Ainv[e] = Wk[(long long)i * w2 + k + c];
+    }
+}
+
+// ---------------------------------------------------------- per application
+constexpr int RS_WARPS = 4;
+
+// partials[b][j] = sum over the rows of block b of Q[l][j] * r_l, r = v - A z (z may be null)
+template <int KPL>
+__global__ void __launch_bounds__(RS_WARPS * 32) k_restrict(Op<double> op, const double* __restrict__ Q, int ldq,
+                                                            const double2* __restrict__ v,
+                                                            const double2* __restrict__ z, int conj,
+                                                            double2* __restrict__ partials, long long rows_per_block) {
+    __shared__ double2 red[RS_WARPS][KPL * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long r0 = (long long)blockIdx.x * rows_per_block;
+    const long long r1 = min(op.N, r0 + rows_per_block);
+    double2 acc[KPL];
+#pragma unroll
+    for (int c = 0; c < KPL; ++c) acc[c] = make_double2(0, 0);
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    for (long long base = r0 + 32 * warp; base < r1; base += 32 * RS_WARPS) {
+        // lane computes r for row base + lane
+        const long long l = base + lane;
+        double2 r = make_double2(0, 0);
+        if (l < r1 && !op.mask[l]) {
+            r = v[l];
+            if (z) {
+                const int i = (int)(l % op.n), j = (int)((l / op.n) % op.n), kk = (int)(l / sz);
+                double2 s = make_double2(0, 0);
+                const uint8_t* mk = op.mask;
+                if (!mk[l - 1]) s = cadd(s, z[l - 1]);
+                if (!mk[l + 1]) s = cadd(s, z[l + 1]);
+                if (!mk[l - sy]) s = cadd(s, z[l - sy]);
+                if (!mk[l + sy]) s = cadd(s, z[l + sy]);
+                if (op.dim == 3) {
+                    if (!mk[l - sz]) s = cadd(s, z[l - sz]);
+                    if (!mk[l + sz]) s = cadd(s, z[l + sz]);
+                }
+                double2 d;
+                if (op.k2) {
+                    d = op.k2[l];
+                    d.x -= 2.0 * op.dim * op.hinv2;
+                } else {
+                    int m = max(layer_index(i, op.n, op.L), layer_index(j, op.n, op.L));
+                    if (op.dim == 3) m = max(m, layer_index(kk, op.n, op.L));
+                    d = make_double2(op.dre, op.im[m]);
+                }
+                if (conj) d.y = -d.y;
+                const double2 zc = z[l];
+                r.x -= op.hinv2 * s.x + (d.x * zc.x - d.y * zc.y);
+                r.y -= op.hinv2 * s.y + (d.x * zc.y + d.y * zc.x);
+            }
+        }
+        const int nrows = (int)min((long long)32, r1 - base);
+        for (int q = 0; q < nrows; ++q) {
+            const double rx = __shfl_sync(0xffffffffu, r.x, q);
+            const double ry = __shfl_sync(0xffffffffu, r.y, q);
+            const double* Qrow = Q + (base + q) * ldq + lane;
+#pragma unroll
+            for (int c = 0; c < KPL; ++c) {
+                const double qv = Qrow[32 * c];
+                acc[c].x = fma(qv, rx, acc[c].x);
+                acc[c].y = fma(qv, ry, acc[c].y);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < KPL; ++c) red[warp][lane + 32 * c] = acc[c];
+    __syncthreads();
+    for (int j = threadIdx.x; j < KPL * 32; j += RS_WARPS * 32) {
+        double2 s = red[0][j];
+        for (int w = 1; w < RS_WARPS; ++w) s = cadd(s, red[w][j]);
+        partials[(long long)blockIdx.x * ldq + j] = s;
+    }
+}
+
+// y = A_c^-1 c (conj: conj(A_c^-1)), c = fixed-order sum of the block partials
+__global__ void __launch_bounds__(1024) k_coarse(const double2* __restrict__ partials, int nblk, int k, int ldq,
+                                                 const double2* __restrict__ Ainv, int conj, double2* __restrict__ y,
+                                                 double2* __restrict__ cbuf) {
+    __shared__ double2 c[kMaxP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < k; j += nw) {
+        double sx = 0, sy = 0;
+        for (int b = lane; b < nblk; b += 32) {
+            double2 q = partials[(long long)b * ldq + j];
+            sx += q.x;
+            sy += q.y;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) {
+            c[j] = make_double2(sx, sy);
+            if (cbuf) cbuf[j] = c[j];
+        }
+    }
+    __syncthreads();
+    for (int i = warp; i < k; i += nw) {
+        double sx = 0, sy = 0;
+        for (int j = lane; j < k; j += 32) {
+            double2 a = Ainv[(long long)i * k + j];
+            if (conj) a.y = -a.y;
+            double2 cj = c[j];
+            sx += a.x * cj.x - a.y * cj.y;
+            sy += a.x * cj.y + a.y * cj.x;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) y[i] = make_double2(sx, sy);
+    }
+}
+
+// z_l += sum_j Q[l][j] y_j, one warp per row
+template <int KPL>
+__global__ void __launch_bounds__(256) k_prolong(const double* __restrict__ Q, int ldq, int k,
+                                                 const double2* __restrict__ y, double2* __restrict__ z, long long N) {
+    const int lane = threadIdx.x & 31;
+    double2 yv[KPL];
+#pragma unroll
+    for (int c = 0; c < KPL; ++c) {
+        int j = lane + 32 * c;
+        yv[c] = j < k ? y[j] : make_double2(0, 0);
+    }
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long l = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); l < N; l += warps) {
+        const double* Qrow = Q + l * ldq + lane;
+        double sx = 0, sy = 0;
+#pragma unroll
+        for (int c = 0; c < KPL; ++c) {
+            const double qv = Qrow[32 * c];
+            sx = fma(qv, yv[c].x, sx);
+            sy = fma(qv, yv[c].y, sy);
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) {
+            double2 zz = z[l];
+            z[l] = make_double2(zz.x + sx, zz.y + sy);
+        }
+    }
+}
+
+}  // namespace
+
+void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p, double* T,
+                       int ldt, cudaStream_t s) {
+    int w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i <= n_layers && i < 8; ++i) w[i] = widths[i];
+    size_t smem = 2 * TR_NB * TR_T * sizeof(double);
+    cudaFuncSetAttribute(k_trunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    long long blocks = (op.N + TR_NB - 1) / TR_NB;
+    k_trunk<<<(unsigned)blocks, TR_T, smem, s>>>(op, dW, make_int4(w[0], w[1], w[2], w[3]),
+                                                 make_int4(w[4], w[5], w[6], w[7]), n_layers, p, T, ldt);
+}
+
+void launch_gram(const double* A, int lda, int p, const double* B, int ldb, int q, long long N, double* partials,
+                 double* out, cudaStream_t s) {
+    int gx = (p + GT - 1) / GT, gy = (q + GT - 1) / GT;
+    int nsplit = (2 * 152 + gx * gy - 1) / (gx * gy);
+    long long rows = (N + nsplit - 1) / nsplit;
+    rows = ((rows + GR - 1) / GR) * GR;
+    nsplit = (int)((N + rows - 1) / rows);
+    k_gram<<<dim3(gx, gy, nsplit), 256, 0, s>>>(A, lda, p, B, ldb, q, N, rows, partials);
+    long long pq = (long long)p * q;
+    k_gram_sum<<<(unsigned)((pq + 255) / 256), 256, 0, s>>>(partials, nsplit, pq, out);
+}
+
+void launch_select_chol(const double* G, int p, int ldg, double tau, double* W, double* R, int* kept, int* nkept,
+                        int* flag, cudaStream_t s) {
+    k_select_chol<<<1, 1024, 0, s>>>(G, p, ldg, tau, W, R, kept, nkept, flag);
+}
+
+void launch_tri_inverse(const double* R, int k, int ldr, double* Rinv, cudaStream_t s) {
+    k_tri_inverse<<<(k + 127) / 128, 128, 0, s>>>(R, k, ldr, Rinv);
+}
+
+void launch_gather_times_upper(const double* T, int ldt, const int* kept, int k, const double* Rinv, int ldr,
+                               double* Q, int ldq, long long N, cudaStream_t s) {
+    size_t smem = GU_NB * k * sizeof(double);
+    cudaFuncSetAttribute(k_gather_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gather_upper<<<(unsigned)((N + GU_NB - 1) / GU_NB), 256, smem, s>>>(T, ldt, kept, k, Rinv, ldr, Q, ldq, N);
+}
+
+void launch_apply_columns(const Op<double>& op, const double* Q, int ldq, int k, double* W, int ldw,
+                          cudaStream_t s) {
+    k_apply_columns<<<4 * 152, 256, 0, s>>>(op, Q, ldq, k, W, ldw);
+}
+
+void launch_gauss_jordan(const double* C, int ldc, int k, double2* Ainv, double2* work, int* flag,
+                         cudaStream_t s) {
+    k_gauss_jordan<<<1, 1024, 0, s>>>(C, ldc, k, Ainv, work, flag);
+}
+
+int restrict_blocks(long long N) {
+    long long b = (N + 255) / 256;
+    return (int)(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
+}
+
+void launch_restrict(const Op<double>& op, const double* Q, int ldq, int k, const double2* v, const double2* z,
+                     int conj, double2* partials, int nblk, cudaStream_t s) {
+    (void)k;
+    long long rows = (op.N + nblk - 1) / nblk;
+    switch (ldq / 32) {
+        case 1: k_restrict<1><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+        case 2: k_restrict<2><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+        case 3: k_restrict<3><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+        case 4: k_restrict<4><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+        case 5: k_restrict<5><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+        case 6: k_restrict<6><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+        case 7: k_restrict<7><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+        default: k_restrict<8><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
+    }
+}
+
+void launch_coarse_apply(const double2* partials, int nblk, int k, int ldq, const double2* Ainv, int conj,
+                         double2* y, double2* cbuf, cudaStream_t s) {
+    k_coarse<<<1, 1024, 0, s>>>(partials, nblk, k, ldq, Ainv, conj, y, cbuf);
+}
+
+void launch_prolong(const double* Q, int ldq, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
+    const int blocks = 4 * 152;
+    switch (ldq / 32) {
+        case 1: k_prolong<1><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+        case 2: k_prolong<2><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+        case 3: k_prolong<3><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+        case 4: k_prolong<4><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+        case 5: k_prolong<5><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+        case 6: k_prolong<6><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+        case 7: k_prolong<7><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+        default: k_prolong<8><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
+    }
+}
+
+}  // namespace helm

@@ -1,0 +1,189 @@
+"""Thin Python layer over libhelm's C ABI: torch tensors in, torch tensors out.
+
+Device memory and streams come from PyTorch; every arithmetic step runs in the
+CUDA kernels behind include/helm.h.  Complex vectors are torch.complex128 (or
+complex64) CUDA tensors of N = n^dim entries, flat index i + n (j + n k).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import SolveOpts, Stats
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"libhelm: {L.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def opts(method="fgmres", relax="jacobi", n_r=1, omega=0.6, correction="tb", tol=1e-8,
+         restart=30, maxit=1000, conj=False) -> SolveOpts:
+    m = {"relax": L.HELM_METHOD_RELAX, "fgmres": L.HELM_METHOD_FGMRES,
+         "bicgstab": L.HELM_METHOD_BICGSTAB}[method]
+    r = {"none": L.HELM_RELAX_NONE, "jacobi": L.HELM_JACOBI, "rbgs": L.HELM_RBGS}[relax]
+    c = {"none": L.HELM_CORR_NONE, "tb": L.HELM_CORR_TB}[correction]
+    return SolveOpts(m, r, int(n_r), float(omega), c, float(tol), int(restart), int(maxit), int(bool(conj)))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dtype_code(t):
+    if t.dtype == torch.complex128:
+        return L.HELM_C128
+    if t.dtype == torch.complex64:
+        return L.HELM_C64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+class Problem:
+    """One discretised Helmholtz problem (helm_create) on the current CUDA device."""
+
+    def __init__(self, dim, n, k0, mask, layer_cells=8, layer_strength=0.5, k2=None, precision="fp64"):
+        self.lib = L.lib()
+        self.dim, self.n = int(dim), int(n)
+        self.N = self.n ** self.dim
+        dev = torch.device("cuda")
+        self.mask = torch.as_tensor(mask, dtype=torch.uint8).reshape(-1).to(dev).contiguous()
+        k2t = None
+        if k2 is not None:
+            k2t = torch.as_tensor(k2).to(dev, torch.complex128).reshape(-1).contiguous()
+        prec = {"fp64": L.HELM_FP64, "mixed": L.HELM_MIXED}[precision]
+        h = C.c_void_p()
+        st = self.lib.helm_create(self.dim, self.n, float(k0), int(layer_cells), float(layer_strength),
+                                  _ptr(self.mask), _ptr(k2t), prec, C.byref(h))
+        if st != 0:
+            raise HelmError(st, "helm_create")
+        self.h = h
+        self.set_stream(torch.cuda.current_stream())
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, st, what=""):
+        if st != 0:
+            msg = self.lib.helm_last_error(self.h)
+            raise HelmError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_stream(self, stream):
+        self._check(self.lib.helm_set_stream(self.h, C.c_void_p(stream.cuda_stream)), "set_stream")
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.helm_set_profiling(self.h, int(bool(on))), "set_profiling")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.helm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self, dtype=torch.complex128):
+        return torch.zeros(self.N, dtype=dtype, device="cuda")
+
+    # ---------------------------------------------------------- operations
+    def layer_k2(self, scale=None):
+        out = self.vec()
+        sc = None if scale is None else torch.as_tensor(scale, dtype=torch.float64).reshape(-1).cuda().contiguous()
+        self._check(self.lib.helm_layer_k2(self.h, _ptr(sc), _ptr(out)), "layer_k2")
+        return out
+
+    def rhs(self, src, g):
+        b = self.vec()
+        self._check(self.lib.helm_rhs(self.h, _ptr(src.contiguous()), _ptr(g.contiguous()), _ptr(b)), "rhs")
+        return b
+
+    def apply(self, x, conj=False, out=None):
+        y = torch.empty_like(x) if out is None else out
+        self._check(self.lib.helm_apply(self.h, _ptr(x), _ptr(y), int(conj), _dtype_code(x)), "apply")
+        return y
+
+    def residual(self, f, x, conj=False, want_norm=True):
+        r = torch.empty_like(x)
+        nrm = torch.zeros(1, dtype=torch.float64, device="cuda") if want_norm else None
+        self._check(self.lib.helm_residual(self.h, _ptr(f), _ptr(x), _ptr(r), _ptr(nrm), int(conj),
+                                           _dtype_code(x)), "residual")
+        return (r, nrm) if want_norm else r
+
+    def relax(self, kind, f, x, sweeps=1, omega=0.6, conj=False):
+        k = {"jacobi": L.HELM_JACOBI, "rbgs": L.HELM_RBGS}[kind]
+        self._check(self.lib.helm_relax(self.h, k, float(omega), int(sweeps), _ptr(f), _ptr(x), int(conj),
+                                        _dtype_code(x)), "relax")
+        return x
+
+    def don_load(self, layers, p, tau=0.0):
+        """layers: [(W[out, in], b[out])] float64, tanh on hidden layers."""
+        widths = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
+        flat = np.ascontiguousarray(np.concatenate(
+            [np.concatenate([np.asarray(W, np.float64).reshape(-1), np.asarray(b, np.float64)])
+             for W, b in layers]))
+        wd = (C.c_int * len(widths))(*widths)
+        self._check(self.lib.don_load(self.h, flat.ctypes.data_as(C.c_void_p), wd, len(layers),
+                                      L.HELM_ACT_TANH, int(p), float(tau)), "don_load")
+        k = C.c_int()
+        idx = (C.c_int * int(p))()
+        self.lib.don_info(self.h, C.byref(k), idx)
+        self.k = k.value
+        self.kept = list(idx)[: self.k]
+        return self.k
+
+    def basis(self):
+        Q = torch.empty(self.N, self.k, dtype=torch.float64, device="cuda")
+        self._check(self.lib.don_get_q(self.h, _ptr(Q)), "don_get_q")
+        return Q
+
+    def coarse_inverse(self):
+        A = torch.empty(self.k, self.k, dtype=torch.complex128, device="cuda")
+        self._check(self.lib.don_get_ainv(self.h, _ptr(A)), "don_get_ainv")
+        return A
+
+    def don_correct(self, r, z=None, conj=False):
+        z = torch.zeros_like(r) if z is None else z
+        self._check(self.lib.don_correct(self.h, L.HELM_CORR_TB, _ptr(r), _ptr(z), int(conj), _dtype_code(r)),
+                    "don_correct")
+        return z
+
+    def precond(self, r, o: SolveOpts):
+        z = torch.empty_like(r)
+        self._check(self.lib.helm_precond(self.h, C.byref(o), _ptr(r), _ptr(z)), "precond")
+        return z
+
+    def solve(self, f, x0=None, o: SolveOpts | None = None, hist_len=4096, raise_on_fail=False):
+        o = o or opts()
+        x = torch.zeros_like(f) if x0 is None else x0.clone()
+        st = Stats()
+        hist = np.zeros(hist_len)
+        rc = self.lib.helm_solve(self.h, C.byref(o), _ptr(f), _ptr(x), C.byref(st),
+                                 hist.ctypes.data_as(C.c_void_p), hist_len)
+        if rc in (L.HELM_BAD_ARG, L.HELM_CUDA_ERROR, L.HELM_NOT_READY, L.HELM_OUT_OF_MEMORY) or (
+                raise_on_fail and rc != 0):
+            self._check(rc, "solve")
+        d = st.as_dict()
+        d["status_name"] = L.STATUS_NAMES.get(d["status"], d["status"])
+        n_hist = min(hist_len, self._hist_count(d, o))
+        d["hist"] = hist[:n_hist]
+        return x, d
+
+    @staticmethod
+    def _hist_count(d, o):
+        if o.method == L.HELM_METHOD_RELAX:
+            return d["iters"] + 1
+        return d["iters"] + 1
+
+    def solve_host(self, f: np.ndarray, x: np.ndarray, o: SolveOpts | None = None):
+        """Host buffers in and out (complex128 numpy arrays, x updated in place)."""
+        o = o or opts()
+        st = Stats()
+        rc = self.lib.helm_solve_host(self.h, C.byref(o), f.ctypes.data_as(C.c_void_p),
+                                      x.ctypes.data_as(C.c_void_p), C.byref(st), None, 0)
+        if rc in (L.HELM_BAD_ARG, L.HELM_CUDA_ERROR, L.HELM_NOT_READY, L.HELM_OUT_OF_MEMORY):
+            self._check(rc, "solve_host")
+        return st.as_dict()
