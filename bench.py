@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Time-to-tolerance of the DeepONet-BiCGStab meta-solver on one GB300.
+
+Workload (scenes.BENCH_WORKLOADS["cube3d-64"]): 3D FP64 Helmholtz on 64^3 nodes,
+k = 16, 8-cell absorbing layer, centred 16^3 sound-soft cube, Gaussian source;
+trunk [3,128,128,128] (seeded), natural-order trunk basis (tau = 1e-6);
+BiCGStab right-preconditioned by the hybrid cycle (3 red-black GS sweeps, then
+the trunk-basis Galerkin correction), tolerance 1e-8 on the true residual.
+
+One step = one complete solve from x0 = 0 (inputs resident on the device, setup
+of the trunk basis done once before the timed region).  `e2e` repeats the step
+through helm_solve_host with pinned host buffers.  Under torchrun every rank
+solves the same problem on its own GPU (replicas: the path has no exchange).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "time-to-1e-6 rel. residual (s) & iterations; stencil GB/s vs HBM peak, 1×GB300"
+WORKLOAD = "cube3d-64"
+FP64_PEAK_GFLOPS = 1250.0     # 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz (nominal 1.25 TFLOP/s)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the CPU sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def reference_iterations(name):
+    try:
+        return json.load(open(os.path.join(ROOT, "oracle", "reference_counts.json")))[name]["iterations"]
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(float(r[2]) for r in rows if len(r) >= 9)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for i, nm in enumerate(names):
+            if any(len(r) >= 9 and "Active" in r[5 + i] and "Not" not in r[5 + i] for r in rows):
+                out["reasons"].append(nm)
+        out["samples"] = len(rows)
+        return out
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(w, sc, n_iter):
+    """Time the oracle's own hybrid-preconditioned BiCGStab for n_iter iterations."""
+    from oracle import assemble, krylov, tb  # test/bench infrastructure only
+    A, b, _ = assemble.problem(sc)
+    t0 = time.perf_counter()
+    X = scenes.node_coords(sc.dim, sc.n)
+    s = tb.tb_setup(A, sc.trunk, X, sc.mask, sc.p, tau=w["tau"])
+    M = tb.hybrid_preconditioner(A, s, w["relax"], w["n_r"], colours=assemble.colour(sc.dim, sc.n))
+    t1 = time.perf_counter()
+    x0 = np.zeros_like(b)
+    t2 = time.perf_counter()
+    krylov.bicgstab(A, b, x0, M, 1e-300, n_iter)
+    t3 = time.perf_counter()
+    return {"setup_s": t1 - t0, "per_iter_s": (t3 - t2) / n_iter, "kept": len(s.kept)}
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = scenes.BENCH_WORKLOADS[args.workload]
+    sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
+    iters = reference_iterations(args.workload)
+    from oracle import assemble, krylov, tb
+    A, b, _ = assemble.problem(sc)
+    X = scenes.node_coords(sc.dim, sc.n)
+    s = tb.tb_setup(A, sc.trunk, X, sc.mask, sc.p, tau=w["tau"])
+    M = tb.hybrid_preconditioner(A, s, w["relax"], w["n_r"], colours=assemble.colour(sc.dim, sc.n))
+    per = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        krylov.bicgstab(A, b, np.zeros_like(b), M, 1e-300, 1)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            per.append(dt)
+    per_iter = statistics.mean(per)
+    value = per_iter * iters if iters else None
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, w, sc, None),
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": f"oracle DeepONet-BiCGStab, 1 iteration per step timed, scaled by the "
+                                   f"oracle's own {iters} iterations to 1e-8 (oracle/reference_counts.json); "
+                                   f"setup excluded; scipy.sparse matvecs single-threaded"},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(name, w, sc, kept):
+    return {"workload": name, "grid": f"{sc.n}^{sc.dim}", "k0": sc.k0, "layer_cells": sc.layer_cells,
+            "scatterer": "centred 16^3 cube", "source": "Gaussian sigma=0.04", "trunk": "[3,128,128,128] seeded",
+            "p": sc.p, "kept": kept, "tau": w["tau"], "method": w["method"], "relax": w["relax"],
+            "n_r": w["n_r"], "correction": w["correction"], "tol": w["tol"],
+            "l2": "256 MiB buffer written between steps (L2 is 129 MB)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def source_hash(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(kernel, k):
+    """dram bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "restrict_cube3d-64_traffic.json")))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2405_12380_gb300", "csrc", "tb.cu")
+    if prof.get("tb_cu_sha256_16") != source_hash(src) or prof.get("k") != k:
+        return None
+    return prof.get("dram_bytes_per_launch")
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2405_12380_gb300 as hm
+    from paper_2405_12380_gb300 import _lib as L
+
+    w = scenes.BENCH_WORKLOADS[args.workload]
+    sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
+    # right-hand side built on the device by the library (helm_rhs), from seeded data
+    P = hm.Problem(sc.dim, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, layer_strength=sc.layer_strength)
+    f = P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = P.don_load(sc.trunk, sc.p, tau=w["tau"])
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    o = hm.opts(w["method"], w["relax"], w["n_r"], correction=w["correction"], tol=w["tol"],
+                restart=w["restart"], maxit=w["maxit"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        x, st = P.solve(f, None, o)
+    P.set_profiling(True)
+    stats = []
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            x, st = P.solve(f, None, o)
+            stats.append(st)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    P.set_profiling(False)
+    solve_ms = [s["ms"] for s in stats]
+    mean_ms = statistics.mean(solve_ms)
+    t = torch.tensor([mean_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mean_ms = float(t.item())
+    # e2e: the same solve through helm_solve_host with pinned host buffers
+    fh = f.cpu().pin_memory()
+    f_np = fh.numpy()
+    xh = torch.zeros(P.N, dtype=torch.complex128).pin_memory()
+    x_np = xh.numpy()
+    e2e = []
+    for step in range(args.warmup + args.steps):
+        x_np[:] = 0
+        flush.fill_(1.0)
+        barrier()
+        t1 = time.perf_counter()
+        P.solve_host(f_np, x_np, o)
+        dt = time.perf_counter() - t1
+        if step >= args.warmup:
+            e2e.append(dt)
+    e2e_s = statistics.mean(e2e)
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    # check the converged solution with an independent FP64 residual (device, library op)
+    r, nrm = P.residual(f, x)
+    rel_res = float(nrm.sqrt().item() / torch.linalg.vector_norm(f).item())
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    st0 = stats[-1]
+    iters = statistics.mean(s["iters"] for s in stats)
+    n_restrict = sum(s["n_restrict"] for s in stats)
+    restrict_ms = sum(s["restrict_ms"] for s in stats)
+    prolong_ms = sum(s["prolong_ms"] for s in stats)
+    avg_restrict_s = restrict_ms / 1e3 / max(1, n_restrict)
+    N = P.N
+    flops = N * (4.0 * k + 24.0)
+    bytes_alg = 8.0 * k * N + 32.0 * N + N
+    achieved = flops / avg_restrict_s / 1e9
+    roofline = {"bound": "alu", "kernel": "k_restrict (FP64 fused residual + Q^T r)",
+                "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_for("k_restrict", k),
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_alg,
+                "achieved_GBps_algorithmic": bytes_alg / avg_restrict_s / 1e9,
+                "avg_launch_us": avg_restrict_s * 1e6,
+                "launches": n_restrict, "restrict_share_of_solve": restrict_ms / sum(solve_ms),
+                "prolong_share_of_solve": prolong_ms / sum(solve_ms),
+                "peak_note": "FP64 nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk); HBM measured "
+                             f"{peaks().get('hbm_gbs')} GB/s"}
+    cpu = None
+    if world == 1 or args.gpus == 1:
+        iters_ref = reference_iterations(args.workload)
+        smp = oracle_sample(w, sc, args.cpu_iters)
+        cpu_value = smp["per_iter_s"] * (iters_ref or iters)
+        cpu = {"value": cpu_value, "unit": "s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"oracle DeepONet-BiCGStab (scipy CSR, numpy Q), {args.cpu_iters} iterations timed "
+                         f"({smp['per_iter_s']:.3f} s/iter), scaled by "
+                         + (f"the oracle's own {iters_ref} iterations to tol (oracle/reference_counts.json)"
+                            if iters_ref else f"the GPU solve's {iters} iterations")
+                         + f"; oracle setup {smp['setup_s']:.1f} s excluded; scipy.sparse single-threaded",
+               "oracle_kept": smp["kept"]}
+    clocks = clk.summary()
+    cfg = workload_config(args.workload, w, sc, k)
+    cfg.update({"iterations": iters, "rel_res": rel_res, "setup_s": setup_s, "replicas": world,
+                "solve_ms_each": solve_ms})
+    line = {
+        "metric": METRIC, "value": mean_ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene, seeded trunk weights)",
+        "config": cfg, "iterations": iters, "status": st0["status_name"],
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": N * 16},
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

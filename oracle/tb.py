@@ -61,25 +61,25 @@ def natural_order_select(T, tau: float, kmax: int | None = None):
     when the trunk's columns are nearly collinear.  Returns (Q, kept)."""
     N, p = T.shape
     kmax = p if kmax is None else kmax
-    cols, kept = [], []
+    Qbuf = np.zeros((N, min(p, kmax)))
+    kept = []
     for j in range(p):
         t = T[:, j]
         tn = np.linalg.norm(t)
         if tn == 0.0:
             continue
         u = t.copy()
-        if cols:
-            Qk = np.stack(cols, axis=1)
+        if kept:
+            Qk = Qbuf[:, : len(kept)]
             u = u - Qk @ (Qk.T @ u)
             u = u - Qk @ (Qk.T @ u)
         un = np.linalg.norm(u)
         if un > tau * tn:
-            cols.append(u / un)
+            Qbuf[:, len(kept)] = u / un
             kept.append(j)
             if len(kept) == kmax:
                 break
-    Q = np.stack(cols, axis=1) if cols else np.zeros((N, 0))
-    return Q, kept
+    return Qbuf[:, : len(kept)].copy(), kept
 
 
 def tb_setup(A, layers, coords, mask, p: int, Q=None, tau: float = 0.0) -> TBSetup:

@@ -172,11 +172,11 @@ helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, do
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
     const int nblk = restrict_blocks(h->N);
     ev_mark(h, 0, 0);
-    launch_restrict(h->op64, h->Q, h->ldq, h->k, v, zres, conj, h->coarse_partials, nblk, h->stream);
+    launch_restrict(h->op64, h->Q, h->k, v, zres, conj, h->coarse_partials, nblk, h->stream);
     ev_mark(h, 0, 1);
-    launch_coarse_apply(h->coarse_partials, nblk, h->k, h->ldq, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
+    launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
     ev_mark(h, 1, 0);
-    launch_prolong(h->Q, h->ldq, h->k, h->ybuf, z, h->N, h->stream);
+    launch_prolong(h->Q, h->k, h->ybuf, z, h->N, h->stream);
     ev_mark(h, 1, 1);
     h->launches += 3;
     CKL();
@@ -184,6 +184,12 @@ helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, do
 }
 
 helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
+    const bool no_relax = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
+    if (no_relax && o->correction == HELM_CORR_NONE) {
+        // neither stage: M is the identity (plain Krylov)
+        CK(cudaMemcpyAsync(z, r, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        return HELM_OK;
+    }
     TRY(relax_from_zero(h, o->relax, o->omega, o->n_r, r, z, conj));
     if (o->correction == HELM_CORR_TB) {
         const bool zero = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
@@ -740,14 +746,17 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         return fail(h, HELM_SINGULAR_COARSE, "second CholeskyQR pass lost rank");
     }
     launch_tri_inverse(R, k, k, Rinv, s);
-    STEP(dalloc(h, &h->Q, (size_t)N * ldq));
-    launch_gather_times_upper(Q1, ldq, nullptr, k, Rinv, k, h->Q, ldq, N, s);
     dfree(T);
+    STEP(dalloc(h, &T, (size_t)N * ldq));            // node-major Q for the setup GEMMs
+    launch_gather_times_upper(Q1, ldq, nullptr, k, Rinv, k, T, ldq, N, s);
+    dfree(Q1);
+    STEP(dalloc(h, &h->Q, (size_t)N * k));           // column-major Q for the per-iteration kernels
+    launch_rm_to_cm(T, ldq, k, h->Q, N, s);
     // A_c = Q^T (A Q)
     STEP(dalloc(h, &Wc, (size_t)N * 2 * ldq));
-    launch_apply_columns(h->op64, h->Q, ldq, k, Wc, 2 * ldq, s);
+    launch_apply_columns(h->op64, T, ldq, k, Wc, 2 * ldq, s);
     STEP(dalloc(h, &Cc, (size_t)k * 2 * k));
-    launch_gram(h->Q, ldq, k, Wc, 2 * ldq, 2 * k, N, part, Cc, s);
+    launch_gram(T, ldq, k, Wc, 2 * ldq, 2 * k, N, part, Cc, s);
     STEP(dalloc(h, &gj, (size_t)k * 2 * k));
     STEP(dalloc(h, &h->Ainv, (size_t)k * k));
     STEPC(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s));
@@ -760,9 +769,9 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         dfree(h->Q); dfree(h->Ainv);
         return fail(h, HELM_SINGULAR_COARSE, "coarse operator A_c is singular");
     }
-    STEP(dalloc(h, &h->coarse_partials, (size_t)restrict_blocks(N) * ldq));
-    STEP(dalloc(h, &h->cbuf, (size_t)ldq));
-    STEP(dalloc(h, &h->ybuf, (size_t)ldq));
+    STEP(dalloc(h, &h->coarse_partials, (size_t)restrict_blocks(N) * k));
+    STEP(dalloc(h, &h->cbuf, (size_t)kMaxP));
+    STEP(dalloc(h, &h->ybuf, (size_t)kMaxP));
     h->p = p;
     h->k = k;
     h->ldq = ldq;
@@ -785,8 +794,8 @@ helm_status don_get_q(const helm_handle* hc, double* q_out) {
     helm_handle* h = const_cast<helm_handle*>(hc);
     if (!h || !q_out) return fail(h, HELM_BAD_ARG, "null argument");
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
-    CK(cudaMemcpy2DAsync(q_out, sizeof(double) * h->k, h->Q, sizeof(double) * h->ldq, sizeof(double) * h->k, h->N,
-                         cudaMemcpyDeviceToDevice, h->stream));
+    launch_cm_to_rm(h->Q, h->k, q_out, h->N, h->stream);
+    CKL();
     return HELM_OK;
 }
 

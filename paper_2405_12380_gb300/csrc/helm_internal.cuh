@@ -3,8 +3,8 @@
 // Data layout in HBM
 //   vectors       N complex, interleaved (double2 / float2), flat index i + n(j + n k)
 //   mask          N uint8 (1 = Dirichlet: outer ring + scatterer)
-//   Q             N x kcap doubles, node-major (the k basis values of a node are
-//                 contiguous, row stride kcap = k rounded up to a multiple of 32)
+//   Q             k x N doubles, column-major: basis vector j is Q[j*N .. j*N+N)
+//                 (node-major copies exist only during setup)
 //   A_c^-1        k x k complex128, row-major
 //   Krylov basis  V: (m+1) x N complex128, Z: m x N complex128, one vector after another
 #pragma once
@@ -142,12 +142,13 @@ void launch_apply_columns(const Op<double>& op, const double* Q, int ldq, int k,
                           cudaStream_t s);
 void launch_gauss_jordan(const double* C, int ldc, int k, double2* Ainv, double2* work, int* flag,
                          cudaStream_t s);
-void launch_restrict(const Op<double>& op, const double* Q, int ldq, int k, const double2* v,
-                     const double2* z, int conj, double2* partials, int nblk, cudaStream_t s);
-void launch_coarse_apply(const double2* partials, int nblk, int k, int ldq, const double2* Ainv, int conj,
-                         double2* y, double2* cbuf, cudaStream_t s);
-void launch_prolong(const double* Q, int ldq, int k, const double2* y, double2* z, long long N,
-                    cudaStream_t s);
+void launch_restrict(const Op<double>& op, const double* Q, int k, const double2* v, const double2* z, int conj,
+                     double2* partials, int nblk, cudaStream_t s);
+void launch_coarse_apply(const double2* partials, int nblk, int k, const double2* Ainv, int conj, double2* y,
+                         double2* cbuf, cudaStream_t s);
+void launch_prolong(const double* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s);
+void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s);
+void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s);
 int restrict_blocks(long long N);
 
 // ------------------------------------------------------------------- handle

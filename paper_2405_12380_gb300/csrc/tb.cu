@@ -7,10 +7,11 @@
 //   Q1 = T_S R^-1, then CholQR2 pass        k_tri_inverse, k_gather_upper
 //   W = A Q (real columns -> complex)       k_apply_columns
 //   A_c = Q^T W, A_c^-1 by Gauss-Jordan     k_gram, k_gauss_jordan (one CTA, partial pivoting)
-// Per application (z += Q A_c^-1 Q^T (v - A z)):
-//   k_restrict   residual on the fly, 32 rows per warp step, lane-owned columns
+// Per application (z += Q A_c^-1 Q^T (v - A z)), Q column-major (k x N):
+//   k_restrict   residual on the fly into a shared tile; warps own columns and
+//                keep their sums in registers across tiles (one reduction per block)
 //   k_coarse     fixed-order sum of block partials, y = A_c^-1 c
-//   k_prolong    z_l += sum_j Q_lj y_j, one warp per row
+//   k_prolong    z_l += sum_j Q_j[l] y_j, one thread per node, y in shared memory
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -367,25 +368,29 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(const double* __restrict_
 }
 
 // ---------------------------------------------------------- per application
-constexpr int RS_WARPS = 4;
+// Q is column-major here: basis vector j occupies Q[j*N .. j*N + N).
+constexpr int RS_T = 256;        // threads per restriction block
+constexpr int RS_TILE = 256;     // rows per tile (one residual per thread)
 
-// partials[b][j] = sum over the rows of block b of Q[l][j] * r_l, r = v - A z (z may be null)
-template <int KPL>
-__global__ void __launch_bounds__(RS_WARPS * 32) k_restrict(Op<double> op, const double* __restrict__ Q, int ldq,
-                                                            const double2* __restrict__ v,
-                                                            const double2* __restrict__ z, int conj,
-                                                            double2* __restrict__ partials, long long rows_per_block) {
-    __shared__ double2 red[RS_WARPS][KPL * 32];
+// partials[b][j] = sum over the rows of block b of Q_j[l] r_l, r = v - A z (z may be null).
+// Each warp owns columns warp, warp + 8, ...; each lane keeps their accumulators over
+// all tiles of the block and reduces once at the end.
+template <int KPW>
+__global__ void __launch_bounds__(RS_T) k_restrict(Op<double> op, const double* __restrict__ Q, int k,
+                                                   const double2* __restrict__ v, const double2* __restrict__ z,
+                                                   int conj, double2* __restrict__ partials, long long rows_per_block) {
+    __shared__ double2 rs[RS_TILE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = RS_T / 32;
     const long long r0 = (long long)blockIdx.x * rows_per_block;
     const long long r1 = min(op.N, r0 + rows_per_block);
-    double2 acc[KPL];
+    const long long N = op.N;
+    double2 acc[KPW];
 #pragma unroll
-    for (int c = 0; c < KPL; ++c) acc[c] = make_double2(0, 0);
+    for (int c = 0; c < KPW; ++c) acc[c] = make_double2(0, 0);
     const long long sy = op.n, sz = (long long)op.n * op.n;
-    for (long long base = r0 + 32 * warp; base < r1; base += 32 * RS_WARPS) {
-        // lane computes r for row base + lane
-        const long long l = base + lane;
+    for (long long t0 = r0; t0 < r1; t0 += RS_TILE) {
+        const long long l = t0 + threadIdx.x;
         double2 r = make_double2(0, 0);
         if (l < r1 && !op.mask[l]) {
             r = v[l];
@@ -416,31 +421,37 @@ __global__ void __launch_bounds__(RS_WARPS * 32) k_restrict(Op<double> op, const
                 r.y -= op.hinv2 * s.y + (d.x * zc.y + d.y * zc.x);
             }
         }
-        const int nrows = (int)min((long long)32, r1 - base);
-        for (int q = 0; q < nrows; ++q) {
-            const double rx = __shfl_sync(0xffffffffu, r.x, q);
-            const double ry = __shfl_sync(0xffffffffu, r.y, q);
-            const double* Qrow = Q + (base + q) * ldq + lane;
+        __syncthreads();
+        rs[threadIdx.x] = r;
+        __syncthreads();
+        const int rows = (int)min((long long)RS_TILE, r1 - t0);
 #pragma unroll
-            for (int c = 0; c < KPL; ++c) {
-                const double qv = Qrow[32 * c];
-                acc[c].x = fma(qv, rx, acc[c].x);
-                acc[c].y = fma(qv, ry, acc[c].y);
+        for (int c = 0; c < KPW; ++c) {
+            const int j = warp + NW * c;
+            if (j < k) {
+                const double* Qj = Q + (long long)j * N + t0;
+                double ax = acc[c].x, ay = acc[c].y;
+                for (int q = lane; q < rows; q += 32) {
+                    const double qv = Qj[q];
+                    const double2 rr = rs[q];
+                    ax = fma(qv, rr.x, ax);
+                    ay = fma(qv, rr.y, ay);
+                }
+                acc[c].x = ax;
+                acc[c].y = ay;
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < KPL; ++c) red[warp][lane + 32 * c] = acc[c];
-    __syncthreads();
-    for (int j = threadIdx.x; j < KPL * 32; j += RS_WARPS * 32) {
-        double2 s = red[0][j];
-        for (int w = 1; w < RS_WARPS; ++w) s = cadd(s, red[w][j]);
-        partials[(long long)blockIdx.x * ldq + j] = s;
+    for (int c = 0; c < KPW; ++c) {
+        const int j = warp + NW * c;
+        const double sx = warp_sum(acc[c].x), sy2 = warp_sum(acc[c].y);
+        if (lane == 0 && j < k) partials[(long long)blockIdx.x * k + j] = make_double2(sx, sy2);
     }
 }
 
 // y = A_c^-1 c (conj: conj(A_c^-1)), c = fixed-order sum of the block partials
-__global__ void __launch_bounds__(1024) k_coarse(const double2* __restrict__ partials, int nblk, int k, int ldq,
+__global__ void __launch_bounds__(1024) k_coarse(const double2* __restrict__ partials, int nblk, int k,
                                                  const double2* __restrict__ Ainv, int conj, double2* __restrict__ y,
                                                  double2* __restrict__ cbuf) {
     __shared__ double2 c[kMaxP];
@@ -448,7 +459,7 @@ __global__ void __launch_bounds__(1024) k_coarse(const double2* __restrict__ par
     for (int j = warp; j < k; j += nw) {
         double sx = 0, sy = 0;
         for (int b = lane; b < nblk; b += 32) {
-            double2 q = partials[(long long)b * ldq + j];
+            double2 q = partials[(long long)b * k + j];
             sx += q.x;
             sy += q.y;
         }
@@ -475,33 +486,58 @@ __global__ void __launch_bounds__(1024) k_coarse(const double2* __restrict__ par
     }
 }
 
-// z_l += sum_j Q[l][j] y_j, one warp per row
-template <int KPL>
-__global__ void __launch_bounds__(256) k_prolong(const double* __restrict__ Q, int ldq, int k,
-                                                 const double2* __restrict__ y, double2* __restrict__ z, long long N) {
-    const int lane = threadIdx.x & 31;
-    double2 yv[KPL];
-#pragma unroll
-    for (int c = 0; c < KPL; ++c) {
-        int j = lane + 32 * c;
-        yv[c] = j < k ? y[j] : make_double2(0, 0);
-    }
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long l = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); l < N; l += warps) {
-        const double* Qrow = Q + l * ldq + lane;
+// z_l += sum_j Q_j[l] y_j, one thread per row, y broadcast from shared memory
+__global__ void __launch_bounds__(256) k_prolong(const double* __restrict__ Q, int k, const double2* __restrict__ y,
+                                                 double2* __restrict__ z, long long N) {
+    __shared__ double2 ys[kMaxP];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
         double sx = 0, sy = 0;
-#pragma unroll
-        for (int c = 0; c < KPL; ++c) {
-            const double qv = Qrow[32 * c];
-            sx = fma(qv, yv[c].x, sx);
-            sy = fma(qv, yv[c].y, sy);
+        const double* q = Q + l;
+#pragma unroll 4
+        for (int j = 0; j < k; ++j) {
+            const double qv = q[(long long)j * N];
+            sx = fma(qv, ys[j].x, sx);
+            sy = fma(qv, ys[j].y, sy);
         }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) {
-            double2 zz = z[l];
-            z[l] = make_double2(zz.x + sx, zz.y + sy);
-        }
+        double2 zz = z[l];
+        z[l] = make_double2(zz.x + sx, zz.y + sy);
+    }
+}
+
+// row-major (N x ld, k used) <-> column-major (k x N)
+__global__ void k_rm_to_cm(const double* __restrict__ A, int ld, int k, double* __restrict__ B, long long N) {
+    __shared__ double tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (l < N && c < k) ? A[l * ld + c] : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        if (c < k && l < N) B[(long long)c * N + l] = tile[threadIdx.x][r];
+    }
+}
+
+__global__ void k_cm_to_rm(const double* __restrict__ B, int k, double* __restrict__ A, long long N) {
+    __shared__ double tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        tile[r][threadIdx.x] = (c < k && l < N) ? B[(long long)c * N + l] : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        if (l < N && c < k) A[l * k + c] = tile[threadIdx.x][r];
     }
 }
 
@@ -557,43 +593,42 @@ void launch_gauss_jordan(const double* C, int ldc, int k, double2* Ainv, double2
 }
 
 int restrict_blocks(long long N) {
-    long long b = (N + 255) / 256;
+    long long b = (N + RS_TILE - 1) / RS_TILE;
     return (int)(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
 }
 
-void launch_restrict(const Op<double>& op, const double* Q, int ldq, int k, const double2* v, const double2* z,
-                     int conj, double2* partials, int nblk, cudaStream_t s) {
-    (void)k;
+void launch_restrict(const Op<double>& op, const double* Q, int k, const double2* v, const double2* z, int conj,
+                     double2* partials, int nblk, cudaStream_t s) {
     long long rows = (op.N + nblk - 1) / nblk;
-    switch (ldq / 32) {
-        case 1: k_restrict<1><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-        case 2: k_restrict<2><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-        case 3: k_restrict<3><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-        case 4: k_restrict<4><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-        case 5: k_restrict<5><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-        case 6: k_restrict<6><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-        case 7: k_restrict<7><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-        default: k_restrict<8><<<nblk, RS_WARPS * 32, 0, s>>>(op, Q, ldq, v, z, conj, partials, rows); break;
-    }
+    const int kpw = (k + 7) / 8;
+#define RS_CASE(K) k_restrict<K><<<nblk, RS_T, 0, s>>>(op, Q, k, v, z, conj, partials, rows)
+    if (kpw <= 1) RS_CASE(1);
+    else if (kpw <= 2) RS_CASE(2);
+    else if (kpw <= 4) RS_CASE(4);
+    else if (kpw <= 8) RS_CASE(8);
+    else if (kpw <= 16) RS_CASE(16);
+    else RS_CASE(32);
+#undef RS_CASE
 }
 
-void launch_coarse_apply(const double2* partials, int nblk, int k, int ldq, const double2* Ainv, int conj,
-                         double2* y, double2* cbuf, cudaStream_t s) {
-    k_coarse<<<1, 1024, 0, s>>>(partials, nblk, k, ldq, Ainv, conj, y, cbuf);
+void launch_coarse_apply(const double2* partials, int nblk, int k, const double2* Ainv, int conj, double2* y,
+                         double2* cbuf, cudaStream_t s) {
+    k_coarse<<<1, 1024, 0, s>>>(partials, nblk, k, Ainv, conj, y, cbuf);
 }
 
-void launch_prolong(const double* Q, int ldq, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
-    const int blocks = 4 * 152;
-    switch (ldq / 32) {
-        case 1: k_prolong<1><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-        case 2: k_prolong<2><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-        case 3: k_prolong<3><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-        case 4: k_prolong<4><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-        case 5: k_prolong<5><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-        case 6: k_prolong<6><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-        case 7: k_prolong<7><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-        default: k_prolong<8><<<blocks, 256, 0, s>>>(Q, ldq, k, y, z, N); break;
-    }
+void launch_prolong(const double* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
+    long long b = (N + 255) / 256;
+    k_prolong<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, N);
+}
+
+void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_rm_to_cm<<<g, dim3(32, 8), 0, s>>>(A, ld, k, B, N);
+}
+
+void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_cm_to_rm<<<g, dim3(32, 8), 0, s>>>(B, k, A, N);
 }
 
 }  // namespace helm

@@ -330,3 +330,20 @@ def bump_cube3d(seed: int = 0, n: int = 96, k0: float = 20.0, width: int | None 
     rec = fibonacci_sphere(n_receivers, 0.4)
     return _finish("bump_cube3d", 3, n, k0, scat, gaussian_source(3, n, c, sigma), trunk=trunk,
                    p=p, k2_scale=scale, extra={"centre": c, "receivers": rec})
+
+
+# ----------------------------------------------------------------- workloads
+# Solver settings of the timed workloads (parameters only, no arithmetic).
+BENCH_WORKLOADS = {
+    # 3D FP64: 64^3, k = 16, centred 16^3 cube, Gaussian source sigma = 0.04, trunk
+    # [3,128,128,128] (p = 128, natural-order selection with tau = 1e-6),
+    # DeepONet-BiCGStab with n_r = 3 red-black GS sweeps per trunk-basis correction
+    # (the cube experiment's ratio, Sec. 4.1), to 1e-8.
+    "cube3d-64": dict(scene="cube3d", n=64, seed=0, method="bicgstab", relax="rbgs", n_r=3,
+                      correction="tb", tau=1e-6, tol=1e-8, maxit=20000, restart=30),
+}
+
+
+def make_scene(name: str, **kw) -> Scene:
+    return {"square2d": square2d, "cube3d": cube3d, "submarine3d": submarine3d,
+            "bump_cube3d": bump_cube3d}[name](**kw)
