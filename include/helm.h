@@ -48,7 +48,8 @@ typedef enum {
     HELM_BREAKDOWN = 6,        /* BiCGStab rho or omega = 0, (t,t) = 0 */
     HELM_SINGULAR_COARSE = 7,  /* zero pivot in the coarse operator A_c */
     HELM_NOT_READY = 8,        /* correction requested before don_load */
-    HELM_OUT_OF_MEMORY = 9
+    HELM_OUT_OF_MEMORY = 9,
+    HELM_SCRATCH_TOO_SMALL = 10  /* problem exceeds the fixed scratch of helm_residual_noalloc */
 } helm_status;
 
 /* dtype of the vectors passed to a call */
@@ -181,6 +182,30 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* opts, const void* 
  * copies to and from the device are part of the call. */
 helm_status helm_solve_host(helm_handle* h, const helm_solve_opts* opts, const double* f,
                             double* x, helm_stats* stats, double* res_hist, int hist_len);
+
+/* Residual without allocation (no counterpart in the paper: an interface for
+ * callers that cannot allocate device memory -- code running inside a memory
+ * pool or arena it does not own, plugins whose host forbids cudaMalloc, code
+ * that must not touch the allocator).  Computes r = f - A x (conj(A) if conj)
+ * and *norm2 = ||r||_2^2 in FP64 exactly like helm_residual, but needs no
+ * handle: the operator is described by the arguments of helm_create (mask [dev]
+ * N bytes with the outer ring masked, k2 [dev] complex128 field or NULL), and
+ * f, x, r [dev] complex128, norm2 [dev] one double are the caller's.
+ *  - Scratch: a file-scope device array of 65536 doubles (512 KiB) that every
+ *    GPU loading the library holds until the process exits.  Problems whose
+ *    operator grid has more than 65536 thread blocks (3D n > 256) are rejected
+ *    with HELM_SCRATCH_TOO_SMALL.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture.
+ *  - Synchronises `stream` (a cudaStream_t, NULL = legacy default) once to check
+ *    that the outer ring is masked (HELM_BAD_ARG otherwise).
+ *  - Every call shares the one array, which keeps the last call's partial sums:
+ *    calls that overlap on the GPU (other streams, other host threads) race. */
+helm_status helm_residual_noalloc(int dim, int n, double k0, int layer_cells, double layer_strength,
+                                  const uint8_t* mask, const double* k2, const double* f,
+                                  const double* x, double* r, double* norm2, int conj, void* stream);
 
 #ifdef __cplusplus
 }

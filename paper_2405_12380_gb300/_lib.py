@@ -13,9 +13,10 @@ LIB_PATH = os.path.join(HERE, "libhelm.so")
 
 HELM_OK, HELM_BAD_ARG, HELM_NO_DEVICE, HELM_CUDA_ERROR = 0, 1, 2, 3
 HELM_NOT_CONVERGED, HELM_DIVERGED, HELM_BREAKDOWN, HELM_SINGULAR_COARSE = 4, 5, 6, 7
-HELM_NOT_READY, HELM_OUT_OF_MEMORY = 8, 9
+HELM_NOT_READY, HELM_OUT_OF_MEMORY, HELM_SCRATCH_TOO_SMALL = 8, 9, 10
 STATUS_NAMES = {0: "ok", 1: "bad_arg", 2: "no_device", 3: "cuda_error", 4: "not_converged",
-                5: "diverged", 6: "breakdown", 7: "singular_coarse", 8: "not_ready", 9: "out_of_memory"}
+                5: "diverged", 6: "breakdown", 7: "singular_coarse", 8: "not_ready", 9: "out_of_memory",
+                10: "scratch_too_small"}
 HELM_C128, HELM_C64 = 0, 1
 HELM_FP64, HELM_MIXED = 0, 1
 HELM_RELAX_NONE, HELM_JACOBI, HELM_RBGS = 0, 1, 2
@@ -63,6 +64,7 @@ SIGNATURES = {
     "helm_precond": (i32, [H, C.POINTER(SolveOpts), vp, vp]),
     "helm_solve": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(Stats), vp, i32]),
     "helm_solve_host": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(Stats), vp, i32]),
+    "helm_residual_noalloc": (i32, [i32, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp, i32, vp]),
 }
 
 _lib = None
