@@ -82,6 +82,17 @@ def natural_order_select(T, tau: float, kmax: int | None = None):
     return Qbuf[:, : len(kept)].copy(), kept
 
 
+def bf16_round(Q):
+    """Round FP64 values to the nearest BF16 value (ties to even), through FP32
+    first (the rounding the mixed-precision basis uses).  BF16 keeps the top 16
+    bits of an FP32 number."""
+    x = np.asarray(Q, dtype=np.float64).astype(np.float32)
+    bits = x.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    rounded = ((bits + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    return rounded.view(np.float32).astype(np.float64)
+
+
 def tb_setup(A, layers, coords, mask, p: int, Q=None, tau: float = 0.0) -> TBSetup:
     """P = natural-order selection of the first p trunk columns (drop tolerance
     tau), Q orthonormal with span(Q) = span(P), A_c = Q^T A Q, LU with partial
@@ -103,6 +114,15 @@ def tb_setup(A, layers, coords, mask, p: int, Q=None, tau: float = 0.0) -> TBSet
 def tb_correct(s: TBSetup, r):
     """M2 r = Q A_c^-1 Q^T r."""
     return s.Q @ sla.lu_solve(s.lu, s.Q.T @ r)
+
+
+def mixed_setup(s: TBSetup, A) -> TBSetup:
+    """Mixed precision: the basis is rounded to BF16 and the coarse operator is
+    rebuilt from the same rounded basis, A_c = Qr^T A Qr, so that the Galerkin
+    property holds for the basis actually used."""
+    Qr = bf16_round(s.Q)
+    Ac = Qr.T @ (A @ Qr)
+    return TBSetup(Q=Qr, Ac=Ac, lu=sla.lu_factor(Ac), kept=s.kept)
 
 
 def hybrid_preconditioner(A, s: "TBSetup | None", kind: str, n_r: int, omega: float = 0.6,

@@ -302,6 +302,24 @@ __global__ void __launch_bounds__(TB) k_mupdate(const double2* __restrict__ V, i
     }
 }
 
+// w += sign * sum_i V_i coef_i with complex64 vectors V (FP64 accumulation)
+__global__ void __launch_bounds__(TB) k_mupdate32(const float2* __restrict__ V, int nv, const double2* __restrict__ coef,
+                                                  double sign, double2* __restrict__ w, long long N) {
+    __shared__ double2 c[kMaxRestart + 1];
+    for (int i = threadIdx.x; i < nv; i += TB) c[i] = cscale(sign, coef[i]);
+    __syncthreads();
+    for (long long l = blockIdx.x * (long long)TB + threadIdx.x; l < N; l += (long long)gridDim.x * TB) {
+        double2 s = w[l];
+        for (int i = 0; i < nv; ++i) {
+            float2 vf = V[(long long)i * N + l];
+            double2 v = make_double2(vf.x, vf.y);
+            s.x += c[i].x * v.x - c[i].y * v.y;
+            s.y += c[i].x * v.y + c[i].y * v.x;
+        }
+        w[l] = s;
+    }
+}
+
 __global__ void __launch_bounds__(TB) k_scale_vec(const double2* __restrict__ w, double2* __restrict__ v,
                                                   const double* norm2, long long N) {
     const double nn = sqrt(*norm2);
@@ -435,6 +453,10 @@ void launch_mupdate(const double2* V, int nv, const double2* coef, double sign, 
 void launch_mdot_finalize(const double2* partials, int nparts, int nv, double2* out, int accumulate,
                           double2* copy, cudaStream_t s) {
     k_mdot_fin<<<1, 512, 0, s>>>(partials, nparts, nv, out, accumulate, copy);
+}
+void launch_mupdate32(const float2* V, int nv, const double2* coef, double sign, double2* w, long long N,
+                      cudaStream_t s) {
+    k_mupdate32<<<stream_blocks(N), TB, 0, s>>>(V, nv, coef, sign, w, N);
 }
 void launch_scale_vec(const double2* w, double2* v, const double* norm2, long long N, cudaStream_t s) {
     k_scale_vec<<<stream_blocks(N), TB, 0, s>>>(w, v, norm2, N);

@@ -183,7 +183,60 @@ helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, do
     return HELM_OK;
 }
 
+// complex64 hybrid cycle with the BF16 basis (MIXED handles): z32 = M(v32)
+helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v, float2* z, int conj) {
+    cudaStream_t s = h->stream;
+    const bool no_relax = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
+    if (no_relax && o->correction == HELM_CORR_NONE) {
+        CK(cudaMemcpyAsync(z, v, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, s));
+        return HELM_OK;
+    }
+    if (no_relax) {
+        CK(cudaMemsetAsync(z, 0, sizeof(float2) * h->N, s));
+    } else if (o->relax == HELM_JACOBI) {
+        TRY(ensure_tmp32(h, 4));
+        float2* a = (o->n_r % 2 == 1) ? z : h->tmp32[3];
+        float2* b = (o->n_r % 2 == 1) ? h->tmp32[3] : z;
+        launch_jacobi<float>(h->op32, o->omega, v, nullptr, a, conj, true, s);
+        for (int q = 1; q < o->n_r; ++q) {
+            launch_jacobi<float>(h->op32, o->omega, v, a, b, conj, false, s);
+            std::swap(a, b);
+        }
+        h->launches += o->n_r;
+    } else {
+        CK(cudaMemsetAsync(z, 0, sizeof(float2) * h->N, s));
+        for (int q = 0; q < o->n_r; ++q) {
+            launch_rbgs_half<float>(h->op32, 0, v, z, conj, q == 0, s);
+            launch_rbgs_half<float>(h->op32, 1, v, z, conj, false, s);
+        }
+        h->launches += 2 * o->n_r;
+    }
+    if (o->correction == HELM_CORR_TB) {
+        if (!h->Qbf) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
+        const int nblk = restrict_blocks(h->N);
+        ev_mark(h, 0, 0);
+        launch_restrict32(h->op32, h->Qbf, h->k, v, no_relax ? nullptr : z, conj, h->partials32, nblk, s);
+        ev_mark(h, 0, 1);
+        launch_coarse_apply32(h->partials32, nblk, h->k, h->Ainv, conj, h->y32, s);
+        ev_mark(h, 1, 0);
+        launch_prolong32(h->Qbf, h->k, h->y32, z, h->N, s);
+        ev_mark(h, 1, 1);
+        h->launches += 3;
+    }
+    CKL();
+    return HELM_OK;
+}
+
 helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
+    if (h->precision == HELM_MIXED) {
+        TRY(ensure_tmp32(h, 4));
+        launch_cvt_f64_to_f32(r, h->tmp32[0], h->N, h->stream);
+        TRY(precond32(h, o, h->tmp32[0], h->tmp32[1], conj));
+        launch_cvt_f32_to_f64(h->tmp32[1], z, h->N, h->stream);
+        h->launches += 2;
+        CKL();
+        return HELM_OK;
+    }
     const bool no_relax = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
     if (no_relax && o->correction == HELM_CORR_NONE) {
         // neither stage: M is the identity (plain Krylov)
@@ -284,10 +337,20 @@ helm_status ensure_krylov(helm_handle* h, int m) {
 helm_status solve_fgmres(helm_handle* h, const helm_solve_opts* o, const double2* f, double2* x, helm_stats* st,
                          Hist& hist, double bnorm) {
     const int m = o->restart;
+    const bool mixed = h->precision == HELM_MIXED;
     TRY(ensure_krylov(h, m));
     const long long N = h->N;
     cudaStream_t s = h->stream;
     const int ldh = m + 1;
+    if (mixed) {
+        TRY(ensure_tmp32(h, 4));
+        if (h->m32_alloc < m) {
+            dfree(h->Z32);
+            h->m32_alloc = 0;
+            TRY(dalloc(h, &h->Z32, (size_t)m * N));
+            h->m32_alloc = m;
+        }
+    }
     double2* h2 = h->y + (kMaxRestart + 1);
     int iters = 0, cycles = 0;
     while (true) {
@@ -312,10 +375,20 @@ helm_status solve_fgmres(helm_handle* h, const helm_solve_opts* o, const double2
             double2* Zj = h->Z + (long long)j * N;
             double2* w = h->V + (long long)(j + 1) * N;
             double2* Hcol = h->Hm + (long long)j * ldh;
-            TRY(precond(h, o, Vj, Zj, o->conj));
+            if (mixed) {
+                // complex64 preconditioner and matvec; the product is widened before CGS2
+                float2* Z32j = h->Z32 + (long long)j * N;
+                launch_cvt_f64_to_f32(Vj, h->tmp32[0], N, s);
+                TRY(precond32(h, o, h->tmp32[0], Z32j, o->conj));
+                launch_apply<float>(h->op32, Z32j, nullptr, h->tmp32[2], nullptr, o->conj, false, s);
+                launch_cvt_f32_to_f64(h->tmp32[2], w, N, s);
+                h->launches += 3;
+            } else {
+                TRY(precond(h, o, Vj, Zj, o->conj));
+                launch_apply<double>(h->op64, Zj, nullptr, w, nullptr, o->conj, false, s);
+                h->launches += 1;
+            }
             ++st->precond_applies;
-            launch_apply<double>(h->op64, Zj, nullptr, w, nullptr, o->conj, false, s);
-            h->launches += 1;
             ++st->matvecs;
             // CGS2: h = V^H w, w -= V h, h2 = V^H w, w -= V h2, h += h2
             launch_mdot(h->V, j + 1, w, N, h->hpart, s);
@@ -339,7 +412,10 @@ helm_status solve_fgmres(helm_handle* h, const helm_solve_opts* o, const double2
             if (wn2 == 0.0 || est <= o->tol || iters >= o->maxit) break;
         }
         launch_hsolve(h->Hm, ldh, kdim, h->g, h->y, s);
-        launch_mupdate(h->Z, kdim, h->y, 1.0, x, N, nullptr, s);
+        if (mixed)
+            launch_mupdate32(h->Z32, kdim, h->y, 1.0, x, N, s);
+        else
+            launch_mupdate(h->Z, kdim, h->y, 1.0, x, N, nullptr, s);
         h->launches += 2;
         CKL();
     }
@@ -539,6 +615,8 @@ helm_status helm_destroy(helm_handle* h) {
     for (auto p : h->tmp) cudaFree(p);
     for (auto p : h->tmp32) cudaFree(p);
     dfree(h->Q); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
+    if (h->Qbf) cudaFree(h->Qbf);
+    dfree(h->partials32); dfree(h->y32); dfree(h->Z32);
     dfree(h->V); dfree(h->Z); dfree(h->Hm); dfree(h->cs); dfree(h->sn); dfree(h->g); dfree(h->y); dfree(h->hpart);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -750,6 +828,13 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     STEP(dalloc(h, &T, (size_t)N * ldq));            // node-major Q for the setup GEMMs
     launch_gather_times_upper(Q1, ldq, nullptr, k, Rinv, k, T, ldq, N, s);
     dfree(Q1);
+    if (h->precision == HELM_MIXED) {
+        // the coarse operator is built from the same rounded basis the kernels use
+        launch_round_bf16(T, ldq, k, N, s);
+        dfree(h->Qbf);
+        STEPC(cudaMalloc(&h->Qbf, (size_t)N * k * 2));
+        launch_rm_to_cm_bf16(T, ldq, k, h->Qbf, N, s);
+    }
     STEP(dalloc(h, &h->Q, (size_t)N * k));           // column-major Q for the per-iteration kernels
     launch_rm_to_cm(T, ldq, k, h->Q, N, s);
     // A_c = Q^T (A Q)
@@ -770,6 +855,11 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         return fail(h, HELM_SINGULAR_COARSE, "coarse operator A_c is singular");
     }
     STEP(dalloc(h, &h->coarse_partials, (size_t)restrict_blocks(N) * k));
+    if (h->precision == HELM_MIXED) {
+        dfree(h->partials32); dfree(h->y32);
+        STEP(dalloc(h, &h->partials32, (size_t)restrict_blocks(N) * k));
+        STEP(dalloc(h, &h->y32, (size_t)kMaxP));
+    }
     STEP(dalloc(h, &h->cbuf, (size_t)kMaxP));
     STEP(dalloc(h, &h->ybuf, (size_t)kMaxP));
     h->p = p;

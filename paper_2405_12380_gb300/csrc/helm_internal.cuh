@@ -127,6 +127,8 @@ void launch_axpy(double2* y, const double2* x, double2 a, long long N, cudaStrea
 void launch_set_masked(double2* x, const double2* f, const uint8_t* mask, long long N, cudaStream_t s);
 void launch_cvt_f64_to_f32(const double2* a, float2* b, long long N, cudaStream_t s);
 void launch_cvt_f32_to_f64(const float2* a, double2* b, long long N, cudaStream_t s);
+void launch_mupdate32(const float2* V, int nv, const double2* coef, double sign, double2* w, long long N,
+                      cudaStream_t s);
 
 // tb.cu
 void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p,
@@ -149,6 +151,15 @@ void launch_coarse_apply(const double2* partials, int nblk, int k, const double2
 void launch_prolong(const double* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s);
 void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s);
 void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s);
+// mixed precision: BF16 basis (column-major k x N), complex64 vectors, FP32 accumulation
+void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s);
+void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long N, cudaStream_t s);
+void launch_cm_bf16_to_rm(const void* B, int k, double* A, long long N, cudaStream_t s);
+void launch_restrict32(const Op<float>& op, const void* Q, int k, const float2* v, const float2* z, int conj,
+                       float2* partials, int nblk, cudaStream_t s);
+void launch_coarse_apply32(const float2* partials, int nblk, int k, const double2* Ainv, int conj, float2* y,
+                           cudaStream_t s);
+void launch_prolong32(const void* Q, int k, const float2* y, float2* z, long long N, cudaStream_t s);
 int restrict_blocks(long long N);
 
 // ------------------------------------------------------------------- handle
@@ -181,6 +192,11 @@ struct helm_handle {
     double* Q = nullptr;
     double2* Ainv = nullptr;
     double2* coarse_partials = nullptr;
+    void* Qbf = nullptr;            // BF16 basis (MIXED handles), column-major k x N
+    float2* partials32 = nullptr;
+    float2* y32 = nullptr;
+    float2* Z32 = nullptr;          // FGMRES preconditioned vectors in complex64 (MIXED)
+    int m32_alloc = 0;
     double2* cbuf = nullptr;
     double2* ybuf = nullptr;
     // Krylov workspace

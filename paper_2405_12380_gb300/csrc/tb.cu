@@ -12,6 +12,8 @@
 //                keep their sums in registers across tiles (one reduction per block)
 //   k_coarse     fixed-order sum of block partials, y = A_c^-1 c
 //   k_prolong    z_l += sum_j Q_j[l] y_j, one thread per node, y in shared memory
+#include <cuda_bf16.h>
+
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -541,6 +543,183 @@ __global__ void k_cm_to_rm(const double* __restrict__ B, int k, double* __restri
     }
 }
 
+
+// ------------------------------------------------- mixed precision (BF16 Q)
+// Q rounded to BF16 (round to nearest even of the FP64 value via FP32).
+__global__ void k_round_bf16(double* __restrict__ A, int ld, int k, long long N) {
+    const long long total = N * (long long)ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        if ((int)(e % ld) < k) A[e] = (double)__bfloat162float(__float2bfloat16_rn((float)A[e]));
+    }
+}
+
+// row-major FP64 (N x ld) -> column-major BF16 (k x N)
+__global__ void k_rm_to_cm_bf16(const double* __restrict__ A, int ld, int k, __nv_bfloat16* __restrict__ B, long long N) {
+    __shared__ float tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (l < N && c < k) ? (float)A[l * ld + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        if (c < k && l < N) B[(long long)c * N + l] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+    }
+}
+
+__global__ void k_cm_bf16_to_rm(const __nv_bfloat16* __restrict__ B, int k, double* __restrict__ A, long long N) {
+    __shared__ double tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        tile[r][threadIdx.x] = (c < k && l < N) ? (double)__bfloat162float(B[(long long)c * N + l]) : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        if (l < N && c < k) A[l * k + c] = tile[threadIdx.x][r];
+    }
+}
+
+// complex64 restriction with a BF16 basis, FP32 accumulation: same structure as k_restrict
+template <int KPW>
+__global__ void __launch_bounds__(RS_T) k_restrict32(Op<float> op, const __nv_bfloat16* __restrict__ Q, int k,
+                                                     const float2* __restrict__ v, const float2* __restrict__ z,
+                                                     int conj, float2* __restrict__ partials,
+                                                     long long rows_per_block) {
+    __shared__ float2 rs[RS_TILE];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = RS_T / 32;
+    const long long r0 = (long long)blockIdx.x * rows_per_block;
+    const long long r1 = min(op.N, r0 + rows_per_block);
+    const long long N = op.N;
+    float2 acc[KPW];
+#pragma unroll
+    for (int c = 0; c < KPW; ++c) acc[c] = make_float2(0.f, 0.f);
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    for (long long t0 = r0; t0 < r1; t0 += RS_TILE) {
+        const long long l = t0 + threadIdx.x;
+        float2 r = make_float2(0.f, 0.f);
+        if (l < r1 && !op.mask[l]) {
+            r = v[l];
+            if (z) {
+                const int i = (int)(l % op.n), j = (int)((l / op.n) % op.n), kk = (int)(l / sz);
+                float2 s = make_float2(0.f, 0.f);
+                const uint8_t* mk = op.mask;
+                if (!mk[l - 1]) s = cadd(s, z[l - 1]);
+                if (!mk[l + 1]) s = cadd(s, z[l + 1]);
+                if (!mk[l - sy]) s = cadd(s, z[l - sy]);
+                if (!mk[l + sy]) s = cadd(s, z[l + sy]);
+                if (op.dim == 3) {
+                    if (!mk[l - sz]) s = cadd(s, z[l - sz]);
+                    if (!mk[l + sz]) s = cadd(s, z[l + sz]);
+                }
+                float2 d;
+                if (op.k2) {
+                    d = op.k2[l];
+                    d.x -= 2.0f * op.dim * op.hinv2;
+                } else {
+                    int m = max(layer_index(i, op.n, op.L), layer_index(j, op.n, op.L));
+                    if (op.dim == 3) m = max(m, layer_index(kk, op.n, op.L));
+                    d = make_float2(op.dre, op.im[m]);
+                }
+                if (conj) d.y = -d.y;
+                const float2 zc = z[l];
+                r.x -= op.hinv2 * s.x + (d.x * zc.x - d.y * zc.y);
+                r.y -= op.hinv2 * s.y + (d.x * zc.y + d.y * zc.x);
+            }
+        }
+        __syncthreads();
+        rs[threadIdx.x] = r;
+        __syncthreads();
+        const int rows = (int)min((long long)RS_TILE, r1 - t0);
+#pragma unroll
+        for (int c = 0; c < KPW; ++c) {
+            const int j = warp + NW * c;
+            if (j < k) {
+                const __nv_bfloat16* Qj = Q + (long long)j * N + t0;
+                float ax = acc[c].x, ay = acc[c].y;
+                for (int q = lane; q < rows; q += 32) {
+                    const float qv = __bfloat162float(Qj[q]);
+                    const float2 rr = rs[q];
+                    ax = fmaf(qv, rr.x, ax);
+                    ay = fmaf(qv, rr.y, ay);
+                }
+                acc[c].x = ax;
+                acc[c].y = ay;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < KPW; ++c) {
+        const int j = warp + NW * c;
+        float sx = acc[c].x, sy2 = acc[c].y;
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy2 += __shfl_xor_sync(0xffffffffu, sy2, o);
+        }
+        if (lane == 0 && j < k) partials[(long long)blockIdx.x * k + j] = make_float2(sx, sy2);
+    }
+}
+
+// y (complex64) = A_c^-1 c, partial sums added in FP64
+__global__ void __launch_bounds__(1024) k_coarse32(const float2* __restrict__ partials, int nblk, int k,
+                                                   const double2* __restrict__ Ainv, int conj, float2* __restrict__ y) {
+    __shared__ double2 c[kMaxP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < k; j += nw) {
+        double sx = 0, sy = 0;
+        for (int b = lane; b < nblk; b += 32) {
+            float2 q = partials[(long long)b * k + j];
+            sx += q.x;
+            sy += q.y;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) c[j] = make_double2(sx, sy);
+    }
+    __syncthreads();
+    for (int i = warp; i < k; i += nw) {
+        double sx = 0, sy = 0;
+        for (int j = lane; j < k; j += 32) {
+            double2 a = Ainv[(long long)i * k + j];
+            if (conj) a.y = -a.y;
+            double2 cj = c[j];
+            sx += a.x * cj.x - a.y * cj.y;
+            sy += a.x * cj.y + a.y * cj.x;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) y[i] = make_float2((float)sx, (float)sy);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_prolong32(const __nv_bfloat16* __restrict__ Q, int k, const float2* __restrict__ y,
+                                                   float2* __restrict__ z, long long N) {
+    __shared__ float2 ys[kMaxP];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
+        float sx = 0.f, sy = 0.f;
+        const __nv_bfloat16* q = Q + l;
+#pragma unroll 8
+        for (int j = 0; j < k; ++j) {
+            const float qv = __bfloat162float(q[(long long)j * N]);
+            sx = fmaf(qv, ys[j].x, sx);
+            sy = fmaf(qv, ys[j].y, sy);
+        }
+        float2 zz = z[l];
+        z[l] = make_float2(zz.x + sx, zz.y + sy);
+    }
+}
+
 }  // namespace
 
 void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p, double* T,
@@ -629,6 +808,45 @@ void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cud
 void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s) {
     dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
     k_cm_to_rm<<<g, dim3(32, 8), 0, s>>>(B, k, A, N);
+}
+
+void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s) {
+    k_round_bf16<<<4 * 152, 256, 0, s>>>(A, ld, k, N);
+}
+
+void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_rm_to_cm_bf16<<<g, dim3(32, 8), 0, s>>>(A, ld, k, static_cast<__nv_bfloat16*>(B), N);
+}
+
+void launch_cm_bf16_to_rm(const void* B, int k, double* A, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_cm_bf16_to_rm<<<g, dim3(32, 8), 0, s>>>(static_cast<const __nv_bfloat16*>(B), k, A, N);
+}
+
+void launch_restrict32(const Op<float>& op, const void* Qv, int k, const float2* v, const float2* z, int conj,
+                       float2* partials, int nblk, cudaStream_t s) {
+    const __nv_bfloat16* Q = static_cast<const __nv_bfloat16*>(Qv);
+    long long rows = (op.N + nblk - 1) / nblk;
+    const int kpw = (k + 7) / 8;
+#define RS_CASE(K) k_restrict32<K><<<nblk, RS_T, 0, s>>>(op, Q, k, v, z, conj, partials, rows)
+    if (kpw <= 1) RS_CASE(1);
+    else if (kpw <= 2) RS_CASE(2);
+    else if (kpw <= 4) RS_CASE(4);
+    else if (kpw <= 8) RS_CASE(8);
+    else if (kpw <= 16) RS_CASE(16);
+    else RS_CASE(32);
+#undef RS_CASE
+}
+
+void launch_coarse_apply32(const float2* partials, int nblk, int k, const double2* Ainv, int conj, float2* y,
+                           cudaStream_t s) {
+    k_coarse32<<<1, 1024, 0, s>>>(partials, nblk, k, Ainv, conj, y);
+}
+
+void launch_prolong32(const void* Q, int k, const float2* y, float2* z, long long N, cudaStream_t s) {
+    long long b = (N + 255) / 256;
+    k_prolong32<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(Q), k, y, z, N);
 }
 
 }  // namespace helm

@@ -341,6 +341,11 @@ BENCH_WORKLOADS = {
     # (the cube experiment's ratio, Sec. 4.1), to 1e-8.
     "cube3d-64": dict(scene="cube3d", n=64, seed=0, method="bicgstab", relax="rbgs", n_r=3,
                       correction="tb", tau=1e-6, tol=1e-8, maxit=20000, restart=30),
+    # 3D mixed precision: 128^3, k = 32, seeded submarine, seeded plane wave; complex64
+    # Jacobi + BF16 trunk basis (p = 256) inside FP64 FGMRES(50), to 1e-6.
+    "submarine3d-128": dict(scene="submarine3d", n=128, seed=0, method="fgmres", relax="jacobi", n_r=1,
+                            correction="tb", tau=1e-6, tol=1e-6, maxit=20000, restart=50,
+                            precision="mixed"),
 }
 
 

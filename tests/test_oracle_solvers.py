@@ -275,3 +275,21 @@ def test_oracle_bicgstab_rounding_sensitivity():
     y1, _ = krylov.bicgstab(A, b, np.zeros_like(b), M, 1e-12, 500)
     y2, _ = krylov.bicgstab(A, bp, np.zeros_like(b), M, 1e-12, 500)
     assert np.linalg.norm(y1 - y2) <= 1e-9 * np.linalg.norm(y1)
+
+
+def test_bf16_round_matches_torch_bfloat16():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    q = np.concatenate([rng.standard_normal(5000) * 10.0 ** rng.integers(-6, 3, 5000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, -3.5e-3]])
+    ref = torch.from_numpy(q.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(tb.bf16_round(q), ref)
+
+
+def test_mixed_setup_keeps_galerkin_property():
+    A, b, mask, rng, X, layers = _tb_small()
+    s = tb.mixed_setup(tb.tb_setup(A, layers, X, mask, 12), A)
+    r = rng.standard_normal(b.size) + 1j * rng.standard_normal(b.size)
+    z = tb.tb_correct(s, r)
+    assert np.linalg.norm(s.Q.T @ (r - A @ z)) <= 1e-11 * np.linalg.norm(s.Q.T @ r)
+    assert np.max(np.abs(s.Q.T @ s.Q - np.eye(12))) > 1e-5        # BF16 basis is only nearly orthonormal
