@@ -183,6 +183,29 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* opts, const void* 
 helm_status helm_solve_host(helm_handle* h, const helm_solve_opts* opts, const double* f,
                             double* x, helm_stats* stats, double* res_hist, int hist_len);
 
+/* ---- adjoint method (receiver-misfit loss, gradient w.r.t. the per-node k^2) ----
+ * Receivers sample u by trilinear interpolation of the 8 nodes of the grid cell
+ * that contains them (3D handles).  For a real loss L(u) with G = dL/dRe u +
+ * i dL/dIm u, the adjoint conj(A) lambda = G (A^H = conj(A), helm_solve with
+ * conj = 1) gives dL/dRe k^2_l + i dL/dIm k^2_l = -lambda_l conj(u_l) on fluid
+ * nodes and 0 on Dirichlet nodes, because dA/dk^2_l = e_l e_l^T on fluid rows. */
+
+/* idx [dev] 8*nrec ints and w [dev] 8*nrec doubles: corner nodes and trilinear
+ * weights of the receivers xyz [dev] (nrec x 3 doubles, coordinates in [0,1]^3). */
+helm_status helm_receivers_setup(helm_handle* h, int nrec, const double* xyz, int* idx, double* w);
+/* out[r] = sum_q w[8r+q] u[idx[8r+q]]  (out [dev] nrec complex128). */
+helm_status helm_receivers_sample(helm_handle* h, int nrec, const int* idx, const double* w,
+                                  const double* u, double* out);
+/* b = S^T e: b [dev] N complex128 is overwritten (zero except at receiver corners). */
+helm_status helm_receivers_adjoint(helm_handle* h, int nrec, const int* idx, const double* w,
+                                   const double* e, double* b);
+/* grad [dev] N complex128 = -lambda conj(u) on fluid nodes, 0 on masked nodes. */
+helm_status helm_k2_gradient(helm_handle* h, const double* lambda, const double* u, double* grad);
+/* Replace the k^2 field (k2 [dev] N complex128, copied).  If a trunk basis is
+ * loaded, the coarse operator A_c = Q^T A Q and its inverse are rebuilt for the
+ * new operator (Q depends only on the trunk and the mask).  Synchronises. */
+helm_status helm_set_k2(helm_handle* h, const double* k2);
+
 /* Residual without allocation (no counterpart in the paper: an interface for
  * callers that cannot allocate device memory -- code running inside a memory
  * pool or arena it does not own, plugins whose host forbids cudaMalloc, code

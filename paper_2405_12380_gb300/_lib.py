@@ -65,6 +65,11 @@ SIGNATURES = {
     "helm_solve": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(Stats), vp, i32]),
     "helm_solve_host": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(Stats), vp, i32]),
     "helm_residual_noalloc": (i32, [i32, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp, i32, vp]),
+    "helm_receivers_setup": (i32, [H, i32, vp, vp, vp]),
+    "helm_receivers_sample": (i32, [H, i32, vp, vp, vp, vp]),
+    "helm_receivers_adjoint": (i32, [H, i32, vp, vp, vp, vp]),
+    "helm_k2_gradient": (i32, [H, vp, vp, vp]),
+    "helm_set_k2": (i32, [H, vp]),
 }
 
 _lib = None

@@ -536,6 +536,37 @@ void fill_tables(helm_handle* h) {
     f.invd = h->invdf;
 }
 
+// A_c = Q^T (A Q) and its inverse from a node-major copy of Q (N x ldq)
+helm_status build_coarse(helm_handle* h, const double* Qrm, int ldq, int k) {
+    const long long N = h->N;
+    cudaStream_t s = h->stream;
+    double *Wc = nullptr, *Cc = nullptr, *part = nullptr;
+    double2* gj = nullptr;
+    auto cleanup = [&]() { dfree(Wc); dfree(Cc); dfree(part); dfree(gj); };
+    helm_status st;
+    if ((st = dalloc(h, &Wc, (size_t)N * 2 * ldq)) != HELM_OK || (st = dalloc(h, &Cc, (size_t)k * 2 * k)) != HELM_OK ||
+        (st = dalloc(h, &part, (size_t)(2 * 152 + 64) * 64 * 64 * 2 + (size_t)k * 2 * k * 2)) != HELM_OK ||
+        (st = dalloc(h, &gj, (size_t)k * 2 * k)) != HELM_OK) {
+        cleanup();
+        return st;
+    }
+    if (!h->Ainv && (st = dalloc(h, &h->Ainv, (size_t)k * k)) != HELM_OK) {
+        cleanup();
+        return st;
+    }
+    launch_apply_columns(h->op64, Qrm, ldq, k, Wc, 2 * ldq, s);
+    launch_gram(Qrm, ldq, k, Wc, 2 * ldq, 2 * k, N, part, Cc, s);
+    cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s);
+    launch_gauss_jordan(Cc, 2 * k, k, h->Ainv, gj, h->dflag, s);
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return fail(h, HELM_CUDA_ERROR, cudaGetErrorString(e));
+    if (flag) return fail(h, HELM_SINGULAR_COARSE, "coarse operator A_c is singular");
+    return HELM_OK;
+}
+
 }  // namespace
 
 // =============================================================== C ABI
@@ -838,21 +869,11 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     STEP(dalloc(h, &h->Q, (size_t)N * k));           // column-major Q for the per-iteration kernels
     launch_rm_to_cm(T, ldq, k, h->Q, N, s);
     // A_c = Q^T (A Q)
-    STEP(dalloc(h, &Wc, (size_t)N * 2 * ldq));
-    launch_apply_columns(h->op64, T, ldq, k, Wc, 2 * ldq, s);
-    STEP(dalloc(h, &Cc, (size_t)k * 2 * k));
-    launch_gram(T, ldq, k, Wc, 2 * ldq, 2 * k, N, part, Cc, s);
-    STEP(dalloc(h, &gj, (size_t)k * 2 * k));
-    STEP(dalloc(h, &h->Ainv, (size_t)k * k));
-    STEPC(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s));
-    launch_gauss_jordan(Cc, 2 * k, k, h->Ainv, gj, h->dflag, s);
-    STEPC(cudaGetLastError());
-    STEPC(cudaMemcpyAsync(hk, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    STEPC(cudaStreamSynchronize(s));
-    if (hk[0] != 0) {
+    st = build_coarse(h, T, ldq, k);
+    if (st != HELM_OK) {
         cleanup();
         dfree(h->Q); dfree(h->Ainv);
-        return fail(h, HELM_SINGULAR_COARSE, "coarse operator A_c is singular");
+        return st;
     }
     STEP(dalloc(h, &h->coarse_partials, (size_t)restrict_blocks(N) * k));
     if (h->precision == HELM_MIXED) {
@@ -950,6 +971,69 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     st.prolong_ms = h->profile ? ev_sum(h, 1) : 0.0;
     if (stats) *stats = st;
     return (helm_status)st.status;
+}
+
+helm_status helm_receivers_setup(helm_handle* h, int nrec, const double* xyz, int* idx, double* w) {
+    if (!h || nrec < 0 || (nrec > 0 && (!xyz || !idx || !w))) return fail(h, HELM_BAD_ARG, "bad argument");
+    if (h->dim != 3) return fail(h, HELM_BAD_ARG, "receivers need a 3D handle");
+    if (nrec == 0) return HELM_OK;
+    launch_receivers_setup(h->n, nrec, xyz, idx, w, h->stream);
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_receivers_sample(helm_handle* h, int nrec, const int* idx, const double* w, const double* u,
+                                  double* out) {
+    if (!h || nrec < 0 || (nrec > 0 && (!idx || !w || !u || !out))) return fail(h, HELM_BAD_ARG, "bad argument");
+    if (nrec == 0) return HELM_OK;
+    launch_receivers_sample(nrec, idx, w, (const double2*)u, (double2*)out, h->stream);
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_receivers_adjoint(helm_handle* h, int nrec, const int* idx, const double* w, const double* e,
+                                   double* b) {
+    if (!h || nrec < 0 || !b || (nrec > 0 && (!idx || !w || !e))) return fail(h, HELM_BAD_ARG, "bad argument");
+    CK(cudaMemsetAsync(b, 0, sizeof(double2) * h->N, h->stream));
+    if (nrec > 0) launch_receivers_adjoint(nrec, idx, w, (const double2*)e, (double2*)b, h->stream);
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_k2_gradient(helm_handle* h, const double* lambda, const double* u, double* grad) {
+    if (!h || !lambda || !u || !grad) return fail(h, HELM_BAD_ARG, "null argument");
+    launch_k2_gradient(h->N, h->mask, (const double2*)lambda, (const double2*)u, (double2*)grad, h->stream);
+    CKL();
+    return HELM_OK;
+}
+
+helm_status helm_set_k2(helm_handle* h, const double* k2) {
+    if (!h || !k2) return fail(h, HELM_BAD_ARG, "null argument");
+    const long long N = h->N;
+    if (!h->k2) {
+        TRY(dalloc(h, &h->k2, (size_t)N));
+        TRY(dalloc(h, &h->invd, (size_t)N));
+        TRY(dalloc(h, &h->k2f, (size_t)N));
+        TRY(dalloc(h, &h->invdf, (size_t)N));
+    }
+    CK(cudaMemcpyAsync(h->k2, k2, sizeof(double2) * N, cudaMemcpyDefault, h->stream));
+    fill_tables(h);
+    launch_invd_field(h->op64, h->invd, h->stream);
+    launch_cvt_f64_to_f32(h->k2, h->k2f, N, h->stream);
+    launch_cvt_f64_to_f32(h->invd, h->invdf, N, h->stream);
+    CKL();
+    if (h->Q) {
+        // rebuild A_c for the new operator from a node-major copy of the (possibly rounded) basis
+        double* Qrm = nullptr;
+        TRY(dalloc(h, &Qrm, (size_t)N * h->k));
+        launch_cm_to_rm(h->Q, h->k, Qrm, N, h->stream);
+        helm_status st = build_coarse(h, Qrm, h->k, h->k);
+        cudaStreamSynchronize(h->stream);
+        dfree(Qrm);
+        if (st != HELM_OK) return st;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return HELM_OK;
 }
 
 helm_status helm_solve_host(helm_handle* h, const helm_solve_opts* o, const double* f, double* x,

@@ -162,6 +162,15 @@ void launch_coarse_apply32(const float2* partials, int nblk, int k, const double
 void launch_prolong32(const void* Q, int k, const float2* y, float2* z, long long N, cudaStream_t s);
 int restrict_blocks(long long N);
 
+// adjoint.cu
+void launch_receivers_setup(int n, int nrec, const double* xyz, int* idx, double* w, cudaStream_t s);
+void launch_receivers_sample(int nrec, const int* idx, const double* w, const double2* u, double2* out,
+                             cudaStream_t s);
+void launch_receivers_adjoint(int nrec, const int* idx, const double* w, const double2* e, double2* b,
+                              cudaStream_t s);
+void launch_k2_gradient(long long N, const uint8_t* mask, const double2* lam, const double2* u, double2* g,
+                        cudaStream_t s);
+
 // ------------------------------------------------------------------- handle
 }  // namespace helm
 

@@ -178,6 +178,40 @@ class Problem:
             return d["iters"] + 1
         return d["iters"] + 1
 
+    # ------------------------------------------------------------ adjoint
+    def set_k2(self, k2):
+        k2t = torch.as_tensor(k2).to("cuda", torch.complex128).reshape(-1).contiguous()
+        self._check(self.lib.helm_set_k2(self.h, _ptr(k2t)), "set_k2")
+
+    def receivers(self, xyz):
+        """(idx, w) device tensors of the trilinear sampling of receivers xyz (R x 3)."""
+        x = torch.as_tensor(xyz, dtype=torch.float64).reshape(-1, 3).cuda().contiguous()
+        R = x.shape[0]
+        idx = torch.empty(8 * R, dtype=torch.int32, device="cuda")
+        w = torch.empty(8 * R, dtype=torch.float64, device="cuda")
+        self._check(self.lib.helm_receivers_setup(self.h, R, _ptr(x), _ptr(idx), _ptr(w)), "receivers_setup")
+        return idx, w
+
+    def sample(self, idx, w, u):
+        R = idx.numel() // 8
+        out = torch.empty(R, dtype=torch.complex128, device="cuda")
+        self._check(self.lib.helm_receivers_sample(self.h, R, _ptr(idx), _ptr(w), _ptr(u.contiguous()), _ptr(out)),
+                    "receivers_sample")
+        return out
+
+    def sample_adjoint(self, idx, w, e):
+        R = idx.numel() // 8
+        b = self.vec()
+        self._check(self.lib.helm_receivers_adjoint(self.h, R, _ptr(idx), _ptr(w), _ptr(e.contiguous()), _ptr(b)),
+                    "receivers_adjoint")
+        return b
+
+    def k2_gradient(self, lam, u):
+        g = self.vec()
+        self._check(self.lib.helm_k2_gradient(self.h, _ptr(lam.contiguous()), _ptr(u.contiguous()), _ptr(g)),
+                    "k2_gradient")
+        return g
+
     def solve_host(self, f: np.ndarray, x: np.ndarray, o: SolveOpts | None = None):
         """Host buffers in and out (complex128 numpy arrays, x updated in place)."""
         o = o or opts()

@@ -293,3 +293,46 @@ def test_mixed_setup_keeps_galerkin_property():
     z = tb.tb_correct(s, r)
     assert np.linalg.norm(s.Q.T @ (r - A @ z)) <= 1e-11 * np.linalg.norm(s.Q.T @ r)
     assert np.max(np.abs(s.Q.T @ s.Q - np.eye(12))) > 1e-5        # BF16 basis is only nearly orthonormal
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """Oracle adjoint gradient against central finite differences of the loss in
+    the real and imaginary parts of k^2 on seeded voxels (direct LU solves)."""
+    from oracle import adjoint
+    n = 13
+    rng = np.random.default_rng(11)
+    mask = (scenes.ring_mask(3, n) | scenes.box_mask(3, n, 5, 7)).reshape(-1).astype(np.uint8)
+    k2 = assemble.k2_field(3, n, 6.0, 3, 0.5) * (1 + 0.05 * rng.standard_normal(n ** 3))
+    src = np.where(mask == 0, rng.standard_normal(n ** 3), 0).astype(complex)
+    b = assemble.rhs(3, n, mask, src, np.zeros(n ** 3, complex))
+    S = adjoint.trilinear(n, scenes.fibonacci_sphere(20, 0.35))
+    d = rng.standard_normal(20) + 1j * rng.standard_normal(20)
+
+    def solve(kk):
+        return spla.spsolve(assemble.assemble(3, n, kk, mask).tocsc(), b)
+    A = assemble.assemble(3, n, k2, mask)
+    u = solve(k2)
+    g, lam = adjoint.gradient_k2(A, S, u, d, mask, lambda r: spla.spsolve(A.conj().tocsc(), r))
+    fluid = np.flatnonzero(mask == 0)
+    for l in rng.choice(fluid, 6, replace=False):
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            eps = 1e-4 * abs(k2[l])
+            kp, km = k2.copy(), k2.copy()
+            kp[l] += eps * unit
+            km[l] -= eps * unit
+            fd = (adjoint.loss(S, solve(kp), d) - adjoint.loss(S, solve(km), d)) / (2 * eps)
+            an = g[l].real if part == "re" else g[l].imag
+            assert abs(fd - an) <= 2e-5 * max(abs(fd), 1e-3 * np.max(np.abs(g))), (l, part, fd, an)
+    assert np.all(g[mask == 1] == 0)
+
+
+def test_trilinear_reproduces_linear_functions():
+    from oracle import adjoint
+    n = 9
+    pts = np.random.default_rng(2).uniform(0.05, 0.95, (30, 3))
+    S = adjoint.trilinear(n, pts)
+    X = scenes.node_coords(3, n)
+    f = 0.3 + 1.7 * X[:, 0] - 0.4 * X[:, 1] + 2.2 * X[:, 2]
+    ref = 0.3 + 1.7 * pts[:, 0] - 0.4 * pts[:, 1] + 2.2 * pts[:, 2]
+    assert np.max(np.abs(S @ f - ref)) < 1e-13
+    assert np.allclose(np.asarray(S.sum(axis=1)).ravel(), 1.0)
