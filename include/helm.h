@@ -61,7 +61,7 @@ enum { HELM_FP64 = 0, HELM_MIXED = 1 };
 /* relaxation kinds (Sec. 3.1.1: M = diag(A) -> Jacobi, lower triangle -> GS) */
 enum { HELM_RELAX_NONE = 0, HELM_JACOBI = 1, HELM_RBGS = 2 };
 /* second-stage correction M2 (Eq. 3): none, trunk-basis Galerkin (App. C) */
-enum { HELM_CORR_NONE = 0, HELM_CORR_TB = 1 };
+enum { HELM_CORR_NONE = 0, HELM_CORR_TB = 1, HELM_CORR_NONLINEAR = 2 };
 /* outer methods */
 enum { HELM_METHOD_RELAX = 0, HELM_METHOD_FGMRES = 1, HELM_METHOD_BICGSTAB = 2 };
 /* trunk activations on hidden layers */
@@ -164,7 +164,17 @@ helm_status don_get_q(const helm_handle* h, double* q_out);
 /* Copy A_c^-1 (k x k complex128, row-major) into out [dev]. */
 helm_status don_get_ainv(const helm_handle* h, double* out);
 
-/* z += M2 r = Q A_c^-1 Q^T r (mode HELM_CORR_TB).  r, z [dev] HELM_C128. */
+/* Load the branch network of the trained DeepONet (App. B): widths[0] = 2N (input
+ * [Re r, Im r] / ||r||, real parts first), widths[n_layers] = 2p (p of don_load:
+ * real-part coefficients first), ReLU on hidden layers, hidden widths <= 4096.
+ * weights [host] FP32: per layer W (row-major out x in) then bias.  Needs
+ * don_load first (the raw trunk matrix T, masked rows zero, is kept in FP32). */
+helm_status don_load_branch(helm_handle* h, const float* weights, const int* widths, int n_layers);
+
+/* z += M2 r.  HELM_CORR_TB: M2 = Q A_c^-1 Q^T (App. C, linear).
+ * HELM_CORR_NONLINEAR: M2 r = s (T b_re + i T b_im), b = Branch([Re r, Im r]/s),
+ * s = ||r|| (DeepONet inference on the residual, Eq. 3; positively homogeneous;
+ * FP32 network).  r, z [dev] HELM_C128. */
 helm_status don_correct(helm_handle* h, int mode, const void* r, void* z, int conj, int dtype);
 
 /* z = M(r), the hybrid cycle of `opts` (Eq. 3).  r, z [dev] HELM_C128. */
@@ -205,6 +215,28 @@ helm_status helm_k2_gradient(helm_handle* h, const double* lambda, const double*
  * loaded, the coarse operator A_c = Q^T A Q and its inverse are rebuilt for the
  * new operator (Q depends only on the trunk and the mask).  Synchronises. */
 helm_status helm_set_k2(helm_handle* h, const double* k2);
+
+/* ---- dense layers for DeepONet training (App. B), FP32, row-major, on `stream` ----
+ * nn_gemm: C = alpha op(A) op(B) + beta C; op(A) is M x K (A stored K x M when
+ * transA), op(B) is K x N (B stored N x K when transB).
+ * nn_bias_act: X = act(X + bias) in place, act 0 = none, 1 = ReLU, 2 = tanh (bias may be NULL).
+ * nn_act_backward: dX *= act'(Y), Y the activation output.
+ * nn_bias_grad: db[c] = sum_r dY[r][c].
+ * nn_adam: Adam with bias correction, step t >= 1.
+ * nn_rel_l2: per-sample ||pred - target||^2 / ||target||^2 over P2 values and the
+ *   gradient of the batch mean with respect to pred.
+ * nn_gather: dst[r][c] = src[row_idx[r]][col_idx[c]] (NULL index = identity). */
+helm_status nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float* A, int lda,
+                    const float* B, int ldb, float beta, float* C, int ldc, void* stream);
+helm_status nn_bias_act(int rows, int cols, float* X, const float* bias, int act, void* stream);
+helm_status nn_act_backward(long long n, float* dX, const float* Y, int act, void* stream);
+helm_status nn_bias_grad(int rows, int cols, const float* dY, float* db, void* stream);
+helm_status nn_adam(long long n, float* p, const float* g, float* m, float* v, float lr, float beta1,
+                    float beta2, float eps, int t, void* stream);
+helm_status nn_rel_l2(int B, int P2, const float* pred, const float* target, float* dpred, float* loss,
+                      void* stream);
+helm_status nn_gather(int rows, int cols, const float* src, long long lds, const int* row_idx,
+                      const int* col_idx, float* dst, void* stream);
 
 /* Residual without allocation (no counterpart in the paper: an interface for
  * callers that cannot allocate device memory -- code running inside a memory

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "ok", 1: "bad_arg", 2: "no_device", 3: "cuda_error", 4: "not_
 HELM_C128, HELM_C64 = 0, 1
 HELM_FP64, HELM_MIXED = 0, 1
 HELM_RELAX_NONE, HELM_JACOBI, HELM_RBGS = 0, 1, 2
-HELM_CORR_NONE, HELM_CORR_TB = 0, 1
+HELM_CORR_NONE, HELM_CORR_TB, HELM_CORR_NONLINEAR = 0, 1, 2
 HELM_METHOD_RELAX, HELM_METHOD_FGMRES, HELM_METHOD_BICGSTAB = 0, 1, 2
 HELM_ACT_TANH = 0
 
@@ -70,6 +70,14 @@ SIGNATURES = {
     "helm_receivers_adjoint": (i32, [H, i32, vp, vp, vp, vp]),
     "helm_k2_gradient": (i32, [H, vp, vp, vp]),
     "helm_set_k2": (i32, [H, vp]),
+    "don_load_branch": (i32, [H, vp, C.POINTER(i32), i32]),
+    "nn_gemm": (i32, [i32, i32, i32, i32, i32, C.c_float, vp, i32, vp, i32, C.c_float, vp, i32, vp]),
+    "nn_bias_act": (i32, [i32, i32, vp, vp, i32, vp]),
+    "nn_act_backward": (i32, [i64, vp, vp, i32, vp]),
+    "nn_bias_grad": (i32, [i32, i32, vp, vp, vp]),
+    "nn_adam": (i32, [i64, vp, vp, vp, vp, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]),
+    "nn_rel_l2": (i32, [i32, i32, vp, vp, vp, vp, vp]),
+    "nn_gather": (i32, [i32, i32, vp, i64, vp, vp, vp, vp]),
 }
 
 _lib = None

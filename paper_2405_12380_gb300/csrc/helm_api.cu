@@ -183,6 +183,33 @@ helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, do
     return HELM_OK;
 }
 
+// z += s (T b_re + i T b_im), b = Branch([Re v, Im v] / s), s = ||v|| (FP32 network)
+helm_status nl_correct(helm_handle* h, const double2* v, double2* z) {
+    if (!h->bw || !h->Traw) return fail(h, HELM_NOT_READY, "branch network not loaded (don_load_branch)");
+    cudaStream_t s = h->stream;
+    TRY(norm2_into(h, v, S_TS));
+    double* s2 = scal(h, S_TS);
+    launch_nl_pack(v, s2, h->nl_x, h->N, s);
+    const float* in = h->nl_x;
+    const float* W = h->bw;
+    const int nl = (int)h->bwidths.size() - 1;
+    float* bufs[2] = {h->nl_h0, h->nl_h1};
+    for (int l = 0; l < nl; ++l) {
+        const int win = h->bwidths[l], wout = h->bwidths[l + 1];
+        float* out = bufs[l % 2];
+        helm_status st = nn_gemm(0, 1, 1, wout, win, 1.0f, in, win, W, win, 0.0f, out, wout, s);
+        if (st != HELM_OK) return fail(h, st, "branch layer");
+        st = nn_bias_act(1, wout, out, W + (size_t)win * wout, l < nl - 1 ? 1 : 0, s);
+        if (st != HELM_OK) return fail(h, st, "branch activation");
+        W += (size_t)win * wout + wout;
+        in = out;
+    }
+    launch_nl_prolong(h->Traw, h->p, in, s2, z, h->N, s);
+    h->launches += 3 + 2 * nl + 2;
+    CKL();
+    return HELM_OK;
+}
+
 // complex64 hybrid cycle with the BF16 basis (MIXED handles): z32 = M(v32)
 helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v, float2* z, int conj) {
     cudaStream_t s = h->stream;
@@ -247,6 +274,17 @@ helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, 
     if (o->correction == HELM_CORR_TB) {
         const bool zero = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
         TRY(tb_correct(h, r, zero ? nullptr : z, z, conj));
+    } else if (o->correction == HELM_CORR_NONLINEAR) {
+        // M2 acts on the residual after the sweeps: r - A z
+        TRY(ensure_tmp(h, 13));
+        double2* rr = h->tmp[12];
+        if (no_relax) {
+            CK(cudaMemcpyAsync(rr, r, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        } else {
+            launch_apply<double>(h->op64, z, r, rr, nullptr, conj, true, h->stream);
+            h->launches += 1;
+        }
+        TRY(nl_correct(h, rr, z));
     }
     return HELM_OK;
 }
@@ -255,8 +293,15 @@ helm_status check_opts(helm_handle* h, const helm_solve_opts* o) {
     if (!o) return fail(h, HELM_BAD_ARG, "opts is NULL");
     if (o->method < 0 || o->method > 2) return fail(h, HELM_BAD_ARG, "unknown method");
     if (o->relax < 0 || o->relax > 2) return fail(h, HELM_BAD_ARG, "unknown relaxation");
-    if (o->correction < 0 || o->correction > 1) return fail(h, HELM_BAD_ARG, "unknown correction");
+    if (o->correction < 0 || o->correction > 2) return fail(h, HELM_BAD_ARG, "unknown correction");
     if (o->correction == HELM_CORR_TB && !h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
+    if (o->correction == HELM_CORR_NONLINEAR) {
+        if (!h->bw) return fail(h, HELM_NOT_READY, "branch network not loaded");
+        if (o->method == HELM_METHOD_BICGSTAB)
+            return fail(h, HELM_BAD_ARG, "the nonlinear correction cannot precondition BiCGStab (needs a linear M)");
+        if (h->precision == HELM_MIXED || o->conj)
+            return fail(h, HELM_BAD_ARG, "the nonlinear correction is FP64-handle, non-conjugate only");
+    }
     if (o->method == HELM_METHOD_FGMRES && (o->restart < 1 || o->restart > kMaxRestart))
         return fail(h, HELM_BAD_ARG, "restart must be in 1..64");
     if (!(o->tol >= 0) || o->maxit < 0 || o->n_r < 0) return fail(h, HELM_BAD_ARG, "bad tol/maxit/n_r");
@@ -308,6 +353,11 @@ helm_status solve_relax(helm_handle* h, const helm_solve_opts* o, const double2*
         CKL();
         if (o->correction == HELM_CORR_TB) {
             TRY(tb_correct(h, f, x, x, o->conj));
+            ++st->precond_applies;
+        } else if (o->correction == HELM_CORR_NONLINEAR) {
+            launch_apply<double>(h->op64, x, f, r, nullptr, o->conj, true, h->stream);
+            h->launches += 1;
+            TRY(nl_correct(h, r, x));
             ++st->precond_applies;
         }
         ++cycles;
@@ -648,6 +698,7 @@ helm_status helm_destroy(helm_handle* h) {
     dfree(h->Q); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
     if (h->Qbf) cudaFree(h->Qbf);
     dfree(h->partials32); dfree(h->y32); dfree(h->Z32);
+    dfree(h->Traw); dfree(h->bw); dfree(h->nl_x); dfree(h->nl_h0); dfree(h->nl_h1);
     dfree(h->V); dfree(h->Z); dfree(h->Hm); dfree(h->cs); dfree(h->sn); dfree(h->g); dfree(h->y); dfree(h->hpart);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -826,6 +877,9 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     STEP(dalloc(h, &kept, (size_t)p));
     STEP(dalloc(h, &part, (size_t)2 * 152 * 64 * 64 * 4 + (size_t)p * 2 * p * 16));
     launch_trunk_eval(h->op64, dW, widths, n_layers, p, T, ldt, s);
+    dfree(h->Traw);
+    STEP(dalloc(h, &h->Traw, (size_t)N * p));
+    launch_rm_to_cm_f32(T, ldt, p, h->Traw, N, s);
     launch_gram(T, ldt, p, T, ldt, p, N, part, G, s);
     STEPC(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s));
     launch_select_chol(G, p, p, tau, Wk, R, kept, h->dflag + 1, h->dflag, s);
@@ -893,6 +947,28 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     return HELM_OK;
 }
 
+helm_status don_load_branch(helm_handle* h, const float* weights, const int* widths, int n_layers) {
+    if (!h || !weights || !widths || n_layers < 1 || n_layers > 8) return fail(h, HELM_BAD_ARG, "bad argument");
+    if (!h->Traw) return fail(h, HELM_NOT_READY, "don_load the trunk first");
+    if ((long long)widths[0] != 2 * h->N) return fail(h, HELM_BAD_ARG, "branch input width must be 2N");
+    if (widths[n_layers] != 2 * h->p) return fail(h, HELM_BAD_ARG, "branch output width must be 2p");
+    size_t total = 0;
+    int hmax = 1;
+    for (int l = 0; l < n_layers; ++l) {
+        if (l > 0 && (widths[l] < 1 || widths[l] > 4096)) return fail(h, HELM_BAD_ARG, "hidden widths must be 1..4096");
+        total += (size_t)widths[l] * widths[l + 1] + widths[l + 1];
+        hmax = std::max(hmax, widths[l + 1]);
+    }
+    dfree(h->bw); dfree(h->nl_x); dfree(h->nl_h0); dfree(h->nl_h1);
+    h->bwidths.assign(widths, widths + n_layers + 1);
+    TRY(dalloc(h, &h->bw, total));
+    TRY(dalloc(h, &h->nl_x, (size_t)2 * h->N));
+    TRY(dalloc(h, &h->nl_h0, (size_t)hmax));
+    TRY(dalloc(h, &h->nl_h1, (size_t)hmax));
+    CK(cudaMemcpy(h->bw, weights, total * sizeof(float), cudaMemcpyHostToDevice));
+    return HELM_OK;
+}
+
 helm_status don_info(const helm_handle* h, int* k, int* kept_idx) {
     if (!h) return HELM_BAD_ARG;
     if (k) *k = h->k;
@@ -920,8 +996,12 @@ helm_status don_get_ainv(const helm_handle* hc, double* out) {
 
 helm_status don_correct(helm_handle* h, int mode, const void* r, void* z, int conj, int dtype) {
     if (!h || !r || !z) return fail(h, HELM_BAD_ARG, "null argument");
-    if (mode != HELM_CORR_TB) return fail(h, HELM_BAD_ARG, "mode");
     if (dtype != HELM_C128) return fail(h, HELM_BAD_ARG, "dtype");
+    if (mode == HELM_CORR_NONLINEAR) {
+        if (conj) return fail(h, HELM_BAD_ARG, "the nonlinear correction has no conjugate form");
+        return nl_correct(h, (const double2*)r, (double2*)z);
+    }
+    if (mode != HELM_CORR_TB) return fail(h, HELM_BAD_ARG, "mode");
     return tb_correct(h, (const double2*)r, nullptr, (double2*)z, conj);
 }
 

@@ -151,6 +151,11 @@ void launch_coarse_apply(const double2* partials, int nblk, int k, const double2
 void launch_prolong(const double* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s);
 void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s);
 void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s);
+// nonlinear DeepONet correction: raw trunk matrix in FP32 (p x N), branch in FP32
+void launch_rm_to_cm_f32(const double* A, int ld, int p, float* B, long long N, cudaStream_t s);
+void launch_nl_pack(const double2* r, const double* s2, float* x, long long N, cudaStream_t s);
+void launch_nl_prolong(const float* T, int p, const float* b, const double* s2, double2* z, long long N,
+                       cudaStream_t s);
 // mixed precision: BF16 basis (column-major k x N), complex64 vectors, FP32 accumulation
 void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s);
 void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long N, cudaStream_t s);
@@ -206,6 +211,13 @@ struct helm_handle {
     float2* y32 = nullptr;
     float2* Z32 = nullptr;          // FGMRES preconditioned vectors in complex64 (MIXED)
     int m32_alloc = 0;
+    // nonlinear correction (trained branch)
+    float* Traw = nullptr;          // p x N FP32, masked rows zero
+    float* bw = nullptr;            // branch weights (per layer W row-major out x in, then bias)
+    std::vector<int> bwidths;
+    float* nl_x = nullptr;          // 2N
+    float* nl_h0 = nullptr;         // hidden activations
+    float* nl_h1 = nullptr;
     double2* cbuf = nullptr;
     double2* ybuf = nullptr;
     // Krylov workspace

@@ -544,6 +544,57 @@ __global__ void k_cm_to_rm(const double* __restrict__ B, int k, double* __restri
 }
 
 
+// ------------------------------------------------ nonlinear DeepONet correction
+// row-major FP64 T (N x ld, p used) -> column-major FP32 (p x N)
+__global__ void k_rm_to_cm_f32(const double* __restrict__ A, int ld, int p, float* __restrict__ B, long long N) {
+    __shared__ float tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (l < N && c < p) ? (float)A[l * ld + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        if (c < p && l < N) B[(long long)c * N + l] = tile[threadIdx.x][r];
+    }
+}
+
+// branch input [Re r, Im r] / s, s^2 read from the device (s = 0 -> zeros)
+__global__ void k_nl_pack(const double2* __restrict__ r, const double* __restrict__ s2, float* __restrict__ x,
+                          long long N) {
+    const double s = sqrt(*s2);
+    const double inv = s > 0 ? 1.0 / s : 0.0;
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
+        const double2 v = r[l];
+        x[l] = (float)(v.x * inv);
+        x[N + l] = (float)(v.y * inv);
+    }
+}
+
+// z_l += s (sum_j T_j[l] b_j + i sum_j T_j[l] b_{p+j})
+__global__ void __launch_bounds__(256) k_nl_prolong(const float* __restrict__ T, int p, const float* __restrict__ b,
+                                                    const double* __restrict__ s2, double2* __restrict__ z, long long N) {
+    __shared__ float bs[2 * kMaxP];
+    for (int j = threadIdx.x; j < 2 * p; j += blockDim.x) bs[j] = b[j];
+    __syncthreads();
+    const double s = sqrt(*s2);
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
+        float re = 0.f, im = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < p; ++j) {
+            const float t = T[(long long)j * N + l];
+            re = fmaf(t, bs[j], re);
+            im = fmaf(t, bs[p + j], im);
+        }
+        double2 zz = z[l];
+        z[l] = make_double2(zz.x + s * re, zz.y + s * im);
+    }
+}
+
 // ------------------------------------------------- mixed precision (BF16 Q)
 // Q rounded to BF16 (round to nearest even of the FP64 value via FP32).
 __global__ void k_round_bf16(double* __restrict__ A, int ld, int k, long long N) {
@@ -808,6 +859,22 @@ void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cud
 void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s) {
     dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
     k_cm_to_rm<<<g, dim3(32, 8), 0, s>>>(B, k, A, N);
+}
+
+void launch_rm_to_cm_f32(const double* A, int ld, int p, float* B, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (p + 31) / 32);
+    k_rm_to_cm_f32<<<g, dim3(32, 8), 0, s>>>(A, ld, p, B, N);
+}
+
+void launch_nl_pack(const double2* r, const double* s2, float* x, long long N, cudaStream_t s) {
+    long long b = (N + 255) / 256;
+    k_nl_pack<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(r, s2, x, N);
+}
+
+void launch_nl_prolong(const float* T, int p, const float* b, const double* s2, double2* z, long long N,
+                       cudaStream_t s) {
+    long long nb = (N + 255) / 256;
+    k_nl_prolong<<<(unsigned)(nb < 8 * 152 ? nb : 8 * 152), 256, 0, s>>>(T, p, b, s2, z, N);
 }
 
 void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s) {

@@ -26,7 +26,7 @@ def opts(method="fgmres", relax="jacobi", n_r=1, omega=0.6, correction="tb", tol
     m = {"relax": L.HELM_METHOD_RELAX, "fgmres": L.HELM_METHOD_FGMRES,
          "bicgstab": L.HELM_METHOD_BICGSTAB}[method]
     r = {"none": L.HELM_RELAX_NONE, "jacobi": L.HELM_JACOBI, "rbgs": L.HELM_RBGS}[relax]
-    c = {"none": L.HELM_CORR_NONE, "tb": L.HELM_CORR_TB}[correction]
+    c = {"none": L.HELM_CORR_NONE, "tb": L.HELM_CORR_TB, "nonlinear": L.HELM_CORR_NONLINEAR}[correction]
     return SolveOpts(m, r, int(n_r), float(omega), c, float(tol), int(restart), int(maxit), int(bool(conj)))
 
 
@@ -134,6 +134,22 @@ class Problem:
         self.k = k.value
         self.kept = list(idx)[: self.k]
         return self.k
+
+    def don_load_branch(self, layers):
+        """layers: [(W[out, in], b[out])] (FP32 values), ReLU on hidden layers;
+        input width 2N, output width 2p."""
+        widths = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
+        flat = np.ascontiguousarray(np.concatenate(
+            [np.concatenate([np.asarray(W, np.float32).reshape(-1), np.asarray(b, np.float32)]) for W, b in layers]))
+        wd = (C.c_int * len(widths))(*widths)
+        self._check(self.lib.don_load_branch(self.h, flat.ctypes.data_as(C.c_void_p), wd, len(layers)),
+                    "don_load_branch")
+
+    def don_correct_nonlinear(self, r, z=None):
+        z = torch.zeros_like(r) if z is None else z
+        self._check(self.lib.don_correct(self.h, L.HELM_CORR_NONLINEAR, _ptr(r), _ptr(z), 0, _dtype_code(r)),
+                    "don_correct")
+        return z
 
     def basis(self):
         Q = torch.empty(self.N, self.k, dtype=torch.float64, device="cuda")

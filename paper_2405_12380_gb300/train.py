@@ -1,0 +1,235 @@
+"""DeepONet training on scatterer-free problems (Sec. 3.2, App. B).
+
+The operator learned is the solution operator of Eq. 1 without the scatterer,
+f -> u.  Training data come from the library's own solver: forcing terms drawn
+from a Gaussian random field (real and imaginary parts independent, RBF kernel,
+App. B), solved on a handle whose mask is the outer ring only.  Pairs are
+normalised by ||f|| (the correction is applied as s * DeepONet(r / s)).
+
+Network: branch [2N, hidden..., 2p] with ReLU, trunk [d, hidden..., p] with
+tanh, output u_l = sum_j b_re,j T_j(x_l) + i sum_j b_im,j T_j(x_l); loss: relative
+L2 on a random subset of nodes per step; Adam (App. B: constant learning rate).
+Every forward, backward and optimiser step runs in libhelm's FP32 kernels
+(nn_gemm, nn_bias_act, nn_act_backward, nn_bias_grad, nn_rel_l2, nn_adam,
+nn_gather); torch only provides device buffers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _ck(st, what):
+    if st != 0:
+        raise RuntimeError(f"{what}: {L.STATUS_NAMES.get(st, st)}")
+
+
+@dataclass
+class Layer:
+    W: torch.Tensor          # out x in, FP32, cuda
+    b: torch.Tensor          # out
+    mW: torch.Tensor = None
+    vW: torch.Tensor = None
+    mb: torch.Tensor = None
+    vb: torch.Tensor = None
+    gW: torch.Tensor = None
+    gb: torch.Tensor = None
+
+    def __post_init__(self):
+        for name in ("mW", "vW", "gW"):
+            setattr(self, name, torch.zeros_like(self.W))
+        for name in ("mb", "vb", "gb"):
+            setattr(self, name, torch.zeros_like(self.b))
+
+
+@dataclass
+class DeepONet:
+    branch: list = field(default_factory=list)
+    trunk: list = field(default_factory=list)
+    step: int = 0
+
+    @staticmethod
+    def init(branch_widths, trunk_widths, seed=0):
+        import scenes
+        rng = np.random.default_rng(seed)
+        mk = lambda ws: [Layer(torch.from_numpy(W.astype(np.float32)).cuda(), torch.from_numpy(b.astype(np.float32)).cuda())
+                         for W, b in scenes.glorot_mlp(rng, ws)]
+        return DeepONet(mk(branch_widths), mk(trunk_widths))
+
+    def numpy_layers(self, part):
+        return [(l.W.cpu().numpy().astype(np.float64), l.b.cpu().numpy().astype(np.float64)) for l in getattr(self, part)]
+
+    def save(self, path):
+        d = {"step": self.step}
+        for part in ("branch", "trunk"):
+            for i, l in enumerate(getattr(self, part)):
+                for nm in ("W", "b", "mW", "vW", "mb", "vb"):
+                    d[f"{part}{i}_{nm}"] = getattr(l, nm).cpu().numpy()
+        np.savez(path, **d)
+
+    @staticmethod
+    def load(path):
+        z = np.load(path)
+        net = DeepONet(step=int(z["step"]))
+        for part in ("branch", "trunk"):
+            i = 0
+            while f"{part}{i}_W" in z:
+                l = Layer(torch.from_numpy(z[f"{part}{i}_W"]).cuda(), torch.from_numpy(z[f"{part}{i}_b"]).cuda())
+                for nm in ("mW", "vW", "mb", "vb"):
+                    getattr(l, nm).copy_(torch.from_numpy(z[f"{part}{i}_{nm}"]))
+                getattr(net, part).append(l)
+                i += 1
+        return net
+
+
+def _forward_mlp(layers, X, act, stream):
+    """Activations [X, H1, ..., out]; act on hidden layers."""
+    lib = L.lib()
+    acts = [X]
+    for i, l in enumerate(layers):
+        rows, fin = acts[-1].shape
+        H = torch.empty(rows, l.W.shape[0], dtype=torch.float32, device="cuda")
+        _ck(lib.nn_gemm(0, 1, rows, l.W.shape[0], fin, 1.0, _p(acts[-1]), fin, _p(l.W), fin, 0.0, _p(H),
+                        l.W.shape[0], stream), "nn_gemm")
+        _ck(lib.nn_bias_act(rows, l.W.shape[0], _p(H), _p(l.b), act if i < len(layers) - 1 else 0, stream),
+            "nn_bias_act")
+        acts.append(H)
+    return acts
+
+
+def _backward_mlp(layers, acts, dout, act, stream, need_input_grad=False):
+    lib = L.lib()
+    d = dout
+    for i in range(len(layers) - 1, -1, -1):
+        l = layers[i]
+        rows = d.shape[0]
+        fout, fin = l.W.shape
+        if i < len(layers) - 1:
+            _ck(lib.nn_act_backward(d.numel(), _p(d), _p(acts[i + 1]), act, stream), "nn_act_backward")
+        _ck(lib.nn_gemm(1, 0, fout, fin, rows, 1.0, _p(d), fout, _p(acts[i]), fin, 0.0, _p(l.gW), fin, stream), "dW")
+        _ck(lib.nn_bias_grad(rows, fout, _p(d), _p(l.gb), stream), "db")
+        if i > 0 or need_input_grad:
+            dn = torch.empty(rows, fin, dtype=torch.float32, device="cuda")
+            _ck(lib.nn_gemm(0, 0, rows, fin, fout, 1.0, _p(d), fout, _p(l.W), fin, 0.0, _p(dn), fin, stream), "dX")
+            d = dn
+
+
+def train_step(net, X, Xc, Y, lr=1e-4, stream=None):
+    """One Adam step on a batch: X (B x 2N) branch inputs, Xc (P x d) trunk inputs,
+    Y (B x 2P) targets on the sampled nodes (real parts then imaginary).  Returns
+    the per-sample relative-L2 losses (before the step)."""
+    lib = L.lib()
+    s = stream if stream is not None else C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    B, P = X.shape[0], Xc.shape[0]
+    ba = _forward_mlp(net.branch, X, 1, s)
+    ta = _forward_mlp(net.trunk, Xc, 2, s)
+    Bo, T = ba[-1], ta[-1]
+    p = T.shape[1]
+    pred = torch.empty(B, 2 * P, dtype=torch.float32, device="cuda")
+    _ck(lib.nn_gemm(0, 1, B, P, p, 1.0, _p(Bo), 2 * p, _p(T), p, 0.0, _p(pred), 2 * P, s), "pred re")
+    _ck(lib.nn_gemm(0, 1, B, P, p, 1.0, C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, _p(T), p, 0.0,
+                    C.c_void_p(pred.data_ptr() + 4 * P), 2 * P, s), "pred im")
+    dpred = torch.empty_like(pred)
+    loss = torch.empty(B, dtype=torch.float32, device="cuda")
+    _ck(lib.nn_rel_l2(B, 2 * P, _p(pred), _p(Y), _p(dpred), _p(loss), s), "nn_rel_l2")
+    dBo = torch.empty_like(Bo)
+    _ck(lib.nn_gemm(0, 0, B, p, P, 1.0, _p(dpred), 2 * P, _p(T), p, 0.0, _p(dBo), 2 * p, s), "dB re")
+    _ck(lib.nn_gemm(0, 0, B, p, P, 1.0, C.c_void_p(dpred.data_ptr() + 4 * P), 2 * P, _p(T), p, 0.0,
+                    C.c_void_p(dBo.data_ptr() + 4 * p), 2 * p, s), "dB im")
+    dT = torch.empty_like(T)
+    _ck(lib.nn_gemm(1, 0, P, p, B, 1.0, _p(dpred), 2 * P, _p(Bo), 2 * p, 0.0, _p(dT), p, s), "dT re")
+    _ck(lib.nn_gemm(1, 0, P, p, B, 1.0, C.c_void_p(dpred.data_ptr() + 4 * P), 2 * P,
+                    C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, 1.0, _p(dT), p, s), "dT im")
+    _backward_mlp(net.branch, ba, dBo, 1, s)
+    _backward_mlp(net.trunk, ta, dT, 2, s)
+    net.step += 1
+    for l in net.branch + net.trunk:
+        _ck(lib.nn_adam(l.W.numel(), _p(l.W), _p(l.gW), _p(l.mW), _p(l.vW), lr, 0.9, 0.999, 1e-8, net.step, s), "adam W")
+        _ck(lib.nn_adam(l.b.numel(), _p(l.b), _p(l.gb), _p(l.mb), _p(l.vb), lr, 0.9, 0.999, 1e-8, net.step, s), "adam b")
+    return loss
+
+
+def make_dataset(problem, fs, opts, log=print):
+    """Solve the scatterer-free problem for each forcing in fs (S x N complex numpy);
+    return X (S x 2N) and Y (S x 2N) FP32 device tensors normalised by ||f||."""
+    S, N = fs.shape
+    X = torch.empty(S, 2 * N, dtype=torch.float32, device="cuda")
+    Y = torch.empty(S, 2 * N, dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    iters = []
+    for i in range(S):
+        f = torch.from_numpy(fs[i]).cuda()
+        u, st = problem.solve(f, None, opts)
+        if st["status"] != 0:
+            raise RuntimeError(f"training solve {i}: {st['status_name']}")
+        iters.append(st["iters"])
+        nf = float(np.linalg.norm(fs[i]))
+        un = u.cpu().numpy() / nf
+        X[i].copy_(torch.from_numpy(np.concatenate([fs[i].real, fs[i].imag]).astype(np.float32) / np.float32(nf)))
+        Y[i].copy_(torch.from_numpy(np.concatenate([un.real, un.imag]).astype(np.float32)))
+    log(f"dataset: {S} solves, mean {np.mean(iters):.0f} iterations, {time.time() - t0:.1f} s")
+    return X, Y
+
+
+def train(net, X, Y, coords, fluid_idx, steps, batch=32, nodes=8192, lr=1e-4, seed=0, log=print,
+          log_every=100, checkpoint=None):
+    """Adam on random batches and random node subsets (fluid nodes only)."""
+    lib = L.lib()
+    rng = np.random.default_rng(seed)
+    S, N2 = X.shape
+    N = N2 // 2
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    hist = []
+    Xb = torch.empty(batch, N2, dtype=torch.float32, device="cuda")
+    Yb = torch.empty(batch, 2 * nodes, dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    for step in range(steps):
+        rows = torch.from_numpy(rng.choice(S, batch, replace=False).astype(np.int32)).cuda()
+        nid = rng.choice(fluid_idx, nodes, replace=False).astype(np.int32)
+        cols = torch.from_numpy(np.concatenate([nid, nid + N]).astype(np.int32)).cuda()
+        Xc = torch.from_numpy(coords[nid].astype(np.float32)).cuda()
+        _ck(lib.nn_gather(batch, N2, _p(X), N2, _p(rows), None, _p(Xb), s), "gather X")
+        _ck(lib.nn_gather(batch, 2 * nodes, _p(Y), N2, _p(rows), _p(cols), _p(Yb), s), "gather Y")
+        loss = train_step(net, Xb, Xc, Yb, lr=lr, stream=s)
+        if step % log_every == 0 or step == steps - 1:
+            l = float(loss.cpu().numpy().mean())
+            hist.append((step, l))
+            log(f"step {step:6d} rel-L2^2 {l:.4e} ({time.time() - t0:.1f} s)")
+        if checkpoint and (step + 1) % 1000 == 0:
+            net.save(checkpoint)
+    return hist
+
+
+def evaluate(net, X, Y, coords, rows):
+    """Mean relative L2 error (not squared) of the DeepONet on the given samples, all nodes."""
+    lib = L.lib()
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    N = X.shape[1] // 2
+    Xc = torch.from_numpy(coords.astype(np.float32)).cuda()
+    ta = _forward_mlp(net.trunk, Xc, 2, s)
+    T = ta[-1]
+    p = T.shape[1]
+    errs = []
+    for r in rows:
+        ba = _forward_mlp(net.branch, X[r:r + 1], 1, s)
+        Bo = ba[-1]
+        pred = torch.empty(1, 2 * N, dtype=torch.float32, device="cuda")
+        _ck(lib.nn_gemm(0, 1, 1, N, p, 1.0, _p(Bo), 2 * p, _p(T), p, 0.0, _p(pred), 2 * N, s), "pred re")
+        _ck(lib.nn_gemm(0, 1, 1, N, p, 1.0, C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, _p(T), p, 0.0,
+                        C.c_void_p(pred.data_ptr() + 4 * N), 2 * N, s), "pred im")
+        d = torch.empty_like(pred)
+        lo = torch.empty(1, dtype=torch.float32, device="cuda")
+        _ck(lib.nn_rel_l2(1, 2 * N, _p(pred), _p(Y[r:r + 1]), _p(d), _p(lo), s), "rel_l2")
+        errs.append(math.sqrt(float(lo.cpu().numpy()[0])))
+    return float(np.mean(errs))

@@ -1,0 +1,119 @@
+"""DeepONet kernels: FP32 GEMM, a full training step (forward, backward, Adam)
+and the nonlinear branch correction, against the FP64 oracle (oracle/mlp.py)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import scenes
+from oracle import assemble, krylov, mlp, tb as otb
+from tests.gpu_common import need_gpu, problem_for, rel, small_scene, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.mark.parametrize("ta,tb,M,N,K", [(0, 0, 70, 130, 33), (1, 0, 64, 65, 17), (0, 1, 5, 300, 1000),
+                                         (1, 1, 33, 31, 129), (0, 1, 1, 96, 40000), (1, 0, 96, 4000, 7)])
+def test_nn_gemm(ta, tb, M, N, K):
+    from paper_2405_12380_gb300 import _lib as L
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((K, M) if ta else (M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K) if tb else (K, N)).astype(np.float32)
+    C0 = rng.standard_normal((M, N)).astype(np.float32)
+    ref = 0.7 * (A.T if ta else A).astype(np.float64) @ (B.T if tb else B).astype(np.float64) - 1.3 * C0
+    Ad, Bd, Cd = to_dev(A), to_dev(B), to_dev(C0)
+    st = L.lib().nn_gemm(ta, tb, M, N, K, 0.7, C.c_void_p(Ad.data_ptr()), A.shape[1], C.c_void_p(Bd.data_ptr()),
+                         B.shape[1], -1.3, C.c_void_p(Cd.data_ptr()), N, None)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert np.max(np.abs(Cd.cpu().numpy() - ref)) <= 2e-6 * np.sqrt(K) * np.max(np.abs(ref)) + 1e-5
+
+
+def test_training_step_matches_oracle():
+    from paper_2405_12380_gb300 import train
+    rng = np.random.default_rng(21)
+    net = train.DeepONet.init([40, 24, 16, 10], [3, 12, 12, 5], seed=4)
+    for l in net.branch + net.trunk:                       # non-zero biases
+        l.b.copy_(torch.from_numpy((0.1 * rng.standard_normal(l.b.shape[0])).astype(np.float32)))
+    X = rng.standard_normal((6, 40)).astype(np.float32)
+    Xc = rng.random((23, 3)).astype(np.float32)
+    Y = rng.standard_normal((6, 46)).astype(np.float32)
+    branch, trunk = net.numpy_layers("branch"), net.numpy_layers("trunk")
+    pred, ba, ta_ = mlp.deeponet_forward(branch, trunk, X, Xc)
+    loss_o, dpred = mlp.rel_l2(pred, Y.astype(np.float64))
+    gb, gt = mlp.deeponet_backward(branch, trunk, ba, ta_, dpred)
+    loss = train.train_step(net, to_dev(X), to_dev(Xc), to_dev(Y), lr=1e-3)
+    torch.cuda.synchronize()
+    assert rel(loss.cpu().numpy(), loss_o) < 1e-5
+    for l, (dW, db) in zip(net.branch + net.trunk, gb + gt):
+        assert rel(l.gW.cpu().numpy(), dW) < 1e-4
+        assert rel(l.gb.cpu().numpy(), db) < 1e-4
+    # the first Adam step moves every parameter with a clear gradient by about lr
+    for l, (W0, _) in zip(net.branch, branch):
+        moved = np.abs(l.W.double().cpu().numpy() - W0)
+        g = np.abs(l.gW.cpu().numpy())
+        assert np.allclose(moved[g > 1e-4], 1e-3, rtol=1e-2)
+
+
+def test_nonlinear_correction_matches_oracle():
+    s = small_scene(3, 21)
+    rng = np.random.default_rng(7)
+    N = 21 ** 3
+    trunk = scenes.glorot_mlp(rng, [3, 16, 16, 8])
+    branch = [(W.astype(np.float32).astype(np.float64), b) for W, b in scenes.glorot_mlp(rng, [2 * N, 32, 16])]
+    P = problem_for(s)
+    P.don_load(trunk, 8, tau=1e-4)
+    P.don_load_branch(branch)
+    r = s["b"] - s["A"] @ (0.1 * rng.standard_normal(N))
+    r[s["mask"] == 1] = 0
+    z = P.don_correct_nonlinear(to_dev(r)).cpu().numpy()
+    T = otb.trunk_matrix(trunk, scenes.node_coords(3, 21), s["mask"], 8)
+    ref = mlp.nonlinear_correction(branch, T, r)
+    assert rel(z, ref) < 1e-5
+    # positive homogeneity holds on the device too
+    z2 = P.don_correct_nonlinear(to_dev(2.5 * r)).cpu().numpy()
+    assert rel(z2, 2.5 * z) < 1e-6
+
+
+def test_nonlinear_relaxation_metasolver_same_iterate():
+    import paper_2405_12380_gb300 as hm
+    s = small_scene(2, 45)
+    rng = np.random.default_rng(9)
+    N = 45 ** 2
+    trunk = scenes.glorot_mlp(rng, [2, 16, 16, 8])
+    branch = [(W.astype(np.float32).astype(np.float64), b) for W, b in scenes.glorot_mlp(rng, [2 * N, 24, 16])]
+    P = problem_for(s)
+    P.don_load(trunk, 8, tau=1e-4)
+    P.don_load_branch(branch)
+    x, st = P.solve(to_dev(s["b"]), None, hm.opts("relax", "rbgs", 2, correction="nonlinear", tol=1e-14, maxit=2))
+    T = otb.trunk_matrix(trunk, scenes.node_coords(2, 45), s["mask"], 8)
+    xo, io = krylov.relaxation_metasolver(s["A"], s["b"], np.zeros_like(s["b"]), "rbgs", 2,
+                                          lambda r: mlp.nonlinear_correction(branch, T, r),
+                                          colours=assemble.colour(2, 45), tol=1e-14, max_cycles=2)
+    assert st["iters"] == io["iters"] == 2
+    assert rel(x.cpu().numpy(), xo) < 1e-5
+
+
+def test_training_reduces_loss_on_scatterer_free_problem():
+    import paper_2405_12380_gb300 as hm
+    from paper_2405_12380_gb300 import train
+    n = 33
+    mask = scenes.ring_mask(2, n).reshape(-1).astype(np.uint8)
+    P = hm.Problem(2, n, 6.0, mask, layer_cells=4)
+    rng = np.random.default_rng(0)
+    fs = scenes.grf_samples(rng, 2, n, 48)
+    fs[:, mask == 1] = 0
+    X, Y = train.make_dataset(P, fs, hm.opts("bicgstab", "rbgs", 2, correction="none", tol=1e-6, maxit=3000),
+                              log=lambda *a: None)
+    net = train.DeepONet.init([2 * n * n, 64, 32], [2, 32, 32, 16], seed=1)
+    coords = scenes.node_coords(2, n)
+    fluid = np.flatnonzero(mask == 0)
+    before = train.evaluate(net, X, Y, coords, range(40, 48))
+    train.train(net, X[:40], Y[:40], coords, fluid, steps=400, batch=16, nodes=512, lr=1e-3, log=lambda *a: None)
+    after_train = train.evaluate(net, X, Y, coords, range(0, 8))
+    assert after_train < 0.5 * before

@@ -336,3 +336,87 @@ def test_trilinear_reproduces_linear_functions():
     ref = 0.3 + 1.7 * pts[:, 0] - 0.4 * pts[:, 1] + 2.2 * pts[:, 2]
     assert np.max(np.abs(S @ f - ref)) < 1e-13
     assert np.allclose(np.asarray(S.sum(axis=1)).ravel(), 1.0)
+
+
+def _tiny_deeponet(rng):
+    branch = scenes.glorot_mlp(rng, [10, 7, 6, 8])
+    trunk = scenes.glorot_mlp(rng, [3, 5, 5, 4])
+    branch = [(W, b + 0.1 * rng.standard_normal(b.shape)) for W, b in branch]
+    trunk = [(W, b + 0.1 * rng.standard_normal(b.shape)) for W, b in trunk]
+    X = rng.standard_normal((3, 10))
+    Xc = rng.random((9, 3))
+    Y = rng.standard_normal((3, 18))
+    return branch, trunk, X, Xc, Y
+
+
+def test_deeponet_backward_matches_torch_autograd():
+    torch = pytest.importorskip("torch")
+    from oracle import mlp
+    rng = np.random.default_rng(12)
+    branch, trunk, X, Xc, Y = _tiny_deeponet(rng)
+    pred, ba, ta = mlp.deeponet_forward(branch, trunk, X, Xc)
+    loss, dpred = mlp.rel_l2(pred, Y)
+    gb, gt = mlp.deeponet_backward(branch, trunk, ba, ta, dpred)
+    tb_ = [(torch.tensor(W, requires_grad=True), torch.tensor(b, requires_grad=True)) for W, b in branch]
+    tt_ = [(torch.tensor(W, requires_grad=True), torch.tensor(b, requires_grad=True)) for W, b in trunk]
+    h = torch.tensor(X)
+    for i, (W, b) in enumerate(tb_):
+        h = h @ W.T + b
+        if i < len(tb_) - 1:
+            h = torch.relu(h)
+    t = torch.tensor(Xc)
+    for i, (W, b) in enumerate(tt_):
+        t = t @ W.T + b
+        if i < len(tt_) - 1:
+            t = torch.tanh(t)
+    p = t.shape[1]
+    pr = torch.cat([h[:, :p] @ t.T, h[:, p:] @ t.T], dim=1)
+    Yt = torch.tensor(Y)
+    L = (((pr - Yt) ** 2).sum(1) / (Yt ** 2).sum(1)).mean()
+    L.backward()
+    assert abs(L.item() - loss.mean()) < 1e-13
+    for (W, b), (dW, db) in zip(tb_ + tt_, gb + gt):
+        assert np.max(np.abs(W.grad.numpy() - dW)) < 1e-12
+        assert np.max(np.abs(b.grad.numpy() - db)) < 1e-12
+
+
+def test_deeponet_backward_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(13)
+    branch, trunk, X, Xc, Y = _tiny_deeponet(rng)
+
+    def L(br, tr):
+        return mlp.rel_l2(mlp.deeponet_forward(br, tr, X, Xc)[0], Y)[0].mean()
+    pred, ba, ta = mlp.deeponet_forward(branch, trunk, X, Xc)
+    gb, gt = mlp.deeponet_backward(branch, trunk, ba, ta, mlp.rel_l2(pred, Y)[1])
+    for which, layers, grads in (("b", branch, gb), ("t", trunk, gt)):
+        for _ in range(10):
+            li = rng.integers(len(layers))
+            W, b = layers[li]
+            i, j = rng.integers(W.shape[0]), rng.integers(W.shape[1])
+            eps = 1e-6
+            Wp, Wm = W.copy(), W.copy()
+            Wp[i, j] += eps
+            Wm[i, j] -= eps
+            lp = [(Wp if k == li else w, bb) for k, (w, bb) in enumerate(layers)]
+            lm = [(Wm if k == li else w, bb) for k, (w, bb) in enumerate(layers)]
+            fd = (L(lp, trunk) - L(lm, trunk)) / (2 * eps) if which == "b" else (L(branch, lp) - L(branch, lm)) / (2 * eps)
+            assert abs(fd - grads[li][0][i, j]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_nonlinear_correction_is_positively_homogeneous():
+    from oracle import mlp
+    rng = np.random.default_rng(14)
+    N, p = 12, 4
+    branch = scenes.glorot_mlp(rng, [2 * N, 9, 2 * p])
+    T = rng.standard_normal((N, p))
+    r = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    z = mlp.nonlinear_correction(branch, T, r)
+    assert np.linalg.norm(mlp.nonlinear_correction(branch, T, 3.7 * r) - 3.7 * z) < 1e-12 * np.linalg.norm(z)
+    assert np.all(mlp.nonlinear_correction(branch, T, 0 * r) == 0)
+
+
+def test_adam_first_step_moves_by_lr():
+    from oracle import mlp
+    p, m, v = mlp.adam_step(np.array([1.0, -2.0]), np.array([0.3, -5.0]), np.zeros(2), np.zeros(2), 1, lr=1e-3)
+    assert np.allclose(p, [1.0 - 1e-3, -2.0 + 1e-3], atol=1e-9)
