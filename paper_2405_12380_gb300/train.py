@@ -161,11 +161,17 @@ def train_step(net, X, Xc, Y, lr=1e-4, stream=None):
 
 
 def make_dataset(problem, fs, opts, log=print):
-    """Solve the scatterer-free problem for each forcing in fs (S x N complex numpy);
-    return X (S x 2N) and Y (S x 2N) FP32 device tensors normalised by ||f||."""
+    """Solve the scatterer-free problem for each forcing in fs (S x N complex numpy).
+    Returns X (S x 2N) and Y (S x 2N) FP32 device tensors and the scales (c_in,
+    c_out): X = c_in [Re f, Im f] / ||f|| (entries of unit RMS) and
+    Y = c_out [Re u, Im u] / ||f|| (c_out set from the first samples so that the
+    targets have unit RMS).  The network learns Y from X; export_branch() folds
+    the two scales back into the first and last branch layers."""
     S, N = fs.shape
     X = torch.empty(S, 2 * N, dtype=torch.float32, device="cuda")
     Y = torch.empty(S, 2 * N, dtype=torch.float32, device="cuda")
+    c_in = float(np.sqrt(2.0 * N))
+    c_out = None
     t0 = time.time()
     iters = []
     for i in range(S):
@@ -176,10 +182,26 @@ def make_dataset(problem, fs, opts, log=print):
         iters.append(st["iters"])
         nf = float(np.linalg.norm(fs[i]))
         un = u.cpu().numpy() / nf
-        X[i].copy_(torch.from_numpy(np.concatenate([fs[i].real, fs[i].imag]).astype(np.float32) / np.float32(nf)))
-        Y[i].copy_(torch.from_numpy(np.concatenate([un.real, un.imag]).astype(np.float32)))
-    log(f"dataset: {S} solves, mean {np.mean(iters):.0f} iterations, {time.time() - t0:.1f} s")
-    return X, Y
+        if c_out is None:
+            c_out = 1.0 / float(np.sqrt(np.mean(un.real ** 2 + un.imag ** 2) / 2.0))
+        X[i].copy_(torch.from_numpy((np.concatenate([fs[i].real, fs[i].imag]) * (c_in / nf)).astype(np.float32)))
+        Y[i].copy_(torch.from_numpy((np.concatenate([un.real, un.imag]) * c_out).astype(np.float32)))
+    log(f"dataset: {S} solves, mean {np.mean(iters):.0f} iterations, {time.time() - t0:.1f} s; "
+        f"scales c_in {c_in:.4g} c_out {c_out:.4g}")
+    return X, Y, (c_in, c_out)
+
+
+def export_branch(net, scales):
+    """Branch layers (FP64 numpy) acting on [Re r, Im r]/||r|| and producing
+    coefficients of u/||r||: the input scale multiplies the first layer's weights,
+    the output scale divides the last layer."""
+    c_in, c_out = scales
+    layers = net.numpy_layers("branch")
+    W0, b0 = layers[0]
+    layers[0] = (W0 * c_in, b0)
+    Wl, bl = layers[-1]
+    layers[-1] = (Wl / c_out, bl / c_out)
+    return layers
 
 
 def train(net, X, Y, coords, fluid_idx, steps, batch=32, nodes=8192, lr=1e-4, seed=0, log=print,
@@ -233,3 +255,83 @@ def evaluate(net, X, Y, coords, rows):
         _ck(lib.nn_rel_l2(1, 2 * N, _p(pred), _p(Y[r:r + 1]), _p(d), _p(lo), s), "rel_l2")
         errs.append(math.sqrt(float(lo.cpu().numpy()[0])))
     return float(np.mean(errs))
+
+
+def train_workload(name, samples=1024, steps=10000, batch=32, nodes=16384, lr=1e-4, seed=0, solve_tol=1e-3,
+                   out=None, log=print):
+    """Train the DeepONet of a workload on its scatterer-free problem (same grid,
+    wavenumber and layer; mask = outer ring) and save the weights."""
+    import os
+    import scenes
+    from . import helm as hm
+    w = scenes.BENCH_WORKLOADS[name]
+    sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
+    mask = scenes.ring_mask(sc.dim, sc.n).reshape(-1).astype(np.uint8)
+    P = hm.Problem(sc.dim, sc.n, sc.k0, mask, layer_cells=sc.layer_cells, layer_strength=sc.layer_strength)
+    rng = np.random.default_rng(seed + 1000)
+    t0 = time.time()
+    fs = scenes.grf_samples(rng, sc.dim, sc.n, samples)
+    fs[:, mask == 1] = 0
+    log(f"GRF samples: {samples} in {time.time() - t0:.1f} s")
+    X, Y, scales = make_dataset(P, fs, hm.opts("bicgstab", "rbgs", 3, correction="none", tol=solve_tol, maxit=20000),
+                                log=log)
+    N = sc.N
+    trunk_widths = [sc.dim] + [W.shape[0] for W, _ in sc.trunk]
+    net = DeepONet.init([2 * N, 256, 256, 2 * sc.p], trunk_widths, seed=seed)
+    coords = scenes.node_coords(sc.dim, sc.n)
+    fluid = np.flatnonzero(mask == 0)
+    n_train = int(samples * 0.9)
+    t0 = time.time()
+    hist = train(net, X[:n_train], Y[:n_train], coords, fluid, steps, batch=batch, nodes=min(nodes, fluid.size),
+                 lr=lr, seed=seed, log=log, log_every=max(1, steps // 20))
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    held = evaluate(net, X, Y, coords, range(n_train, samples))
+    seen = evaluate(net, X, Y, coords, range(0, min(32, n_train)))
+    log(f"training {steps} steps in {t_train:.1f} s; relative L2: held-out {held:.3f}, training {seen:.3f}")
+    info = {"samples": samples, "steps": steps, "batch": batch, "nodes": nodes, "lr": lr, "train_s": t_train,
+            "held_out_rel_l2": held, "train_rel_l2": seen, "loss_history": hist, "scales": scales,
+            "solve_tol": solve_tol}
+    if out:
+        os.makedirs(os.path.dirname(out) or ".", exist_ok=True)
+        tr = net.numpy_layers("trunk")
+        np.savez(out + "_trunk.npz", **{f"W{i}": W for i, (W, _) in enumerate(tr)},
+                 **{f"b{i}": b for i, (_, b) in enumerate(tr)}, info=json_dump(info))
+    return net, info
+
+
+def json_dump(d):
+    import json
+    return np.array(json.dumps(d))
+
+
+def load_trunk(path):
+    """[(W, b)] FP64 trunk layers from a file written by train_workload."""
+    z = np.load(path)
+    layers = []
+    i = 0
+    while f"W{i}" in z:
+        layers.append((z[f"W{i}"].astype(np.float64), z[f"b{i}"].astype(np.float64)))
+        i += 1
+    return layers
+
+
+if __name__ == "__main__":
+    import argparse
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="cube3d-64")
+    ap.add_argument("--samples", type=int, default=1024)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--nodes", type=int, default=16384)
+    ap.add_argument("--lr", type=float, default=1e-4)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--full", default=None, help="also save the full network and Adam state (.npz)")
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    net, info = train_workload(a.workload, a.samples, a.steps, a.batch, a.nodes, a.lr, out=a.out)
+    if a.full:
+        net.save(a.full)

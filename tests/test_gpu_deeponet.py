@@ -108,8 +108,8 @@ def test_training_reduces_loss_on_scatterer_free_problem():
     rng = np.random.default_rng(0)
     fs = scenes.grf_samples(rng, 2, n, 48)
     fs[:, mask == 1] = 0
-    X, Y = train.make_dataset(P, fs, hm.opts("bicgstab", "rbgs", 2, correction="none", tol=1e-6, maxit=3000),
-                              log=lambda *a: None)
+    X, Y, scales = train.make_dataset(P, fs, hm.opts("bicgstab", "rbgs", 2, correction="none", tol=1e-6,
+                                                     maxit=3000), log=lambda *a: None)
     net = train.DeepONet.init([2 * n * n, 64, 32], [2, 32, 32, 16], seed=1)
     coords = scenes.node_coords(2, n)
     fluid = np.flatnonzero(mask == 0)
