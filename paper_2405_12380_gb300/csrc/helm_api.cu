@@ -170,15 +170,23 @@ double ev_sum(helm_handle* h, int ph) {
 // z += Q A_c^-1 Q^T (v - A zres)   (zres may be null: plain restriction of v)
 helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, double2* z, int conj) {
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
-    const int nblk = restrict_blocks(h->N);
+    const int nblk = project_blocks(h->N);
+    const double2* r = v;
+    if (zres) {
+        // r = v - A zres (FP64 stencil), then the projection streams Q once
+        TRY(ensure_tmp(h, 14));
+        launch_apply<double>(h->op64, zres, v, h->tmp[13], nullptr, conj, true, h->stream);
+        h->launches += 1;
+        r = h->tmp[13];
+    }
     ev_mark(h, 0, 0);
-    launch_restrict(h->op64, h->Q, h->k, v, zres, conj, h->coarse_partials, nblk, h->stream);
+    launch_project_df(h->Q, h->k, r, h->N, h->coarse_partials, nblk, h->stream);
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
     ev_mark(h, 1, 0);
-    launch_prolong(h->Q, h->k, h->ybuf, z, h->N, h->stream);
+    launch_prolong_df(h->Q, h->k, h->ybuf, z, h->N, h->stream);
     ev_mark(h, 1, 1);
-    h->launches += 3;
+    h->launches += 4;
     CKL();
     return HELM_OK;
 }
@@ -571,6 +579,7 @@ void fill_tables(helm_handle* h) {
     o.dre = h->k0 * h->k0 - 2.0 * h->dim / (h->h * h->h);
     f.dre = (float)o.dre;
     o.mask = f.mask = h->mask;
+    o.lidx = f.lidx = h->lidx;
     for (int m = 0; m <= kMaxLayerCells; ++m) {
         double eta = (h->L > 0 && m <= h->L) ? (double)m / (double)h->L : 0.0;
         double im = h->k0 * h->k0 * ((h->strength * eta) * eta);
@@ -670,7 +679,9 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
             return bail(HELM_OUT_OF_MEMORY);
         if (cudaMemcpy(h->k2, k2, sizeof(double2) * N, cudaMemcpyDefault) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     }
+    if (dalloc(h, &h->lidx, (size_t)N) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
     fill_tables(h);
+    launch_layer_index(h->op64, h->lidx, nullptr);
     if (k2) {
         launch_invd_field(h->op64, h->invd, nullptr);
         launch_cvt_f64_to_f32(h->k2, h->k2f, N, nullptr);
@@ -690,7 +701,7 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
 
 helm_status helm_destroy(helm_handle* h) {
     if (!h) return HELM_BAD_ARG;
-    dfree(h->mask); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
+    dfree(h->mask); dfree(h->lidx); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
     dfree(h->red); dfree(h->sc); dfree(h->dflag);
     if (h->hpin) cudaFreeHost(h->hpin);
     for (auto p : h->tmp) cudaFree(p);
@@ -920,8 +931,10 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         STEPC(cudaMalloc(&h->Qbf, (size_t)N * k * 2));
         launch_rm_to_cm_bf16(T, ldq, k, h->Qbf, N, s);
     }
-    STEP(dalloc(h, &h->Q, (size_t)N * k));           // column-major Q for the per-iteration kernels
-    launch_rm_to_cm(T, ldq, k, h->Q, N, s);
+    // column-major FP32-pair Q for the per-iteration kernels; T becomes hi + lo so that
+    // A_c is built from exactly the basis the kernels apply
+    STEP(dalloc(h, &h->Q, (size_t)N * k));
+    launch_split_basis(T, ldq, k, h->Q, N, s);
     // A_c = Q^T (A Q)
     st = build_coarse(h, T, ldq, k);
     if (st != HELM_OK) {
@@ -929,7 +942,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         dfree(h->Q); dfree(h->Ainv);
         return st;
     }
-    STEP(dalloc(h, &h->coarse_partials, (size_t)restrict_blocks(N) * k));
+    STEP(dalloc(h, &h->coarse_partials, (size_t)std::max(restrict_blocks(N), project_blocks(N)) * k));
     if (h->precision == HELM_MIXED) {
         dfree(h->partials32); dfree(h->y32);
         STEP(dalloc(h, &h->partials32, (size_t)restrict_blocks(N) * k));
@@ -981,7 +994,7 @@ helm_status don_get_q(const helm_handle* hc, double* q_out) {
     helm_handle* h = const_cast<helm_handle*>(hc);
     if (!h || !q_out) return fail(h, HELM_BAD_ARG, "null argument");
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
-    launch_cm_to_rm(h->Q, h->k, q_out, h->N, h->stream);
+    launch_cm_pair_to_rm(h->Q, h->k, q_out, h->N, h->stream);
     CKL();
     return HELM_OK;
 }
@@ -1106,7 +1119,7 @@ helm_status helm_set_k2(helm_handle* h, const double* k2) {
         // rebuild A_c for the new operator from a node-major copy of the (possibly rounded) basis
         double* Qrm = nullptr;
         TRY(dalloc(h, &Qrm, (size_t)N * h->k));
-        launch_cm_to_rm(h->Q, h->k, Qrm, N, h->stream);
+        launch_cm_pair_to_rm(h->Q, h->k, Qrm, N, h->stream);
         helm_status st = build_coarse(h, Qrm, h->k, h->k);
         cudaStreamSynchronize(h->stream);
         dfree(Qrm);

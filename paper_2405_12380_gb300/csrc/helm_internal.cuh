@@ -3,8 +3,8 @@
 // Data layout in HBM
 //   vectors       N complex, interleaved (double2 / float2), flat index i + n(j + n k)
 //   mask          N uint8 (1 = Dirichlet: outer ring + scatterer)
-//   Q             k x N doubles, column-major: basis vector j is Q[j*N .. j*N+N)
-//                 (node-major copies exist only during setup)
+//   Q             k x N pairs (hi, lo) of FP32 (= the FP64 basis to ~2^-48), column-major:
+//                 basis vector j is Q[j*N .. j*N+N) (node-major copies exist only during setup)
 //   A_c^-1        k x k complex128, row-major
 //   Krylov basis  V: (m+1) x N complex128, Z: m x N complex128, one vector after another
 #pragma once
@@ -64,6 +64,7 @@ struct Op {
     R hinv2;                 // h^-2
     R dre;                   // k0^2 - 2 d h^-2 (real part of the diagonal, layer form)
     const uint8_t* mask;
+    const uint8_t* lidx;     // per-node layer index m (flat-index kernels; avoids index division)
     const C* k2;             // stored k^2 field or nullptr
     const C* invd;           // per-node 1/diag for the stored field, or nullptr
     R im[kMaxLayerCells + 1];        // Im k^2 by layer index
@@ -93,6 +94,7 @@ void launch_layer_k2(const Op<double>& op, double k0, double strength, const dou
                      double2* k2, cudaStream_t s);
 void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s);
 void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s);
+void launch_layer_index(const Op<double>& op, uint8_t* lidx, cudaStream_t s);
 
 // blas.cu
 // partial reductions over a fixed grid of kRedBlocks blocks
@@ -144,12 +146,16 @@ void launch_apply_columns(const Op<double>& op, const double* Q, int ldq, int k,
                           cudaStream_t s);
 void launch_gauss_jordan(const double* C, int ldc, int k, double2* Ainv, double2* work, int* flag,
                          cudaStream_t s);
-void launch_restrict(const Op<double>& op, const double* Q, int k, const double2* v, const double2* z, int conj,
-                     double2* partials, int nblk, cudaStream_t s);
 void launch_coarse_apply(const double2* partials, int nblk, int k, const double2* Ainv, int conj, double2* y,
                          double2* cbuf, cudaStream_t s);
-void launch_prolong(const double* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s);
 void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s);
+// FP64 projection on FP32 pipes: Q as (hi, lo) FP32 pairs, column-major k x N
+int project_blocks(long long N);
+void launch_project_df(const float2* Q, int k, const double2* r, long long N, double2* partials, int nblk,
+                       cudaStream_t s);
+void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s);
+void launch_split_basis(double* A, int ld, int k, float2* B, long long N, cudaStream_t s);
+void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, cudaStream_t s);
 void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s);
 // nonlinear DeepONet correction: raw trunk matrix in FP32 (p x N), branch in FP32
 void launch_rm_to_cm_f32(const double* A, int ld, int p, float* B, long long N, cudaStream_t s);
@@ -188,6 +194,7 @@ struct helm_handle {
     helm::Op<double> op64{};
     helm::Op<float> op32{};
     uint8_t* mask = nullptr;
+    uint8_t* lidx = nullptr;
     double2* k2 = nullptr;
     double2* invd = nullptr;
     float2* k2f = nullptr;
@@ -203,7 +210,7 @@ struct helm_handle {
     // trunk basis
     int p = 0, k = 0, ldq = 0;
     std::vector<int> kept;
-    double* Q = nullptr;
+    float2* Q = nullptr;            // FP32 pairs, k x N
     double2* Ainv = nullptr;
     double2* coarse_partials = nullptr;
     void* Qbf = nullptr;            // BF16 basis (MIXED handles), column-major k x N

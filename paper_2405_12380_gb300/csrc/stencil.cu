@@ -82,118 +82,138 @@ __device__ __forceinline__ void block_reduce_store(double v, double* out) {
     }
 }
 
-// y = A x, or y = f - A x (resid); optional per-block ||y||^2 partials.
+// y = A x, or y = f - A x (resid), at one node; returns |y_l|^2
+template <typename R, bool RESID>
+__device__ __forceinline__ double apply_point(const Op<R>& op, const typename CT<R>::T* __restrict__ x,
+                                              const typename CT<R>::T* __restrict__ f, typename CT<R>::T* __restrict__ y,
+                                              int conj, int i, int j, int k) {
+    using C = typename CT<R>::T;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const C xc = x[l];
+    C out;
+    if (op.mask[l]) {
+        out = xc;
+    } else {
+        const C s = nbr_sum(op, x, l);
+        const C d = diag_of(op, l, node_layer(op, i, j, k), conj);
+        out.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
+        out.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
+    }
+    if (RESID) out = csub(f[l], out);
+    y[l] = out;
+    return (double)out.x * out.x + (double)out.y * out.y;
+}
+
+// y = A x, or y = f - A x (resid); two z-planes per thread; optional per-block ||y||^2 partials.
 template <typename R, bool RESID, bool NORM>
 __global__ void __launch_bounds__(BX * BY) k_apply(Op<R> op, const typename CT<R>::T* __restrict__ x,
                                                    const typename CT<R>::T* __restrict__ f,
                                                    typename CT<R>::T* __restrict__ y, double* partials,
                                                    int conj) {
-    using C = typename CT<R>::T;
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k0 = op.dim == 3 ? 2 * blockIdx.z : 0;
     double acc = 0.0;
     if (i < op.n && j < op.n) {
-        const long long l = i + (long long)op.n * (j + (long long)op.n * k);
-        C xc = x[l];
-        C out;
-        if (op.mask[l]) {
-            out = xc;
-        } else {
-            C s = nbr_sum(op, x, l);
-            C d = diag_of(op, l, node_layer(op, i, j, k), conj);
-            out.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
-            out.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
-        }
-        if (RESID) out = csub(f[l], out);
-        y[l] = out;
-        if (NORM) acc = (double)out.x * out.x + (double)out.y * out.y;
+        acc = apply_point<R, RESID>(op, x, f, y, conj, i, j, k0);
+        if (op.dim == 3 && k0 + 1 < op.n) acc += apply_point<R, RESID>(op, x, f, y, conj, i, j, k0 + 1);
     }
     if (NORM) {
         block_reduce_store<R>(acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
     }
 }
 
-// one damped-Jacobi sweep: xout = xin + omega D^-1 (f - A xin)
+// one damped-Jacobi sweep: xout = xin + omega D^-1 (f - A xin), evaluated on a
+// fluid node as (1 - omega) x + omega D^-1 (f - h^-2 sum of fluid neighbours)
+// (the diagonal term cancels: fewer FP64 operations, same value up to rounding)
 template <typename R, bool XZERO>
-__global__ void __launch_bounds__(BX * BY) k_jacobi(Op<R> op, R omega, const typename CT<R>::T* __restrict__ f,
-                                                    const typename CT<R>::T* __restrict__ xin,
-                                                    typename CT<R>::T* __restrict__ xout, int conj) {
+__device__ __forceinline__ void jacobi_point(const Op<R>& op, R omega, const typename CT<R>::T* __restrict__ f,
+                                             const typename CT<R>::T* __restrict__ xin,
+                                             typename CT<R>::T* __restrict__ xout, int conj, int i, int j, int k) {
     using C = typename CT<R>::T;
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= op.n || j >= op.n) return;
     const long long l = i + (long long)op.n * (j + (long long)op.n * k);
-    C fl = f[l];
+    const C fl = f[l];
     C out;
     if (op.mask[l]) {
         if (XZERO) {
             out = cscale(omega, fl);
         } else {
-            C xc = xin[l];
+            const C xc = xin[l];
             out = cadd(xc, cscale(omega, csub(fl, xc)));
         }
     } else {
         const int m = node_layer(op, i, j, k);
-        C r;
-        C xc;
-        if (XZERO) {
-            xc.x = 0; xc.y = 0;
-            r = fl;
-        } else {
-            xc = xin[l];
-            C s = nbr_sum(op, xin, l);
-            C d = diag_of(op, l, m, conj);
-            C ax;
-            ax.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
-            ax.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
-            r = csub(fl, ax);
-        }
         C id = invd_of(op, l, m, conj);
-        out = cadd(xc, cscale(omega, cmul(id, r)));
+        if (XZERO) {
+            out = cscale(omega, cmul(id, fl));
+        } else {
+            const C xc = xin[l];
+            const C s = nbr_sum(op, xin, l);
+            C g;
+            g.x = fl.x - op.hinv2 * s.x;
+            g.y = fl.y - op.hinv2 * s.y;
+            const C t = cmul(id, g);
+            const R w1 = (R)1 - omega;
+            out.x = w1 * xc.x + omega * t.x;
+            out.y = w1 * xc.y + omega * t.y;
+        }
     }
     xout[l] = out;
 }
 
-// red-black Gauss-Seidel half-sweep on colour c, in place
+// Two z-planes per thread (independent points: more FP64 work in flight per warp).
+template <typename R, bool XZERO>
+__global__ void __launch_bounds__(BX * BY) k_jacobi(Op<R> op, R omega, const typename CT<R>::T* __restrict__ f,
+                                                    const typename CT<R>::T* __restrict__ xin,
+                                                    typename CT<R>::T* __restrict__ xout, int conj) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k0 = op.dim == 3 ? 2 * blockIdx.z : 0;
+    if (i >= op.n || j >= op.n) return;
+    jacobi_point<R, XZERO>(op, omega, f, xin, xout, conj, i, j, k0);
+    if (op.dim == 3 && k0 + 1 < op.n) jacobi_point<R, XZERO>(op, omega, f, xin, xout, conj, i, j, k0 + 1);
+}
+
+// red-black Gauss-Seidel update of one node of the swept colour, in place:
+// x_l = D_l^-1 (f_l - h^-2 sum of fluid neighbours) on fluid nodes (the Gauss-Seidel
+// value x + D^-1 (f - A x) with the diagonal term cancelled), f_l on masked nodes
+template <typename R, bool XZERO>
+__device__ __forceinline__ void rbgs_point(const Op<R>& op, const typename CT<R>::T* __restrict__ f,
+                                           typename CT<R>::T* x, int conj, int i, int j, int k) {
+    using C = typename CT<R>::T;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const C fl = f[l];
+    C out;
+    if (op.mask[l]) {
+        out = fl;
+    } else {
+        const int m = node_layer(op, i, j, k);
+        const C id = invd_of(op, l, m, conj);
+        if (XZERO) {
+            out = cmul(id, fl);
+        } else {
+            const C s = nbr_sum(op, x, l);
+            C g;
+            g.x = fl.x - op.hinv2 * s.x;
+            g.y = fl.y - op.hinv2 * s.y;
+            out = cmul(id, g);
+        }
+    }
+    x[l] = out;
+}
+
 template <typename R, bool XZERO>
 __global__ void __launch_bounds__(BX * BY) k_rbgs(Op<R> op, int colour, const typename CT<R>::T* __restrict__ f,
                                                   typename CT<R>::T* x, int conj) {
-    using C = typename CT<R>::T;
     const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + colour) & 1);
-    if (i >= op.n || j >= op.n) return;
-    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
-    C fl = f[l];
-    C out;
-    if (op.mask[l]) {
-        if (XZERO) {
-            out = fl;
-        } else {
-            C xc = x[l];
-            out = cadd(xc, csub(fl, xc));
-        }
-    } else {
-        const int m = node_layer(op, i, j, k);
-        C xc;
-        C r;
-        if (XZERO) {
-            xc.x = 0; xc.y = 0;
-            r = fl;
-        } else {
-            xc = x[l];
-            C s = nbr_sum(op, x, l);
-            C d = diag_of(op, l, m, conj);
-            C ax;
-            ax.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
-            ax.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
-            r = csub(fl, ax);
-        }
-        out = cadd(xc, cmul(invd_of(op, l, m, conj), r));
+    const int k0 = op.dim == 3 ? 2 * blockIdx.z : 0;
+    if (j >= op.n) return;
+    const int i0 = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k0 + colour) & 1);
+    if (i0 < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i0, j, k0);
+    if (op.dim == 3 && k0 + 1 < op.n) {
+        const int i1 = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k0 + 1 + colour) & 1);
+        if (i1 < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i1, j, k0 + 1);
     }
-    x[l] = out;
 }
 
 __global__ void k_rhs(Op<double> op, const double2* __restrict__ src, const double2* __restrict__ g,
@@ -245,6 +265,15 @@ __global__ void k_invd_field(Op<double> op, double2* __restrict__ invd) {
     invd[l] = op.mask[l] ? make_double2(1.0, 0.0) : cdiv(make_double2(1.0, 0.0), d);
 }
 
+__global__ void k_layer_index(Op<double> op, uint8_t* __restrict__ lidx) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    lidx[l] = (uint8_t)node_layer(op, i, j, k);
+}
+
 __global__ void k_check_ring(Op<double> op, int* bad) {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
@@ -256,22 +285,22 @@ __global__ void k_check_ring(Op<double> op, int* bad) {
     if (ring && !op.mask[l]) atomicOr(bad, 1);
 }
 
-dim3 grid_for(int dim, int n, int xdiv = 1) {
+dim3 grid_for(int dim, int n, int xdiv = 1, int zdiv = 1) {
     int nx = (n + xdiv - 1) / xdiv;
-    return dim3((nx + BX - 1) / BX, (n + BY - 1) / BY, dim == 3 ? n : 1);
+    return dim3((nx + BX - 1) / BX, (n + BY - 1) / BY, dim == 3 ? (n + zdiv - 1) / zdiv : 1);
 }
 
 }  // namespace
 
 int apply_grid_blocks(int dim, int n) {
-    dim3 g = grid_for(dim, n);
+    dim3 g = grid_for(dim, n, 1, 2);
     return g.x * g.y * g.z;
 }
 
 template <typename R>
 void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f,
                   typename CT<R>::T* y, double* partials, int conj, bool resid, cudaStream_t s) {
-    dim3 g = grid_for(op.dim, op.n), b(BX, BY);
+    dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
     if (resid) {
         if (partials) k_apply<R, true, true><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
         else k_apply<R, true, false><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
@@ -284,7 +313,7 @@ void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT
 template <typename R>
 void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f, const typename CT<R>::T* xin,
                    typename CT<R>::T* xout, int conj, bool xzero, cudaStream_t s) {
-    dim3 g = grid_for(op.dim, op.n), b(BX, BY);
+    dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
     if (xzero) k_jacobi<R, true><<<g, b, 0, s>>>(op, (R)omega, f, xin, xout, conj);
     else k_jacobi<R, false><<<g, b, 0, s>>>(op, (R)omega, f, xin, xout, conj);
 }
@@ -292,7 +321,7 @@ void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f, co
 template <typename R>
 void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x, int conj,
                       bool xzero, cudaStream_t s) {
-    dim3 g = grid_for(op.dim, op.n, 2), b(BX, BY);
+    dim3 g = grid_for(op.dim, op.n, 2, 2), b(BX, BY);
     if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj);
     else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj);
 }
@@ -320,6 +349,10 @@ void launch_layer_k2(const Op<double>& op, double k0, double strength, const dou
 
 void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s) {
     k_invd_field<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, invd);
+}
+
+void launch_layer_index(const Op<double>& op, uint8_t* lidx, cudaStream_t s) {
+    k_layer_index<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, lidx);
 }
 
 void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s) {

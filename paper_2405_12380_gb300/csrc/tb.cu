@@ -7,11 +7,13 @@
 //   Q1 = T_S R^-1, then CholQR2 pass        k_tri_inverse, k_gather_upper
 //   W = A Q (real columns -> complex)       k_apply_columns
 //   A_c = Q^T W, A_c^-1 by Gauss-Jordan     k_gram, k_gauss_jordan (one CTA, partial pivoting)
-// Per application (z += Q A_c^-1 Q^T (v - A z)), Q column-major (k x N):
-//   k_restrict   residual on the fly into a shared tile; warps own columns and
-//                keep their sums in registers across tiles (one reduction per block)
-//   k_coarse     fixed-order sum of block partials, y = A_c^-1 c
-//   k_prolong    z_l += sum_j Q_j[l] y_j, one thread per node, y in shared memory
+// Per application (z += Q A_c^-1 Q^T (v - A z)), Q column-major (k x N) as FP32 pairs:
+//   k_apply        r = v - A z (FP64 stencil, stencil.cu) when the sweeps left a z
+//   k_project_df   r tile split once into FP32 pairs in shared memory; warps own
+//                  columns and keep FP32-pair sums in registers across tiles (one
+//                  FP32-pair warp reduction per block)
+//   k_coarse_*     fixed-order sum of block partials, y = A_c^-1 c (FP64, one block per row)
+//   k_prolong_df   z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 #include <cuda_bf16.h>
 
 #include "helm_internal.cuh"
@@ -266,7 +268,6 @@ __global__ void __launch_bounds__(256) k_apply_columns(Op<double> op, const doub
         const int c = (int)(e % k);
         double re = 0, im = 0;
         if (!op.mask[l]) {
-            const int i = (int)(l % op.n), j = (int)((l / op.n) % op.n), kk = (int)(l / sz);
             double s = 0;
             if (!op.mask[l - 1]) s += Q[(l - 1) * ldq + c];
             if (!op.mask[l + 1]) s += Q[(l + 1) * ldq + c];
@@ -282,10 +283,8 @@ __global__ void __launch_bounds__(256) k_apply_columns(Op<double> op, const doub
                 dre = kk2.x - 2.0 * op.dim * op.hinv2;
                 dim_ = kk2.y;
             } else {
-                int m = max(layer_index(i, op.n, op.L), layer_index(j, op.n, op.L));
-                if (op.dim == 3) m = max(m, layer_index(kk, op.n, op.L));
                 dre = op.dre;
-                dim_ = op.im[m];
+                dim_ = op.im[op.lidx[l]];
             }
             const double qv = Q[l * ldq + c];
             re = op.hinv2 * s + dre * qv;
@@ -374,137 +373,224 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(const double* __restrict_
 constexpr int RS_T = 256;        // threads per restriction block
 constexpr int RS_TILE = 256;     // rows per tile (one residual per thread)
 
-// partials[b][j] = sum over the rows of block b of Q_j[l] r_l, r = v - A z (z may be null).
-// Each warp owns columns warp, warp + 8, ...; each lane keeps their accumulators over
-// all tiles of the block and reduces once at the end.
+// ---------------------------------------------- FP32-pair (df64) projection
+// GB300 issues FP32 FMAs 64x faster than FP64 ones, so the FP64 restriction and
+// prolongation keep Q as pairs (hi, lo) of FP32 numbers with Q = hi + lo to ~2^-48
+// and run the products and sums in FP32-pair arithmetic: a product is formed
+// exactly as p + e (e from an FMA), the cross terms hi*lo are added to e, and the
+// running sum is kept as an unevaluated pair with an exact two-sum.  Only the
+// operand r (or y) is split once per node (or once per block), and the result is
+// converted back to FP64 once per sum.
+
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+}
+
+// (sh, sl) += (ah + al) * (bh + bl), dropping al*bl (~2^-48 relative)
+__device__ __forceinline__ void pair_fma(float& sh, float& sl, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = sh + p;
+    const float bb = s - sh;
+    const float err = (sh - (s - bb)) + (p - bb);
+    sh = s;
+    sl += err + e;
+}
+
+// (sh, sl) summed over the warp in FP32-pair arithmetic (exact two-sums); the
+// result is valid in every lane
+__device__ __forceinline__ void pair_warp_sum(float& sh, float& sl) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+        const float s = sh + oh;
+        const float bb = s - sh;
+        const float err = (sh - (s - bb)) + (oh - bb);
+        sh = s;
+        sl = sl + ol + err;
+    }
+}
+
+constexpr int PJ_T = 512;        // threads per projection block (16 warps)
+constexpr int PJ_TILE = 512;     // rows per tile (one per thread)
+
+// partials[b][j] = sum over the rows of block b of Q_j[l] r_l (r given, FP64)
 template <int KPW>
-__global__ void __launch_bounds__(RS_T) k_restrict(Op<double> op, const double* __restrict__ Q, int k,
-                                                   const double2* __restrict__ v, const double2* __restrict__ z,
-                                                   int conj, double2* __restrict__ partials, long long rows_per_block) {
-    __shared__ double2 rs[RS_TILE];
+__global__ void __launch_bounds__(PJ_T) k_project_df(const float2* __restrict__ Q, int k, const double2* __restrict__ r,
+                                                     long long N, double2* __restrict__ partials, long long rows_per_block) {
+    __shared__ float4 rs[PJ_TILE];       // (re hi, re lo, im hi, im lo)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = RS_T / 32;
+    constexpr int NW = PJ_T / 32;
+    constexpr int RPL = PJ_TILE / 32;
     const long long r0 = (long long)blockIdx.x * rows_per_block;
-    const long long r1 = min(op.N, r0 + rows_per_block);
-    const long long N = op.N;
-    double2 acc[KPW];
+    const long long r1 = min(N, r0 + rows_per_block);
+    float acc[KPW][4];
 #pragma unroll
-    for (int c = 0; c < KPW; ++c) acc[c] = make_double2(0, 0);
-    const long long sy = op.n, sz = (long long)op.n * op.n;
-    for (long long t0 = r0; t0 < r1; t0 += RS_TILE) {
+    for (int c = 0; c < KPW; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
+    for (long long t0 = r0; t0 < r1; t0 += PJ_TILE) {
         const long long l = t0 + threadIdx.x;
-        double2 r = make_double2(0, 0);
-        if (l < r1 && !op.mask[l]) {
-            r = v[l];
-            if (z) {
-                const int i = (int)(l % op.n), j = (int)((l / op.n) % op.n), kk = (int)(l / sz);
-                double2 s = make_double2(0, 0);
-                const uint8_t* mk = op.mask;
-                if (!mk[l - 1]) s = cadd(s, z[l - 1]);
-                if (!mk[l + 1]) s = cadd(s, z[l + 1]);
-                if (!mk[l - sy]) s = cadd(s, z[l - sy]);
-                if (!mk[l + sy]) s = cadd(s, z[l + sy]);
-                if (op.dim == 3) {
-                    if (!mk[l - sz]) s = cadd(s, z[l - sz]);
-                    if (!mk[l + sz]) s = cadd(s, z[l + sz]);
-                }
-                double2 d;
-                if (op.k2) {
-                    d = op.k2[l];
-                    d.x -= 2.0 * op.dim * op.hinv2;
-                } else {
-                    int m = max(layer_index(i, op.n, op.L), layer_index(j, op.n, op.L));
-                    if (op.dim == 3) m = max(m, layer_index(kk, op.n, op.L));
-                    d = make_double2(op.dre, op.im[m]);
-                }
-                if (conj) d.y = -d.y;
-                const double2 zc = z[l];
-                r.x -= op.hinv2 * s.x + (d.x * zc.x - d.y * zc.y);
-                r.y -= op.hinv2 * s.y + (d.x * zc.y + d.y * zc.x);
-            }
-        }
+        const double2 rv = l < r1 ? r[l] : make_double2(0, 0);
+        float4 rp;
+        split_f64(rv.x, rp.x, rp.y);
+        split_f64(rv.y, rp.z, rp.w);
         __syncthreads();
-        rs[threadIdx.x] = r;
+        rs[threadIdx.x] = rp;
         __syncthreads();
-        const int rows = (int)min((long long)RS_TILE, r1 - t0);
+        const int rows = (int)min((long long)PJ_TILE, r1 - t0);
 #pragma unroll
         for (int c = 0; c < KPW; ++c) {
             const int j = warp + NW * c;
             if (j < k) {
-                const double* Qj = Q + (long long)j * N + t0;
-                double ax = acc[c].x, ay = acc[c].y;
-                for (int q = lane; q < rows; q += 32) {
-                    const double qv = Qj[q];
-                    const double2 rr = rs[q];
-                    ax = fma(qv, rr.x, ax);
-                    ay = fma(qv, rr.y, ay);
+                const float2* Qj = Q + (long long)j * N + t0;
+                float a0 = acc[c][0], a1 = acc[c][1], a2 = acc[c][2], a3 = acc[c][3];
+                // all loads of the column issued before use (rows past the end of the
+                // block read nothing and meet r = 0 in shared memory)
+                float2 qv[RPL];
+#pragma unroll
+                for (int u = 0; u < RPL; ++u)
+                    qv[u] = (lane + 32 * u < rows) ? __ldg(Qj + lane + 32 * u) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < RPL; ++u) {
+                    const float4 rr = rs[lane + 32 * u];
+                    pair_fma(a0, a1, qv[u].x, qv[u].y, rr.x, rr.y);
+                    pair_fma(a2, a3, qv[u].x, qv[u].y, rr.z, rr.w);
                 }
-                acc[c].x = ax;
-                acc[c].y = ay;
+                acc[c][0] = a0; acc[c][1] = a1; acc[c][2] = a2; acc[c][3] = a3;
             }
         }
     }
 #pragma unroll
     for (int c = 0; c < KPW; ++c) {
         const int j = warp + NW * c;
-        const double sx = warp_sum(acc[c].x), sy2 = warp_sum(acc[c].y);
-        if (lane == 0 && j < k) partials[(long long)blockIdx.x * k + j] = make_double2(sx, sy2);
+        pair_warp_sum(acc[c][0], acc[c][1]);
+        pair_warp_sum(acc[c][2], acc[c][3]);
+        if (lane == 0 && j < k)
+            partials[(long long)blockIdx.x * k + j] =
+                make_double2((double)acc[c][0] + (double)acc[c][1], (double)acc[c][2] + (double)acc[c][3]);
     }
 }
 
-// y = A_c^-1 c (conj: conj(A_c^-1)), c = fixed-order sum of the block partials
-__global__ void __launch_bounds__(1024) k_coarse(const double2* __restrict__ partials, int nblk, int k,
-                                                 const double2* __restrict__ Ainv, int conj, double2* __restrict__ y,
-                                                 double2* __restrict__ cbuf) {
-    __shared__ double2 c[kMaxP];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < k; j += nw) {
-        double sx = 0, sy = 0;
-        for (int b = lane; b < nblk; b += 32) {
-            double2 q = partials[(long long)b * k + j];
-            sx += q.x;
-            sy += q.y;
-        }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) {
-            c[j] = make_double2(sx, sy);
-            if (cbuf) cbuf[j] = c[j];
-        }
+// c_j = fixed-order sum of the block partials, one block per column
+__global__ void __launch_bounds__(64) k_coarse_reduce(const double2* __restrict__ partials, int nblk, int k,
+                                                      double2* __restrict__ c) {
+    __shared__ double2 red[2];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double sx = 0, sy = 0;
+    for (int b = threadIdx.x; b < nblk; b += 64) {
+        const double2 q = partials[(long long)b * k + j];
+        sx += q.x;
+        sy += q.y;
     }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) red[w] = make_double2(sx, sy);
     __syncthreads();
-    for (int i = warp; i < k; i += nw) {
-        double sx = 0, sy = 0;
-        for (int j = lane; j < k; j += 32) {
-            double2 a = Ainv[(long long)i * k + j];
-            if (conj) a.y = -a.y;
-            double2 cj = c[j];
-            sx += a.x * cj.x - a.y * cj.y;
-            sy += a.x * cj.y + a.y * cj.x;
-        }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) y[i] = make_double2(sx, sy);
-    }
+    if (threadIdx.x == 0) c[j] = make_double2(red[0].x + red[1].x, red[0].y + red[1].y);
 }
 
-// z_l += sum_j Q_j[l] y_j, one thread per row, y broadcast from shared memory
-__global__ void __launch_bounds__(256) k_prolong(const double* __restrict__ Q, int k, const double2* __restrict__ y,
-                                                 double2* __restrict__ z, long long N) {
-    __shared__ double2 ys[kMaxP];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+// y_i = sum_j A_c^-1[i][j] c_j (conj: conj(A_c^-1)), one block per row
+__global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ Ainv, int k, int conj,
+                                                    const double2* __restrict__ c, double2* __restrict__ y) {
+    __shared__ double2 red[2];
+    const int i = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double sx = 0, sy = 0;
+    for (int j = threadIdx.x; j < k; j += 64) {
+        double2 a = Ainv[(long long)i * k + j];
+        if (conj) a.y = -a.y;
+        const double2 cj = c[j];
+        sx += a.x * cj.x - a.y * cj.y;
+        sy += a.x * cj.y + a.y * cj.x;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) red[w] = make_double2(sx, sy);
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = make_double2(red[0].x + red[1].x, red[0].y + red[1].y);
+}
+
+// z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
+__global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q, int k, const double2* __restrict__ y,
+                                                    double2* __restrict__ z, long long N) {
+    __shared__ float4 ys[kMaxP];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        float4 t;
+        split_f64(y[j].x, t.x, t.y);
+        split_f64(y[j].y, t.z, t.w);
+        ys[j] = t;
+    }
     __syncthreads();
     for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
-        double sx = 0, sy = 0;
-        const double* q = Q + l;
-#pragma unroll 4
-        for (int j = 0; j < k; ++j) {
-            const double qv = q[(long long)j * N];
-            sx = fma(qv, ys[j].x, sx);
-            sy = fma(qv, ys[j].y, sy);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const float2* q = Q + l;
+        int j = 0;
+        for (; j + 8 <= k; j += 8) {
+            float2 qv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(j + u) * N);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 yy = ys[j + u];
+                pair_fma(a0, a1, qv[u].x, qv[u].y, yy.x, yy.y);
+                pair_fma(a2, a3, qv[u].x, qv[u].y, yy.z, yy.w);
+            }
+        }
+        for (; j < k; ++j) {
+            const float2 qv = q[(long long)j * N];
+            const float4 yy = ys[j];
+            pair_fma(a0, a1, qv.x, qv.y, yy.x, yy.y);
+            pair_fma(a2, a3, qv.x, qv.y, yy.z, yy.w);
         }
         double2 zz = z[l];
-        z[l] = make_double2(zz.x + sx, zz.y + sy);
+        z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
+    }
+}
+
+// FP64 row-major Q (N x ld) -> column-major pairs (k x N) of FP32 (hi, lo), and
+// the row-major FP64 values replaced by hi + lo (the basis the kernels use)
+__global__ void k_split_basis(double* __restrict__ A, int ld, int k, float2* __restrict__ B, long long N) {
+    __shared__ float2 tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < N && c < k) {
+            split_f64(A[l * ld + c], v.x, v.y);
+            A[l * ld + c] = (double)v.x + (double)v.y;
+        }
+        tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        if (c < k && l < N) B[(long long)c * N + l] = tile[threadIdx.x][r];
+    }
+}
+
+__global__ void k_cm_pair_to_rm(const float2* __restrict__ B, int k, double* __restrict__ A, long long N) {
+    __shared__ double tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        double v = 0.0;
+        if (c < k && l < N) {
+            const float2 q = B[(long long)c * N + l];
+            v = (double)q.x + (double)q.y;
+        }
+        tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        if (l < N && c < k) A[l * k + c] = tile[threadIdx.x][r];
     }
 }
 
@@ -661,7 +747,6 @@ __global__ void __launch_bounds__(RS_T) k_restrict32(Op<float> op, const __nv_bf
         if (l < r1 && !op.mask[l]) {
             r = v[l];
             if (z) {
-                const int i = (int)(l % op.n), j = (int)((l / op.n) % op.n), kk = (int)(l / sz);
                 float2 s = make_float2(0.f, 0.f);
                 const uint8_t* mk = op.mask;
                 if (!mk[l - 1]) s = cadd(s, z[l - 1]);
@@ -677,9 +762,7 @@ __global__ void __launch_bounds__(RS_T) k_restrict32(Op<float> op, const __nv_bf
                     d = op.k2[l];
                     d.x -= 2.0f * op.dim * op.hinv2;
                 } else {
-                    int m = max(layer_index(i, op.n, op.L), layer_index(j, op.n, op.L));
-                    if (op.dim == 3) m = max(m, layer_index(kk, op.n, op.L));
-                    d = make_float2(op.dre, op.im[m]);
+                    d = make_float2(op.dre, op.im[op.lidx[l]]);
                 }
                 if (conj) d.y = -d.y;
                 const float2 zc = z[l];
@@ -827,28 +910,45 @@ int restrict_blocks(long long N) {
     return (int)(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
 }
 
-void launch_restrict(const Op<double>& op, const double* Q, int k, const double2* v, const double2* z, int conj,
-                     double2* partials, int nblk, cudaStream_t s) {
-    long long rows = (op.N + nblk - 1) / nblk;
-    const int kpw = (k + 7) / 8;
-#define RS_CASE(K) k_restrict<K><<<nblk, RS_T, 0, s>>>(op, Q, k, v, z, conj, partials, rows)
-    if (kpw <= 1) RS_CASE(1);
-    else if (kpw <= 2) RS_CASE(2);
-    else if (kpw <= 4) RS_CASE(4);
-    else if (kpw <= 8) RS_CASE(8);
-    else if (kpw <= 16) RS_CASE(16);
-    else RS_CASE(32);
-#undef RS_CASE
-}
-
 void launch_coarse_apply(const double2* partials, int nblk, int k, const double2* Ainv, int conj, double2* y,
                          double2* cbuf, cudaStream_t s) {
-    k_coarse<<<1, 1024, 0, s>>>(partials, nblk, k, Ainv, conj, y, cbuf);
+    // two small launches spread over k SMs (FP64 is 2 FMA/clk per SM: one CTA would serialise)
+    k_coarse_reduce<<<k, 64, 0, s>>>(partials, nblk, k, cbuf);
+    k_coarse_gemv<<<k, 64, 0, s>>>(Ainv, k, conj, cbuf, y);
 }
 
-void launch_prolong(const double* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
+
+int project_blocks(long long N) {
+    long long b = (N + PJ_TILE - 1) / PJ_TILE;
+    return (int)(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
+}
+
+void launch_project_df(const float2* Q, int k, const double2* r, long long N, double2* partials, int nblk,
+                       cudaStream_t s) {
+    long long rows = (N + nblk - 1) / nblk;
+    const int kpw = (k + 15) / 16;
+#define PJ_CASE(K) k_project_df<K><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, partials, rows)
+    if (kpw <= 1) PJ_CASE(1);
+    else if (kpw <= 2) PJ_CASE(2);
+    else if (kpw <= 4) PJ_CASE(4);
+    else if (kpw <= 8) PJ_CASE(8);
+    else PJ_CASE(16);
+#undef PJ_CASE
+}
+
+void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
     long long b = (N + 255) / 256;
-    k_prolong<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, N);
+    k_prolong_df<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, N);
+}
+
+void launch_split_basis(double* A, int ld, int k, float2* B, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_split_basis<<<g, dim3(32, 8), 0, s>>>(A, ld, k, B, N);
+}
+
+void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_cm_pair_to_rm<<<g, dim3(32, 8), 0, s>>>(B, k, A, N);
 }
 
 void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s) {
