@@ -238,6 +238,26 @@ helm_status nn_rel_l2(int B, int P2, const float* pred, const float* target, flo
 helm_status nn_gather(int rows, int cols, const float* src, long long lds, const int* row_idx,
                       const int* col_idx, float* dst, void* stream);
 
+/* ---- batched solves (many independent problems, one launch per phase) ----
+ * The problems are existing HELM_MIXED handles with a loaded trunk basis; their
+ * vectors are packed one after another and every phase of FGMRES runs as one
+ * persistent launch over a queue of tiles (tile_rows consecutive nodes of one
+ * problem) for all problems at once, with per-problem reductions, Givens
+ * rotations, convergence and Krylov dimensions.  Preconditioner: complex64
+ * damped Jacobi (relax HELM_JACOBI, n_r sweeps, or none) + trunk-basis correction
+ * with each problem's BF16 basis; Arnoldi, Hessenberg, Givens and the true
+ * residual in FP64.  The handles must outlive the batch; it uses the stream of hs[0]. */
+typedef struct helm_batch helm_batch;
+helm_status helm_batch_create(int nprob, helm_handle** hs, helm_batch** out);
+helm_status helm_batch_destroy(helm_batch* b);
+/* Tile length (multiple of 32, 32..8192 nodes) and persistent grid size. */
+helm_status helm_batch_set_tile(helm_batch* b, int tile_rows, int grid);
+/* FGMRES(opts->restart) on every problem: f[i], x[i] [dev] complex128 of problem i
+ * (x: initial guess in, solution out); stats [host] nprob entries or NULL.
+ * Returns HELM_OK when every problem converged, else the last failing status. */
+helm_status helm_batch_solve(helm_batch* b, const helm_solve_opts* opts, const double* const* f,
+                             double* const* x, helm_stats* stats);
+
 /* Residual without allocation (no counterpart in the paper: an interface for
  * callers that cannot allocate device memory -- code running inside a memory
  * pool or arena it does not own, plugins whose host forbids cudaMalloc, code

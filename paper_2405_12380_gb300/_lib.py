@@ -78,6 +78,10 @@ SIGNATURES = {
     "nn_adam": (i32, [i64, vp, vp, vp, vp, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]),
     "nn_rel_l2": (i32, [i32, i32, vp, vp, vp, vp, vp]),
     "nn_gather": (i32, [i32, i32, vp, i64, vp, vp, vp, vp]),
+    "helm_batch_create": (i32, [i32, C.POINTER(H), C.POINTER(H)]),
+    "helm_batch_destroy": (i32, [H]),
+    "helm_batch_set_tile": (i32, [H, i32, i32]),
+    "helm_batch_solve": (i32, [H, C.POINTER(SolveOpts), C.POINTER(vp), C.POINTER(vp), C.POINTER(Stats)]),
 }
 
 _lib = None

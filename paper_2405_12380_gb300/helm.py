@@ -237,3 +237,94 @@ class Problem:
         if rc in (L.HELM_BAD_ARG, L.HELM_CUDA_ERROR, L.HELM_NOT_READY, L.HELM_OUT_OF_MEMORY):
             self._check(rc, "solve_host")
         return st.as_dict()
+
+
+class Batch:
+    """Many independent problems (HELM_MIXED Problems with a loaded trunk basis)
+    solved together by batched FGMRES: one launch per phase over all problems."""
+
+    def __init__(self, problems):
+        self.lib = L.lib()
+        self.problems = list(problems)
+        hs = (C.c_void_p * len(self.problems))(*[P.h for P in self.problems])
+        b = C.c_void_p()
+        st = self.lib.helm_batch_create(len(self.problems), hs, C.byref(b))
+        if st != 0:
+            raise HelmError(st, "helm_batch_create")
+        self.b = b
+        self.tile = (1024, 4 * 152)
+
+    def set_tile(self, tile_rows, grid=4 * 152):
+        st = self.lib.helm_batch_set_tile(self.b, int(tile_rows), int(grid))
+        if st != 0:
+            raise HelmError(st, "helm_batch_set_tile")
+        self.tile = (int(tile_rows), int(grid))
+
+    def solve(self, fs, xs=None, o: SolveOpts | None = None):
+        o = o or opts("fgmres", "jacobi", 1, tol=1e-6, restart=30, maxit=5000)
+        n = len(self.problems)
+        xs = [torch.zeros_like(f) for f in fs] if xs is None else [x.clone() for x in xs]
+        fp = (C.c_void_p * n)(*[f.data_ptr() for f in fs])
+        xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        stats = (Stats * n)()
+        rc = self.lib.helm_batch_solve(self.b, C.byref(o), fp, xp, stats)
+        if rc in (L.HELM_BAD_ARG, L.HELM_CUDA_ERROR, L.HELM_NOT_READY, L.HELM_OUT_OF_MEMORY):
+            raise HelmError(rc, "helm_batch_solve")
+        out = []
+        for s in stats:
+            d = s.as_dict()
+            d["status_name"] = L.STATUS_NAMES.get(d["status"], d["status"])
+            out.append(d)
+        return xs, out
+
+    def autotune(self, fs, o: SolveOpts | None = None, candidates=(256, 512, 1024, 2048, 4096), trial_iters=6,
+                 cache=None):
+        """Pick the tile length by timing a few FGMRES steps for each candidate;
+        results are cached per GPU, driver, problem count and total size."""
+        import json
+        import os
+        import time
+        key = None
+        if cache:
+            prop = torch.cuda.get_device_properties(0)
+            key = f"{prop.name}|{torch.version.cuda}|{len(self.problems)}|{sum(P.N for P in self.problems)}"
+            try:
+                table = json.load(open(cache))
+                if key in table:
+                    self.set_tile(table[key])
+                    return table[key], {}
+            except Exception:
+                table = {}
+        o = o or opts("fgmres", "jacobi", 1, tol=1e-12, restart=30, maxit=trial_iters)
+        trial = SolveOpts(o.method, o.relax, o.n_r, o.omega, o.correction, 1e-30, o.restart, trial_iters, o.conj)
+        times = {}
+        for t in candidates:
+            self.set_tile(t)
+            self.solve(fs, None, trial)                   # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            self.solve(fs, None, trial)
+            torch.cuda.synchronize()
+            times[t] = time.perf_counter() - t0
+        best = min(times, key=times.get)
+        self.set_tile(best)
+        if cache and key:
+            try:
+                table = json.load(open(cache)) if os.path.exists(cache) else {}
+            except Exception:
+                table = {}
+            table[key] = best
+            os.makedirs(os.path.dirname(cache) or ".", exist_ok=True)
+            json.dump(table, open(cache, "w"), indent=1)
+        return best, times
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.helm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

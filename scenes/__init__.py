@@ -352,3 +352,43 @@ BENCH_WORKLOADS = {
 def make_scene(name: str, **kw) -> Scene:
     return {"square2d": square2d, "cube3d": cube3d, "submarine3d": submarine3d,
             "bump_cube3d": bump_cube3d}[name](**kw)
+
+
+def batch_scenes(seed: int = 0, count: int = 64, n_min: int = 48, n_max: int = 128, k_range=(8.0, 32.0),
+                 p: int = 32, trunk_widths=(3, 64, 64, 32), sigma: float = 0.04, layer_cells: int = LAYER_CELLS):
+    """Batched workload: `count` problems on uneven cubic grids, k ~ U[k_range] with at
+    least 10 points per wavelength (n >= 10 k / (2 pi) + 1), scatterer drawn from
+    {cube, sphere, submarine} with scale U[0.1, 0.3] and a seeded rotation, one
+    Gaussian source each (seeded centre outside the scatterer's bounding box)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        k0 = float(rng.uniform(*k_range))
+        lo_n = max(n_min, int(math.ceil(10.0 * k0 / (2 * math.pi))) + 1)
+        n = int(rng.integers(lo_n, max(lo_n, n_max) + 1))
+        shape = ["cube", "sphere", "submarine"][int(rng.integers(3))]
+        scale = float(rng.uniform(0.1, 0.3))
+        rot = random_rotation(rng)
+        if shape == "cube":
+            scat = rotated_cube_mask(n, (0.5, 0.5, 0.5), scale / 2, rot)
+        elif shape == "sphere":
+            scat = sphere_mask(n, (0.5, 0.5, 0.5), scale / 2)
+        else:
+            scat = submarine_mask(n, rot, scale=scale / 0.7)
+        # source centre in the interior box, outside a sphere that encloses the scatterer
+        radius = (scale / 2) * (math.sqrt(3.0) if shape == "cube" else 1.0) + 2 * sigma
+        h = 1.0 / (n - 1)
+        lo, hi = layer_cells * h + sigma, 1.0 - layer_cells * h - sigma
+        if hi <= lo or np.linalg.norm(np.full(3, hi) - 0.5) <= radius:
+            raise ValueError(f"no room for a source outside the scatterer (n={n}, layer={layer_cells})")
+        for _ in range(100000):
+            c = rng.uniform(lo, hi, size=3)
+            if np.linalg.norm(c - 0.5) > radius:
+                break
+        else:
+            raise RuntimeError("no admissible source centre")
+        trunk = glorot_mlp(rng, list(trunk_widths[:-1]) + [p])
+        sc = _finish(f"batch{b}", 3, n, k0, scat, gaussian_source(3, n, c, sigma), trunk=trunk, p=p,
+                     layer_cells=layer_cells, extra={"shape": shape, "scale": scale, "centre": c})
+        out.append(sc)
+    return out

@@ -1,0 +1,68 @@
+"""Batched DeepONet-FGMRES (mixed precision): every problem of a heterogeneous
+batch converges to the tolerance on the oracle's own residual, agrees with the
+direct solution, and matches the single-problem mixed solve."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import scenes
+from oracle import assemble
+from tests.gpu_common import need_gpu, rel, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _batch(count=5, seed=3):
+    import paper_2405_12380_gb300 as hm
+    scs = scenes.batch_scenes(seed, count=count, n_min=17, n_max=25, k_range=(4.0, 9.0), p=12,
+                              trunk_widths=(3, 24, 24, 12), sigma=0.05, layer_cells=4)
+    probs, fs = [], []
+    for sc in scs:
+        P = hm.Problem(3, sc.n, sc.k0, sc.mask, layer_cells=4, precision="mixed")
+        P.don_load(sc.trunk, sc.p, tau=1e-3)
+        probs.append(P)
+        fs.append(P.rhs(to_dev(sc.src), to_dev(sc.g)))
+    return scs, probs, fs
+
+
+def test_batched_fgmres_matches_single_and_lu():
+    import paper_2405_12380_gb300 as hm
+    scs, probs, fs = _batch()
+    B = hm.Batch(probs)
+    o = hm.opts("fgmres", "jacobi", 1, tol=1e-6, restart=20, maxit=3000)
+    xs, st = B.solve(fs, None, o)
+    for sc, P, f, x, s in zip(scs, probs, fs, xs, st):
+        assert s["status"] == 0, s
+        layer = assemble.k2_field(3, sc.n, sc.k0, 4, 0.5)
+        A = assemble.assemble(3, sc.n, layer, sc.mask)
+        b = assemble.rhs(3, sc.n, sc.mask, sc.src, sc.g)
+        xh = x.cpu().numpy()
+        res = np.linalg.norm(b - A @ xh) / np.linalg.norm(b)
+        assert res <= 1e-6 and abs(res - s["rel_res"]) <= 1e-3 * res + 1e-12
+        u = spla.spsolve(A.tocsc(), b)
+        assert rel(xh, u) < 1e-3
+        xs1, s1 = P.solve(f, None, o)                     # the same problem alone
+        assert s1["status"] == 0
+        assert abs(s1["iters"] - s["iters"]) <= max(3, 0.1 * s1["iters"])
+        assert rel(xh, xs1.cpu().numpy()) < 1e-4
+
+
+def test_batched_tiles_and_autotune_agree():
+    import paper_2405_12380_gb300 as hm
+    scs, probs, fs = _batch(count=3, seed=4)
+    B = hm.Batch(probs)
+    o = hm.opts("fgmres", "jacobi", 1, tol=1e-6, restart=20, maxit=3000)
+    ref, st = B.solve(fs, None, o)
+    for t in (64, 512, 4096):
+        B.set_tile(t, 200)
+        xs, st2 = B.solve(fs, None, o)
+        for a, b_, s in zip(xs, ref, st2):
+            assert s["status"] == 0
+            assert rel(a.cpu().numpy(), b_.cpu().numpy()) < 1e-4
+    best, times = B.autotune(fs, candidates=(256, 1024), trial_iters=3)
+    assert best in (256, 1024) and len(times) == 2
