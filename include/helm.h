@@ -244,7 +244,7 @@ helm_status nn_gather(int rows, int cols, const float* src, long long lds, const
  * persistent launch over a queue of tiles (tile_rows consecutive nodes of one
  * problem) for all problems at once, with per-problem reductions, Givens
  * rotations, convergence and Krylov dimensions.  Preconditioner: complex64
- * damped Jacobi (relax HELM_JACOBI, n_r sweeps, or none) + trunk-basis correction
+ * damped Jacobi or red-black GS (n_r sweeps, or none) + trunk-basis correction
  * with each problem's BF16 basis; Arnoldi, Hessenberg, Givens and the true
  * residual in FP64.  The handles must outlive the batch; it uses the stream of hs[0]. */
 typedef struct helm_batch helm_batch;

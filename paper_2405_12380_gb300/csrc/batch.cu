@@ -159,6 +159,45 @@ __global__ void __launch_bounds__(BT) kb_jacobi32(const BProb* __restrict__ prob
     }
 }
 
+// red-black Gauss-Seidel half-sweep in complex64, in place: nodes of colour c get
+// D^-1 (v - h^-2 sum of fluid neighbours) (masked: v); xzero: z starts at zero
+__global__ void __launch_bounds__(BT) kb_rbgs32(const BProb* __restrict__ probs, const Tile* __restrict__ tiles,
+                                                int ntiles, int tile_rows, int colour, int xzero,
+                                                const float2* __restrict__ v, float2* __restrict__ z,
+                                                const int* __restrict__ active) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        if (!active[T.prob]) continue;
+        const BProb& P = probs[T.prob];
+        const float2* vb = v + P.off;
+        float2* zb = z + P.off;
+        for (int r = threadIdx.x; r < tile_rows; r += BT) {
+            const long long l = T.first + r;
+            if (l >= P.N) break;
+            int i, j, k;
+            node_ijk(P, l, i, j, k);
+            if (((i + j + (P.dim == 3 ? k : 0)) & 1) != colour) {
+                if (xzero) zb[l] = make_float2(0.f, 0.f);
+                continue;
+            }
+            const float2 fl = vb[l];
+            float2 out;
+            if (P.mask[l]) {
+                out = fl;
+            } else {
+                const float2 id = b_invd32(P, l);
+                if (xzero) {
+                    out = cmul(id, fl);
+                } else {
+                    const float2 s = b_nbr_sum32(P, zb, l);
+                    out = cmul(id, make_float2(fl.x - P.hinv2f * s.x, fl.y - P.hinv2f * s.y));
+                }
+            }
+            zb[l] = out;
+        }
+    }
+}
+
 // r32 = v32 - A32 z32
 __global__ void __launch_bounds__(BT) kb_resid32(const BProb* __restrict__ probs, const Tile* __restrict__ tiles,
                                                  int ntiles, int tile_rows, const float2* __restrict__ v,
@@ -742,8 +781,8 @@ helm_status helm_batch_set_tile(helm_batch* B, int tile_rows, int grid) {
 helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const double* const* f, double* const* x,
                              helm_stats* stats) {
     if (!B || !o || !f || !x) return HELM_BAD_ARG;
-    if (o->method != HELM_METHOD_FGMRES || o->restart < 1 || o->restart > kMaxRestart ||
-        (o->relax != HELM_JACOBI && o->relax != HELM_RELAX_NONE) || o->conj)
+    if (o->method != HELM_METHOD_FGMRES || o->restart < 1 || o->restart > kMaxRestart || o->conj ||
+        o->correction == HELM_CORR_NONLINEAR)
         return HELM_BAD_ARG;
     const int m = o->restart;
     helm_status st = ensure_batch_krylov(B, m);
@@ -780,7 +819,7 @@ helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const doub
     launches += 2;
     for (int b = 0; b < P; ++b) bnorm[b] = std::sqrt(B->hpin[b]);
     const double omega = o->omega;
-    const int nr = o->relax == HELM_JACOBI ? o->n_r : 0;
+    const int nr = o->relax == HELM_RELAX_NONE ? 0 : o->n_r;
     const bool tb = o->correction == HELM_CORR_TB;
     while (true) {
         // true residual and restart decisions
@@ -815,6 +854,13 @@ helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const doub
             kb_cvt64to32<<<G, BT, 0, s>>>(Vj, B->v32, NT);
             if (nr == 0) {
                 cudaMemsetAsync(Zj, 0, sizeof(float2) * NT, s);
+            } else if (o->relax == HELM_RBGS) {
+                for (int q = 0; q < nr; ++q) {
+                    // the first red half-sweep from zero also clears the black nodes
+                    kb_rbgs32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, 0, q == 0, B->v32, Zj, B->active);
+                    kb_rbgs32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, 1, 0, B->v32, Zj, B->active);
+                }
+                launches += 2 * nr;
             } else {
                 float2* a = (nr % 2 == 1) ? Zj : B->z32tmp;
                 float2* bb = (nr % 2 == 1) ? B->z32tmp : Zj;

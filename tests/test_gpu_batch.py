@@ -52,6 +52,21 @@ def test_batched_fgmres_matches_single_and_lu():
         assert rel(xh, xs1.cpu().numpy()) < 1e-4
 
 
+def test_batched_rbgs_cycle_converges():
+    import paper_2405_12380_gb300 as hm
+    scs, probs, fs = _batch(count=4, seed=5)
+    B = hm.Batch(probs)
+    o = hm.opts("fgmres", "rbgs", 2, tol=1e-6, restart=20, maxit=3000)
+    xs, st = B.solve(fs, None, o)
+    for sc, P, f, x, s in zip(scs, probs, fs, xs, st):
+        assert s["status"] == 0, s
+        A = assemble.assemble(3, sc.n, assemble.k2_field(3, sc.n, sc.k0, 4, 0.5), sc.mask)
+        b = assemble.rhs(3, sc.n, sc.mask, sc.src, sc.g)
+        assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1e-6 * np.linalg.norm(b)
+        x1, s1 = P.solve(f, None, o)
+        assert rel(x.cpu().numpy(), x1.cpu().numpy()) < 1e-4
+
+
 def test_batched_tiles_and_autotune_agree():
     import paper_2405_12380_gb300 as hm
     scs, probs, fs = _batch(count=3, seed=4)
