@@ -580,6 +580,7 @@ void fill_tables(helm_handle* h) {
     f.dre = (float)o.dre;
     o.mask = f.mask = h->mask;
     o.lidx = f.lidx = h->lidx;
+    o.nbm = f.nbm = h->nbm;
     for (int m = 0; m <= kMaxLayerCells; ++m) {
         double eta = (h->L > 0 && m <= h->L) ? (double)m / (double)h->L : 0.0;
         double im = h->k0 * h->k0 * ((h->strength * eta) * eta);
@@ -680,6 +681,7 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
         if (cudaMemcpy(h->k2, k2, sizeof(double2) * N, cudaMemcpyDefault) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     }
     if (dalloc(h, &h->lidx, (size_t)N) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (dalloc(h, &h->nbm, (size_t)N) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
     fill_tables(h);
     launch_layer_index(h->op64, h->lidx, nullptr);
     if (k2) {
@@ -693,6 +695,8 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
     if (cudaMemcpy(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (bad) return bail(HELM_BAD_ARG);
+    launch_nbr_code(h->op64, h->nbm, nullptr);
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(HELM_CUDA_ERROR);
     cudaEventCreate(&h->ev0);
     cudaEventCreate(&h->ev1);
     *out = h;
@@ -701,7 +705,7 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
 
 helm_status helm_destroy(helm_handle* h) {
     if (!h) return HELM_BAD_ARG;
-    dfree(h->mask); dfree(h->lidx); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
+    dfree(h->mask); dfree(h->lidx); dfree(h->nbm); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
     dfree(h->red); dfree(h->sc); dfree(h->dflag);
     if (h->hpin) cudaFreeHost(h->hpin);
     for (auto p : h->tmp) cudaFree(p);

@@ -65,6 +65,7 @@ struct Op {
     R dre;                   // k0^2 - 2 d h^-2 (real part of the diagonal, layer form)
     const uint8_t* mask;
     const uint8_t* lidx;     // per-node layer index m (flat-index kernels; avoids index division)
+    const uint8_t* nbm;      // per-node neighbour code: bit q = neighbour q fluid, 0x80 = masked node
     const C* k2;             // stored k^2 field or nullptr
     const C* invd;           // per-node 1/diag for the stored field, or nullptr
     R im[kMaxLayerCells + 1];        // Im k^2 by layer index
@@ -95,6 +96,7 @@ void launch_layer_k2(const Op<double>& op, double k0, double strength, const dou
 void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s);
 void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s);
 void launch_layer_index(const Op<double>& op, uint8_t* lidx, cudaStream_t s);
+void launch_nbr_code(const Op<double>& op, uint8_t* code, cudaStream_t s);
 
 // blas.cu
 // partial reductions over a fixed grid of kRedBlocks blocks
@@ -195,6 +197,7 @@ struct helm_handle {
     helm::Op<float> op32{};
     uint8_t* mask = nullptr;
     uint8_t* lidx = nullptr;
+    uint8_t* nbm = nullptr;
     double2* k2 = nullptr;
     double2* invd = nullptr;
     float2* k2f = nullptr;

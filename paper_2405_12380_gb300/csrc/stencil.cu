@@ -46,24 +46,49 @@ __device__ __forceinline__ typename CT<R>::T invd_of(const Op<R>& op, long long 
     return d;
 }
 
-// sum of the fluid neighbours of an interior node
+// sum of the fluid neighbours of a fluid node; `code` is the node's neighbour code
+// (bit q set: neighbour q is fluid, q = -x, +x, -y, +y, -z, +z), one byte load
+// instead of six mask loads
 template <typename R>
 __device__ __forceinline__ typename CT<R>::T nbr_sum(const Op<R>& op, const typename CT<R>::T* __restrict__ x,
-                                                     long long l) {
+                                                     long long l, unsigned code) {
     using C = typename CT<R>::T;
     const long long sy = op.n, sz = (long long)op.n * op.n;
     C s;
     s.x = 0; s.y = 0;
-    const uint8_t* mk = op.mask;
-    if (!mk[l - 1]) s = cadd(s, x[l - 1]);
-    if (!mk[l + 1]) s = cadd(s, x[l + 1]);
-    if (!mk[l - sy]) s = cadd(s, x[l - sy]);
-    if (!mk[l + sy]) s = cadd(s, x[l + sy]);
-    if (op.dim == 3) {
-        if (!mk[l - sz]) s = cadd(s, x[l - sz]);
-        if (!mk[l + sz]) s = cadd(s, x[l + sz]);
-    }
+    if (code & 1u) s = cadd(s, x[l - 1]);
+    if (code & 2u) s = cadd(s, x[l + 1]);
+    if (code & 4u) s = cadd(s, x[l - sy]);
+    if (code & 8u) s = cadd(s, x[l + sy]);
+    if (code & 16u) s = cadd(s, x[l - sz]);
+    if (code & 32u) s = cadd(s, x[l + sz]);
     return s;
+}
+
+constexpr unsigned kMasked = 0x80u;
+
+// neighbour code and layer index of a node: from the handle's tables, or from the
+// mask and the indices when the operator carries no tables (no-allocation path)
+template <typename R>
+__device__ __forceinline__ unsigned node_code(const Op<R>& op, long long l) {
+    if (op.nbm) return op.nbm[l];
+    if (op.mask[l]) return kMasked;
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    unsigned c = 0;
+    if (!op.mask[l - 1]) c |= 1u;
+    if (!op.mask[l + 1]) c |= 2u;
+    if (!op.mask[l - sy]) c |= 4u;
+    if (!op.mask[l + sy]) c |= 8u;
+    if (op.dim == 3) {
+        if (!op.mask[l - sz]) c |= 16u;
+        if (!op.mask[l + sz]) c |= 32u;
+    }
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ int node_lidx(const Op<R>& op, long long l, int i, int j, int k) {
+    return op.lidx ? (int)op.lidx[l] : node_layer(op, i, j, k);
 }
 
 template <typename R>
@@ -90,12 +115,13 @@ __device__ __forceinline__ double apply_point(const Op<R>& op, const typename CT
     using C = typename CT<R>::T;
     const long long l = i + (long long)op.n * (j + (long long)op.n * k);
     const C xc = x[l];
+    const unsigned code = node_code(op, l);
     C out;
-    if (op.mask[l]) {
+    if (code & kMasked) {
         out = xc;
     } else {
-        const C s = nbr_sum(op, x, l);
-        const C d = diag_of(op, l, node_layer(op, i, j, k), conj);
+        const C s = nbr_sum(op, x, l, code);
+        const C d = diag_of(op, l, node_lidx(op, l, i, j, k), conj);
         out.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
         out.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
     }
@@ -133,8 +159,9 @@ __device__ __forceinline__ void jacobi_point(const Op<R>& op, R omega, const typ
     using C = typename CT<R>::T;
     const long long l = i + (long long)op.n * (j + (long long)op.n * k);
     const C fl = f[l];
+    const unsigned code = node_code(op, l);
     C out;
-    if (op.mask[l]) {
+    if (code & kMasked) {
         if (XZERO) {
             out = cscale(omega, fl);
         } else {
@@ -142,13 +169,12 @@ __device__ __forceinline__ void jacobi_point(const Op<R>& op, R omega, const typ
             out = cadd(xc, cscale(omega, csub(fl, xc)));
         }
     } else {
-        const int m = node_layer(op, i, j, k);
-        C id = invd_of(op, l, m, conj);
+        C id = invd_of(op, l, node_lidx(op, l, i, j, k), conj);
         if (XZERO) {
             out = cscale(omega, cmul(id, fl));
         } else {
             const C xc = xin[l];
-            const C s = nbr_sum(op, xin, l);
+            const C s = nbr_sum(op, xin, l, code);
             C g;
             g.x = fl.x - op.hinv2 * s.x;
             g.y = fl.y - op.hinv2 * s.y;
@@ -183,16 +209,16 @@ __device__ __forceinline__ void rbgs_point(const Op<R>& op, const typename CT<R>
     using C = typename CT<R>::T;
     const long long l = i + (long long)op.n * (j + (long long)op.n * k);
     const C fl = f[l];
+    const unsigned code = node_code(op, l);
     C out;
-    if (op.mask[l]) {
+    if (code & kMasked) {
         out = fl;
     } else {
-        const int m = node_layer(op, i, j, k);
-        const C id = invd_of(op, l, m, conj);
+        const C id = invd_of(op, l, node_lidx(op, l, i, j, k), conj);
         if (XZERO) {
             out = cmul(id, fl);
         } else {
-            const C s = nbr_sum(op, x, l);
+            const C s = nbr_sum(op, x, l, code);
             C g;
             g.x = fl.x - op.hinv2 * s.x;
             g.y = fl.y - op.hinv2 * s.y;
@@ -274,6 +300,30 @@ __global__ void k_layer_index(Op<double> op, uint8_t* __restrict__ lidx) {
     lidx[l] = (uint8_t)node_layer(op, i, j, k);
 }
 
+__global__ void k_nbr_code(Op<double> op, uint8_t* __restrict__ code) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    unsigned c = 0;
+    if (op.mask[l]) {
+        c = kMasked;
+    } else {
+        // fluid nodes are interior (the outer ring is masked), so all neighbours exist
+        if (!op.mask[l - 1]) c |= 1u;
+        if (!op.mask[l + 1]) c |= 2u;
+        if (!op.mask[l - sy]) c |= 4u;
+        if (!op.mask[l + sy]) c |= 8u;
+        if (op.dim == 3) {
+            if (!op.mask[l - sz]) c |= 16u;
+            if (!op.mask[l + sz]) c |= 32u;
+        }
+    }
+    code[l] = (uint8_t)c;
+}
+
 __global__ void k_check_ring(Op<double> op, int* bad) {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
@@ -353,6 +403,10 @@ void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s) {
 
 void launch_layer_index(const Op<double>& op, uint8_t* lidx, cudaStream_t s) {
     k_layer_index<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, lidx);
+}
+
+void launch_nbr_code(const Op<double>& op, uint8_t* code, cudaStream_t s) {
+    k_nbr_code<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, code);
 }
 
 void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s) {

@@ -414,12 +414,12 @@ __device__ __forceinline__ void pair_warp_sum(float& sh, float& sl) {
     }
 }
 
-constexpr int PJ_T = 512;        // threads per projection block (16 warps)
+constexpr int PJ_T = 512;        // threads per projection block (16 warps), two blocks per SM
 constexpr int PJ_TILE = 512;     // rows per tile (one per thread)
 
 // partials[b][j] = sum over the rows of block b of Q_j[l] r_l (r given, FP64)
 template <int KPW>
-__global__ void __launch_bounds__(PJ_T) k_project_df(const float2* __restrict__ Q, int k, const double2* __restrict__ r,
+__global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, int k, const double2* __restrict__ r,
                                                      long long N, double2* __restrict__ partials, long long rows_per_block) {
     __shared__ float4 rs[PJ_TILE];       // (re hi, re lo, im hi, im lo)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
