@@ -4,6 +4,7 @@
 // partial per block, and a single block sums the partials in a fixed order.
 // Scalars (rho, alpha, omega, beta, norms, Hessenberg columns, Givens
 // rotations) stay in device memory; the host only reads a status word.
+#include "bicg.cuh"
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -176,6 +177,74 @@ __global__ void __launch_bounds__(TB) k_bicg_xr(double2* __restrict__ x, double2
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// s = r - alpha v with ||s||^2, the scalar update in the last block
+__global__ void __launch_bounds__(kFusedThreads) k_bicg_s_fused(const double2* __restrict__ r, const double2* __restrict__ v,
+                                                                double2* __restrict__ s, double2* sc, long long N,
+                                                                double* parts, unsigned* counter, double tol_abs) {
+    const double2 alpha = sc[S_ALPHA];
+    double acc = 0;
+    for (long long l = blockIdx.x * (long long)kFusedThreads + threadIdx.x; l < N; l += (long long)gridDim.x * kFusedThreads) {
+        const double2 q = csub(r[l], cmul(alpha, v[l]));
+        s[l] = q;
+        acc += q.x * q.x + q.y * q.y;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+    if (last_block_done(counter, gridDim.x)) {
+        double tot[1];
+        sum_parts<1>(parts, gridDim.x, threadIdx.x, tot);
+        if (threadIdx.x == 0) {
+            bicg_snorm(sc, tot[0], tol_abs);
+            *counter = 0;
+        }
+    }
+}
+
+// x += alpha phat + omega shat; r = s - omega t; ||r||^2 and the next rho = <rhat, r>
+// with beta, in the last block (breakdown flag 3: rho = 0 for the next iteration)
+__global__ void __launch_bounds__(kFusedThreads) k_bicg_xr_fused(double2* __restrict__ x, double2* __restrict__ r,
+                                                                 const double2* __restrict__ phat,
+                                                                 const double2* __restrict__ shat,
+                                                                 const double2* __restrict__ s,
+                                                                 const double2* __restrict__ t,
+                                                                 const double2* __restrict__ rhat, double2* sc,
+                                                                 long long N, double* parts, unsigned* counter) {
+    const double2 alpha = sc[S_ALPHA], omega = sc[S_OMEGA];
+    const bool skip = sc[S_FLAGS].y == 1.0;
+    double rn = 0;
+    double2 rho = make_double2(0, 0);
+    for (long long l = blockIdx.x * (long long)kFusedThreads + threadIdx.x; l < N && !skip;
+         l += (long long)gridDim.x * kFusedThreads) {
+        double2 xv = cadd(x[l], cmul(alpha, phat[l]));
+        xv = cadd(xv, cmul(omega, shat[l]));
+        x[l] = xv;
+        const double2 q = csub(s[l], cmul(omega, t[l]));
+        r[l] = q;
+        rn += q.x * q.x + q.y * q.y;
+        const double2 h = rhat[l];
+        rho.x += h.x * q.x + h.y * q.y;
+        rho.y += h.x * q.y - h.y * q.x;
+    }
+    rn = block_sum(rn);
+    rho = block_sum(rho);
+    if (threadIdx.x == 0) {
+        parts[3 * blockIdx.x + 0] = rn;
+        parts[3 * blockIdx.x + 1] = rho.x;
+        parts[3 * blockIdx.x + 2] = rho.y;
+    }
+    if (last_block_done(counter, gridDim.x)) {
+        double tot[3];
+        sum_parts<3>(parts, gridDim.x, threadIdx.x, tot);
+        if (threadIdx.x == 0) {
+            if (!skip) {
+                bicg_rnorm(sc, tot[0]);
+                bicg_rho_beta(sc, make_double2(tot[1], tot[2]), 3.0);
+            }
+            *counter = 0;
+        }
+    }
 }
 
 // recipes: 0 = rho & beta (complex partials), 1 = alpha, 2 = ||s||^2, 3 = omega, 4 = ||r||^2, 5 = reset
@@ -437,6 +506,15 @@ void launch_bicg_omega_dots(const double2* t, const double2* sv, long long N, do
 void launch_bicg_xr(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
                     const double2* t, const double2* sc, long long N, double* partials, cudaStream_t s) {
     k_bicg_xr<<<kRedBlocks, TB, 0, s>>>(x, r, phat, shat, sv, t, sc, N, partials);
+}
+void launch_bicg_s_fused(const double2* r, const double2* v, double2* sv, double2* sc, long long N, double* parts,
+                         unsigned* counter, double tol_abs, cudaStream_t s) {
+    k_bicg_s_fused<<<kRedBlocks, kFusedThreads, 0, s>>>(r, v, sv, sc, N, parts, counter, tol_abs);
+}
+void launch_bicg_xr_fused(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
+                          const double2* t, const double2* rhat, double2* sc, long long N, double* parts,
+                          unsigned* counter, cudaStream_t s) {
+    k_bicg_xr_fused<<<kRedBlocks, kFusedThreads, 0, s>>>(x, r, phat, shat, sv, t, rhat, sc, N, parts, counter);
 }
 void launch_bicg_scalar(int recipe, const double* partials, int nparts, double2* sc, double tol_abs,
                         cudaStream_t s) {

@@ -508,29 +508,27 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
         CK(cudaMemsetAsync(p, 0, sizeof(double2) * N, s));
         CK(cudaMemsetAsync(v, 0, sizeof(double2) * N, s));
         launch_bicg_scalar(5, h->red, 0, h->sc, 0.0, s);
-        h->launches += 1;
+        // rho = <rhat, r> and beta for the first iteration of this (re)start
+        launch_dot(rh, r, N, reinterpret_cast<double2*>(h->red), s);
+        launch_bicg_scalar(0, h->red, kRedBlocks, h->sc, tol_abs, s);
+        h->launches += 3;
         CKL();
         return HELM_OK;
     };
     TRY(restart());
     st->status = HELM_NOT_CONVERGED;
+    // one iteration: p update, M p, v = A p with alpha, s with ||s||, M s, t = A s with
+    // omega, x/r update with ||r|| and the next rho/beta -- each reduction and its scalar
+    // recurrence fused into the kernel that produces the vector
     while (iters < o->maxit) {
-        launch_dot(rh, r, N, reinterpret_cast<double2*>(h->red), s);
-        launch_bicg_scalar(0, h->red, kRedBlocks, h->sc, tol_abs, s);
         launch_bicg_update_p(r, v, p, h->sc, N, s);
         TRY(precond(h, o, p, ph, o->conj));
-        launch_apply<double>(h->op64, ph, nullptr, v, nullptr, o->conj, false, s);
-        launch_dot(rh, v, N, reinterpret_cast<double2*>(h->red), s);
-        launch_bicg_scalar(1, h->red, kRedBlocks, h->sc, tol_abs, s);
-        launch_bicg_s(r, v, sv, h->sc, N, h->red, s);
-        launch_bicg_scalar(2, h->red, kRedBlocks, h->sc, tol_abs, s);
+        launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
+        launch_bicg_s_fused(r, v, sv, h->sc, N, h->fparts, h->counter, tol_abs, s);
         TRY(precond(h, o, sv, sh, o->conj));
-        launch_apply<double>(h->op64, sh, nullptr, t, nullptr, o->conj, false, s);
-        launch_bicg_omega_dots(t, sv, N, h->red, s);
-        launch_bicg_scalar(3, h->red, kRedBlocks, h->sc, tol_abs, s);
-        launch_bicg_xr(x, r, ph, sh, sv, t, h->sc, N, h->red, s);
-        launch_bicg_scalar(4, h->red, kRedBlocks, h->sc, tol_abs, s);
-        h->launches += 13;
+        launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
+        launch_bicg_xr_fused(x, r, ph, sh, sv, t, rh, h->sc, N, h->fparts, h->counter, s);
+        h->launches += 5;
         CKL();
         st->precond_applies += 2;
         st->matvecs += 2;
@@ -553,7 +551,7 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
             }
             ++restarts;
             TRY(restart());
-        } else if (brk == 2.0) {
+        } else if (brk == 2.0 || brk == 3.0) {
             st->status = HELM_BREAKDOWN;
             break;
         }
@@ -672,6 +670,10 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
     if (dalloc(h, &h->red, (size_t)h->red_len) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
     if (dalloc(h, &h->sc, (size_t)S_NSLOTS) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
     if (dalloc(h, &h->dflag, 8) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (dalloc(h, &h->counter, 4) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (dalloc(h, &h->fparts, (size_t)4 * std::max<long long>(apply_grid_blocks(dim, n), kRedBlocks)) != HELM_OK)
+        return bail(HELM_OUT_OF_MEMORY);
+    if (cudaMemset(h->counter, 0, 4 * sizeof(unsigned)) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (cudaMallocHost((void**)&h->hpin, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_OUT_OF_MEMORY);
     if (cudaMemset(h->sc, 0, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (k2) {
@@ -706,7 +708,7 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
 helm_status helm_destroy(helm_handle* h) {
     if (!h) return HELM_BAD_ARG;
     dfree(h->mask); dfree(h->lidx); dfree(h->nbm); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
-    dfree(h->red); dfree(h->sc); dfree(h->dflag);
+    dfree(h->red); dfree(h->sc); dfree(h->dflag); dfree(h->counter); dfree(h->fparts);
     if (h->hpin) cudaFreeHost(h->hpin);
     for (auto p : h->tmp) cudaFree(p);
     for (auto p : h->tmp32) cudaFree(p);

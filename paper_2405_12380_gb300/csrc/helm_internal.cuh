@@ -97,6 +97,14 @@ void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s);
 void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s);
 void launch_layer_index(const Op<double>& op, uint8_t* lidx, cudaStream_t s);
 void launch_nbr_code(const Op<double>& op, uint8_t* code, cudaStream_t s);
+// BiCGStab fused kernels (reduction + scalar update in the last block; counter zero between uses)
+void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2* y, const double2* w, int conj,
+                       double2* sc, double* parts, unsigned* counter, cudaStream_t s);
+void launch_bicg_s_fused(const double2* r, const double2* v, double2* sv, double2* sc, long long N, double* parts,
+                         unsigned* counter, double tol_abs, cudaStream_t s);
+void launch_bicg_xr_fused(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
+                          const double2* t, const double2* rhat, double2* sc, long long N, double* parts,
+                          unsigned* counter, cudaStream_t s);
 
 // blas.cu
 // partial reductions over a fixed grid of kRedBlocks blocks
@@ -208,6 +216,8 @@ struct helm_handle {
     double2* sc = nullptr;          // device scalars (BiCGStab/FGMRES)
     double* hpin = nullptr;         // pinned host mirror for status polling
     int* dflag = nullptr;           // device int flags
+    unsigned* counter = nullptr;    // block counter of the fused reductions (zero between kernels)
+    double* fparts = nullptr;       // partials of the fused reductions
     // general temporaries (N complex128 each)
     std::vector<double2*> tmp;
     // trunk basis

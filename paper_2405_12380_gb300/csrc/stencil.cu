@@ -5,6 +5,7 @@
 // from the tables in Op (or the stored field).  FP64 is the scarce pipe on
 // GB300, so per node the operator costs 2d complex adds, one scale and one
 // complex multiply-add, and the sweeps multiply by a tabulated reciprocal.
+#include "bicg.cuh"
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -146,6 +147,61 @@ __global__ void __launch_bounds__(BX * BY) k_apply(Op<R> op, const typename CT<R
     }
     if (NORM) {
         block_reduce_store<R>(acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    }
+}
+
+// y = A x with a BiCGStab reduction in the epilogue and its scalar update in the
+// last block.  mode 1: <w, y> -> alpha = rho / <rhat, v> (w = rhat);
+// mode 2: <y, w>, <y, y> -> omega (w = s).
+template <int MODE>
+__global__ void __launch_bounds__(BX * BY) k_apply_bicg(Op<double> op, const double2* __restrict__ x,
+                                                        double2* __restrict__ y, const double2* __restrict__ w,
+                                                        int conj, double2* sc, double* parts, unsigned* counter) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k0 = op.dim == 3 ? 2 * blockIdx.z : 0;
+    double a = 0, b = 0, c = 0;
+    if (i < op.n && j < op.n) {
+        for (int kk = k0; kk < (op.dim == 3 ? min(k0 + 2, op.n) : 1); ++kk) {
+            apply_point<double, false>(op, x, nullptr, y, conj, i, j, kk);
+            const long long l = i + (long long)op.n * (j + (long long)op.n * kk);
+            const double2 yv = y[l], wv = w[l];
+            if (MODE == 1) {          // conj(w) y
+                a += wv.x * yv.x + wv.y * yv.y;
+                b += wv.x * yv.y - wv.y * yv.x;
+            } else {                  // conj(y) w and |y|^2
+                a += yv.x * wv.x + yv.y * wv.y;
+                b += yv.x * wv.y - yv.y * wv.x;
+                c += yv.x * yv.x + yv.y * yv.y;
+            }
+        }
+    }
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    __shared__ double red[3][BX * BY / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((tid & 31) == 0) { red[0][tid >> 5] = a; red[1][tid >> 5] = b; red[2][tid >> 5] = c; }
+    __syncthreads();
+    if (tid == 0) {
+        double sa = 0, sb = 0, scc = 0;
+        for (int q = 0; q < BX * BY / 32; ++q) { sa += red[0][q]; sb += red[1][q]; scc += red[2][q]; }
+        parts[3 * bid + 0] = sa;
+        parts[3 * bid + 1] = sb;
+        parts[3 * bid + 2] = scc;
+    }
+    if (last_block_done(counter, nblk)) {
+        double tot[3];
+        sum_parts<3>(parts, nblk, tid, tot);
+        if (tid == 0) {
+            if (MODE == 1) bicg_alpha(sc, make_double2(tot[0], tot[1]));
+            else bicg_omega(sc, make_double2(tot[0], tot[1]), tot[2]);
+            *counter = 0;
+        }
     }
 }
 
@@ -374,6 +430,13 @@ void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, t
     dim3 g = grid_for(op.dim, op.n, 2, 2), b(BX, BY);
     if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj);
     else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj);
+}
+
+void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2* y, const double2* w, int conj,
+                       double2* sc, double* parts, unsigned* counter, cudaStream_t s) {
+    dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
+    if (mode == 1) k_apply_bicg<1><<<g, b, 0, s>>>(op, x, y, w, conj, sc, parts, counter);
+    else k_apply_bicg<2><<<g, b, 0, s>>>(op, x, y, w, conj, sc, parts, counter);
 }
 
 template void launch_apply<double>(const Op<double>&, const double2*, const double2*, double2*, double*, int,
