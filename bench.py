@@ -195,6 +195,41 @@ def traffic_for(kernel, k):
     return prof.get("dram_bytes_per_launch")
 
 
+def stencil_bench(hm, torch, n=256, reps=20):
+    """Achieved HBM bandwidth of the operator kernel y = A x on an n^3 grid (vectors
+    larger than L2, inputs rotated over three buffers), complex64 and complex128.
+    Algorithmic bytes per node: read x once, write y, read one mask byte
+    (17 B complex64, 33 B complex128)."""
+    sc = scenes.cube3d(0, n=n, width=n // 4, p=8, trunk_widths=(3, 8, 8, 8))
+    P = hm.Problem(3, n, 16.0, sc.mask, layer_cells=8, layer_strength=0.5)
+    out = {"grid": f"{n}^3"}
+    for dt, nbytes in ((torch.complex64, 17), (torch.complex128, 33)):
+        xs = [torch.randn(P.N, dtype=dt, device="cuda") for _ in range(3)]
+        y = torch.empty_like(xs[0])
+        for q in range(3):
+            P.apply(xs[q], out=y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for q in range(reps):
+            P.apply(xs[q % 3], out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = nbytes * P.N / (ms * 1e-3) / 1e9
+        key = "c64" if dt == torch.complex64 else "c128"
+        out[key] = {"us_per_apply": ms * 1e3, "GBps": gbs, "bytes_per_node": nbytes}
+        del xs, y
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    out["hbm_peak_GBps"] = hbm
+    out["c64_frac_of_hbm"] = out["c64"]["GBps"] / hbm
+    out["c128_frac_of_hbm"] = out["c128"]["GBps"] / hbm
+    out["note"] = "c128 is bound by GB300's FP64 rate (~18 FP64 operations per node), not by HBM"
+    P.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -309,6 +344,7 @@ def gpu_arm(args):
                          + f"; oracle setup {smp['setup_s']:.1f} s excluded; scipy.sparse single-threaded",
                "oracle_kept": smp["kept"]}
     clocks = clk.summary()
+    stencil = stencil_bench(hm, torch)
     cfg = workload_config(args.workload, w, sc, k)
     cfg.update({"iterations": iters, "rel_res": rel_res, "setup_s": setup_s, "replicas": world,
                 "solve_ms_each": solve_ms})
@@ -319,7 +355,8 @@ def gpu_arm(args):
         "config": cfg, "iterations": iters, "status": st0["status_name"],
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": N * 16},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed_region": t_wall,
+        "roofline": roofline, "stencil": stencil, "cpu_baseline": cpu, "clocks": clocks,
+        "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

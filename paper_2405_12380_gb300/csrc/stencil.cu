@@ -55,14 +55,19 @@ __device__ __forceinline__ typename CT<R>::T nbr_sum(const Op<R>& op, const type
                                                      long long l, unsigned code) {
     using C = typename CT<R>::T;
     const long long sy = op.n, sz = (long long)op.n * op.n;
-    C s;
-    s.x = 0; s.y = 0;
-    if (code & 1u) s = cadd(s, x[l - 1]);
-    if (code & 2u) s = cadd(s, x[l + 1]);
-    if (code & 4u) s = cadd(s, x[l - sy]);
-    if (code & 8u) s = cadd(s, x[l + sy]);
-    if (code & 16u) s = cadd(s, x[l - sz]);
-    if (code & 32u) s = cadd(s, x[l + sz]);
+    C z;
+    z.x = 0; z.y = 0;
+    // pairwise (tree) sum: three independent adds, then two -- shorter FP64 dependency chains
+    const C a = (code & 1u) ? x[l - 1] : z;
+    const C b = (code & 2u) ? x[l + 1] : z;
+    const C c = (code & 4u) ? x[l - sy] : z;
+    const C d = (code & 8u) ? x[l + sy] : z;
+    C s = cadd(cadd(a, b), cadd(c, d));
+    if (op.dim == 3) {
+        const C e = (code & 16u) ? x[l - sz] : z;
+        const C f = (code & 32u) ? x[l + sz] : z;
+        s = cadd(s, cadd(e, f));
+    }
     return s;
 }
 
@@ -288,14 +293,10 @@ template <typename R, bool XZERO>
 __global__ void __launch_bounds__(BX * BY) k_rbgs(Op<R> op, int colour, const typename CT<R>::T* __restrict__ f,
                                                   typename CT<R>::T* x, int conj) {
     const int j = blockIdx.y * BY + threadIdx.y;
-    const int k0 = op.dim == 3 ? 2 * blockIdx.z : 0;
+    const int k = op.dim == 3 ? blockIdx.z : 0;
     if (j >= op.n) return;
-    const int i0 = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k0 + colour) & 1);
-    if (i0 < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i0, j, k0);
-    if (op.dim == 3 && k0 + 1 < op.n) {
-        const int i1 = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k0 + 1 + colour) & 1);
-        if (i1 < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i1, j, k0 + 1);
-    }
+    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + colour) & 1);
+    if (i < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i, j, k);
 }
 
 __global__ void k_rhs(Op<double> op, const double2* __restrict__ src, const double2* __restrict__ g,
@@ -427,7 +428,7 @@ void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f, co
 template <typename R>
 void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x, int conj,
                       bool xzero, cudaStream_t s) {
-    dim3 g = grid_for(op.dim, op.n, 2, 2), b(BX, BY);
+    dim3 g = grid_for(op.dim, op.n, 2, 1), b(BX, BY);
     if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj);
     else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj);
 }
