@@ -268,7 +268,7 @@ helm_status helm_batch_solve(helm_batch* b, const helm_solve_opts* opts, const d
  * f, x, r [dev] complex128, norm2 [dev] one double are the caller's.
  *  - Scratch: a file-scope device array of 65536 doubles (512 KiB) that every
  *    GPU loading the library holds until the process exits.  Problems whose
- *    operator grid has more than 65536 thread blocks (3D n > 320) are rejected
+ *    operator grid has more than 65536 thread blocks (3D n > 640) are rejected
  *    with HELM_SCRATCH_TOO_SMALL.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  *  - The first call on a device looks up the array's device address (once per

@@ -671,7 +671,9 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
     if (dalloc(h, &h->sc, (size_t)S_NSLOTS) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
     if (dalloc(h, &h->dflag, 8) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
     if (dalloc(h, &h->counter, 4) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
-    if (dalloc(h, &h->fparts, (size_t)4 * std::max<long long>(apply_grid_blocks(dim, n), kRedBlocks)) != HELM_OK)
+    if (dalloc(h, &h->fparts,
+               (size_t)4 * std::max<long long>(std::max(apply_grid_blocks(dim, n), bicg_grid_blocks(dim, n)),
+                                               kRedBlocks)) != HELM_OK)
         return bail(HELM_OUT_OF_MEMORY);
     if (cudaMemset(h->counter, 0, 4 * sizeof(unsigned)) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (cudaMallocHost((void**)&h->hpin, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_OUT_OF_MEMORY);

@@ -90,6 +90,7 @@ template <typename R>
 void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x,
                       int conj, bool xzero, cudaStream_t s);
 int apply_grid_blocks(int dim, int n);
+int bicg_grid_blocks(int dim, int n);
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s);
 void launch_layer_k2(const Op<double>& op, double k0, double strength, const double* scale,
                      double2* k2, cudaStream_t s);

@@ -136,20 +136,85 @@ __device__ __forceinline__ double apply_point(const Op<R>& op, const typename CT
     return (double)out.x * out.x + (double)out.y * out.y;
 }
 
+// 3D operator marching in z: a block owns a 32 x 8 tile of (x, y) and walks zc
+// planes (zc chosen so that the grid still has a few blocks per SM).  The
+// z-neighbours come from registers (each plane of x is loaded once, two planes
+// ahead of its use), the x-neighbours from warp shuffles (a warp is one row of 32
+// consecutive nodes; the two row ends load from memory), the y-neighbours from L1.
+constexpr int ZC = 16;      // largest z chunk
+
+template <typename R, bool RESID, bool NORM>
+__global__ void __launch_bounds__(BX * BY) k_apply_z(Op<R> op, int zc, const typename CT<R>::T* __restrict__ x,
+                                                     const typename CT<R>::T* __restrict__ f,
+                                                     typename CT<R>::T* __restrict__ y, double* partials, int conj) {
+    using C = typename CT<R>::T;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k0 = blockIdx.z * zc;
+    const int k1 = min(op.n, k0 + zc);
+    const bool valid = i < op.n && j < op.n;
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    const int lane = threadIdx.x;
+    C zero;
+    zero.x = 0; zero.y = 0;
+    long long l = i + (long long)op.n * (j + (long long)op.n * k0);
+    C prev = (valid && k0 > 0) ? x[l - sz] : zero;
+    C cur = valid ? x[l] : zero;
+    C next = (valid && k0 + 1 < op.n) ? x[l + sz] : zero;
+    double acc = 0.0;
+    for (int k = k0; k < k1; ++k, l += sz) {
+        const C next2 = (valid && k + 2 < op.n && k + 1 < k1) ? x[l + 2 * sz] : zero;
+        const unsigned code = valid ? (unsigned)op.nbm[l] : kMasked;
+        C xm, xp;
+        xm.x = __shfl_up_sync(0xffffffffu, cur.x, 1);
+        xm.y = __shfl_up_sync(0xffffffffu, cur.y, 1);
+        xp.x = __shfl_down_sync(0xffffffffu, cur.x, 1);
+        xp.y = __shfl_down_sync(0xffffffffu, cur.y, 1);
+        if (lane == 0 && (code & 1u)) xm = x[l - 1];
+        if (lane == BX - 1 && (code & 2u)) xp = x[l + 1];
+        C out;
+        if (code & kMasked) {
+            out = cur;
+        } else {
+            const C a = (code & 1u) ? xm : zero;
+            const C b = (code & 2u) ? xp : zero;
+            const C c = (code & 4u) ? x[l - sy] : zero;
+            const C d = (code & 8u) ? x[l + sy] : zero;
+            const C e = (code & 16u) ? prev : zero;
+            const C g = (code & 32u) ? next : zero;
+            const C s = cadd(cadd(cadd(a, b), cadd(c, d)), cadd(e, g));
+            const C dg = diag_of(op, l, (int)op.lidx[l], conj);
+            out.x = op.hinv2 * s.x + (dg.x * cur.x - dg.y * cur.y);
+            out.y = op.hinv2 * s.y + (dg.x * cur.y + dg.y * cur.x);
+        }
+        if (valid) {
+            if (RESID) out = csub(f[l], out);
+            y[l] = out;
+            if (NORM) acc += (double)out.x * out.x + (double)out.y * out.y;
+        }
+        prev = cur;
+        cur = next;
+        next = next2;
+    }
+    if (NORM) {
+        block_reduce_store<R>(acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    }
+}
+
 // y = A x, or y = f - A x (resid); two z-planes per thread; optional per-block ||y||^2 partials.
 template <typename R, bool RESID, bool NORM>
-__global__ void __launch_bounds__(BX * BY) k_apply(Op<R> op, const typename CT<R>::T* __restrict__ x,
+__global__ void __launch_bounds__(BX * BY) k_apply(Op<R> op, int zc, const typename CT<R>::T* __restrict__ x,
                                                    const typename CT<R>::T* __restrict__ f,
                                                    typename CT<R>::T* __restrict__ y, double* partials,
                                                    int conj) {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
-    const int k0 = op.dim == 3 ? 2 * blockIdx.z : 0;
+    // 3D: zc planes per block (the grid of k_apply_z, so partial counts agree)
+    const int k0 = op.dim == 3 ? zc * blockIdx.z : 0;
+    const int k1 = op.dim == 3 ? min(op.n, k0 + zc) : 1;
     double acc = 0.0;
-    if (i < op.n && j < op.n) {
-        acc = apply_point<R, RESID>(op, x, f, y, conj, i, j, k0);
-        if (op.dim == 3 && k0 + 1 < op.n) acc += apply_point<R, RESID>(op, x, f, y, conj, i, j, k0 + 1);
-    }
+    if (i < op.n && j < op.n)
+        for (int kk = k0; kk < k1; ++kk) acc += apply_point<R, RESID>(op, x, f, y, conj, i, j, kk);
     if (NORM) {
         block_reduce_store<R>(acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
     }
@@ -399,21 +464,49 @@ dim3 grid_for(int dim, int n, int xdiv = 1, int zdiv = 1) {
 
 }  // namespace
 
-int apply_grid_blocks(int dim, int n) {
+int bicg_grid_blocks(int dim, int n) {
     dim3 g = grid_for(dim, n, 1, 2);
+    return g.x * g.y * g.z;
+}
+
+// z chunk of the 3D operator grid: the largest of 16, 8, 4, 2, 1 that leaves at
+// least four blocks per SM
+int apply_zc(int dim, int n) {
+    if (dim != 3) return 1;
+    const long long xy = (long long)((n + BX - 1) / BX) * ((n + BY - 1) / BY);
+    int zc = ZC;
+    while (zc > 1 && xy * ((n + zc - 1) / zc) < 4 * 152) zc /= 2;
+    return zc;
+}
+
+int apply_grid_blocks(int dim, int n) {
+    dim3 g = grid_for(dim, n, 1, apply_zc(dim, n));
     return g.x * g.y * g.z;
 }
 
 template <typename R>
 void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f,
                   typename CT<R>::T* y, double* partials, int conj, bool resid, cudaStream_t s) {
-    dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
+    const int zc = apply_zc(op.dim, op.n);
+    dim3 g = grid_for(op.dim, op.n, 1, zc), b(BX, BY);
+    if (op.dim == 3 && op.nbm && op.lidx) {
+        if (resid) {
+            if (partials) k_apply_z<R, true, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
+            else k_apply_z<R, true, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
+        } else {
+            if (partials) k_apply_z<R, false, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
+            else k_apply_z<R, false, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
+        }
+        return;
+    }
+    // 2D, or an operator without the per-node tables (the allocation-free path):
+    // the same grid, so that partial counts agree
     if (resid) {
-        if (partials) k_apply<R, true, true><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
-        else k_apply<R, true, false><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
+        if (partials) k_apply<R, true, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
+        else k_apply<R, true, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
     } else {
-        if (partials) k_apply<R, false, true><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
-        else k_apply<R, false, false><<<g, b, 0, s>>>(op, x, f, y, partials, conj);
+        if (partials) k_apply<R, false, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
+        else k_apply<R, false, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
     }
 }
 

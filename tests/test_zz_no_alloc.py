@@ -45,8 +45,8 @@ def test_noalloc_rejects_oversized_and_unmasked():
     lib = L.lib()
     dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
     p = ctypes.c_void_p(dummy.data_ptr())
-    # 3D n = 400: more operator blocks than scratch entries -> rejected before any launch
-    st = lib.helm_residual_noalloc(3, 400, 5.0, 8, 0.5, p, None, p, p, p, p, 0, None)
+    # 3D n = 700: more operator blocks than scratch entries -> rejected before any launch
+    st = lib.helm_residual_noalloc(3, 700, 5.0, 8, 0.5, p, None, p, p, p, p, 0, None)
     assert st == L.HELM_SCRATCH_TOO_SMALL
     s = small_scene(2, 33)
     m = s["mask"].copy(); m[5] = 0                       # hole in the outer ring
