@@ -179,6 +179,10 @@ def workload_config(name, w, sc, kept):
 
 
 # ------------------------------------------------------------------ GPU arm
+# the trunk-basis projection after red-black Gauss-Seidel reads the red rows only
+RED_ONLY_PROJECTION = False
+
+
 def source_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
@@ -263,7 +267,6 @@ def gpu_arm(args):
 
     for _ in range(args.warmup):
         x, st = P.solve(f, None, o)
-    P.set_profiling(True)
     stats = []
     barrier()
     with ClockSampler(local) as clk:
@@ -275,6 +278,12 @@ def gpu_arm(args):
             stats.append(st)
         barrier()
         t_wall = time.perf_counter() - t_wall0
+    # per-kernel durations: one more solve of the same workload with an event pair
+    # around every launch of the kernels of interest (kept out of the timed solves,
+    # whose time the event records would lengthen)
+    flush.fill_(1.0)
+    P.set_profiling(True)
+    _, st_prof = P.solve(f, None, o)
     P.set_profiling(False)
     solve_ms = [s["ms"] for s in stats]
     mean_ms = statistics.mean(solve_ms)
@@ -311,26 +320,68 @@ def gpu_arm(args):
         return
     st0 = stats[-1]
     iters = statistics.mean(s["iters"] for s in stats)
-    n_restrict = sum(s["n_restrict"] for s in stats)
-    restrict_ms = sum(s["restrict_ms"] for s in stats)
-    prolong_ms = sum(s["prolong_ms"] for s in stats)
-    avg_restrict_s = restrict_ms / 1e3 / max(1, n_restrict)
     N = P.N
-    # dominant kernel of the trunk-basis correction: the projection c = Q^T r, with Q
-    # stored as FP32 pairs (8 B per entry) and r complex128; FP32-pipe arithmetic, so
-    # HBM is the roofline
-    bytes_alg = 8.0 * k * N + 16.0 * N
-    flops = 24.0 * k * N
-    achieved = bytes_alg / avg_restrict_s / 1e9
+    M = (N + 1) // 2
+    fluid = int(N - int(sc.mask.astype(bool).sum()))
     hbm = peaks().get("hbm_gbs") or 6800.0
-    roofline = {"bound": "hbm", "kernel": "k_project_df (Q^T r, FP32-pair arithmetic)",
-                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks().get("hbm_gbs") else "fallback",
-                "traffic": traffic_for("k_project_df", k),
-                "algorithmic_bytes_per_launch": bytes_alg, "fp32_ops_per_launch": flops,
-                "avg_launch_us": avg_restrict_s * 1e6, "launches": n_restrict,
-                "restrict_share_of_solve": restrict_ms / sum(solve_ms),
-                "prolong_share_of_solve": prolong_ms / sum(solve_ms)}
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks().get("hbm_gbs") else "fallback"
+    # FP64 issue peak: 2 FP64 instructions per clock per SM (DADD, DMUL or DFMA), 152 SMs,
+    # at the maximum SM clock seen by the clock sampler
+    sm_mhz = (clk.summary().get("sm_max_mhz") or 2070.0)
+    fp64_peak = 2 * 152 * sm_mhz * 1e6 / 1e12
+    red_only = RED_ONLY_PROJECTION and w["relax"] == "rbgs" and w["n_r"] > 0
+
+    def phase(n_key, ms_key):
+        n = st_prof[n_key]
+        ms = st_prof[ms_key]
+        return n, ms, (ms / 1e3 / n if n else None)
+
+    kernels = []
+    # trunk-basis projection c = Q^T r: Q as FP32 pairs (8 B per entry), r complex128
+    n_, ms_, avg = phase("n_restrict", "restrict_ms")
+    rows = M if red_only else N
+    if avg:
+        b = 8.0 * k * rows + 16.0 * rows
+        kernels.append({"bound": "hbm", "kernel": "k_project_df (Q^T r%s, FP32-pair arithmetic)" % (
+                            ", red rows" if red_only else ""),
+                        "achieved": b / avg / 1e9, "peak": hbm, "unit": "GB/s", "frac": b / avg / 1e9 / hbm,
+                        "peak_source": hbm_src, "traffic": traffic_for("k_project_df", k),
+                        "algorithmic_bytes_per_launch": b, "avg_launch_us": avg * 1e6, "launches": n_,
+                        "share_of_solve": ms_ / st_prof["ms"]})
+    # prolongation z += Q y: all of Q, z read and written
+    n_, ms_, avg = phase("n_prolong", "prolong_ms")
+    if avg:
+        b = 8.0 * k * N + 32.0 * N
+        kernels.append({"bound": "hbm", "kernel": "k_prolong_df (z += Q y, FP32-pair arithmetic)",
+                        "achieved": b / avg / 1e9, "peak": hbm, "unit": "GB/s", "frac": b / avg / 1e9 / hbm,
+                        "peak_source": hbm_src, "traffic": None,
+                        "algorithmic_bytes_per_launch": b, "avg_launch_us": avg * 1e6, "launches": n_,
+                        "share_of_solve": ms_ / st_prof["ms"]})
+    # relaxation half-sweep: per updated fluid node 10 DADD (neighbour sum), 2 DFMA
+    # (f - h^-2 s) and a complex multiply (2 DMUL + 2 DFMA): 16 FP64 instructions
+    n_, ms_, avg = phase("n_sweep", "sweep_ms")
+    if avg:
+        ops = 16.0 * fluid / 2
+        kernels.append({"bound": "alu", "kernel": "k_%s (FP64 half-sweep)" % w["relax"],
+                        "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",
+                        "frac": ops / avg / 1e12 / fp64_peak,
+                        "peak_source": "2 FP64 instructions/clk/SM x 152 SMs x max SM clock",
+                        "traffic": None, "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
+                        "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
+    # BiCGStab operator with its fused reduction: 16 FP64 instructions for A x per
+    # fluid node plus 4 (<rhat, v>) or 6 (<t, s>, <t, t>): 21 on average
+    n_, ms_, avg = phase("n_apply", "apply_ms")
+    if avg:
+        ops = 21.0 * fluid
+        kernels.append({"bound": "alu", "kernel": "k_apply_bicg (FP64 A x + fused dots)",
+                        "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",
+                        "frac": ops / avg / 1e12 / fp64_peak,
+                        "peak_source": "2 FP64 instructions/clk/SM x 152 SMs x max SM clock",
+                        "traffic": None, "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
+                        "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
+    for e in kernels:
+        e["timing"] = "CUDA events around every launch, one profiled solve after the timed solves"
+    roofline = max(kernels, key=lambda e: e["share_of_solve"]) if kernels else None
     cpu = None
     if world == 1 or args.gpus == 1:
         iters_ref = reference_iterations(args.workload)
@@ -355,7 +406,7 @@ def gpu_arm(args):
         "config": cfg, "iterations": iters, "status": st0["status_name"],
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": N * 16},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
-        "roofline": roofline, "stencil": stencil, "cpu_baseline": cpu, "clocks": clocks,
+        "roofline": roofline, "kernels": kernels, "stencil": stencil, "cpu_baseline": cpu, "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)

@@ -100,6 +100,10 @@ typedef struct {
     int n_prolong;       /* trunk-basis prolongations (z += Q y) */
     double restrict_ms;  /* summed CUDA-event time of the restriction kernels (profiling on) */
     double prolong_ms;   /* summed CUDA-event time of the prolongation kernels (profiling on) */
+    int n_sweep;         /* relaxation half-sweeps that read neighbours (FP64 handles, profiling on) */
+    int n_apply;         /* operator applications of the BiCGStab loop (profiling on) */
+    double sweep_ms;     /* their summed CUDA-event time */
+    double apply_ms;     /* their summed CUDA-event time */
 } helm_stats;
 
 /* Create a problem handle.  Eq. 1 on n^dim nodes (dim 2 or 3, 3 <= n <= 2048,

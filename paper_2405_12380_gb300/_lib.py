@@ -35,7 +35,8 @@ class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("cycles", C.c_int),
                 ("precond_applies", C.c_int), ("matvecs", C.c_int), ("rel_res", C.c_double),
                 ("ms", C.c_double), ("launches", C.c_longlong), ("n_restrict", C.c_int),
-                ("n_prolong", C.c_int), ("restrict_ms", C.c_double), ("prolong_ms", C.c_double)]
+                ("n_prolong", C.c_int), ("restrict_ms", C.c_double), ("prolong_ms", C.c_double),
+                ("n_sweep", C.c_int), ("n_apply", C.c_int), ("sweep_ms", C.c_double), ("apply_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

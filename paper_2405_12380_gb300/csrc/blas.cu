@@ -210,9 +210,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_bicg_xr_fused(double2* __rest
                                                                  const double2* __restrict__ s,
                                                                  const double2* __restrict__ t,
                                                                  const double2* __restrict__ rhat, double2* sc,
-                                                                 long long N, double* parts, unsigned* counter) {
+                                                                 long long N, double* parts, unsigned* counter,
+                                                                 double tol, double bnorm) {
     const double2 alpha = sc[S_ALPHA], omega = sc[S_OMEGA];
-    const bool skip = sc[S_FLAGS].y == 1.0;
+    const bool skip = sc[S_FLAGS].y == 1.0 || sc[S_STOP].x != 0.0;
     double rn = 0;
     double2 rho = make_double2(0, 0);
     for (long long l = blockIdx.x * (long long)kFusedThreads + threadIdx.x; l < N && !skip;
@@ -241,6 +242,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_bicg_xr_fused(double2* __rest
             if (!skip) {
                 bicg_rnorm(sc, tot[0]);
                 bicg_rho_beta(sc, make_double2(tot[1], tot[2]), 3.0);
+            }
+            if (sc[S_STOP].x == 0.0) {
+                const double res = sqrt(sc[S_RN2].x) / bnorm;
+                if (sc[S_FLAGS].y != 0.0 || !isfinite(res) || res <= tol) sc[S_STOP].x = 1.0;
             }
             *counter = 0;
         }
@@ -299,6 +304,7 @@ __global__ void __launch_bounds__(kFinThreads) k_bicg_scalar(int recipe, const d
         sc[S_ALPHA] = make_double2(1, 0);
         sc[S_OMEGA] = make_double2(1, 0);
         sc[S_FLAGS] = make_double2(0, 0);
+        sc[S_STOP] = make_double2(0, 0);
     }
 }
 
@@ -513,8 +519,9 @@ void launch_bicg_s_fused(const double2* r, const double2* v, double2* sv, double
 }
 void launch_bicg_xr_fused(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
                           const double2* t, const double2* rhat, double2* sc, long long N, double* parts,
-                          unsigned* counter, cudaStream_t s) {
-    k_bicg_xr_fused<<<kRedBlocks, kFusedThreads, 0, s>>>(x, r, phat, shat, sv, t, rhat, sc, N, parts, counter);
+                          unsigned* counter, double tol, double bnorm, cudaStream_t s) {
+    k_bicg_xr_fused<<<kRedBlocks, kFusedThreads, 0, s>>>(x, r, phat, shat, sv, t, rhat, sc, N, parts, counter, tol,
+                                                         bnorm);
 }
 void launch_bicg_scalar(int recipe, const double* partials, int nparts, double2* sc, double tol_abs,
                         cudaStream_t s) {

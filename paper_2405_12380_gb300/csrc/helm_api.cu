@@ -93,8 +93,8 @@ double hs(const helm_handle* h, int slot, int im = 0) { return h->hpin[2 * slot 
 
 // ||f - A x||^2 into slot (FP64)
 helm_status residual_norm(helm_handle* h, const double2* f, const double2* x, double2* r, int conj, int slot) {
-    launch_apply<double>(h->op64, x, f, r, h->red, conj, true, h->stream);
-    launch_sum_real(h->red, apply_grid_blocks(h->dim, h->n), scal(h, slot), h->stream);
+    const int nb = launch_apply<double>(h->op64, x, f, r, h->red, conj, true, h->stream);
+    launch_sum_real(h->red, nb, scal(h, slot), h->stream);
     h->launches += 2;
     CKL();
     return HELM_OK;
@@ -108,42 +108,7 @@ helm_status norm2_into(helm_handle* h, const double2* a, int slot) {
     return HELM_OK;
 }
 
-// z = n sweeps of the relaxation on A z = r from z = 0 (FP64)
-helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, const double2* r, double2* z,
-                            int conj) {
-    cudaStream_t s = h->stream;
-    if (kind == HELM_RELAX_NONE || sweeps <= 0) {
-        CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
-        return HELM_OK;
-    }
-    if (kind == HELM_JACOBI) {
-        TRY(ensure_tmp(h, 1));
-        // sweep 1 from zero writes z; later sweeps ping-pong so that the last lands in z
-        double2* a = (sweeps % 2 == 1) ? z : h->tmp[0];
-        double2* b = (sweeps % 2 == 1) ? h->tmp[0] : z;
-        launch_jacobi<double>(h->op64, omega, r, nullptr, a, conj, true, s);
-        for (int q = 1; q < sweeps; ++q) {
-            launch_jacobi<double>(h->op64, omega, r, a, b, conj, false, s);
-            std::swap(a, b);
-        }
-        h->launches += sweeps;
-        CKL();
-        return HELM_OK;
-    }
-    if (kind == HELM_RBGS) {
-        CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
-        for (int q = 0; q < sweeps; ++q) {
-            launch_rbgs_half<double>(h->op64, 0, r, z, conj, q == 0, s);
-            launch_rbgs_half<double>(h->op64, 1, r, z, conj, false, s);
-        }
-        h->launches += 2 * sweeps;
-        CKL();
-        return HELM_OK;
-    }
-    return fail(h, HELM_BAD_ARG, "unknown relaxation kind");
-}
-
-// event pair around one launch of phase ph (0 = restrict, 1 = prolong)
+// event pair around one launch of phase ph (0 restrict, 1 prolong, 2 sweep, 3 operator)
 void ev_mark(helm_handle* h, int ph, int end) {
     if (!h->profile) return;
     auto& pool = h->evpool[ph];
@@ -165,6 +130,47 @@ double ev_sum(helm_handle* h, int ph) {
         t += ms;
     }
     return t;
+}
+
+// z = n sweeps of the relaxation on A z = r from z = 0 (FP64)
+helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, const double2* r, double2* z,
+                            int conj) {
+    cudaStream_t s = h->stream;
+    if (kind == HELM_RELAX_NONE || sweeps <= 0) {
+        CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
+        return HELM_OK;
+    }
+    if (kind == HELM_JACOBI) {
+        TRY(ensure_tmp(h, 1));
+        // sweep 1 from zero writes z; later sweeps ping-pong so that the last lands in z
+        double2* a = (sweeps % 2 == 1) ? z : h->tmp[0];
+        double2* b = (sweeps % 2 == 1) ? h->tmp[0] : z;
+        launch_jacobi<double>(h->op64, omega, r, nullptr, a, conj, true, s);
+        for (int q = 1; q < sweeps; ++q) {
+            ev_mark(h, 2, 0);
+            launch_jacobi<double>(h->op64, omega, r, a, b, conj, false, s);
+            ev_mark(h, 2, 1);
+            std::swap(a, b);
+        }
+        h->launches += sweeps;
+        CKL();
+        return HELM_OK;
+    }
+    if (kind == HELM_RBGS) {
+        CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
+        for (int q = 0; q < sweeps; ++q) {
+            if (q > 0) ev_mark(h, 2, 0);
+            launch_rbgs_half<double>(h->op64, 0, r, z, conj, q == 0, s);
+            if (q > 0) ev_mark(h, 2, 1);
+            ev_mark(h, 2, 0);
+            launch_rbgs_half<double>(h->op64, 1, r, z, conj, false, s);
+            ev_mark(h, 2, 1);
+        }
+        h->launches += 2 * sweeps;
+        CKL();
+        return HELM_OK;
+    }
+    return fail(h, HELM_BAD_ARG, "unknown relaxation kind");
 }
 
 // z += Q A_c^-1 Q^T (v - A zres)   (zres may be null: plain restriction of v)
@@ -519,27 +525,59 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
     st->status = HELM_NOT_CONVERGED;
     // one iteration: p update, M p, v = A p with alpha, s with ||s||, M s, t = A s with
     // omega, x/r update with ||r|| and the next rho/beta -- each reduction and its scalar
-    // recurrence fused into the kernel that produces the vector
-    while (iters < o->maxit) {
+    // recurrence fused into the kernel that produces the vector.  The iteration ends by
+    // copying the scalars into one of two pinned snapshots.
+    auto launch_iter = [&](int slot) -> helm_status {
         launch_bicg_update_p(r, v, p, h->sc, N, s);
         TRY(precond(h, o, p, ph, o->conj));
+        ev_mark(h, 3, 0);
         launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
+        ev_mark(h, 3, 1);
         launch_bicg_s_fused(r, v, sv, h->sc, N, h->fparts, h->counter, tol_abs, s);
         TRY(precond(h, o, sv, sh, o->conj));
+        ev_mark(h, 3, 0);
         launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
-        launch_bicg_xr_fused(x, r, ph, sh, sv, t, rh, h->sc, N, h->fparts, h->counter, s);
+        ev_mark(h, 3, 1);
+        launch_bicg_xr_fused(x, r, ph, sh, sv, t, rh, h->sc, N, h->fparts, h->counter, o->tol, bnorm, s);
         h->launches += 5;
+        CK(cudaMemcpyAsync(h->hring + 2 * S_NSLOTS * slot, h->sc, S_NSLOTS * sizeof(double2),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(h->evring[slot], s));
         CKL();
+        return HELM_OK;
+    };
+    // Lagged polling: iteration i + 1 is queued before the host waits for the scalars
+    // of iteration i, so the GPU does not idle while the host decides.  When iteration
+    // i ends the loop, its x/r kernel has set S_STOP on the device and the queued
+    // iteration leaves x and r untouched (its other outputs are scratch), so the state
+    // is exactly that of iteration i.
+    int inflight = 0, head = 0;   // queued but unread iterations; slot of the oldest
+    while (true) {
+        if (inflight == 0) {
+            if (iters >= o->maxit) break;
+            TRY(launch_iter(head));
+            inflight = 1;
+        }
+        if (inflight == 1 && iters + 1 < o->maxit) {
+            TRY(launch_iter(head ^ 1));
+            inflight = 2;
+        }
+        CK(cudaEventSynchronize(h->evring[head]));
+        const double* snap = h->hring + 2 * S_NSLOTS * head;
+        head ^= 1;
+        --inflight;
         st->precond_applies += 2;
         st->matvecs += 2;
         ++iters;
-        TRY(poll(h));
-        const double brk = hs(h, S_FLAGS, 1);
+        const double brk = snap[2 * S_FLAGS + 1];
         if (brk == 1.0) { st->status = HELM_BREAKDOWN; break; }
-        res = std::sqrt(hs(h, S_RN2)) / bnorm;
+        res = std::sqrt(snap[2 * S_RN2]) / bnorm;
         hist.push(res);
         if (!std::isfinite(res)) { st->status = HELM_DIVERGED; break; }
         if (res <= o->tol) {
+            // any queued iteration is a no-op on x and r; drop it
+            inflight = 0;
+            head = 0;
             TRY(residual_norm(h, f, x, r, o->conj, S_RN2));
             ++st->matvecs;
             TRY(poll(h));
@@ -677,6 +715,10 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
         return bail(HELM_OUT_OF_MEMORY);
     if (cudaMemset(h->counter, 0, 4 * sizeof(unsigned)) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (cudaMallocHost((void**)&h->hpin, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_OUT_OF_MEMORY);
+    if (cudaMallocHost((void**)&h->hring, 2 * sizeof(double2) * S_NSLOTS) != cudaSuccess)
+        return bail(HELM_OUT_OF_MEMORY);
+    for (auto& e : h->evring)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (cudaMemset(h->sc, 0, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_CUDA_ERROR);
     if (k2) {
         if (dalloc(h, &h->k2, (size_t)N) != HELM_OK || dalloc(h, &h->invd, (size_t)N) != HELM_OK ||
@@ -712,6 +754,9 @@ helm_status helm_destroy(helm_handle* h) {
     dfree(h->mask); dfree(h->lidx); dfree(h->nbm); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
     dfree(h->red); dfree(h->sc); dfree(h->dflag); dfree(h->counter); dfree(h->fparts);
     if (h->hpin) cudaFreeHost(h->hpin);
+    if (h->hring) cudaFreeHost(h->hring);
+    for (auto e : h->evring)
+        if (e) cudaEventDestroy(e);
     for (auto p : h->tmp) cudaFree(p);
     for (auto p : h->tmp32) cudaFree(p);
     dfree(h->Q); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
@@ -779,13 +824,16 @@ helm_status helm_residual(helm_handle* h, const void* f, const void* x, void* r,
                           int dtype) {
     if (!h || !f || !x || !r) return fail(h, HELM_BAD_ARG, "null argument");
     double* part = norm2 ? h->red : nullptr;
+    int nb = 0;
     if (dtype == HELM_C128)
-        launch_apply<double>(h->op64, (const double2*)x, (const double2*)f, (double2*)r, part, conj, true, h->stream);
+        nb = launch_apply<double>(h->op64, (const double2*)x, (const double2*)f, (double2*)r, part, conj, true,
+                                  h->stream);
     else if (dtype == HELM_C64)
-        launch_apply<float>(h->op32, (const float2*)x, (const float2*)f, (float2*)r, part, conj, true, h->stream);
+        nb = launch_apply<float>(h->op32, (const float2*)x, (const float2*)f, (float2*)r, part, conj, true,
+                                 h->stream);
     else
         return fail(h, HELM_BAD_ARG, "dtype");
-    if (norm2) launch_sum_real(h->red, apply_grid_blocks(h->dim, h->n), norm2, h->stream);
+    if (norm2) launch_sum_real(h->red, nb, norm2, h->stream);
     CKL();
     return HELM_OK;
 }
@@ -1042,7 +1090,7 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     st.status = HELM_NOT_CONVERGED;
     Hist hist{res_hist, hist_len};
     h->launches = 0;
-    h->evn[0] = h->evn[1] = 0;
+    for (int& e : h->evn) e = 0;
     CK(cudaEventRecord(h->ev0, h->stream));
     launch_set_masked(x, f, h->mask, h->N, h->stream);
     h->launches += 1;
@@ -1070,6 +1118,10 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     st.n_prolong = h->evn[1];
     st.restrict_ms = h->profile ? ev_sum(h, 0) : 0.0;
     st.prolong_ms = h->profile ? ev_sum(h, 1) : 0.0;
+    st.n_sweep = h->evn[2];
+    st.sweep_ms = h->profile ? ev_sum(h, 2) : 0.0;
+    st.n_apply = h->evn[3];
+    st.apply_ms = h->profile ? ev_sum(h, 3) : 0.0;
     if (stats) *stats = st;
     return (helm_status)st.status;
 }

@@ -74,14 +74,17 @@ struct Op {
 
 // device scalar slots of the Krylov drivers (double2 each, in helm_handle::sc)
 enum { S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_SN2, S_RN2, S_FLAGS, S_TS, S_TT,
-       S_BETA2, S_WN2, S_EST, S_BN2, S_NSLOTS };
+       S_BETA2, S_WN2, S_EST, S_BN2, S_STOP, S_NSLOTS };
 // S_FLAGS.x = 1: ||s|| met the tolerance this iteration; S_FLAGS.y = 1: breakdown
+// S_STOP.x = 1: the BiCGStab iteration that set it ended the loop (converged, broke
+// down or diverged); later x/r updates are no-ops until the next reset
 
 // ------------------------------------------------------------ kernel launchers
 // stencil.cu
+// returns the number of per-block partial sums written to `partials` (when given)
 template <typename R>
-void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f,
-                  typename CT<R>::T* y, double* partials, int conj, bool resid, cudaStream_t s);
+int launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f,
+                 typename CT<R>::T* y, double* partials, int conj, bool resid, cudaStream_t s);
 template <typename R>
 void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f,
                    const typename CT<R>::T* xin, typename CT<R>::T* xout, int conj, bool xzero,
@@ -103,9 +106,11 @@ void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2
                        double2* sc, double* parts, unsigned* counter, cudaStream_t s);
 void launch_bicg_s_fused(const double2* r, const double2* v, double2* sv, double2* sc, long long N, double* parts,
                          unsigned* counter, double tol_abs, cudaStream_t s);
+// x/r update; its last block also decides S_STOP from ||r|| / bnorm <= tol, a
+// breakdown flag or a non-finite residual (the host's test, evaluated identically)
 void launch_bicg_xr_fused(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
                           const double2* t, const double2* rhat, double2* sc, long long N, double* parts,
-                          unsigned* counter, cudaStream_t s);
+                          unsigned* counter, double tol, double bnorm, cudaStream_t s);
 
 // blas.cu
 // partial reductions over a fixed grid of kRedBlocks blocks
@@ -216,6 +221,8 @@ struct helm_handle {
     long long red_len = 0;
     double2* sc = nullptr;          // device scalars (BiCGStab/FGMRES)
     double* hpin = nullptr;         // pinned host mirror for status polling
+    double* hring = nullptr;        // two pinned snapshots of the scalars (lagged BiCGStab polling)
+    cudaEvent_t evring[2] = {nullptr, nullptr};
     int* dflag = nullptr;           // device int flags
     unsigned* counter = nullptr;    // block counter of the fused reductions (zero between kernels)
     double* fparts = nullptr;       // partials of the fused reductions
@@ -257,6 +264,8 @@ struct helm_handle {
     // launch accounting and per-kernel event timing (helm_set_profiling)
     int profile = 0;
     long long launches = 0;
-    std::vector<cudaEvent_t> evpool[2];
-    int evn[2] = {0, 0};
+    // phases: 0 restriction, 1 prolongation, 2 relaxation half-sweeps that read
+    // neighbours, 3 operator applications of the Krylov loop
+    std::vector<cudaEvent_t> evpool[4];
+    int evn[4] = {0, 0, 0, 0};
 };

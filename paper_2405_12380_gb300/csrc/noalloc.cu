@@ -93,9 +93,9 @@ extern "C" helm_status helm_residual_noalloc(int dim, int n, double k0, int laye
         return HELM_CUDA_ERROR;
     if (bad) return HELM_BAD_ARG;
     // every block writes its own partial, so the scratch needs no clearing
-    launch_apply<double>(op, reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(f),
-                         reinterpret_cast<double2*>(r), scratch, conj, true, s);
-    launch_sum_real(scratch, apply_grid_blocks(dim, n), norm2, s);
+    const int nb = launch_apply<double>(op, reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(f),
+                                        reinterpret_cast<double2*>(r), scratch, conj, true, s);
+    launch_sum_real(scratch, nb, norm2, s);
     if (cudaGetLastError() != cudaSuccess) return HELM_CUDA_ERROR;
     return HELM_OK;
 }

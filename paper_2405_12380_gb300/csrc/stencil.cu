@@ -5,6 +5,10 @@
 // from the tables in Op (or the stored field).  FP64 is the scarce pipe on
 // GB300, so per node the operator costs 2d complex adds, one scale and one
 // complex multiply-add, and the sweeps multiply by a tabulated reciprocal.
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
 #include "bicg.cuh"
 #include "helm_internal.cuh"
 
@@ -161,10 +165,16 @@ __global__ void __launch_bounds__(BX * BY) k_apply_z(Op<R> op, int zc, const typ
     C prev = (valid && k0 > 0) ? x[l - sz] : zero;
     C cur = valid ? x[l] : zero;
     C next = (valid && k0 + 1 < op.n) ? x[l + sz] : zero;
+    // the per-node tables are read one plane ahead as well, so that no load of
+    // the loop is used in the iteration that issues it
+    unsigned code = valid ? (unsigned)op.nbm[l] : kMasked;
+    int li = valid ? (int)op.lidx[l] : 0;
     double acc = 0.0;
     for (int k = k0; k < k1; ++k, l += sz) {
-        const C next2 = (valid && k + 2 < op.n && k + 1 < k1) ? x[l + 2 * sz] : zero;
-        const unsigned code = valid ? (unsigned)op.nbm[l] : kMasked;
+        const bool more = valid && k + 1 < k1;
+        const C next2 = (more && k + 2 < op.n) ? x[l + 2 * sz] : zero;
+        const unsigned code_n = more ? (unsigned)op.nbm[l + sz] : kMasked;
+        const int li_n = more ? (int)op.lidx[l + sz] : 0;
         C xm, xp;
         xm.x = __shfl_up_sync(0xffffffffu, cur.x, 1);
         xm.y = __shfl_up_sync(0xffffffffu, cur.y, 1);
@@ -183,7 +193,7 @@ __global__ void __launch_bounds__(BX * BY) k_apply_z(Op<R> op, int zc, const typ
             const C e = (code & 16u) ? prev : zero;
             const C g = (code & 32u) ? next : zero;
             const C s = cadd(cadd(cadd(a, b), cadd(c, d)), cadd(e, g));
-            const C dg = diag_of(op, l, (int)op.lidx[l], conj);
+            const C dg = diag_of(op, l, li, conj);
             out.x = op.hinv2 * s.x + (dg.x * cur.x - dg.y * cur.y);
             out.y = op.hinv2 * s.y + (dg.x * cur.y + dg.y * cur.x);
         }
@@ -195,9 +205,166 @@ __global__ void __launch_bounds__(BX * BY) k_apply_z(Op<R> op, int zc, const typ
         prev = cur;
         cur = next;
         next = next2;
+        code = code_n;
+        li = li_n;
     }
     if (NORM) {
         block_reduce_store<R>(acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    }
+}
+
+// ---- complex64 in 3D: two consecutive x-nodes per thread, so that every vector
+// access is one 16-byte load or store and a warp covers 64 nodes of a row.  Needs
+// n even (every row starts on a 16-byte boundary) and 16-byte aligned vectors; the
+// per-node tables are read as byte pairs.  Marches in z like k_apply_z, with the
+// right-hand side prefetched one plane ahead too.  A pair whose two nodes have
+// all six neighbours fluid (the common case) takes no selects.
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 pick(unsigned c, unsigned bit, float2 v) {
+    return (c & bit) ? v : make_float2(0.f, 0.f);
+}
+
+// neighbour sums of the two nodes of a pair (same summation tree as k_apply_z)
+__device__ __forceinline__ void pair_sums(unsigned c0, unsigned c1, float2 left, float2 right, float4 cur,
+                                          float4 ym, float4 yp, float4 zm, float4 zp, float2& s0, float2& s1) {
+    if ((c0 & c1) == 0x3Fu) {
+        s0 = cadd(cadd(cadd(left, hi2(cur)), cadd(lo2(ym), lo2(yp))), cadd(lo2(zm), lo2(zp)));
+        s1 = cadd(cadd(cadd(lo2(cur), right), cadd(hi2(ym), hi2(yp))), cadd(hi2(zm), hi2(zp)));
+    } else {
+        s0 = cadd(cadd(cadd(pick(c0, 1u, left), pick(c0, 2u, hi2(cur))),
+                       cadd(pick(c0, 4u, lo2(ym)), pick(c0, 8u, lo2(yp)))),
+                  cadd(pick(c0, 16u, lo2(zm)), pick(c0, 32u, lo2(zp))));
+        s1 = cadd(cadd(cadd(pick(c1, 1u, lo2(cur)), pick(c1, 2u, right)),
+                       cadd(pick(c1, 4u, hi2(ym)), pick(c1, 8u, hi2(yp)))),
+                  cadd(pick(c1, 16u, hi2(zm)), pick(c1, 32u, hi2(zp))));
+    }
+}
+
+// KIND 0: y = A x (FLAG: y = f - A x); KIND 1: damped-Jacobi sweep y = x + omega
+// D^-1 (f - A x) (FLAG: from x = 0, x not read)
+template <int KIND, bool FLAG, bool NORM>
+__global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, float omega,
+                                                       const float4* __restrict__ x, const float4* __restrict__ f,
+                                                       float4* __restrict__ y, double* partials, int conj) {
+    constexpr bool NBR = !(KIND == 1 && FLAG);             // neighbours (and x) are read
+    constexpr bool RHS = KIND == 1 || FLAG;                // f is read
+    constexpr unsigned kMM = kMasked | (kMasked << 8);
+    const int n = op.n, h = n >> 1;
+    const int i2 = blockIdx.x * BX + threadIdx.x;          // pair index within the row
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k0 = blockIdx.z * zc;
+    const int k1 = min(n, k0 + zc);
+    const bool valid = i2 < h && j < n;
+    const int sy = h, sz = h * n;                          // strides in pairs (N < 2^31)
+    const int lane = threadIdx.x;
+    const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
+    const unsigned short* lidx2 = reinterpret_cast<const unsigned short*>(op.lidx);
+    const float2* x1 = reinterpret_cast<const float2*>(x);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int l = i2 + h * (j + n * k0);
+    float4 prev = z4, cur = z4, next = z4, fv = z4;
+    if (NBR) {
+        prev = (valid && k0 > 0) ? x[l - sz] : z4;
+        cur = valid ? x[l] : z4;
+        next = (valid && k0 + 1 < n) ? x[l + sz] : z4;
+    }
+    if (RHS) fv = valid ? f[l] : z4;
+    unsigned cc = valid ? (unsigned)code2[l] : kMM;
+    unsigned li = valid ? (unsigned)lidx2[l] : 0u;
+    float acc = 0.f;
+    for (int k = k0; k < k1; ++k, l += sz) {
+        const bool more = valid && k + 1 < k1;
+        float4 next2 = z4, f_n = z4;
+        if (NBR) next2 = (more && k + 2 < n) ? x[l + 2 * sz] : z4;
+        if (RHS) f_n = more ? f[l + sz] : z4;
+        const unsigned cc_n = more ? (unsigned)code2[l + sz] : kMM;
+        const unsigned li_n = more ? (unsigned)lidx2[l + sz] : 0u;
+        const unsigned c0 = cc & 0xffu, c1 = cc >> 8;
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+        if (NBR) {
+            float2 left, right;
+            left.x = __shfl_up_sync(0xffffffffu, cur.z, 1);
+            left.y = __shfl_up_sync(0xffffffffu, cur.w, 1);
+            right.x = __shfl_down_sync(0xffffffffu, cur.x, 1);
+            right.y = __shfl_down_sync(0xffffffffu, cur.y, 1);
+            // the row-segment ends: node i-1 of lane 0 and node i+2 of the last lane
+            // (fluid nodes are interior, so these exist whenever the bit is set)
+            if (lane == 0 && (c0 & 1u)) left = x1[2 * l - 1];
+            if (lane == BX - 1 && (c1 & 2u)) right = x1[2 * l + 2];
+            const unsigned any = c0 | c1;                  // a masked code has no neighbour bits
+            const float4 ym = (any & 4u) ? x[l - sy] : z4;
+            const float4 yp = (any & 8u) ? x[l + sy] : z4;
+            pair_sums(c0, c1, left, right, cur, ym, yp, prev, next, s0, s1);
+        }
+        float2 o0, o1;
+        if (KIND == 0) {
+            float2 d0, d1;
+            if (op.k2) {
+                const float4 kk = reinterpret_cast<const float4*>(op.k2)[l];
+                d0 = make_float2(kk.x - 6.f * op.hinv2, kk.y);
+                d1 = make_float2(kk.z - 6.f * op.hinv2, kk.w);
+            } else {
+                d0 = make_float2(op.dre, op.im[li & 0xffu]);
+                d1 = make_float2(op.dre, op.im[li >> 8]);
+            }
+            if (conj) { d0.y = -d0.y; d1.y = -d1.y; }
+            const float2 x0 = lo2(cur), xh = hi2(cur);
+            o0 = (c0 & kMasked) ? x0
+                                : make_float2(op.hinv2 * s0.x + (d0.x * x0.x - d0.y * x0.y),
+                                              op.hinv2 * s0.y + (d0.x * x0.y + d0.y * x0.x));
+            o1 = (c1 & kMasked) ? xh
+                                : make_float2(op.hinv2 * s1.x + (d1.x * xh.x - d1.y * xh.y),
+                                              op.hinv2 * s1.y + (d1.x * xh.y + d1.y * xh.x));
+            if (FLAG) {
+                o0 = csub(lo2(fv), o0);
+                o1 = csub(hi2(fv), o1);
+            }
+        } else {
+            float2 id0, id1;
+            if (op.k2) {
+                const float4 iv = reinterpret_cast<const float4*>(op.invd)[l];
+                id0 = lo2(iv);
+                id1 = hi2(iv);
+            } else {
+                id0 = op.invd_tab[li & 0xffu];
+                id1 = op.invd_tab[li >> 8];
+            }
+            if (conj) { id0.y = -id0.y; id1.y = -id1.y; }
+            const float2 f0 = lo2(fv), fh = hi2(fv);
+            if (FLAG) {
+                o0 = cscale(omega, (c0 & kMasked) ? f0 : cmul(id0, f0));
+                o1 = cscale(omega, (c1 & kMasked) ? fh : cmul(id1, fh));
+            } else {
+                const float w1 = 1.f - omega;
+                const float2 x0 = lo2(cur), xh = hi2(cur);
+                if (c0 & kMasked) {
+                    o0 = cadd(x0, cscale(omega, csub(f0, x0)));
+                } else {
+                    const float2 t = cmul(id0, make_float2(f0.x - op.hinv2 * s0.x, f0.y - op.hinv2 * s0.y));
+                    o0 = make_float2(w1 * x0.x + omega * t.x, w1 * x0.y + omega * t.y);
+                }
+                if (c1 & kMasked) {
+                    o1 = cadd(xh, cscale(omega, csub(fh, xh)));
+                } else {
+                    const float2 t = cmul(id1, make_float2(fh.x - op.hinv2 * s1.x, fh.y - op.hinv2 * s1.y));
+                    o1 = make_float2(w1 * xh.x + omega * t.x, w1 * xh.y + omega * t.y);
+                }
+            }
+        }
+        if (valid) {
+            y[l] = make_float4(o0.x, o0.y, o1.x, o1.y);
+            if (NORM) acc += (o0.x * o0.x + o0.y * o0.y) + (o1.x * o1.x + o1.y * o1.y);
+        }
+        prev = cur;
+        cur = next;
+        next = next2;
+        fv = f_n;
+        cc = cc_n;
+        li = li_n;
+    }
+    if (NORM) {
+        block_reduce_store<float>((double)acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
     }
 }
 
@@ -469,24 +636,67 @@ int bicg_grid_blocks(int dim, int n) {
     return g.x * g.y * g.z;
 }
 
-// z chunk of the 3D operator grid: the largest of 16, 8, 4, 2, 1 that leaves at
-// least four blocks per SM
-int apply_zc(int dim, int n) {
-    if (dim != 3) return 1;
-    const long long xy = (long long)((n + BX - 1) / BX) * ((n + BY - 1) / BY);
+// z chunk of a 3D marching grid with xy blocks per plane: the largest of 16, 8,
+// 4, 2, 1 that leaves at least four blocks per SM
+int march_zc(long long xy, int n) {
     int zc = ZC;
     while (zc > 1 && xy * ((n + zc - 1) / zc) < 4 * 152) zc /= 2;
     return zc;
 }
 
+int apply_zc(int dim, int n) {
+    if (dim != 3) return 1;
+    return march_zc((long long)((n + BX - 1) / BX) * ((n + BY - 1) / BY), n);
+}
+
+// grid of the two-nodes-per-thread complex64 kernels
+dim3 pair_grid(int n, int* zc) {
+    const int h = n / 2;
+    const int gx = (h + BX - 1) / BX, gy = (n + BY - 1) / BY;
+    *zc = march_zc((long long)gx * gy, n);
+    return dim3(gx, gy, (n + *zc - 1) / *zc);
+}
+
+bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// the complex64 pair kernels apply: 3D, tables present, n even, 16-byte aligned vectors
+bool pair_ok(const Op<float>& op, const void* a, const void* b, const void* c) {
+    return op.dim == 3 && op.nbm && op.lidx && (op.n % 2) == 0 && aligned16(a) && aligned16(b) && aligned16(c) &&
+           aligned16(op.k2) && aligned16(op.invd);
+}
+
+// an upper bound on the partial sums any operator launch writes (buffer sizing)
 int apply_grid_blocks(int dim, int n) {
     dim3 g = grid_for(dim, n, 1, apply_zc(dim, n));
-    return g.x * g.y * g.z;
+    long long b = (long long)g.x * g.y * g.z;
+    if (dim == 3 && n % 2 == 0) {
+        int zc;
+        dim3 p = pair_grid(n, &zc);
+        b = std::max(b, (long long)p.x * p.y * p.z);
+    }
+    return (int)b;
 }
 
 template <typename R>
-void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f,
-                  typename CT<R>::T* y, double* partials, int conj, bool resid, cudaStream_t s) {
+int launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<R>::T* f, typename CT<R>::T* y,
+                 double* partials, int conj, bool resid, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (pair_ok(op, x, resid ? f : nullptr, y)) {
+            int zc;
+            const dim3 g = pair_grid(op.n, &zc), b(BX, BY);
+            const float4* x4 = reinterpret_cast<const float4*>(x);
+            const float4* f4 = reinterpret_cast<const float4*>(f);
+            float4* y4 = reinterpret_cast<float4*>(y);
+            if (resid) {
+                if (partials) k_march_c64<0, true, true><<<g, b, 0, s>>>(op, zc, 0.f, x4, f4, y4, partials, conj);
+                else k_march_c64<0, true, false><<<g, b, 0, s>>>(op, zc, 0.f, x4, f4, y4, partials, conj);
+            } else {
+                if (partials) k_march_c64<0, false, true><<<g, b, 0, s>>>(op, zc, 0.f, x4, f4, y4, partials, conj);
+                else k_march_c64<0, false, false><<<g, b, 0, s>>>(op, zc, 0.f, x4, f4, y4, partials, conj);
+            }
+            return (int)(g.x * g.y * g.z);
+        }
+    }
     const int zc = apply_zc(op.dim, op.n);
     dim3 g = grid_for(op.dim, op.n, 1, zc), b(BX, BY);
     if (op.dim == 3 && op.nbm && op.lidx) {
@@ -497,10 +707,9 @@ void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT
             if (partials) k_apply_z<R, false, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
             else k_apply_z<R, false, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
         }
-        return;
+        return (int)(g.x * g.y * g.z);
     }
-    // 2D, or an operator without the per-node tables (the allocation-free path):
-    // the same grid, so that partial counts agree
+    // 2D, or an operator without the per-node tables (the allocation-free path)
     if (resid) {
         if (partials) k_apply<R, true, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
         else k_apply<R, true, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
@@ -508,11 +717,24 @@ void launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT
         if (partials) k_apply<R, false, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
         else k_apply<R, false, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
     }
+    return (int)(g.x * g.y * g.z);
 }
 
 template <typename R>
 void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f, const typename CT<R>::T* xin,
                    typename CT<R>::T* xout, int conj, bool xzero, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (pair_ok(op, f, xzero ? nullptr : xin, xout)) {
+            int zc;
+            const dim3 g = pair_grid(op.n, &zc), b(BX, BY);
+            const float4* x4 = reinterpret_cast<const float4*>(xin);
+            const float4* f4 = reinterpret_cast<const float4*>(f);
+            float4* y4 = reinterpret_cast<float4*>(xout);
+            if (xzero) k_march_c64<1, true, false><<<g, b, 0, s>>>(op, zc, (float)omega, x4, f4, y4, nullptr, conj);
+            else k_march_c64<1, false, false><<<g, b, 0, s>>>(op, zc, (float)omega, x4, f4, y4, nullptr, conj);
+            return;
+        }
+    }
     dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
     if (xzero) k_jacobi<R, true><<<g, b, 0, s>>>(op, (R)omega, f, xin, xout, conj);
     else k_jacobi<R, false><<<g, b, 0, s>>>(op, (R)omega, f, xin, xout, conj);
@@ -533,10 +755,10 @@ void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2
     else k_apply_bicg<2><<<g, b, 0, s>>>(op, x, y, w, conj, sc, parts, counter);
 }
 
-template void launch_apply<double>(const Op<double>&, const double2*, const double2*, double2*, double*, int,
-                                   bool, cudaStream_t);
-template void launch_apply<float>(const Op<float>&, const float2*, const float2*, float2*, double*, int, bool,
-                                  cudaStream_t);
+template int launch_apply<double>(const Op<double>&, const double2*, const double2*, double2*, double*, int,
+                                  bool, cudaStream_t);
+template int launch_apply<float>(const Op<float>&, const float2*, const float2*, float2*, double*, int, bool,
+                                 cudaStream_t);
 template void launch_jacobi<double>(const Op<double>&, double, const double2*, const double2*, double2*, int,
                                     bool, cudaStream_t);
 template void launch_jacobi<float>(const Op<float>&, double, const float2*, const float2*, float2*, int, bool,
