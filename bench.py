@@ -180,7 +180,7 @@ def workload_config(name, w, sc, kept):
 
 # ------------------------------------------------------------------ GPU arm
 # the trunk-basis projection after red-black Gauss-Seidel reads the red rows only
-RED_ONLY_PROJECTION = False
+RED_ONLY_PROJECTION = True
 
 
 def source_hash(path):

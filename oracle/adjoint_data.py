@@ -4,7 +4,7 @@ d = S u0, where u0 solves the unperturbed problem (k^2 from the layer formula,
 no bumps) of scenes.bump_cube3d, computed by the oracle's BiCGStab with three
 red-black Gauss-Seidel sweeps per iteration to a relative residual of 1e-10,
 and S samples the 256 receivers trilinearly.  Writes
-oracle/adjoint_d_<name>.npz.  Test/bench infrastructure: calls only the oracle
+tests/golden/adjoint_d_<name>.npz.  Test/bench infrastructure: calls only the oracle
 and the input generators.
 
     python -m oracle.adjoint_data [n]
@@ -34,7 +34,7 @@ def make(n: int = 96, seed: int = 0, tol: float = 1e-10):
     u0, info = krylov.bicgstab(A, b, np.zeros_like(b), M, tol, 20000)
     S = adjoint.trilinear(n, sc.extra["receivers"])
     d = S @ u0
-    out = os.path.join(HERE, f"adjoint_d_bump_cube3d-{n}.npz")
+    out = os.path.join(os.path.dirname(HERE), "tests", "golden", f"adjoint_d_bump_cube3d-{n}.npz")
     np.savez(out, d=d, iters=info["iters"], status=info["status"], rel_res=info["res"][-1],
              seconds=time.perf_counter() - t0)
     print(out, info["status"], info["iters"], info["res"][-1], flush=True)

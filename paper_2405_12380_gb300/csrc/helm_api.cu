@@ -173,24 +173,31 @@ helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, 
     return fail(h, HELM_BAD_ARG, "unknown relaxation kind");
 }
 
-// z += Q A_c^-1 Q^T (v - A zres)   (zres may be null: plain restriction of v)
-helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, double2* z, int conj) {
+// z += Q A_c^-1 Q^T (v - A zres)   (zres may be null: plain restriction of v).
+// black_zero: zres is the result of red-black Gauss-Seidel sweeps ending with the
+// black half-sweep, so v - A zres vanishes on black and masked nodes (each black
+// row was just solved exactly; masked rows hold x = v) and only the red rows are
+// computed and projected.
+helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, double2* z, int conj,
+                       bool black_zero = false) {
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
     const int nblk = project_blocks(h->N);
     const double2* r = v;
+    const bool red_only = zres && black_zero;
     if (zres) {
         // r = v - A zres (FP64 stencil), then the projection streams Q once
         TRY(ensure_tmp(h, 14));
-        launch_apply<double>(h->op64, zres, v, h->tmp[13], nullptr, conj, true, h->stream);
+        if (red_only) launch_residual_red(h->op64, zres, v, h->tmp[13], conj, h->stream);
+        else launch_apply<double>(h->op64, zres, v, h->tmp[13], nullptr, conj, true, h->stream);
         h->launches += 1;
         r = h->tmp[13];
     }
     ev_mark(h, 0, 0);
-    launch_project_df(h->Q, h->k, r, h->N, h->coarse_partials, nblk, h->stream);
+    launch_project_df(h->Q, h->k, r, red_only, h->N, h->n, h->coarse_partials, nblk, h->stream);
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
     ev_mark(h, 1, 0);
-    launch_prolong_df(h->Q, h->k, h->ybuf, z, h->N, h->stream);
+    launch_prolong_df(h->Q, h->k, h->ybuf, z, h->N, h->n, h->stream);
     ev_mark(h, 1, 1);
     h->launches += 4;
     CKL();
@@ -287,7 +294,7 @@ helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, 
     TRY(relax_from_zero(h, o->relax, o->omega, o->n_r, r, z, conj));
     if (o->correction == HELM_CORR_TB) {
         const bool zero = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
-        TRY(tb_correct(h, r, zero ? nullptr : z, z, conj));
+        TRY(tb_correct(h, r, zero ? nullptr : z, z, conj, o->relax == HELM_RBGS));
     } else if (o->correction == HELM_CORR_NONLINEAR) {
         // M2 acts on the residual after the sweeps: r - A z
         TRY(ensure_tmp(h, 13));
@@ -366,7 +373,7 @@ helm_status solve_relax(helm_handle* h, const helm_solve_opts* o, const double2*
         }
         CKL();
         if (o->correction == HELM_CORR_TB) {
-            TRY(tb_correct(h, f, x, x, o->conj));
+            TRY(tb_correct(h, f, x, x, o->conj, o->relax == HELM_RBGS && o->n_r > 0));
             ++st->precond_applies;
         } else if (o->correction == HELM_CORR_NONLINEAR) {
             launch_apply<double>(h->op64, x, f, r, nullptr, o->conj, true, h->stream);
@@ -989,8 +996,9 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     }
     // column-major FP32-pair Q for the per-iteration kernels; T becomes hi + lo so that
     // A_c is built from exactly the basis the kernels apply
-    STEP(dalloc(h, &h->Q, (size_t)N * k));
-    launch_split_basis(T, ldq, k, h->Q, N, s);
+    STEP(dalloc(h, &h->Q, (size_t)2 * ((N + 1) / 2) * k));
+    STEPC(cudaMemsetAsync(h->Q, 0, sizeof(float2) * 2 * ((N + 1) / 2) * k, s));   // odd N: one padding slot
+    launch_split_basis(T, ldq, k, h->Q, N, h->n, s);
     // A_c = Q^T (A Q)
     st = build_coarse(h, T, ldq, k);
     if (st != HELM_OK) {
@@ -1050,7 +1058,7 @@ helm_status don_get_q(const helm_handle* hc, double* q_out) {
     helm_handle* h = const_cast<helm_handle*>(hc);
     if (!h || !q_out) return fail(h, HELM_BAD_ARG, "null argument");
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
-    launch_cm_pair_to_rm(h->Q, h->k, q_out, h->N, h->stream);
+    launch_cm_pair_to_rm(h->Q, h->k, q_out, h->N, h->n, h->stream);
     CKL();
     return HELM_OK;
 }
@@ -1179,7 +1187,7 @@ helm_status helm_set_k2(helm_handle* h, const double* k2) {
         // rebuild A_c for the new operator from a node-major copy of the (possibly rounded) basis
         double* Qrm = nullptr;
         TRY(dalloc(h, &Qrm, (size_t)N * h->k));
-        launch_cm_pair_to_rm(h->Q, h->k, Qrm, N, h->stream);
+        launch_cm_pair_to_rm(h->Q, h->k, Qrm, N, h->n, h->stream);
         helm_status st = build_coarse(h, Qrm, h->k, h->k);
         cudaStreamSynchronize(h->stream);
         dfree(Qrm);

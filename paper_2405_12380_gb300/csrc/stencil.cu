@@ -531,6 +531,30 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs(Op<R> op, int colour, const ty
     if (i < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i, j, k);
 }
 
+// r_red[l / 2] = (v - A z)_l at the red nodes l (one per node pair (2m, 2m + 1))
+__global__ void __launch_bounds__(BX * BY) k_residual_red(Op<double> op, const double2* __restrict__ z,
+                                                          const double2* __restrict__ v,
+                                                          double2* __restrict__ r_red, int conj) {
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = op.dim == 3 ? blockIdx.z : 0;
+    if (j >= op.n) return;
+    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k) & 1);
+    if (i >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const double2 xc = z[l];
+    const unsigned code = node_code(op, l);
+    double2 out;
+    if (code & kMasked) {
+        out = xc;
+    } else {
+        const double2 s = nbr_sum(op, z, l, code);
+        const double2 d = diag_of(op, l, node_lidx(op, l, i, j, k), conj);
+        out.x = op.hinv2 * s.x + (d.x * xc.x - d.y * xc.y);
+        out.y = op.hinv2 * s.y + (d.x * xc.y + d.y * xc.x);
+    }
+    r_red[l >> 1] = csub(v[l], out);
+}
+
 __global__ void k_rhs(Op<double> op, const double2* __restrict__ src, const double2* __restrict__ g,
                       double2* __restrict__ b) {
     const int i = blockIdx.x * BX + threadIdx.x;
@@ -766,6 +790,11 @@ template void launch_jacobi<float>(const Op<float>&, double, const float2*, cons
 template void launch_rbgs_half<double>(const Op<double>&, int, const double2*, double2*, int, bool,
                                        cudaStream_t);
 template void launch_rbgs_half<float>(const Op<float>&, int, const float2*, float2*, int, bool, cudaStream_t);
+
+void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
+                         cudaStream_t s) {
+    k_residual_red<<<grid_for(op.dim, op.n, 2, 1), dim3(BX, BY), 0, s>>>(op, z, v, r_red, conj);
+}
 
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s) {
     k_rhs<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, src, g, b);
