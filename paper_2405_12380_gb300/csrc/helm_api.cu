@@ -181,9 +181,10 @@ helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, 
 helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, double2* z, int conj,
                        bool black_zero = false) {
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
-    const int nblk = project_blocks(h->N);
     const double2* r = v;
     const bool red_only = zres && black_zero;
+    const long long rows = red_only ? (h->N + 1) / 2 : h->N;
+    const int nblk = project_blocks(rows);
     if (zres) {
         // r = v - A zres (FP64 stencil), then the projection streams Q once
         TRY(ensure_tmp(h, 14));
@@ -193,11 +194,11 @@ helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, do
         r = h->tmp[13];
     }
     ev_mark(h, 0, 0);
-    launch_project_df(h->Q, h->k, r, red_only, h->N, h->n, h->coarse_partials, nblk, h->stream);
+    launch_project_df(red_only ? h->Qr : h->Q, h->k, r, rows, h->coarse_partials, nblk, h->stream);
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
     ev_mark(h, 1, 0);
-    launch_prolong_df(h->Q, h->k, h->ybuf, z, h->N, h->n, h->stream);
+    launch_prolong_df(h->Q, h->k, h->ybuf, z, h->N, h->stream);
     ev_mark(h, 1, 1);
     h->launches += 4;
     CKL();
@@ -766,7 +767,7 @@ helm_status helm_destroy(helm_handle* h) {
         if (e) cudaEventDestroy(e);
     for (auto p : h->tmp) cudaFree(p);
     for (auto p : h->tmp32) cudaFree(p);
-    dfree(h->Q); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
+    dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
     if (h->Qbf) cudaFree(h->Qbf);
     dfree(h->partials32); dfree(h->y32); dfree(h->Z32);
     dfree(h->Traw); dfree(h->bw); dfree(h->nl_x); dfree(h->nl_h0); dfree(h->nl_h1);
@@ -912,7 +913,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         for (int o = 0; o < wout; ++o) hw.push_back(b[o]);
         off += (size_t)win * wout + wout;
     }
-    dfree(h->Q); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
+    dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
     h->k = 0;
     const long long N = h->N;
     const int ldt = round32(p);
@@ -996,14 +997,16 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     }
     // column-major FP32-pair Q for the per-iteration kernels; T becomes hi + lo so that
     // A_c is built from exactly the basis the kernels apply
-    STEP(dalloc(h, &h->Q, (size_t)2 * ((N + 1) / 2) * k));
-    STEPC(cudaMemsetAsync(h->Q, 0, sizeof(float2) * 2 * ((N + 1) / 2) * k, s));   // odd N: one padding slot
-    launch_split_basis(T, ldq, k, h->Q, N, h->n, s);
+    STEP(dalloc(h, &h->Q, (size_t)N * k));
+    launch_split_basis(T, ldq, k, h->Q, N, s);
+    dfree(h->Qr);
+    STEP(dalloc(h, &h->Qr, (size_t)((N + 1) / 2) * k));
+    launch_red_rows(h->Q, k, N, h->n, h->Qr, s);
     // A_c = Q^T (A Q)
     st = build_coarse(h, T, ldq, k);
     if (st != HELM_OK) {
         cleanup();
-        dfree(h->Q); dfree(h->Ainv);
+        dfree(h->Q); dfree(h->Qr); dfree(h->Ainv);
         return st;
     }
     STEP(dalloc(h, &h->coarse_partials, (size_t)std::max(restrict_blocks(N), project_blocks(N)) * k));
@@ -1058,7 +1061,7 @@ helm_status don_get_q(const helm_handle* hc, double* q_out) {
     helm_handle* h = const_cast<helm_handle*>(hc);
     if (!h || !q_out) return fail(h, HELM_BAD_ARG, "null argument");
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
-    launch_cm_pair_to_rm(h->Q, h->k, q_out, h->N, h->n, h->stream);
+    launch_cm_pair_to_rm(h->Q, h->k, q_out, h->N, h->stream);
     CKL();
     return HELM_OK;
 }
@@ -1187,7 +1190,7 @@ helm_status helm_set_k2(helm_handle* h, const double* k2) {
         // rebuild A_c for the new operator from a node-major copy of the (possibly rounded) basis
         double* Qrm = nullptr;
         TRY(dalloc(h, &Qrm, (size_t)N * h->k));
-        launch_cm_pair_to_rm(h->Q, h->k, Qrm, N, h->n, h->stream);
+        launch_cm_pair_to_rm(h->Q, h->k, Qrm, N, h->stream);
         helm_status st = build_coarse(h, Qrm, h->k, h->k);
         cudaStreamSynchronize(h->stream);
         dfree(Qrm);

@@ -165,15 +165,16 @@ void launch_gauss_jordan(const double* C, int ldc, int k, double2* Ainv, double2
 void launch_coarse_apply(const double2* partials, int nblk, int k, const double2* Ainv, int conj, double2* y,
                          double2* cbuf, cudaStream_t s);
 void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s);
-// FP64 projection on FP32 pipes: Q as (hi, lo) FP32 pairs in the colour-split
-// layout (2 k columns of M = ceil(N / 2) pair entries: red halves, then black)
+// FP64 projection on FP32 pipes: Q as (hi, lo) FP32 pairs, column-major k x N
+// (N rows: the projection also runs on the compact red rows, N = ceil(N / 2))
 int project_blocks(long long N);
-// red_only: r is the compact red residual (M entries), the black rows being zero
-void launch_project_df(const float2* Q, int k, const double2* r, bool red_only, long long N, int n,
-                       double2* partials, int nblk, cudaStream_t s);
-void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, int n, cudaStream_t s);
-void launch_split_basis(double* A, int ld, int k, float2* B, long long N, int n, cudaStream_t s);
-void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, int n, cudaStream_t s);
+void launch_project_df(const float2* Q, int k, const double2* r, long long N, double2* partials, int nblk,
+                       cudaStream_t s);
+void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s);
+void launch_split_basis(double* A, int ld, int k, float2* B, long long N, cudaStream_t s);
+void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, cudaStream_t s);
+// Q_red (k x ceil(N / 2)): the red rows of Q, row m = the red node of pair (2m, 2m + 1)
+void launch_red_rows(const float2* Q, int k, long long N, int n, float2* Qr, cudaStream_t s);
 // r_red[m] = (v - A z) at the red node of pair m (stencil.cu)
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s);
@@ -237,6 +238,7 @@ struct helm_handle {
     int p = 0, k = 0, ldq = 0;
     std::vector<int> kept;
     float2* Q = nullptr;            // FP32 pairs, k x N
+    float2* Qr = nullptr;           // its red rows, k x ceil(N / 2)
     double2* Ainv = nullptr;
     double2* coarse_partials = nullptr;
     void* Qbf = nullptr;            // BF16 basis (MIXED handles), column-major k x N

@@ -7,17 +7,17 @@
 //   Q1 = T_S R^-1, then CholQR2 pass        k_tri_inverse, k_gather_upper
 //   W = A Q (real columns -> complex)       k_apply_columns
 //   A_c = Q^T W, A_c^-1 by Gauss-Jordan     k_gram, k_gauss_jordan (one CTA, partial pivoting)
-// Per application (z += Q A_c^-1 Q^T (v - A z)), Q as FP32 pairs in a colour-split
-// column-major layout: the nodes are taken in pairs (2m, 2m + 1), one red and one
-// black (red: i + j + k even), and Q_j of the red node of pair m sits at
-// [j][m], of the black node at [k + j][m] (M = ceil(N / 2) pairs per column).
+// Per application (z += Q A_c^-1 Q^T (v - A z)), Q column-major (k x N) as FP32 pairs,
+// plus a compact copy Q_red (k x M, M = ceil(N / 2)) of its red rows (i + j + k
+// even), row m holding the red node of the node pair (2m, 2m + 1):
 //   k_apply        r = v - A z (FP64 stencil, stencil.cu) when the sweeps left a z;
-//                  after a red-black Gauss-Seidel sweep only the red rows of r are
-//                  nonzero, computed into a compact array by k_residual_red
+//                  after a red-black Gauss-Seidel sweep r vanishes on the black
+//                  rows and k_residual_red computes the red rows into a compact
+//                  array (one entry per pair)
 //   k_project_df   r tile split once into FP32 pairs in shared memory; warps own
 //                  columns and keep FP32-pair sums in registers across tiles (one
-//                  FP32-pair warp reduction per block); red rows only when the
-//                  black rows of r vanish (half the basis is read)
+//                  FP32-pair warp reduction per block); on Q_red with the compact
+//                  r after red-black Gauss-Seidel (half the basis is read)
 //   k_coarse_*     fixed-order sum of block partials, y = A_c^-1 c (FP64, one block per row)
 //   k_prolong_df   z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 #include <cuda_bf16.h>
@@ -420,90 +420,51 @@ __device__ __forceinline__ void pair_warp_sum(float& sh, float& sl) {
     }
 }
 
-// colour of node l of a grid with n nodes per side: (i + j + k) mod 2, 0 = red.
-// 32-bit division (N < 2^31): the 64-bit one is a long software sequence
-__device__ __forceinline__ int node_colour(long long l, int n) {
-    const unsigned ul = (unsigned)l, un = (unsigned)n;
-    const unsigned r = ul / un;          // row index j + n k
-    const unsigned kk = r / un;
-    return (int)(((ul - r * un) + (r - kk * un) + kk) & 1u);
-}
-
 constexpr int PJ_T = 512;        // threads per projection block (16 warps), two blocks per SM
-constexpr int PJ_TILE = 512;     // pairs per tile (one per thread)
+constexpr int PJ_TILE = 512;     // rows per tile (one per thread)
 
-__device__ __forceinline__ float4 split_c(double2 v) {
-    float4 p;
-    split_f64(v.x, p.x, p.y);
-    split_f64(v.y, p.z, p.w);
-    return p;
-}
-
-// (a0, a1) + i (a2, a3) += sum over the tile rows of Qj[u] rs[u]
-template <int RPL>
-__device__ __forceinline__ void column_tile(const float2* __restrict__ Qj, const float4* rs, int lane, int rows,
-                                            float& a0, float& a1, float& a2, float& a3) {
-    // all loads of the column issued before use (rows past the end of the block
-    // read nothing and meet r = 0 in shared memory)
-    float2 qv[RPL];
-#pragma unroll
-    for (int u = 0; u < RPL; ++u)
-        qv[u] = (lane + 32 * u < rows) ? __ldg(Qj + lane + 32 * u) : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int u = 0; u < RPL; ++u) {
-        const float4 rr = rs[lane + 32 * u];
-        pair_fma(a0, a1, qv[u].x, qv[u].y, rr.x, rr.y);
-        pair_fma(a2, a3, qv[u].x, qv[u].y, rr.z, rr.w);
-    }
-}
-
-// partials[b][j] = sum over the pairs of block b of Q_j r.  RED_ONLY: r is the
-// compact red residual (one entry per pair) and only the red half of Q is read;
-// otherwise r is the natural-order vector of N nodes.
-template <int KPW, bool RED_ONLY>
-__global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, int k,
-                                                        const double2* __restrict__ r, long long N, int n,
-                                                        double2* __restrict__ partials, long long rows_per_block) {
-    constexpr int NS = RED_ONLY ? 1 : 2;
-    __shared__ float4 rs[NS][PJ_TILE];   // (re hi, re lo, im hi, im lo) of the red / black node
-    const long long M = (N + 1) / 2;
+// partials[b][j] = sum over the rows of block b of Q_j[l] r_l (r given, FP64)
+template <int KPW>
+__global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, int k, const double2* __restrict__ r,
+                                                     long long N, double2* __restrict__ partials, long long rows_per_block) {
+    __shared__ float4 rs[PJ_TILE];       // (re hi, re lo, im hi, im lo)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = PJ_T / 32;
     constexpr int RPL = PJ_TILE / 32;
     const long long r0 = (long long)blockIdx.x * rows_per_block;
-    const long long r1 = min(M, r0 + rows_per_block);
+    const long long r1 = min(N, r0 + rows_per_block);
     float acc[KPW][4];
 #pragma unroll
     for (int c = 0; c < KPW; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
     for (long long t0 = r0; t0 < r1; t0 += PJ_TILE) {
-        const long long m = t0 + threadIdx.x;
-        float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
-        if (m < r1) {
-            if (RED_ONLY) {
-                p0 = split_c(r[m]);
-            } else {
-                const long long l = 2 * m;
-                const double2 a = r[l];
-                const double2 b = l + 1 < N ? r[l + 1] : make_double2(0, 0);
-                const bool red_first = node_colour(l, n) == 0;
-                p0 = split_c(red_first ? a : b);
-                p1 = split_c(red_first ? b : a);
-            }
-        }
+        const long long l = t0 + threadIdx.x;
+        const double2 rv = l < r1 ? r[l] : make_double2(0, 0);
+        float4 rp;
+        split_f64(rv.x, rp.x, rp.y);
+        split_f64(rv.y, rp.z, rp.w);
         __syncthreads();
-        rs[0][threadIdx.x] = p0;
-        if (!RED_ONLY) rs[NS - 1][threadIdx.x] = p1;
+        rs[threadIdx.x] = rp;
         __syncthreads();
         const int rows = (int)min((long long)PJ_TILE, r1 - t0);
 #pragma unroll
         for (int c = 0; c < KPW; ++c) {
             const int j = warp + NW * c;
             if (j < k) {
-                column_tile<RPL>(Q + (long long)j * M + t0, rs[0], lane, rows, acc[c][0], acc[c][1], acc[c][2],
-                                 acc[c][3]);
-                if (!RED_ONLY)
-                    column_tile<RPL>(Q + (long long)(k + j) * M + t0, rs[NS - 1], lane, rows, acc[c][0], acc[c][1],
-                                     acc[c][2], acc[c][3]);
+                const float2* Qj = Q + (long long)j * N + t0;
+                float a0 = acc[c][0], a1 = acc[c][1], a2 = acc[c][2], a3 = acc[c][3];
+                // all loads of the column issued before use (rows past the end of the
+                // block read nothing and meet r = 0 in shared memory)
+                float2 qv[RPL];
+#pragma unroll
+                for (int u = 0; u < RPL; ++u)
+                    qv[u] = (lane + 32 * u < rows) ? __ldg(Qj + lane + 32 * u) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < RPL; ++u) {
+                    const float4 rr = rs[lane + 32 * u];
+                    pair_fma(a0, a1, qv[u].x, qv[u].y, rr.x, rr.y);
+                    pair_fma(a2, a3, qv[u].x, qv[u].y, rr.z, rr.w);
+                }
+                acc[c][0] = a0; acc[c][1] = a1; acc[c][2] = a2; acc[c][3] = a3;
             }
         }
     }
@@ -556,23 +517,25 @@ __global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ 
     if (threadIdx.x == 0) y[i] = make_double2(red[0].x + red[1].x, red[0].y + red[1].y);
 }
 
-// z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node (the two
-// nodes of a pair read the two halves of Q at the same index, so a warp reads 16
-// consecutive entries of each half)
+// z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q, int k, const double2* __restrict__ y,
-                                                    double2* __restrict__ z, long long N, int n) {
+                                                    double2* __restrict__ z, long long N) {
     __shared__ float4 ys[kMaxP];
-    const long long M = (N + 1) / 2;
-    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = split_c(y[j]);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        float4 t;
+        split_f64(y[j].x, t.x, t.y);
+        split_f64(y[j].y, t.z, t.w);
+        ys[j] = t;
+    }
     __syncthreads();
     for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        const float2* q = Q + (long long)node_colour(l, n) * k * M + (l >> 1);
+        const float2* q = Q + l;
         int j = 0;
         for (; j + 8 <= k; j += 8) {
             float2 qv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(j + u) * M);
+            for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(j + u) * N);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const float4 yy = ys[j + u];
@@ -581,38 +544,80 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
             }
         }
         for (; j < k; ++j) {
-            const float2 qv = q[(long long)j * M];
+            const float2 qv = q[(long long)j * N];
             const float4 yy = ys[j];
             pair_fma(a0, a1, qv.x, qv.y, yy.x, yy.y);
             pair_fma(a2, a3, qv.x, qv.y, yy.z, yy.w);
         }
-        const double2 zz = z[l];
+        double2 zz = z[l];
         z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
+    }
+}
+
+// colour of node l of a grid with n nodes per side: (i + j + k) mod 2, 0 = red
+__device__ __forceinline__ int node_colour(long long l, int n) {
+    const unsigned ul = (unsigned)l, un = (unsigned)n;
+    const unsigned r = ul / un;          // row index j + n k
+    const unsigned kk = r / un;
+    return (int)(((ul - r * un) + (r - kk * un) + kk) & 1u);
+}
+
+// Q_red[j][m] = Q[j][red node of pair m]; every pair (2m, 2m + 1) holds one red and
+// one black node (rows of even length start on even l; for odd n the colour is the
+// parity of l), and a last single node (odd N) is red
+__global__ void k_red_rows(const float2* __restrict__ Q, int k, long long N, int n, float2* __restrict__ Qr) {
+    const long long M = (N + 1) / 2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < M * k;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long j = idx / M, m = idx - j * M;
+        const long long l = 2 * m + node_colour(2 * m, n);
+        Qr[idx] = Q[j * N + l];
     }
 }
 
 // FP64 row-major Q (N x ld) -> column-major pairs (k x N) of FP32 (hi, lo), and
 // the row-major FP64 values replaced by hi + lo (the basis the kernels use)
-__global__ void k_split_basis(double* __restrict__ A, int ld, int k, float2* __restrict__ B, long long N, int n) {
-    const long long M = (N + 1) / 2;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N * k;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long l = idx / k;
-        const int c = (int)(idx - l * k);
-        float2 v;
-        split_f64(A[l * ld + c], v.x, v.y);
-        A[l * ld + c] = (double)v.x + (double)v.y;
-        B[((long long)node_colour(l, n) * k + c) * M + (l >> 1)] = v;
+__global__ void k_split_basis(double* __restrict__ A, int ld, int k, float2* __restrict__ B, long long N) {
+    __shared__ float2 tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < N && c < k) {
+            split_f64(A[l * ld + c], v.x, v.y);
+            A[l * ld + c] = (double)v.x + (double)v.y;
+        }
+        tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        if (c < k && l < N) B[(long long)c * N + l] = tile[threadIdx.x][r];
     }
 }
-__global__ void k_cm_pair_to_rm(const float2* __restrict__ B, int k, double* __restrict__ A, long long N, int n) {
-    const long long M = (N + 1) / 2;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N * k;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long l = idx / k;
-        const int c = (int)(idx - l * k);
-        const float2 q = B[((long long)node_colour(l, n) * k + c) * M + (l >> 1)];
-        A[l * k + c] = (double)q.x + (double)q.y;
+
+__global__ void k_cm_pair_to_rm(const float2* __restrict__ B, int k, double* __restrict__ A, long long N) {
+    __shared__ double tile[32][33];
+    const long long l0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int c = c0 + r;
+        long long l = l0 + threadIdx.x;
+        double v = 0.0;
+        if (c < k && l < N) {
+            const float2 q = B[(long long)c * N + l];
+            v = (double)q.x + (double)q.y;
+        }
+        tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        long long l = l0 + r;
+        int c = c0 + threadIdx.x;
+        if (l < N && c < k) A[l * k + c] = tile[threadIdx.x][r];
     }
 }
 
@@ -941,21 +946,15 @@ void launch_coarse_apply(const double2* partials, int nblk, int k, const double2
 
 
 int project_blocks(long long N) {
-    const long long M = (N + 1) / 2;
-    long long b = (M + PJ_TILE - 1) / PJ_TILE;
+    long long b = (N + PJ_TILE - 1) / PJ_TILE;
     return (int)(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
 }
 
-void launch_project_df(const float2* Q, int k, const double2* r, bool red_only, long long N, int n,
-                       double2* partials, int nblk, cudaStream_t s) {
-    const long long M = (N + 1) / 2;
-    long long rows = (M + nblk - 1) / nblk;
+void launch_project_df(const float2* Q, int k, const double2* r, long long N, double2* partials, int nblk,
+                       cudaStream_t s) {
+    long long rows = (N + nblk - 1) / nblk;
     const int kpw = (k + 15) / 16;
-#define PJ_CASE(K)                                                                                 \
-    do {                                                                                           \
-        if (red_only) k_project_df<K, true><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, n, partials, rows);  \
-        else k_project_df<K, false><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, n, partials, rows);          \
-    } while (0)
+#define PJ_CASE(K) k_project_df<K><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, partials, rows)
     if (kpw <= 1) PJ_CASE(1);
     else if (kpw <= 2) PJ_CASE(2);
     else if (kpw <= 4) PJ_CASE(4);
@@ -964,17 +963,23 @@ void launch_project_df(const float2* Q, int k, const double2* r, bool red_only, 
 #undef PJ_CASE
 }
 
-void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, int n, cudaStream_t s) {
+void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
     long long b = (N + 255) / 256;
-    k_prolong_df<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, N, n);
+    k_prolong_df<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, N);
 }
 
-void launch_split_basis(double* A, int ld, int k, float2* B, long long N, int n, cudaStream_t s) {
-    k_split_basis<<<4 * 152, 256, 0, s>>>(A, ld, k, B, N, n);
+void launch_red_rows(const float2* Q, int k, long long N, int n, float2* Qr, cudaStream_t s) {
+    k_red_rows<<<4 * 152, 256, 0, s>>>(Q, k, N, n, Qr);
 }
 
-void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, int n, cudaStream_t s) {
-    k_cm_pair_to_rm<<<4 * 152, 256, 0, s>>>(B, k, A, N, n);
+void launch_split_basis(double* A, int ld, int k, float2* B, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_split_basis<<<g, dim3(32, 8), 0, s>>>(A, ld, k, B, N);
+}
+
+void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, cudaStream_t s) {
+    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
+    k_cm_pair_to_rm<<<g, dim3(32, 8), 0, s>>>(B, k, A, N);
 }
 
 void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s) {
