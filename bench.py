@@ -337,7 +337,8 @@ def gpu_arm(args):
         return n, ms, (ms / 1e3 / n if n else None)
 
     kernels = []
-    # trunk-basis projection c = Q^T r: Q as FP32 pairs (8 B per entry), r complex128
+    # trunk-basis projection c = Q^T r: Q as FP32 pairs (8 B per entry), r as 16 B
+    # per entry (complex128, or FP32 pairs after the double-float sweeps)
     n_, ms_, avg = phase("n_restrict", "restrict_ms")
     rows = M if red_only else N
     if avg:
@@ -357,10 +358,24 @@ def gpu_arm(args):
                         "peak_source": hbm_src, "traffic": None,
                         "algorithmic_bytes_per_launch": b, "avg_launch_us": avg * 1e6, "launches": n_,
                         "share_of_solve": ms_ / st_prof["ms"]})
-    # relaxation half-sweep: per updated fluid node 10 DADD (neighbour sum), 2 DFMA
-    # (f - h^-2 s) and a complex multiply (2 DMUL + 2 DFMA): 16 FP64 instructions
+    # relaxation half-sweep.  FP64 kernels: per updated fluid node 10 DADD (neighbour
+    # sum), 2 DFMA (f - h^-2 s), a complex multiply (2 DMUL + 2 DFMA) = 16 FP64
+    # instructions.  The double-float red-black Gauss-Seidel of the trunk-basis cycle:
+    # 10 pair additions (11 FP32 instructions each), 2 pair products (7) for h^-2 s,
+    # 2 pair additions for f - h^-2 s and a complex pair product (4 x 7 + 2 x 11) =
+    # 196 FP32 instructions
     n_, ms_, avg = phase("n_sweep", "sweep_ms")
-    if avg:
+    df_sweep = w["relax"] == "rbgs" and w["n_r"] > 0 and w["correction"] == "tb"
+    fp32_peak = 128 * 152 * sm_mhz * 1e6 / 1e12
+    if avg and df_sweep:
+        ops = 196.0 * fluid / 2
+        kernels.append({"bound": "alu", "kernel": "k_rbgs_df (double-float half-sweep)",
+                        "achieved": ops / avg / 1e12, "peak": fp32_peak, "unit": "T FP32 inst/s",
+                        "frac": ops / avg / 1e12 / fp32_peak,
+                        "peak_source": "128 FP32 instructions/clk/SM x 152 SMs x max SM clock",
+                        "traffic": None, "algorithmic_fp32_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
+                        "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
+    elif avg:
         ops = 16.0 * fluid / 2
         kernels.append({"bound": "alu", "kernel": "k_%s (FP64 half-sweep)" % w["relax"],
                         "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",

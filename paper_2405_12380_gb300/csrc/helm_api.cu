@@ -276,6 +276,44 @@ helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v,
     return HELM_OK;
 }
 
+// The hybrid cycle with red-black Gauss-Seidel and the trunk-basis correction on an
+// FP64 handle, with the sweeps in double-float arithmetic on the FP32 pipes:
+// z = n_r sweeps on A z = r from z = 0, then z += Q A_c^-1 Q^T (r - A z), where the
+// residual is formed on the red rows only (after the black half-sweep it vanishes on
+// black and masked rows) and z is converted to FP64 once, inside the prolongation.
+helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
+    if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
+    TRY(ensure_tmp(h, 16));
+    cudaStream_t s = h->stream;
+    float4* fs = reinterpret_cast<float4*>(h->tmp[14]);
+    float4* xs = reinterpret_cast<float4*>(h->tmp[15]);
+    float4* rr = reinterpret_cast<float4*>(h->tmp[13]);
+    launch_rbgs_df_first(h->op64, h->dft, r, fs, xs, conj, s);
+    for (int q = 0; q < o->n_r; ++q) {
+        if (q > 0) {
+            ev_mark(h, 2, 0);
+            launch_rbgs_df(h->op64, h->dft, 0, fs, xs, conj, s);
+            ev_mark(h, 2, 1);
+        }
+        ev_mark(h, 2, 0);
+        launch_rbgs_df(h->op64, h->dft, 1, fs, xs, conj, s);
+        ev_mark(h, 2, 1);
+    }
+    launch_residual_red_df(h->op64, h->dft, fs, xs, rr, conj, s);
+    const long long rows = (h->N + 1) / 2;
+    const int nblk = project_blocks(rows);
+    ev_mark(h, 0, 0);
+    launch_project_df_split(h->Qr, h->k, rr, rows, h->coarse_partials, nblk, s);
+    ev_mark(h, 0, 1);
+    launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, s);
+    ev_mark(h, 1, 0);
+    launch_prolong_df_base(h->Q, h->k, h->ybuf, xs, z, h->N, s);
+    ev_mark(h, 1, 1);
+    h->launches += 2 * o->n_r + 5;
+    CKL();
+    return HELM_OK;
+}
+
 helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
     if (h->precision == HELM_MIXED) {
         TRY(ensure_tmp32(h, 4));
@@ -292,6 +330,7 @@ helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, 
         CK(cudaMemcpyAsync(z, r, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, h->stream));
         return HELM_OK;
     }
+    if (o->relax == HELM_RBGS && o->n_r > 0 && o->correction == HELM_CORR_TB && !h->k2) return precond_rbgs_tb_df(h, o, r, z, conj);
     TRY(relax_from_zero(h, o->relax, o->omega, o->n_r, r, z, conj));
     if (o->correction == HELM_CORR_TB) {
         const bool zero = o->relax == HELM_RELAX_NONE || o->n_r <= 0;
@@ -638,6 +677,19 @@ void fill_tables(helm_handle* h) {
     o.invd = h->invd;
     f.k2 = h->k2f;
     f.invd = h->invdf;
+    // FP32-pair copies (hi = nearest float, lo = nearest float of the remainder)
+    auto split = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    DfTab& t = h->dft;
+    t.hinv2 = split(o.hinv2);
+    t.dre = split(o.dre);
+    for (int m = 0; m <= kMaxLayerCells; ++m) {
+        t.im[m] = split(o.im[m]);
+        const float2 re = split(o.invd_tab[m].x), im = split(o.invd_tab[m].y);
+        t.invd[m] = make_float4(re.x, re.y, im.x, im.y);
+    }
 }
 
 // A_c = Q^T (A Q) and its inverse from a node-major copy of Q (N x ldq)

@@ -72,6 +72,15 @@ struct Op {
     C invd_tab[kMaxLayerCells + 1];  // 1/(diag) by layer index (fluid nodes)
 };
 
+// Double-float (FP32 pair, hi + lo) copies of the operator constants, for the
+// red-black Gauss-Seidel cycle of FP64 handles that runs on the FP32 pipes
+struct DfTab {
+    float2 hinv2;                            // h^-2
+    float2 dre;                              // real part of the tabulated diagonal
+    float2 im[kMaxLayerCells + 1];           // Im k^2 by layer index
+    float4 invd[kMaxLayerCells + 1];         // 1/diag by layer index: (re hi, re lo, im hi, im lo)
+};
+
 // device scalar slots of the Krylov drivers (double2 each, in helm_handle::sc)
 enum { S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_SN2, S_RN2, S_FLAGS, S_TS, S_TT,
        S_BETA2, S_WN2, S_EST, S_BN2, S_STOP, S_NSLOTS };
@@ -175,6 +184,21 @@ void launch_split_basis(double* A, int ld, int k, float2* B, long long N, cudaSt
 void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, cudaStream_t s);
 // Q_red (k x ceil(N / 2)): the red rows of Q, row m = the red node of pair (2m, 2m + 1)
 void launch_red_rows(const float2* Q, int k, long long N, int n, float2* Qr, cudaStream_t s);
+// double-float red-black Gauss-Seidel (stencil.cu): fs = f as FP32 pairs and the
+// first (red) half-sweep from x = 0; later half-sweeps; the red-row residual
+// written as FP32 pairs (one entry per node pair)
+void launch_rbgs_df_first(const Op<double>& op, const DfTab& t, const double2* f, float4* fs, float4* xs, int conj,
+                          cudaStream_t s);
+void launch_rbgs_df(const Op<double>& op, const DfTab& t, int colour, const float4* fs, float4* xs, int conj,
+                    cudaStream_t s);
+void launch_residual_red_df(const Op<double>& op, const DfTab& t, const float4* fs, const float4* xs, float4* r_red,
+                            int conj, cudaStream_t s);
+// projection of a residual given as FP32 pairs (float4 per complex entry, N rows)
+void launch_project_df_split(const float2* Q, int k, const float4* r, long long N, double2* partials, int nblk,
+                             cudaStream_t s);
+// z = base + Q y with base given as FP32 pairs (float4 per complex entry)
+void launch_prolong_df_base(const float2* Q, int k, const double2* y, const float4* base, double2* z, long long N,
+                            cudaStream_t s);
 // r_red[m] = (v - A z) at the red node of pair m (stencil.cu)
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s);
@@ -215,6 +239,7 @@ struct helm_handle {
     std::string err;
     helm::Op<double> op64{};
     helm::Op<float> op32{};
+    helm::DfTab dft{};
     uint8_t* mask = nullptr;
     uint8_t* lidx = nullptr;
     uint8_t* nbm = nullptr;

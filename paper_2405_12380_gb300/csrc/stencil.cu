@@ -555,6 +555,141 @@ __global__ void __launch_bounds__(BX * BY) k_residual_red(Op<double> op, const d
     r_red[l >> 1] = csub(v[l], out);
 }
 
+// ---- double-float red-black Gauss-Seidel for FP64 handles.  The sweeps of the
+// hybrid cycle keep f and x as FP32 pairs (value = hi + lo, a 48-bit significand)
+// and run on the FP32 pipes, which this GPU has ~64x more of than FP64 pipes:
+// f is split once (the first red half-sweep), the residual leaves as pairs for the
+// projection, and the prolongation converts back to FP64 once.  Additions are
+// two-sums with one renormalisation, products an FMA-exact product plus the cross
+// terms (the lo*lo term, ~2^-48 relative, is dropped).
+__device__ __forceinline__ float2 df_norm(float s, float e) {
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    return df_norm(s, e);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ float2 df_split(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+struct Cdf {          // complex double-float
+    float2 re, im;
+};
+__device__ __forceinline__ Cdf cdf_load(const float4* p, long long l) {
+    const float4 v = p[l];
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ float4 cdf_pack(Cdf a) { return make_float4(a.re.x, a.re.y, a.im.x, a.im.y); }
+__device__ __forceinline__ Cdf cdf_add(Cdf a, Cdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ Cdf cdf_sub(Cdf a, Cdf b) { return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))}; }
+__device__ __forceinline__ Cdf cdf_scale(float2 s, Cdf a) { return {df_mul(s, a.re), df_mul(s, a.im)}; }
+__device__ __forceinline__ Cdf cdf_mul(Cdf a, Cdf b) {
+    return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ Cdf cdf_zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+__device__ __forceinline__ Cdf invd_df(const DfTab& t, int m, int conj) {
+    const float4 v = t.invd[m];
+    Cdf d = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    if (conj) d.im = df_neg(d.im);
+    return d;
+}
+
+// sum of the fluid neighbours (same tree as nbr_sum)
+__device__ __forceinline__ Cdf nbr_sum_df(const Op<double>& op, const float4* __restrict__ x, long long l,
+                                          unsigned code) {
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    const Cdf a = (code & 1u) ? cdf_load(x, l - 1) : cdf_zero();
+    const Cdf b = (code & 2u) ? cdf_load(x, l + 1) : cdf_zero();
+    const Cdf c = (code & 4u) ? cdf_load(x, l - sy) : cdf_zero();
+    const Cdf d = (code & 8u) ? cdf_load(x, l + sy) : cdf_zero();
+    Cdf s = cdf_add(cdf_add(a, b), cdf_add(c, d));
+    if (op.dim == 3) {
+        const Cdf e = (code & 16u) ? cdf_load(x, l - sz) : cdf_zero();
+        const Cdf f = (code & 32u) ? cdf_load(x, l + sz) : cdf_zero();
+        s = cdf_add(s, cdf_add(e, f));
+    }
+    return s;
+}
+
+// fs = f as pairs on every node; x = D^-1 f on red fluid nodes, f on red masked
+// nodes, 0 on black nodes (the first red half-sweep from x = 0)
+__global__ void k_rbgs_df_first(Op<double> op, DfTab t, const double2* __restrict__ f, float4* __restrict__ fs,
+                                float4* __restrict__ xs, int conj) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = op.dim == 3 ? blockIdx.z : 0;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const double2 fv = f[l];
+    const Cdf F = {df_split(fv.x), df_split(fv.y)};
+    fs[l] = cdf_pack(F);
+    Cdf x = cdf_zero();
+    if (((i + j + k) & 1) == 0) {
+        const unsigned code = node_code(op, l);
+        x = (code & kMasked) ? F : cdf_mul(invd_df(t, node_lidx(op, l, i, j, k), conj), F);
+    }
+    xs[l] = cdf_pack(x);
+}
+
+// one half-sweep of colour `colour`: x = D^-1 (f - h^-2 s) on fluid nodes, f on masked
+__global__ void __launch_bounds__(BX * BY) k_rbgs_df(Op<double> op, DfTab t, int colour,
+                                                     const float4* __restrict__ fs, float4* xs, int conj) {
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = op.dim == 3 ? blockIdx.z : 0;
+    if (j >= op.n) return;
+    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + colour) & 1);
+    if (i >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const unsigned code = node_code(op, l);
+    const Cdf F = cdf_load(fs, l);
+    Cdf x;
+    if (code & kMasked) {
+        x = F;
+    } else {
+        const Cdf sum = nbr_sum_df(op, xs, l, code);
+        x = cdf_mul(invd_df(t, node_lidx(op, l, i, j, k), conj), cdf_sub(F, cdf_scale(t.hinv2, sum)));
+    }
+    xs[l] = cdf_pack(x);
+}
+
+// r_red[l / 2] = (f - A x)_l on the red nodes, as pairs
+__global__ void __launch_bounds__(BX * BY) k_residual_red_df(Op<double> op, DfTab t, const float4* __restrict__ fs,
+                                                             const float4* __restrict__ xs,
+                                                             float4* __restrict__ r_red, int conj) {
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = op.dim == 3 ? blockIdx.z : 0;
+    if (j >= op.n) return;
+    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k) & 1);
+    if (i >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const unsigned code = node_code(op, l);
+    const Cdf x = cdf_load(xs, l);
+    Cdf out;
+    if (code & kMasked) {
+        out = x;
+    } else {
+        const Cdf sum = nbr_sum_df(op, xs, l, code);
+        const int m = node_lidx(op, l, i, j, k);
+        const Cdf d = {t.dre, conj ? df_neg(t.im[m]) : t.im[m]};
+        out = cdf_add(cdf_scale(t.hinv2, sum), cdf_mul(d, x));
+    }
+    r_red[l >> 1] = cdf_pack(cdf_sub(cdf_load(fs, l), out));
+}
+
 __global__ void k_rhs(Op<double> op, const double2* __restrict__ src, const double2* __restrict__ g,
                       double2* __restrict__ b) {
     const int i = blockIdx.x * BX + threadIdx.x;
@@ -794,6 +929,21 @@ template void launch_rbgs_half<float>(const Op<float>&, int, const float2*, floa
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s) {
     k_residual_red<<<grid_for(op.dim, op.n, 2, 1), dim3(BX, BY), 0, s>>>(op, z, v, r_red, conj);
+}
+
+void launch_rbgs_df_first(const Op<double>& op, const DfTab& t, const double2* f, float4* fs, float4* xs, int conj,
+                          cudaStream_t s) {
+    k_rbgs_df_first<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, t, f, fs, xs, conj);
+}
+
+void launch_rbgs_df(const Op<double>& op, const DfTab& t, int colour, const float4* fs, float4* xs, int conj,
+                    cudaStream_t s) {
+    k_rbgs_df<<<grid_for(op.dim, op.n, 2, 1), dim3(BX, BY), 0, s>>>(op, t, colour, fs, xs, conj);
+}
+
+void launch_residual_red_df(const Op<double>& op, const DfTab& t, const float4* fs, const float4* xs, float4* r_red,
+                            int conj, cudaStream_t s) {
+    k_residual_red_df<<<grid_for(op.dim, op.n, 2, 1), dim3(BX, BY), 0, s>>>(op, t, fs, xs, r_red, conj);
 }
 
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s) {

@@ -423,9 +423,10 @@ __device__ __forceinline__ void pair_warp_sum(float& sh, float& sl) {
 constexpr int PJ_T = 512;        // threads per projection block (16 warps), two blocks per SM
 constexpr int PJ_TILE = 512;     // rows per tile (one per thread)
 
-// partials[b][j] = sum over the rows of block b of Q_j[l] r_l (r given, FP64)
-template <int KPW>
-__global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, int k, const double2* __restrict__ r,
+// partials[b][j] = sum over the rows of block b of Q_j[l] r_l (r given in FP64, or
+// SPLIT: already as FP32 pairs, one float4 per complex entry)
+template <int KPW, bool SPLIT>
+__global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, int k, const void* __restrict__ rv_,
                                                      long long N, double2* __restrict__ partials, long long rows_per_block) {
     __shared__ float4 rs[PJ_TILE];       // (re hi, re lo, im hi, im lo)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -438,10 +439,14 @@ __global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict
     for (int c = 0; c < KPW; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
     for (long long t0 = r0; t0 < r1; t0 += PJ_TILE) {
         const long long l = t0 + threadIdx.x;
-        const double2 rv = l < r1 ? r[l] : make_double2(0, 0);
-        float4 rp;
-        split_f64(rv.x, rp.x, rp.y);
-        split_f64(rv.y, rp.z, rp.w);
+        float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (SPLIT) {
+            if (l < r1) rp = static_cast<const float4*>(rv_)[l];
+        } else {
+            const double2 rv = l < r1 ? static_cast<const double2*>(rv_)[l] : make_double2(0, 0);
+            split_f64(rv.x, rp.x, rp.y);
+            split_f64(rv.y, rp.z, rp.w);
+        }
         __syncthreads();
         rs[threadIdx.x] = rp;
         __syncthreads();
@@ -518,8 +523,11 @@ __global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ 
 }
 
 // z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
+// BASE: z_l = base_l + sum_j Q_j[l] y_j with base given as FP32 pairs
+template <bool BASE>
 __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q, int k, const double2* __restrict__ y,
-                                                    double2* __restrict__ z, long long N) {
+                                                    double2* __restrict__ z, const float4* __restrict__ base,
+                                                    long long N) {
     __shared__ float4 ys[kMaxP];
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         float4 t;
@@ -549,8 +557,18 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
             pair_fma(a0, a1, qv.x, qv.y, yy.x, yy.y);
             pair_fma(a2, a3, qv.x, qv.y, yy.z, yy.w);
         }
-        double2 zz = z[l];
-        z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
+        if (BASE) {
+            // (b + a) as a pair sum, then one conversion to FP64
+            const float4 b = base[l];
+            float s0 = b.x + a0, bb = s0 - b.x, e0 = (b.x - (s0 - bb)) + (a0 - bb) + (b.y + a1);
+            float s1 = b.z + a2;
+            bb = s1 - b.z;
+            const float e1 = (b.z - (s1 - bb)) + (a2 - bb) + (b.w + a3);
+            z[l] = make_double2((double)s0 + (double)e0, (double)s1 + (double)e1);
+        } else {
+            double2 zz = z[l];
+            z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
+        }
     }
 }
 
@@ -954,7 +972,7 @@ void launch_project_df(const float2* Q, int k, const double2* r, long long N, do
                        cudaStream_t s) {
     long long rows = (N + nblk - 1) / nblk;
     const int kpw = (k + 15) / 16;
-#define PJ_CASE(K) k_project_df<K><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, partials, rows)
+#define PJ_CASE(K) k_project_df<K, false><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, partials, rows)
     if (kpw <= 1) PJ_CASE(1);
     else if (kpw <= 2) PJ_CASE(2);
     else if (kpw <= 4) PJ_CASE(4);
@@ -965,7 +983,26 @@ void launch_project_df(const float2* Q, int k, const double2* r, long long N, do
 
 void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
     long long b = (N + 255) / 256;
-    k_prolong_df<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, N);
+    k_prolong_df<false><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, nullptr, N);
+}
+
+void launch_prolong_df_base(const float2* Q, int k, const double2* y, const float4* base, double2* z, long long N,
+                            cudaStream_t s) {
+    long long b = (N + 255) / 256;
+    k_prolong_df<true><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, base, N);
+}
+
+void launch_project_df_split(const float2* Q, int k, const float4* r, long long N, double2* partials, int nblk,
+                             cudaStream_t s) {
+    long long rows = (N + nblk - 1) / nblk;
+    const int kpw = (k + 15) / 16;
+#define PJ_CASE(K) k_project_df<K, true><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, partials, rows)
+    if (kpw <= 1) PJ_CASE(1);
+    else if (kpw <= 2) PJ_CASE(2);
+    else if (kpw <= 4) PJ_CASE(4);
+    else if (kpw <= 8) PJ_CASE(8);
+    else PJ_CASE(16);
+#undef PJ_CASE
 }
 
 void launch_red_rows(const float2* Q, int k, long long N, int n, float2* Qr, cudaStream_t s) {
