@@ -194,11 +194,12 @@ helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, do
         r = h->tmp[13];
     }
     ev_mark(h, 0, 0);
-    launch_project_df(red_only ? h->Qr : h->Q, h->k, r, rows, h->coarse_partials, nblk, h->stream);
+    launch_project_df(red_only ? h->Qr : h->Q, red_only ? basis_ld((h->N + 1) / 2) : basis_ld(h->N), h->k, r, rows,
+                      h->coarse_partials, nblk, h->stream);
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
     ev_mark(h, 1, 0);
-    launch_prolong_df(h->Q, h->k, h->ybuf, z, h->N, h->stream);
+    launch_prolong_tma(h->Q, basis_ld(h->N), h->k, h->ybuf, z, nullptr, h->N, h->dflag + 2, h->stream);
     ev_mark(h, 1, 1);
     h->launches += 4;
     CKL();
@@ -301,13 +302,13 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
     }
     launch_residual_red_df(h->op64, h->dft, fs, xs, rr, conj, s);
     const long long rows = (h->N + 1) / 2;
-    const int nblk = project_blocks(rows);
+    const int nblk = project_tma_blocks(rows);
     ev_mark(h, 0, 0);
-    launch_project_df_split(h->Qr, h->k, rr, rows, h->coarse_partials, nblk, s);
+    launch_project_tma(h->Qr, basis_ld(rows), h->k, rr, rows, h->coarse_partials, h->dflag + 2, s);
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, s);
     ev_mark(h, 1, 0);
-    launch_prolong_df_base(h->Q, h->k, h->ybuf, xs, z, h->N, s);
+    launch_prolong_tma(h->Q, basis_ld(h->N), h->k, h->ybuf, z, xs, h->N, h->dflag + 2, s);
     ev_mark(h, 1, 1);
     h->launches += 2 * o->n_r + 5;
     CKL();
@@ -1049,11 +1050,14 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     }
     // column-major FP32-pair Q for the per-iteration kernels; T becomes hi + lo so that
     // A_c is built from exactly the basis the kernels apply
-    STEP(dalloc(h, &h->Q, (size_t)N * k));
-    launch_split_basis(T, ldq, k, h->Q, N, s);
+    // column strides padded (basis_ld): zero-filled so that padding rows are finite
+    STEP(dalloc(h, &h->Q, (size_t)basis_ld(N) * k));
+    STEPC(cudaMemsetAsync(h->Q, 0, sizeof(float2) * basis_ld(N) * k, s));
+    launch_split_basis(T, ldq, k, h->Q, basis_ld(N), N, s);
     dfree(h->Qr);
-    STEP(dalloc(h, &h->Qr, (size_t)((N + 1) / 2) * k));
-    launch_red_rows(h->Q, k, N, h->n, h->Qr, s);
+    STEP(dalloc(h, &h->Qr, (size_t)basis_ld((N + 1) / 2) * k));
+    STEPC(cudaMemsetAsync(h->Qr, 0, sizeof(float2) * basis_ld((N + 1) / 2) * k, s));
+    launch_red_rows(h->Q, basis_ld(N), k, N, h->n, h->Qr, basis_ld((N + 1) / 2), s);
     // A_c = Q^T (A Q)
     st = build_coarse(h, T, ldq, k);
     if (st != HELM_OK) {
@@ -1113,7 +1117,7 @@ helm_status don_get_q(const helm_handle* hc, double* q_out) {
     helm_handle* h = const_cast<helm_handle*>(hc);
     if (!h || !q_out) return fail(h, HELM_BAD_ARG, "null argument");
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
-    launch_cm_pair_to_rm(h->Q, h->k, q_out, h->N, h->stream);
+    launch_cm_pair_to_rm(h->Q, basis_ld(h->N), h->k, q_out, h->N, h->stream);
     CKL();
     return HELM_OK;
 }
@@ -1173,6 +1177,13 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     }
     CK(cudaEventRecord(h->ev1, h->stream));
     CK(cudaEventSynchronize(h->ev1));
+    // a bounded wait of a staged kernel that gave up leaves a flag (never expected)
+    int waited_out = 0;
+    CK(cudaMemcpy(&waited_out, h->dflag + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (waited_out) {
+        CK(cudaMemset(h->dflag + 2, 0, sizeof(int)));
+        return fail(h, HELM_CUDA_ERROR, "a bulk-copy wait in the trunk-basis kernels timed out");
+    }
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     st.ms = ms;
@@ -1242,7 +1253,7 @@ helm_status helm_set_k2(helm_handle* h, const double* k2) {
         // rebuild A_c for the new operator from a node-major copy of the (possibly rounded) basis
         double* Qrm = nullptr;
         TRY(dalloc(h, &Qrm, (size_t)N * h->k));
-        launch_cm_pair_to_rm(h->Q, h->k, Qrm, N, h->stream);
+        launch_cm_pair_to_rm(h->Q, basis_ld(N), h->k, Qrm, N, h->stream);
         helm_status st = build_coarse(h, Qrm, h->k, h->k);
         cudaStreamSynchronize(h->stream);
         dfree(Qrm);

@@ -177,13 +177,18 @@ void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cud
 // FP64 projection on FP32 pipes: Q as (hi, lo) FP32 pairs, column-major k x N
 // (N rows: the projection also runs on the compact red rows, N = ceil(N / 2))
 int project_blocks(long long N);
-void launch_project_df(const float2* Q, int k, const double2* r, long long N, double2* partials, int nblk,
+// column stride of a column-major basis with `rows` rows: a multiple of 64 entries
+// with at least one padding entry (bulk copies of an even number of rows stay inside)
+inline long long basis_ld(long long rows) { return (rows + 1 + 63) / 64 * 64; }
+void launch_project_df(const float2* Q, long long ld, int k, const double2* r, long long N, double2* partials,
+                       int nblk, cudaStream_t s);
+void launch_prolong_df(const float2* Q, long long ld, int k, const double2* y, double2* z, long long N,
                        cudaStream_t s);
-void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s);
-void launch_split_basis(double* A, int ld, int k, float2* B, long long N, cudaStream_t s);
-void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, cudaStream_t s);
+void launch_split_basis(double* A, int ld, int k, float2* B, long long ldb, long long N, cudaStream_t s);
+void launch_cm_pair_to_rm(const float2* B, long long ldb, int k, double* A, long long N, cudaStream_t s);
 // Q_red (k x ceil(N / 2)): the red rows of Q, row m = the red node of pair (2m, 2m + 1)
-void launch_red_rows(const float2* Q, int k, long long N, int n, float2* Qr, cudaStream_t s);
+void launch_red_rows(const float2* Q, long long ldq, int k, long long N, int n, float2* Qr, long long ldr,
+                     cudaStream_t s);
 // double-float red-black Gauss-Seidel (stencil.cu): fs = f as FP32 pairs and the
 // first (red) half-sweep from x = 0; later half-sweeps; the red-row residual
 // written as FP32 pairs (one entry per node pair)
@@ -194,11 +199,18 @@ void launch_rbgs_df(const Op<double>& op, const DfTab& t, int colour, const floa
 void launch_residual_red_df(const Op<double>& op, const DfTab& t, const float4* fs, const float4* xs, float4* r_red,
                             int conj, cudaStream_t s);
 // projection of a residual given as FP32 pairs (float4 per complex entry, N rows)
-void launch_project_df_split(const float2* Q, int k, const float4* r, long long N, double2* partials, int nblk,
-                             cudaStream_t s);
+void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
+                             int nblk, cudaStream_t s);
 // z = base + Q y with base given as FP32 pairs (float4 per complex entry)
-void launch_prolong_df_base(const float2* Q, int k, const double2* y, const float4* base, double2* z, long long N,
-                            cudaStream_t s);
+void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
+                            long long N, cudaStream_t s);
+// the same two operations with the basis staged through shared memory by bulk
+// copies (one block per SM); *err is set if a copy wait times out
+int project_tma_blocks(long long R);
+void launch_project_tma(const float2* Q, long long ld, int k, const float4* r, long long R, double2* partials,
+                        int* err, cudaStream_t s);
+void launch_prolong_tma(const float2* Q, long long ld, int k, const double2* y, double2* z, const float4* base,
+                        long long N, int* err, cudaStream_t s);
 // r_red[m] = (v - A z) at the red node of pair m (stencil.cu)
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s);

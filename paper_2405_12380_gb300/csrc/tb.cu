@@ -426,8 +426,9 @@ constexpr int PJ_TILE = 512;     // rows per tile (one per thread)
 // partials[b][j] = sum over the rows of block b of Q_j[l] r_l (r given in FP64, or
 // SPLIT: already as FP32 pairs, one float4 per complex entry)
 template <int KPW, bool SPLIT>
-__global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, int k, const void* __restrict__ rv_,
-                                                     long long N, double2* __restrict__ partials, long long rows_per_block) {
+__global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, long long ld, int k,
+                                                     const void* __restrict__ rv_, long long N,
+                                                     double2* __restrict__ partials, long long rows_per_block) {
     __shared__ float4 rs[PJ_TILE];       // (re hi, re lo, im hi, im lo)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = PJ_T / 32;
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict
         for (int c = 0; c < KPW; ++c) {
             const int j = warp + NW * c;
             if (j < k) {
-                const float2* Qj = Q + (long long)j * N + t0;
+                const float2* Qj = Q + (long long)j * ld + t0;
                 float a0 = acc[c][0], a1 = acc[c][1], a2 = acc[c][2], a3 = acc[c][3];
                 // all loads of the column issued before use (rows past the end of the
                 // block read nothing and meet r = 0 in shared memory)
@@ -525,9 +526,9 @@ __global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ 
 // z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 // BASE: z_l = base_l + sum_j Q_j[l] y_j with base given as FP32 pairs
 template <bool BASE>
-__global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q, int k, const double2* __restrict__ y,
-                                                    double2* __restrict__ z, const float4* __restrict__ base,
-                                                    long long N) {
+__global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q, long long ld, int k,
+                                                    const double2* __restrict__ y, double2* __restrict__ z,
+                                                    const float4* __restrict__ base, long long N) {
     __shared__ float4 ys[kMaxP];
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         float4 t;
@@ -543,7 +544,7 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
         for (; j + 8 <= k; j += 8) {
             float2 qv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(j + u) * N);
+            for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(j + u) * ld);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const float4 yy = ys[j + u];
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
             }
         }
         for (; j < k; ++j) {
-            const float2 qv = q[(long long)j * N];
+            const float2 qv = q[(long long)j * ld];
             const float4 yy = ys[j];
             pair_fma(a0, a1, qv.x, qv.y, yy.x, yy.y);
             pair_fma(a2, a3, qv.x, qv.y, yy.z, yy.w);
@@ -572,6 +573,242 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
     }
 }
 
+// ---------------------------------------------------- bulk-copy staged kernels
+// The projection and prolongation stream the basis once per application.  Here
+// each block (one per SM) walks its rows in tiles of TM_ROWS and the columns in
+// chunks of TM_KC; a tile-chunk of Q (and, for the projection, the tile of r) is
+// brought into shared memory by one elected thread with cp.async.bulk, completing
+// on an mbarrier, three stages deep, so that the copies of the next two units are
+// in flight while the block computes on the current one.  Every copy starts on a
+// 16-byte boundary: column strides are even (basis_ld), tiles start on even rows
+// and cover an even number of rows (one padding row at an odd end is read and
+// ignored).  Waits are bounded: on a timeout the block records it in *err (never
+// expected; the host reports HELM_CUDA_ERROR) after draining its copies.
+constexpr int TM_T = 512;        // threads: 16 warps
+constexpr int TM_ROWS = 512;     // rows per tile
+constexpr int TM_KC = 16;        // columns per chunk (one per warp in the projection)
+constexpr int TM_ST = 3;         // pipeline stages
+constexpr unsigned kWaitLimit = 1u << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// one unit: rows [t0, t0 + rows) of columns [j0, j0 + kc) into stage buffer qs
+// (row stride TM_ROWS), plus optionally rows of r into rs; thread 0 only
+__device__ __forceinline__ void issue_unit(const float2* Q, long long ld, int j0, int kc, long long t0, int rows,
+                                           float2* qs, const float4* r, float4* rs, unsigned long long* bar) {
+    const int rows_c = (rows + 1) & ~1;
+    const unsigned qbytes = (unsigned)rows_c * 8u;
+    const unsigned total = (unsigned)kc * qbytes + (r ? (unsigned)rows_c * 16u : 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, total);
+    for (int jj = 0; jj < kc; ++jj) bulk_g2s(qs + jj * TM_ROWS, Q + (long long)(j0 + jj) * ld + t0, qbytes, bar);
+    if (r) bulk_g2s(rs, r + t0, (unsigned)rows_c * 16u, bar);
+}
+
+struct TmUnits {         // unit u of a block: its chunk, its tile
+    long long r0, r1;
+    int ntiles, nchunks;
+};
+__device__ __forceinline__ TmUnits tm_units(long long R, long long rows_per_block, int k) {
+    TmUnits t;
+    t.r0 = (long long)blockIdx.x * rows_per_block;
+    t.r1 = min(R, t.r0 + rows_per_block);
+    t.ntiles = t.r1 > t.r0 ? (int)((t.r1 - t.r0 + TM_ROWS - 1) / TM_ROWS) : 0;
+    t.nchunks = (k + TM_KC - 1) / TM_KC;
+    return t;
+}
+
+// partials[b][j] = sum over the rows of block b of Q_j[l] r_l, r given as FP32 pairs
+// (float4 per complex entry).  Units chunk-major: warp w owns column j0 + w of the
+// current chunk and keeps its pair sums in registers over the block's tiles.
+__global__ void __launch_bounds__(TM_T, 1) k_project_tma(const float2* __restrict__ Q, long long ld, int k,
+                                                         const float4* __restrict__ r, long long R,
+                                                         double2* __restrict__ partials, long long rows_per_block,
+                                                         int* err) {
+    extern __shared__ __align__(128) unsigned char tm_smem[];
+    float2* qs = reinterpret_cast<float2*>(tm_smem);                                   // [ST][KC][ROWS]
+    float4* rsm = reinterpret_cast<float4*>(tm_smem + (size_t)TM_ST * TM_KC * TM_ROWS * sizeof(float2));
+    __shared__ __align__(8) unsigned long long bar[TM_ST];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TmUnits U = tm_units(R, rows_per_block, k);
+    const int nunits = U.ntiles * U.nchunks;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < TM_ST; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto unit_of = [&](int u, int& j0, int& kc, long long& t0, int& rows) {
+        const int c = u / U.ntiles, i = u - c * U.ntiles;
+        j0 = c * TM_KC;
+        kc = min(TM_KC, k - j0);
+        t0 = U.r0 + (long long)i * TM_ROWS;
+        rows = (int)min((long long)TM_ROWS, U.r1 - t0);
+    };
+    if (threadIdx.x == 0)
+        for (int u = 0; u < min(TM_ST, nunits); ++u) {
+            int j0, kc, rows;
+            long long t0;
+            unit_of(u, j0, kc, t0, rows);
+            issue_unit(Q, ld, j0, kc, t0, rows, qs + (size_t)u * TM_KC * TM_ROWS, r, rsm + (size_t)u * TM_ROWS,
+                       &bar[u]);
+        }
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    unsigned phase = 0;          // bit st: parity of the next completion of stage st
+    for (int u = 0; u < nunits; ++u) {
+        const int st = u % TM_ST;
+        int j0, kc, rows;
+        long long t0;
+        unit_of(u, j0, kc, t0, rows);
+        if (!mbar_wait(&bar[st], (phase >> st) & 1u)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            for (int q = 0; q < TM_ST; ++q) mbar_wait(&bar[q], (phase >> q) & 1u);
+            return;
+        }
+        phase ^= 1u << st;
+        const float2* qcol = qs + (size_t)st * TM_KC * TM_ROWS + (size_t)warp * TM_ROWS;
+        const float4* rr = rsm + (size_t)st * TM_ROWS;
+        if (warp < kc) {
+#pragma unroll 4
+            for (int v = lane; v < rows; v += 32) {
+                const float2 q = qcol[v];
+                const float4 x = rr[v];
+                pair_fma(a0, a1, q.x, q.y, x.x, x.y);
+                pair_fma(a2, a3, q.x, q.y, x.z, x.w);
+            }
+        }
+        const bool chunk_end = (u % U.ntiles) == U.ntiles - 1;
+        if (chunk_end) {
+            pair_warp_sum(a0, a1);
+            pair_warp_sum(a2, a3);
+            if (lane == 0 && warp < kc)
+                partials[(long long)blockIdx.x * k + j0 + warp] =
+                    make_double2((double)a0 + (double)a1, (double)a2 + (double)a3);
+            a0 = a1 = a2 = a3 = 0.f;
+        }
+        __syncthreads();         // stage st is read by everyone: refill it
+        if (threadIdx.x == 0 && u + TM_ST < nunits) {
+            int j0n, kcn, rowsn;
+            long long t0n;
+            unit_of(u + TM_ST, j0n, kcn, t0n, rowsn);
+            issue_unit(Q, ld, j0n, kcn, t0n, rowsn, qs + (size_t)st * TM_KC * TM_ROWS, r,
+                       rsm + (size_t)st * TM_ROWS, &bar[st]);
+        }
+    }
+    // blocks without rows still own a partial row of zeros
+    if (nunits == 0 && threadIdx.x < k) partials[(long long)blockIdx.x * k + threadIdx.x] = make_double2(0, 0);
+}
+
+// z_l = (base_l or z_l) + sum_j Q_j[l] y_j, one thread per row of a tile; units
+// tile-major, the pair sums of a row kept in registers over the chunks
+template <bool BASE>
+__global__ void __launch_bounds__(TM_T, 1) k_prolong_tma(const float2* __restrict__ Q, long long ld, int k,
+                                                         const double2* __restrict__ y, double2* __restrict__ z,
+                                                         const float4* __restrict__ base, long long N,
+                                                         long long rows_per_block, int* err) {
+    extern __shared__ __align__(128) unsigned char tm_smem[];
+    float2* qs = reinterpret_cast<float2*>(tm_smem);
+    __shared__ float4 ys[kMaxP];
+    __shared__ __align__(8) unsigned long long bar[TM_ST];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        float4 t;
+        split_f64(y[j].x, t.x, t.y);
+        split_f64(y[j].y, t.z, t.w);
+        ys[j] = t;
+    }
+    const TmUnits U = tm_units(N, rows_per_block, k);
+    const int nunits = U.ntiles * U.nchunks;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < TM_ST; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto unit_of = [&](int u, int& j0, int& kc, long long& t0, int& rows) {
+        const int i = u / U.nchunks, c = u - i * U.nchunks;
+        j0 = c * TM_KC;
+        kc = min(TM_KC, k - j0);
+        t0 = U.r0 + (long long)i * TM_ROWS;
+        rows = (int)min((long long)TM_ROWS, U.r1 - t0);
+    };
+    if (threadIdx.x == 0)
+        for (int u = 0; u < min(TM_ST, nunits); ++u) {
+            int j0, kc, rows;
+            long long t0;
+            unit_of(u, j0, kc, t0, rows);
+            issue_unit(Q, ld, j0, kc, t0, rows, qs + (size_t)u * TM_KC * TM_ROWS, nullptr, nullptr, &bar[u]);
+        }
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    unsigned phase = 0;
+    for (int u = 0; u < nunits; ++u) {
+        const int st = u % TM_ST;
+        int j0, kc, rows;
+        long long t0;
+        unit_of(u, j0, kc, t0, rows);
+        if (!mbar_wait(&bar[st], (phase >> st) & 1u)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            for (int q = 0; q < TM_ST; ++q) mbar_wait(&bar[q], (phase >> q) & 1u);
+            return;
+        }
+        phase ^= 1u << st;
+        const float2* qt = qs + (size_t)st * TM_KC * TM_ROWS + threadIdx.x;
+        if (threadIdx.x < rows) {
+            for (int jj = 0; jj < kc; ++jj) {
+                const float2 q = qt[jj * TM_ROWS];
+                const float4 yy = ys[j0 + jj];
+                pair_fma(a0, a1, q.x, q.y, yy.x, yy.y);
+                pair_fma(a2, a3, q.x, q.y, yy.z, yy.w);
+            }
+            if (j0 + kc == k) {   // last chunk of the tile: write the row
+                const long long l = t0 + threadIdx.x;
+                if (BASE) {
+                    const float4 b = base[l];
+                    const float s0 = b.x + a0, bb0 = s0 - b.x;
+                    const float e0 = (b.x - (s0 - bb0)) + (a0 - bb0) + (b.y + a1);
+                    const float s1 = b.z + a2, bb1 = s1 - b.z;
+                    const float e1 = (b.z - (s1 - bb1)) + (a2 - bb1) + (b.w + a3);
+                    z[l] = make_double2((double)s0 + (double)e0, (double)s1 + (double)e1);
+                } else {
+                    const double2 zz = z[l];
+                    z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
+                }
+                a0 = a1 = a2 = a3 = 0.f;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && u + TM_ST < nunits) {
+            int j0n, kcn, rowsn;
+            long long t0n;
+            unit_of(u + TM_ST, j0n, kcn, t0n, rowsn);
+            issue_unit(Q, ld, j0n, kcn, t0n, rowsn, qs + (size_t)st * TM_KC * TM_ROWS, nullptr, nullptr, &bar[st]);
+        }
+    }
+}
+
 // colour of node l of a grid with n nodes per side: (i + j + k) mod 2, 0 = red
 __device__ __forceinline__ int node_colour(long long l, int n) {
     const unsigned ul = (unsigned)l, un = (unsigned)n;
@@ -583,19 +820,21 @@ __device__ __forceinline__ int node_colour(long long l, int n) {
 // Q_red[j][m] = Q[j][red node of pair m]; every pair (2m, 2m + 1) holds one red and
 // one black node (rows of even length start on even l; for odd n the colour is the
 // parity of l), and a last single node (odd N) is red
-__global__ void k_red_rows(const float2* __restrict__ Q, int k, long long N, int n, float2* __restrict__ Qr) {
+__global__ void k_red_rows(const float2* __restrict__ Q, long long ldq, int k, long long N, int n,
+                           float2* __restrict__ Qr, long long ldr) {
     const long long M = (N + 1) / 2;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < M * k;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long j = idx / M, m = idx - j * M;
         const long long l = 2 * m + node_colour(2 * m, n);
-        Qr[idx] = Q[j * N + l];
+        Qr[j * ldr + m] = Q[j * ldq + l];
     }
 }
 
 // FP64 row-major Q (N x ld) -> column-major pairs (k x N) of FP32 (hi, lo), and
 // the row-major FP64 values replaced by hi + lo (the basis the kernels use)
-__global__ void k_split_basis(double* __restrict__ A, int ld, int k, float2* __restrict__ B, long long N) {
+__global__ void k_split_basis(double* __restrict__ A, int ld, int k, float2* __restrict__ B, long long ldb,
+                              long long N) {
     __shared__ float2 tile[32][33];
     const long long l0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -613,11 +852,12 @@ __global__ void k_split_basis(double* __restrict__ A, int ld, int k, float2* __r
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         int c = c0 + r;
         long long l = l0 + threadIdx.x;
-        if (c < k && l < N) B[(long long)c * N + l] = tile[threadIdx.x][r];
+        if (c < k && l < N) B[(long long)c * ldb + l] = tile[threadIdx.x][r];
     }
 }
 
-__global__ void k_cm_pair_to_rm(const float2* __restrict__ B, int k, double* __restrict__ A, long long N) {
+__global__ void k_cm_pair_to_rm(const float2* __restrict__ B, long long ldb, int k, double* __restrict__ A,
+                                long long N) {
     __shared__ double tile[32][33];
     const long long l0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -626,7 +866,7 @@ __global__ void k_cm_pair_to_rm(const float2* __restrict__ B, int k, double* __r
         long long l = l0 + threadIdx.x;
         double v = 0.0;
         if (c < k && l < N) {
-            const float2 q = B[(long long)c * N + l];
+            const float2 q = B[(long long)c * ldb + l];
             v = (double)q.x + (double)q.y;
         }
         tile[r][threadIdx.x] = v;
@@ -968,11 +1208,36 @@ int project_blocks(long long N) {
     return (int)(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
 }
 
-void launch_project_df(const float2* Q, int k, const double2* r, long long N, double2* partials, int nblk,
+void launch_project_df(const float2* Q, long long ld, int k, const double2* r, long long N, double2* partials,
+                       int nblk, cudaStream_t s) {
+    long long rows = (N + nblk - 1) / nblk;
+    const int kpw = (k + 15) / 16;
+#define PJ_CASE(K) k_project_df<K, false><<<nblk, PJ_T, 0, s>>>(Q, ld, k, r, N, partials, rows)
+    if (kpw <= 1) PJ_CASE(1);
+    else if (kpw <= 2) PJ_CASE(2);
+    else if (kpw <= 4) PJ_CASE(4);
+    else if (kpw <= 8) PJ_CASE(8);
+    else PJ_CASE(16);
+#undef PJ_CASE
+}
+
+void launch_prolong_df(const float2* Q, long long ld, int k, const double2* y, double2* z, long long N,
                        cudaStream_t s) {
+    long long b = (N + 255) / 256;
+    k_prolong_df<false><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, nullptr, N);
+}
+
+void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
+                            long long N, cudaStream_t s) {
+    long long b = (N + 255) / 256;
+    k_prolong_df<true><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, base, N);
+}
+
+void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
+                             int nblk, cudaStream_t s) {
     long long rows = (N + nblk - 1) / nblk;
     const int kpw = (k + 15) / 16;
-#define PJ_CASE(K) k_project_df<K, false><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, partials, rows)
+#define PJ_CASE(K) k_project_df<K, true><<<nblk, PJ_T, 0, s>>>(Q, ld, k, r, N, partials, rows)
     if (kpw <= 1) PJ_CASE(1);
     else if (kpw <= 2) PJ_CASE(2);
     else if (kpw <= 4) PJ_CASE(4);
@@ -981,42 +1246,61 @@ void launch_project_df(const float2* Q, int k, const double2* r, long long N, do
 #undef PJ_CASE
 }
 
-void launch_prolong_df(const float2* Q, int k, const double2* y, double2* z, long long N, cudaStream_t s) {
-    long long b = (N + 255) / 256;
-    k_prolong_df<false><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, nullptr, N);
+// rows per block of the staged kernels: whole tiles over at most 152 blocks
+static long long tm_rows_per_block(long long R, int* nblk) {
+    const long long tiles = (R + TM_ROWS - 1) / TM_ROWS;
+    const long long b = tiles < 152 ? (tiles < 1 ? 1 : tiles) : 152;
+    *nblk = (int)b;
+    return (tiles + b - 1) / b * TM_ROWS;
 }
 
-void launch_prolong_df_base(const float2* Q, int k, const double2* y, const float4* base, double2* z, long long N,
-                            cudaStream_t s) {
-    long long b = (N + 255) / 256;
-    k_prolong_df<true><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, k, y, z, base, N);
+int project_tma_blocks(long long R) {
+    int nblk;
+    tm_rows_per_block(R, &nblk);
+    return nblk;
 }
 
-void launch_project_df_split(const float2* Q, int k, const float4* r, long long N, double2* partials, int nblk,
-                             cudaStream_t s) {
-    long long rows = (N + nblk - 1) / nblk;
-    const int kpw = (k + 15) / 16;
-#define PJ_CASE(K) k_project_df<K, true><<<nblk, PJ_T, 0, s>>>(Q, k, r, N, partials, rows)
-    if (kpw <= 1) PJ_CASE(1);
-    else if (kpw <= 2) PJ_CASE(2);
-    else if (kpw <= 4) PJ_CASE(4);
-    else if (kpw <= 8) PJ_CASE(8);
-    else PJ_CASE(16);
-#undef PJ_CASE
+void launch_project_tma(const float2* Q, long long ld, int k, const float4* r, long long R, double2* partials,
+                        int* err, cudaStream_t s) {
+    const size_t smem = (size_t)TM_ST * TM_KC * TM_ROWS * sizeof(float2) + (size_t)TM_ST * TM_ROWS * sizeof(float4);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_project_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    int nblk;
+    const long long rpb = tm_rows_per_block(R, &nblk);
+    k_project_tma<<<nblk, TM_T, smem, s>>>(Q, ld, k, r, R, partials, rpb, err);
 }
 
-void launch_red_rows(const float2* Q, int k, long long N, int n, float2* Qr, cudaStream_t s) {
-    k_red_rows<<<4 * 152, 256, 0, s>>>(Q, k, N, n, Qr);
+void launch_prolong_tma(const float2* Q, long long ld, int k, const double2* y, double2* z, const float4* base,
+                        long long N, int* err, cudaStream_t s) {
+    const size_t smem = (size_t)TM_ST * TM_KC * TM_ROWS * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_prolong_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_prolong_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    int nblk;
+    const long long rpb = tm_rows_per_block(N, &nblk);
+    if (base) k_prolong_tma<true><<<nblk, TM_T, smem, s>>>(Q, ld, k, y, z, base, N, rpb, err);
+    else k_prolong_tma<false><<<nblk, TM_T, smem, s>>>(Q, ld, k, y, z, nullptr, N, rpb, err);
 }
 
-void launch_split_basis(double* A, int ld, int k, float2* B, long long N, cudaStream_t s) {
+void launch_red_rows(const float2* Q, long long ldq, int k, long long N, int n, float2* Qr, long long ldr,
+                     cudaStream_t s) {
+    k_red_rows<<<4 * 152, 256, 0, s>>>(Q, ldq, k, N, n, Qr, ldr);
+}
+
+void launch_split_basis(double* A, int ld, int k, float2* B, long long ldb, long long N, cudaStream_t s) {
     dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
-    k_split_basis<<<g, dim3(32, 8), 0, s>>>(A, ld, k, B, N);
+    k_split_basis<<<g, dim3(32, 8), 0, s>>>(A, ld, k, B, ldb, N);
 }
 
-void launch_cm_pair_to_rm(const float2* B, int k, double* A, long long N, cudaStream_t s) {
+void launch_cm_pair_to_rm(const float2* B, long long ldb, int k, double* A, long long N, cudaStream_t s) {
     dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
-    k_cm_pair_to_rm<<<g, dim3(32, 8), 0, s>>>(B, k, A, N);
+    k_cm_pair_to_rm<<<g, dim3(32, 8), 0, s>>>(B, ldb, k, A, N);
 }
 
 void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s) {
