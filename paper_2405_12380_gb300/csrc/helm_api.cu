@@ -1065,7 +1065,8 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         dfree(h->Q); dfree(h->Qr); dfree(h->Ainv);
         return st;
     }
-    STEP(dalloc(h, &h->coarse_partials, (size_t)std::max(restrict_blocks(N), project_blocks(N)) * k));
+    STEP(dalloc(h, &h->coarse_partials,
+                (size_t)std::max(std::max(restrict_blocks(N), project_blocks(N)), project_tma_blocks((N + 1) / 2)) * k));
     if (h->precision == HELM_MIXED) {
         dfree(h->partials32); dfree(h->y32);
         STEP(dalloc(h, &h->partials32, (size_t)restrict_blocks(N) * k));

@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
 
 // ---------------------------------------------------- bulk-copy staged kernels
 // The projection and prolongation stream the basis once per application.  Here
-// each block (one per SM) walks its rows in tiles of TM_ROWS and the columns in
+// each block (two per SM) walks its rows in tiles of TM_ROWS and the columns in
 // chunks of TM_KC; a tile-chunk of Q (and, for the projection, the tile of r) is
 // brought into shared memory by one elected thread with cp.async.bulk, completing
 // on an mbarrier, three stages deep, so that the copies of the next two units are
@@ -584,10 +584,10 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
 // and cover an even number of rows (one padding row at an odd end is read and
 // ignored).  Waits are bounded: on a timeout the block records it in *err (never
 // expected; the host reports HELM_CUDA_ERROR) after draining its copies.
-constexpr int TM_T = 512;        // threads: 16 warps
-constexpr int TM_ROWS = 512;     // rows per tile
-constexpr int TM_KC = 16;        // columns per chunk (one per warp in the projection)
-constexpr int TM_ST = 3;         // pipeline stages
+constexpr int TM_T = 256;        // threads: 8 warps; two blocks per SM
+constexpr int TM_ROWS = 256;     // rows per tile
+constexpr int TM_KC = 16;        // columns per chunk (two per warp in the projection)
+constexpr int TM_ST = 3;         // pipeline stages (3 x 36 KB per block)
 constexpr unsigned kWaitLimit = 1u << 20;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -645,9 +645,10 @@ __device__ __forceinline__ TmUnits tm_units(long long R, long long rows_per_bloc
 }
 
 // partials[b][j] = sum over the rows of block b of Q_j[l] r_l, r given as FP32 pairs
-// (float4 per complex entry).  Units chunk-major: warp w owns column j0 + w of the
-// current chunk and keeps its pair sums in registers over the block's tiles.
-__global__ void __launch_bounds__(TM_T, 1) k_project_tma(const float2* __restrict__ Q, long long ld, int k,
+// (float4 per complex entry).  Units chunk-major: warp w owns columns j0 + w and
+// j0 + w + 8 of the current chunk and keeps their pair sums in registers over the
+// block's tiles.
+__global__ void __launch_bounds__(TM_T, 2) k_project_tma(const float2* __restrict__ Q, long long ld, int k,
                                                          const float4* __restrict__ r, long long R,
                                                          double2* __restrict__ partials, long long rows_per_block,
                                                          int* err) {
@@ -678,7 +679,7 @@ __global__ void __launch_bounds__(TM_T, 1) k_project_tma(const float2* __restric
             issue_unit(Q, ld, j0, kc, t0, rows, qs + (size_t)u * TM_KC * TM_ROWS, r, rsm + (size_t)u * TM_ROWS,
                        &bar[u]);
         }
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
     unsigned phase = 0;          // bit st: parity of the next completion of stage st
     for (int u = 0; u < nunits; ++u) {
         const int st = u % TM_ST;
@@ -691,25 +692,33 @@ __global__ void __launch_bounds__(TM_T, 1) k_project_tma(const float2* __restric
             return;
         }
         phase ^= 1u << st;
-        const float2* qcol = qs + (size_t)st * TM_KC * TM_ROWS + (size_t)warp * TM_ROWS;
         const float4* rr = rsm + (size_t)st * TM_ROWS;
-        if (warp < kc) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = warp + 8 * h;
+            if (jj < kc) {
+                const float2* qcol = qs + (size_t)st * TM_KC * TM_ROWS + (size_t)jj * TM_ROWS;
 #pragma unroll 4
-            for (int v = lane; v < rows; v += 32) {
-                const float2 q = qcol[v];
-                const float4 x = rr[v];
-                pair_fma(a0, a1, q.x, q.y, x.x, x.y);
-                pair_fma(a2, a3, q.x, q.y, x.z, x.w);
+                for (int v = lane; v < rows; v += 32) {
+                    const float2 q = qcol[v];
+                    const float4 x = rr[v];
+                    pair_fma(acc[h][0], acc[h][1], q.x, q.y, x.x, x.y);
+                    pair_fma(acc[h][2], acc[h][3], q.x, q.y, x.z, x.w);
+                }
             }
         }
         const bool chunk_end = (u % U.ntiles) == U.ntiles - 1;
         if (chunk_end) {
-            pair_warp_sum(a0, a1);
-            pair_warp_sum(a2, a3);
-            if (lane == 0 && warp < kc)
-                partials[(long long)blockIdx.x * k + j0 + warp] =
-                    make_double2((double)a0 + (double)a1, (double)a2 + (double)a3);
-            a0 = a1 = a2 = a3 = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int jj = warp + 8 * h;
+                pair_warp_sum(acc[h][0], acc[h][1]);
+                pair_warp_sum(acc[h][2], acc[h][3]);
+                if (lane == 0 && jj < kc)
+                    partials[(long long)blockIdx.x * k + j0 + jj] =
+                        make_double2((double)acc[h][0] + (double)acc[h][1], (double)acc[h][2] + (double)acc[h][3]);
+                acc[h][0] = acc[h][1] = acc[h][2] = acc[h][3] = 0.f;
+            }
         }
         __syncthreads();         // stage st is read by everyone: refill it
         if (threadIdx.x == 0 && u + TM_ST < nunits) {
@@ -721,13 +730,14 @@ __global__ void __launch_bounds__(TM_T, 1) k_project_tma(const float2* __restric
         }
     }
     // blocks without rows still own a partial row of zeros
-    if (nunits == 0 && threadIdx.x < k) partials[(long long)blockIdx.x * k + threadIdx.x] = make_double2(0, 0);
+    if (nunits == 0)
+        for (int j = threadIdx.x; j < k; j += TM_T) partials[(long long)blockIdx.x * k + j] = make_double2(0, 0);
 }
 
 // z_l = (base_l or z_l) + sum_j Q_j[l] y_j, one thread per row of a tile; units
 // tile-major, the pair sums of a row kept in registers over the chunks
 template <bool BASE>
-__global__ void __launch_bounds__(TM_T, 1) k_prolong_tma(const float2* __restrict__ Q, long long ld, int k,
+__global__ void __launch_bounds__(TM_T, 2) k_prolong_tma(const float2* __restrict__ Q, long long ld, int k,
                                                          const double2* __restrict__ y, double2* __restrict__ z,
                                                          const float4* __restrict__ base, long long N,
                                                          long long rows_per_block, int* err) {
@@ -1246,10 +1256,10 @@ void launch_project_df_split(const float2* Q, long long ld, int k, const float4*
 #undef PJ_CASE
 }
 
-// rows per block of the staged kernels: whole tiles over at most 152 blocks
+// rows per block of the staged kernels: whole tiles over at most 2 x 152 blocks
 static long long tm_rows_per_block(long long R, int* nblk) {
     const long long tiles = (R + TM_ROWS - 1) / TM_ROWS;
-    const long long b = tiles < 152 ? (tiles < 1 ? 1 : tiles) : 152;
+    const long long b = tiles < 304 ? (tiles < 1 ? 1 : tiles) : 304;
     *nblk = (int)b;
     return (tiles + b - 1) / b * TM_ROWS;
 }
