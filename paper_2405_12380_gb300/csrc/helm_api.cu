@@ -199,7 +199,7 @@ helm_status tb_correct(helm_handle* h, const double2* v, const double2* zres, do
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, h->stream);
     ev_mark(h, 1, 0);
-    launch_prolong_tma(h->Q, basis_ld(h->N), h->k, h->ybuf, z, nullptr, h->N, h->dflag + 2, h->stream);
+    launch_prolong_df(h->Q, basis_ld(h->N), h->k, h->ybuf, z, h->N, h->stream);
     ev_mark(h, 1, 1);
     h->launches += 4;
     CKL();
@@ -302,13 +302,13 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
     }
     launch_residual_red_df(h->op64, h->dft, fs, xs, rr, conj, s);
     const long long rows = (h->N + 1) / 2;
-    const int nblk = project_tma_blocks(rows);
+    const int nblk = project_blocks(rows);
     ev_mark(h, 0, 0);
-    launch_project_tma(h->Qr, basis_ld(rows), h->k, rr, rows, h->coarse_partials, h->dflag + 2, s);
+    launch_project_df_split(h->Qr, basis_ld(rows), h->k, rr, rows, h->coarse_partials, nblk, s);
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, s);
     ev_mark(h, 1, 0);
-    launch_prolong_tma(h->Q, basis_ld(h->N), h->k, h->ybuf, z, xs, h->N, h->dflag + 2, s);
+    launch_prolong_df_base(h->Q, basis_ld(h->N), h->k, h->ybuf, xs, z, h->N, s);
     ev_mark(h, 1, 1);
     h->launches += 2 * o->n_r + 5;
     CKL();
@@ -1065,8 +1065,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         dfree(h->Q); dfree(h->Qr); dfree(h->Ainv);
         return st;
     }
-    STEP(dalloc(h, &h->coarse_partials,
-                (size_t)std::max(std::max(restrict_blocks(N), project_blocks(N)), project_tma_blocks((N + 1) / 2)) * k));
+    STEP(dalloc(h, &h->coarse_partials, (size_t)std::max(restrict_blocks(N), project_blocks(N)) * k));
     if (h->precision == HELM_MIXED) {
         dfree(h->partials32); dfree(h->y32);
         STEP(dalloc(h, &h->partials32, (size_t)restrict_blocks(N) * k));
@@ -1178,13 +1177,6 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     }
     CK(cudaEventRecord(h->ev1, h->stream));
     CK(cudaEventSynchronize(h->ev1));
-    // a bounded wait of a staged kernel that gave up leaves a flag (never expected)
-    int waited_out = 0;
-    CK(cudaMemcpy(&waited_out, h->dflag + 2, sizeof(int), cudaMemcpyDeviceToHost));
-    if (waited_out) {
-        CK(cudaMemset(h->dflag + 2, 0, sizeof(int)));
-        return fail(h, HELM_CUDA_ERROR, "a bulk-copy wait in the trunk-basis kernels timed out");
-    }
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     st.ms = ms;

@@ -178,7 +178,7 @@ void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cud
 // (N rows: the projection also runs on the compact red rows, N = ceil(N / 2))
 int project_blocks(long long N);
 // column stride of a column-major basis with `rows` rows: a multiple of 64 entries
-// with at least one padding entry (bulk copies of an even number of rows stay inside)
+// (512-byte aligned columns) with at least one zero padding entry
 inline long long basis_ld(long long rows) { return (rows + 1 + 63) / 64 * 64; }
 void launch_project_df(const float2* Q, long long ld, int k, const double2* r, long long N, double2* partials,
                        int nblk, cudaStream_t s);
@@ -204,13 +204,6 @@ void launch_project_df_split(const float2* Q, long long ld, int k, const float4*
 // z = base + Q y with base given as FP32 pairs (float4 per complex entry)
 void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
                             long long N, cudaStream_t s);
-// the same two operations with the basis staged through shared memory by bulk
-// copies (one block per SM); *err is set if a copy wait times out
-int project_tma_blocks(long long R);
-void launch_project_tma(const float2* Q, long long ld, int k, const float4* r, long long R, double2* partials,
-                        int* err, cudaStream_t s);
-void launch_prolong_tma(const float2* Q, long long ld, int k, const double2* y, double2* z, const float4* base,
-                        long long N, int* err, cudaStream_t s);
 // r_red[m] = (v - A z) at the red node of pair m (stencil.cu)
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s);

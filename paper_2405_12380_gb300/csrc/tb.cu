@@ -573,272 +573,6 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
     }
 }
 
-// ---------------------------------------------------- bulk-copy staged kernels
-// The projection and prolongation stream the basis once per application.  Here
-// each block (one per SM, 32 warps) walks its rows in tiles and the columns in
-// chunks; a tile-chunk of Q (and, for the projection, the tile of r) is brought
-// into shared memory by one elected thread with cp.async.bulk, completing on an
-// mbarrier, three or four stages deep, so that the copies of the next units are
-// in flight while the block computes on the current one.  Every copy starts on a
-// 16-byte boundary: column strides are even (basis_ld), tiles start on even rows
-// and cover an even number of rows (one padding row at an odd end is read and
-// ignored).  Waits are bounded: on a timeout the block records it in *err (never
-// expected; the host reports HELM_CUDA_ERROR) after draining its copies.
-// projection: 32 warps, 512-row tiles, 8 columns per chunk, 4 stages (4 x 40 KB);
-// prolongation: 32 warps, 1024-row tiles (one row per thread), 8 columns, 3 stages
-// (3 x 64 KB); one block per SM, rows split evenly over the blocks
-constexpr int TM_T = 1024;
-constexpr int PJT_ROWS = 512, PJT_KC = 8, PJT_ST = 4;
-constexpr int PLT_ROWS = 1024, PLT_KC = 8, PLT_ST = 3;
-constexpr unsigned kWaitLimit = 1u << 20;
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (unsigned it = 0; it < kWaitLimit; ++it) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-// one unit: rows [t0, t0 + rows) of columns [j0, j0 + kc) into stage buffer qs
-// (row stride ROWS), plus optionally the same rows of r into rs; thread 0 only
-template <int ROWS>
-__device__ __forceinline__ void issue_unit(const float2* Q, long long ld, int j0, int kc, long long t0, int rows,
-                                           float2* qs, const float4* r, float4* rs, unsigned long long* bar) {
-    const int rows_c = (rows + 1) & ~1;
-    const unsigned qbytes = (unsigned)rows_c * 8u;
-    const unsigned total = (unsigned)kc * qbytes + (r ? (unsigned)rows_c * 16u : 0u);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, total);
-    for (int jj = 0; jj < kc; ++jj) bulk_g2s(qs + jj * ROWS, Q + (long long)(j0 + jj) * ld + t0, qbytes, bar);
-    if (r) bulk_g2s(rs, r + t0, (unsigned)rows_c * 16u, bar);
-}
-
-// a block's rows [r0, r1) in tiles of ROWS and the columns in chunks of KC
-template <int ROWS, int KC>
-struct TmUnits {
-    long long r0, r1;
-    int ntiles, nchunks;
-    __device__ TmUnits(long long R, long long rows_per_block, int k) {
-        r0 = (long long)blockIdx.x * rows_per_block;
-        r1 = min(R, r0 + rows_per_block);
-        ntiles = r1 > r0 ? (int)((r1 - r0 + ROWS - 1) / ROWS) : 0;
-        nchunks = (k + KC - 1) / KC;
-    }
-};
-
-// partials[b][j] = sum over the rows of block b of Q_j[l] r_l, r given as FP32 pairs
-// (float4 per complex entry).  Units chunk-major; warp w owns column w % KC of the
-// chunk on the rows of group w / KC of each tile, keeping its pair sums in
-// registers over the tiles; at the end of a chunk the groups are added in a fixed
-// order.
-__global__ void __launch_bounds__(TM_T, 1) k_project_tma(const float2* __restrict__ Q, long long ld, int k,
-                                                         const float4* __restrict__ r, long long R,
-                                                         double2* __restrict__ partials, long long rows_per_block,
-                                                         int* err) {
-    constexpr int ROWS = PJT_ROWS, KC = PJT_KC, ST = PJT_ST;
-    constexpr int G = TM_T / 32 / KC;            // row groups per tile (4)
-    constexpr int GR = ROWS / G;                 // rows per group (128)
-    extern __shared__ __align__(128) unsigned char tm_smem[];
-    float2* qs = reinterpret_cast<float2*>(tm_smem);                                   // [ST][KC][ROWS]
-    float4* rsm = reinterpret_cast<float4*>(tm_smem + (size_t)ST * KC * ROWS * sizeof(float2));
-    __shared__ __align__(8) unsigned long long bar[ST];
-    __shared__ float4 gsum[G][KC];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int jj = warp % KC, g = warp / KC;
-    const TmUnits<ROWS, KC> U(R, rows_per_block, k);
-    const int nunits = U.ntiles * U.nchunks;
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < ST; ++st) mbar_init(&bar[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    auto unit_of = [&](int u, int& j0, int& kc, long long& t0, int& rows) {
-        const int c = u / U.ntiles, i = u - c * U.ntiles;
-        j0 = c * KC;
-        kc = min(KC, k - j0);
-        t0 = U.r0 + (long long)i * ROWS;
-        rows = (int)min((long long)ROWS, U.r1 - t0);
-    };
-    if (threadIdx.x == 0)
-        for (int u = 0; u < min(ST, nunits); ++u) {
-            int j0, kc, rows;
-            long long t0;
-            unit_of(u, j0, kc, t0, rows);
-            issue_unit<ROWS>(Q, ld, j0, kc, t0, rows, qs + (size_t)u * KC * ROWS, r, rsm + (size_t)u * ROWS, &bar[u]);
-        }
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    unsigned phase = 0;          // bit st: parity of the next completion of stage st
-    for (int u = 0; u < nunits; ++u) {
-        const int st = u % ST;
-        int j0, kc, rows;
-        long long t0;
-        unit_of(u, j0, kc, t0, rows);
-        if (!mbar_wait(&bar[st], (phase >> st) & 1u)) {
-            if (threadIdx.x == 0) atomicExch(err, 1);
-            for (int q = 0; q < ST; ++q) mbar_wait(&bar[q], (phase >> q) & 1u);
-            return;
-        }
-        phase ^= 1u << st;
-        if (jj < kc) {
-            const float2* qcol = qs + (size_t)st * KC * ROWS + (size_t)jj * ROWS;
-            const float4* rr = rsm + (size_t)st * ROWS;
-            const int v1 = min(rows, (g + 1) * GR);
-#pragma unroll 4
-            for (int v = g * GR + lane; v < v1; v += 32) {
-                const float2 q = qcol[v];
-                const float4 x = rr[v];
-                pair_fma(a0, a1, q.x, q.y, x.x, x.y);
-                pair_fma(a2, a3, q.x, q.y, x.z, x.w);
-            }
-        }
-        if ((u % U.ntiles) == U.ntiles - 1) {    // end of a chunk
-            pair_warp_sum(a0, a1);
-            pair_warp_sum(a2, a3);
-            if (lane == 0) gsum[g][jj] = make_float4(a0, a1, a2, a3);
-            a0 = a1 = a2 = a3 = 0.f;
-            __syncthreads();
-            if (threadIdx.x < kc) {
-                float4 t = gsum[0][threadIdx.x];
-                for (int q = 1; q < G; ++q) {    // fixed-order pair sums of the groups
-                    const float4 o = gsum[q][threadIdx.x];
-                    float s = t.x + o.x, bb = s - t.x;
-                    float e = (t.x - (s - bb)) + (o.x - bb);
-                    t.x = s;
-                    t.y = t.y + o.y + e;
-                    s = t.z + o.z;
-                    bb = s - t.z;
-                    e = (t.z - (s - bb)) + (o.z - bb);
-                    t.z = s;
-                    t.w = t.w + o.w + e;
-                }
-                partials[(long long)blockIdx.x * k + j0 + threadIdx.x] =
-                    make_double2((double)t.x + (double)t.y, (double)t.z + (double)t.w);
-            }
-        }
-        __syncthreads();         // stage st is read by everyone: refill it
-        if (threadIdx.x == 0 && u + ST < nunits) {
-            int j0n, kcn, rowsn;
-            long long t0n;
-            unit_of(u + ST, j0n, kcn, t0n, rowsn);
-            issue_unit<ROWS>(Q, ld, j0n, kcn, t0n, rowsn, qs + (size_t)st * KC * ROWS, r, rsm + (size_t)st * ROWS,
-                             &bar[st]);
-        }
-    }
-    // blocks without rows still own a partial row of zeros
-    if (nunits == 0)
-        for (int j = threadIdx.x; j < k; j += TM_T) partials[(long long)blockIdx.x * k + j] = make_double2(0, 0);
-}
-
-// z_l = (base_l or z_l) + sum_j Q_j[l] y_j, one thread per row of a tile; units
-// tile-major, the pair sums of a row kept in registers over the chunks
-template <bool BASE>
-__global__ void __launch_bounds__(TM_T, 1) k_prolong_tma(const float2* __restrict__ Q, long long ld, int k,
-                                                         const double2* __restrict__ y, double2* __restrict__ z,
-                                                         const float4* __restrict__ base, long long N,
-                                                         long long rows_per_block, int* err) {
-    constexpr int ROWS = PLT_ROWS, KC = PLT_KC, ST = PLT_ST;
-    extern __shared__ __align__(128) unsigned char tm_smem[];
-    float2* qs = reinterpret_cast<float2*>(tm_smem);
-    __shared__ float4 ys[kMaxP];
-    __shared__ __align__(8) unsigned long long bar[ST];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        float4 t;
-        split_f64(y[j].x, t.x, t.y);
-        split_f64(y[j].y, t.z, t.w);
-        ys[j] = t;
-    }
-    const TmUnits<ROWS, KC> U(N, rows_per_block, k);
-    const int nunits = U.ntiles * U.nchunks;
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < ST; ++st) mbar_init(&bar[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    auto unit_of = [&](int u, int& j0, int& kc, long long& t0, int& rows) {
-        const int i = u / U.nchunks, c = u - i * U.nchunks;
-        j0 = c * KC;
-        kc = min(KC, k - j0);
-        t0 = U.r0 + (long long)i * ROWS;
-        rows = (int)min((long long)ROWS, U.r1 - t0);
-    };
-    if (threadIdx.x == 0)
-        for (int u = 0; u < min(ST, nunits); ++u) {
-            int j0, kc, rows;
-            long long t0;
-            unit_of(u, j0, kc, t0, rows);
-            issue_unit<ROWS>(Q, ld, j0, kc, t0, rows, qs + (size_t)u * KC * ROWS, nullptr, nullptr, &bar[u]);
-        }
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    unsigned phase = 0;
-    for (int u = 0; u < nunits; ++u) {
-        const int st = u % ST;
-        int j0, kc, rows;
-        long long t0;
-        unit_of(u, j0, kc, t0, rows);
-        if (!mbar_wait(&bar[st], (phase >> st) & 1u)) {
-            if (threadIdx.x == 0) atomicExch(err, 1);
-            for (int q = 0; q < ST; ++q) mbar_wait(&bar[q], (phase >> q) & 1u);
-            return;
-        }
-        phase ^= 1u << st;
-        const float2* qt = qs + (size_t)st * KC * ROWS + threadIdx.x;
-        if (threadIdx.x < rows) {
-#pragma unroll
-            for (int jj = 0; jj < KC; ++jj) {
-                if (jj < kc) {
-                    const float2 q = qt[jj * ROWS];
-                    const float4 yy = ys[j0 + jj];
-                    pair_fma(a0, a1, q.x, q.y, yy.x, yy.y);
-                    pair_fma(a2, a3, q.x, q.y, yy.z, yy.w);
-                }
-            }
-            if (j0 + kc == k) {   // last chunk of the tile: write the row
-                const long long l = t0 + threadIdx.x;
-                if (BASE) {
-                    const float4 b = base[l];
-                    const float s0 = b.x + a0, bb0 = s0 - b.x;
-                    const float e0 = (b.x - (s0 - bb0)) + (a0 - bb0) + (b.y + a1);
-                    const float s1 = b.z + a2, bb1 = s1 - b.z;
-                    const float e1 = (b.z - (s1 - bb1)) + (a2 - bb1) + (b.w + a3);
-                    z[l] = make_double2((double)s0 + (double)e0, (double)s1 + (double)e1);
-                } else {
-                    const double2 zz = z[l];
-                    z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
-                }
-                a0 = a1 = a2 = a3 = 0.f;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && u + ST < nunits) {
-            int j0n, kcn, rowsn;
-            long long t0n;
-            unit_of(u + ST, j0n, kcn, t0n, rowsn);
-            issue_unit<ROWS>(Q, ld, j0n, kcn, t0n, rowsn, qs + (size_t)st * KC * ROWS, nullptr, nullptr, &bar[st]);
-        }
-    }
-}
-
 // colour of node l of a grid with n nodes per side: (i + j + k) mod 2, 0 = red
 __device__ __forceinline__ int node_colour(long long l, int n) {
     const unsigned ul = (unsigned)l, un = (unsigned)n;
@@ -1274,51 +1008,6 @@ void launch_project_df_split(const float2* Q, long long ld, int k, const float4*
     else if (kpw <= 8) PJ_CASE(8);
     else PJ_CASE(16);
 #undef PJ_CASE
-}
-
-// rows per block of the staged kernels: an even share of the rows (even, so that
-// every tile starts on a 16-byte boundary) for at most one block per SM
-static long long tm_rows_per_block(long long R, int tile_rows, int* nblk) {
-    long long b = (R + tile_rows / 2 - 1) / (tile_rows / 2);      // no block below half a tile
-    b = b < 1 ? 1 : (b > 152 ? 152 : b);
-    long long rpb = (R + b - 1) / b;
-    rpb += rpb & 1;
-    *nblk = (int)((R + rpb - 1) / rpb);
-    return rpb;
-}
-
-int project_tma_blocks(long long R) {
-    int nblk;
-    tm_rows_per_block(R, PJT_ROWS, &nblk);
-    return nblk;
-}
-
-void launch_project_tma(const float2* Q, long long ld, int k, const float4* r, long long R, double2* partials,
-                        int* err, cudaStream_t s) {
-    const size_t smem = (size_t)PJT_ST * PJT_KC * PJT_ROWS * sizeof(float2) + (size_t)PJT_ST * PJT_ROWS * sizeof(float4);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_project_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    int nblk;
-    const long long rpb = tm_rows_per_block(R, PJT_ROWS, &nblk);
-    k_project_tma<<<nblk, TM_T, smem, s>>>(Q, ld, k, r, R, partials, rpb, err);
-}
-
-void launch_prolong_tma(const float2* Q, long long ld, int k, const double2* y, double2* z, const float4* base,
-                        long long N, int* err, cudaStream_t s) {
-    const size_t smem = (size_t)PLT_ST * PLT_KC * PLT_ROWS * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_prolong_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_prolong_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    int nblk;
-    const long long rpb = tm_rows_per_block(N, PLT_ROWS, &nblk);
-    if (base) k_prolong_tma<true><<<nblk, TM_T, smem, s>>>(Q, ld, k, y, z, base, N, rpb, err);
-    else k_prolong_tma<false><<<nblk, TM_T, smem, s>>>(Q, ld, k, y, z, nullptr, N, rpb, err);
 }
 
 void launch_red_rows(const float2* Q, long long ldq, int k, long long N, int n, float2* Qr, long long ldr,
