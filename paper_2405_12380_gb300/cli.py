@@ -38,15 +38,19 @@ def main(argv=None):
     ap.add_argument("--experiment", choices=["mixed", "batch", "adjoint"], default=None)
     ap.add_argument("--count", type=int, default=64, help="batch: number of problems")
     ap.add_argument("--fd", type=int, default=32, help="adjoint: voxels checked by central differences")
+    ap.add_argument("--relax", default=None, help="experiments: jacobi | rbgs (default: the workload's)")
+    ap.add_argument("--n-r", type=int, default=None, help="experiments: sweeps per preconditioner application")
+    ap.add_argument("--method", default=None, help="experiments: fgmres | bicgstab")
     a = ap.parse_args(argv)
     if a.stencil:
         return stencil(a.stencil, a.reps)
+    over = {k: v for k, v in (("relax", a.relax), ("n_r", a.n_r), ("method", a.method)) if v is not None}
     if a.experiment == "mixed":
-        return exp_mixed(a.maxit)
+        return exp_mixed(a.maxit, over)
     if a.experiment == "batch":
-        return exp_batch(a.count, a.maxit)
+        return exp_batch(a.count, a.maxit, over)
     if a.experiment == "adjoint":
-        return exp_adjoint(a.fd, a.maxit)
+        return exp_adjoint(a.fd, a.maxit, over)
     w = dict(scenes.BENCH_WORKLOADS[a.workload])
     if a.maxit is not None:
         w["maxit"] = a.maxit
@@ -93,7 +97,7 @@ def _emit(d):
     print(json.dumps(d), flush=True)
 
 
-def exp_mixed(maxit=None):
+def exp_mixed(maxit=None, over=None):
     """The 128^3 submarine scattering problem solved by DeepONet-FGMRES(50) (one Jacobi
     sweep + trunk-basis correction per preconditioner application) to 1e-6, once with
     the mixed-precision handle (complex64 preconditioner, BF16 basis, FP64 Arnoldi and
@@ -103,6 +107,7 @@ def exp_mixed(maxit=None):
     import scenes
     import paper_2405_12380_gb300 as hm
     w = dict(scenes.BENCH_WORKLOADS["submarine3d-128"])
+    w.update(over or {})
     sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
     torch.cuda.set_device(0)
     o = hm.opts(w["method"], w["relax"], w["n_r"], correction=w["correction"], tol=w["tol"],
@@ -121,6 +126,7 @@ def exp_mixed(maxit=None):
         st.pop("hist", None)
         xs[prec] = x
         _emit({"experiment": "mixed", "precision": prec, "workload": "submarine3d-128", "kept": k,
+               "method": w["method"], "relax": w["relax"], "n_r": w["n_r"],
                "setup_s": setup, "solve_s": st["ms"] / 1e3, "iters": st["iters"], "cycles": st["cycles"],
                "rel_res_fp64": st["rel_res"], "status": st["status_name"]})
         P.close()
@@ -130,7 +136,7 @@ def exp_mixed(maxit=None):
     _emit({"experiment": "mixed", "rel_diff_mixed_vs_fp64_solution": float(d)})
 
 
-def exp_batch(count=64, maxit=None):
+def exp_batch(count=64, maxit=None, over=None):
     """`count` problems on uneven grids 48^3-128^3 (seeded k, scatterers, sources):
     one batched mixed-precision DeepONet-FGMRES(30) solve (Jacobi + trunk basis, to
     1e-6) against the same problems solved one after another with the FP64 handle."""
@@ -140,7 +146,9 @@ def exp_batch(count=64, maxit=None):
     import paper_2405_12380_gb300 as hm
     torch.cuda.set_device(0)
     scs = scenes.batch_scenes(0, count=count)
-    o = hm.opts("fgmres", "jacobi", 1, tol=1e-6, restart=30, maxit=maxit or 20000)
+    ov = over or {}
+    o = hm.opts(ov.get("method", "fgmres"), ov.get("relax", "jacobi"), ov.get("n_r", 1), tol=1e-6, restart=30,
+                maxit=maxit or 20000)
     probs, fs = [], []
     for sc in scs:
         P = hm.Problem(3, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, precision="mixed")
@@ -155,7 +163,7 @@ def exp_batch(count=64, maxit=None):
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     ok = sum(1 for s_ in stb if s_["status"] == 0)
-    _emit({"experiment": "batch", "form": "batched mixed", "problems": count,
+    _emit({"experiment": "batch", "form": "batched mixed", "problems": count, "relax": o.relax, "n_r": o.n_r,
            "nodes": int(sum(P.N for P in probs)), "tile": tile, "wall_s": tb, "converged": ok,
            "iters_max": max(s_["iters"] for s_ in stb), "rel_res_max": max(s_["rel_res"] for s_ in stb)})
     B.close()
@@ -184,7 +192,7 @@ def exp_batch(count=64, maxit=None):
            "speedup_batched": t_seq / tb})
 
 
-def exp_adjoint(n_fd=32, maxit=None):
+def exp_adjoint(n_fd=32, maxit=None, over=None):
     """The 96^3 adjoint workload: receiver misfit of the bump-perturbed k^2 against
     data from the unperturbed field (here from a GPU solve; the tests use the
     oracle's), gradient by the adjoint DeepONet-FGMRES solve, timed, and checked
@@ -203,7 +211,9 @@ def exp_adjoint(n_fd=32, maxit=None):
     P = hm.Problem(3, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, layer_strength=sc.layer_strength, k2=k2)
     f = P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda())
     k = P.don_load(sc.trunk, sc.p, tau=1e-6)
-    o = hm.opts("fgmres", "rbgs", 1, tol=1e-10, restart=30, maxit=maxit or 20000)
+    ov = over or {}
+    o = hm.opts(ov.get("method", "fgmres"), ov.get("relax", "rbgs"), ov.get("n_r", 3), tol=1e-10, restart=30,
+                maxit=maxit or 20000)
     idx, w = P.receivers(sc.extra["receivers"])
     P.set_k2(k20)
     u0, st0 = P.solve(f, None, o)
@@ -219,7 +229,8 @@ def exp_adjoint(n_fd=32, maxit=None):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     g = k2t.grad.clone()
-    _emit({"experiment": "adjoint", "workload": "bump_cube3d-96", "kept": k, "loss": float(L),
+    _emit({"experiment": "adjoint", "workload": "bump_cube3d-96", "kept": k, "loss": float(L), "method": o.method,
+           "relax": o.relax, "n_r": o.n_r,
            "forward_backward_s": min(times), "forward_iters": st0["iters"]})
     # central differences on seeded fluid voxels (real and imaginary directions)
     rng = np.random.default_rng(7)
