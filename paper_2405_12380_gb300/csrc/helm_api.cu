@@ -289,18 +289,26 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
     float4* fs = reinterpret_cast<float4*>(h->tmp[14]);
     float4* xs = reinterpret_cast<float4*>(h->tmp[15]);
     float4* rr = reinterpret_cast<float4*>(h->tmp[13]);
-    launch_rbgs_df_first(h->op64, h->dft, r, fs, xs, conj, s);
-    for (int q = 0; q < o->n_r; ++q) {
-        if (q > 0) {
+    if (cycle_df_blocks(h->N) > 0) {
+        // one cooperative launch for the whole red-black part and the red residual
+        ev_mark(h, 2, 0);
+        CK(launch_cycle_df(h->op64, h->dft, r, fs, xs, rr, o->n_r, conj, h->counter + 2, h->dflag + 2, s));
+        ev_mark(h, 2, 1);
+        h->launches -= 2 * o->n_r;
+    } else {
+        launch_rbgs_df_first(h->op64, h->dft, r, fs, xs, conj, s);
+        for (int q = 0; q < o->n_r; ++q) {
+            if (q > 0) {
+                ev_mark(h, 2, 0);
+                launch_rbgs_df(h->op64, h->dft, 0, fs, xs, conj, s);
+                ev_mark(h, 2, 1);
+            }
             ev_mark(h, 2, 0);
-            launch_rbgs_df(h->op64, h->dft, 0, fs, xs, conj, s);
+            launch_rbgs_df(h->op64, h->dft, 1, fs, xs, conj, s);
             ev_mark(h, 2, 1);
         }
-        ev_mark(h, 2, 0);
-        launch_rbgs_df(h->op64, h->dft, 1, fs, xs, conj, s);
-        ev_mark(h, 2, 1);
+        launch_residual_red_df(h->op64, h->dft, fs, xs, rr, conj, s);
     }
-    launch_residual_red_df(h->op64, h->dft, fs, xs, rr, conj, s);
     const long long rows = (h->N + 1) / 2;
     const int nblk = project_blocks(rows);
     ev_mark(h, 0, 0);
@@ -1177,6 +1185,13 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     }
     CK(cudaEventRecord(h->ev1, h->stream));
     CK(cudaEventSynchronize(h->ev1));
+    // a grid-barrier wait that gave up leaves a flag (never expected)
+    int waited_out = 0;
+    CK(cudaMemcpy(&waited_out, h->dflag + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (waited_out) {
+        CK(cudaMemset(h->dflag + 2, 0, sizeof(int)));
+        return fail(h, HELM_CUDA_ERROR, "a grid-barrier wait of the red-black cycle timed out");
+    }
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     st.ms = ms;

@@ -198,6 +198,13 @@ void launch_rbgs_df(const Op<double>& op, const DfTab& t, int colour, const floa
                     cudaStream_t s);
 void launch_residual_red_df(const Op<double>& op, const DfTab& t, const float4* fs, const float4* xs, float4* r_red,
                             int conj, cudaStream_t s);
+// the same cycle (first half-sweep, n_r sweeps, red residual) as one cooperative
+// launch with grid barriers; bar2 = two zeroed counters, *err set if a barrier
+// wait times out.  Returns cudaErrorNotSupported where cooperative launch is not
+// available (the caller then uses the kernels above).
+int cycle_df_blocks(long long N);
+cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, const double2* f, float4* fs, float4* xs,
+                            float4* r_red, int n_r, int conj, unsigned* bar2, int* err, cudaStream_t s);
 // projection of a residual given as FP32 pairs (float4 per complex entry, N rows)
 void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
                              int nblk, cudaStream_t s);

@@ -690,6 +690,127 @@ __global__ void __launch_bounds__(BX * BY) k_residual_red_df(Op<double> op, DfTa
     r_red[l >> 1] = cdf_pack(cdf_sub(cdf_load(fs, l), out));
 }
 
+// ---- the red-black part of the trunk-basis hybrid cycle in one cooperative
+// launch: f as pairs with the first red half-sweep from x = 0, the remaining
+// half-sweeps, and the red-row residual, each phase over the whole grid and the
+// phases separated by a grid barrier (one block per SM, all blocks resident).
+// Values written in an earlier phase by other blocks are read past L1 (ld.cg).
+// The barrier's wait is bounded: on a timeout it records *err and lets the block
+// go on (the host reports the solve as failed).
+struct GridBar {
+    unsigned* count;        // arrivals in the current barrier
+    unsigned* gen;          // barrier generation
+    int* err;
+};
+constexpr unsigned kBarSpinLimit = 1u << 22;
+
+__device__ __forceinline__ void grid_barrier(const GridBar& b) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = b.gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
+            atomicExch(b.count, 0u);
+            __threadfence();
+            atomicAdd(b.gen, 1u);
+        } else {
+            for (unsigned it = 0; *gen == g; ++it)
+                if (it > kBarSpinLimit) {
+                    atomicExch(b.err, 1);
+                    break;
+                }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int colour_of(long long l, int n) {
+    const unsigned ul = (unsigned)l, un = (unsigned)n;
+    const unsigned r = ul / un;          // row index j + n k
+    const unsigned kk = r / un;
+    return (int)(((ul - r * un) + (r - kk * un) + kk) & 1u);
+}
+
+__device__ __forceinline__ Cdf cdf_load_cg(const float4* p, long long l) {
+    const float4 v = __ldcg(p + l);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
+__device__ __forceinline__ Cdf nbr_sum_df_cg(const Op<double>& op, const float4* x, long long l, unsigned code) {
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    const Cdf a = (code & 1u) ? cdf_load_cg(x, l - 1) : cdf_zero();
+    const Cdf b = (code & 2u) ? cdf_load_cg(x, l + 1) : cdf_zero();
+    const Cdf c = (code & 4u) ? cdf_load_cg(x, l - sy) : cdf_zero();
+    const Cdf d = (code & 8u) ? cdf_load_cg(x, l + sy) : cdf_zero();
+    Cdf s = cdf_add(cdf_add(a, b), cdf_add(c, d));
+    if (op.dim == 3) {
+        const Cdf e = (code & 16u) ? cdf_load_cg(x, l - sz) : cdf_zero();
+        const Cdf f = (code & 32u) ? cdf_load_cg(x, l + sz) : cdf_zero();
+        s = cdf_add(s, cdf_add(e, f));
+    }
+    return s;
+}
+
+constexpr int kCycleThreads = 1024;
+
+__global__ void __launch_bounds__(kCycleThreads, 1) k_cycle_df(Op<double> op, DfTab t, const double2* __restrict__ f,
+                                                               float4* fs, float4* xs, float4* r_red, int n_r, int conj,
+                                                               GridBar bar) {
+    const long long N = op.N, M = (N + 1) / 2;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    // fs = f as pairs; x = D^-1 f on red fluid nodes, f on red masked nodes, 0 on black
+    for (long long l = tid; l < N; l += nth) {
+        const double2 fv = f[l];
+        const Cdf F = {df_split(fv.x), df_split(fv.y)};
+        __stcg(fs + l, cdf_pack(F));
+        Cdf x = cdf_zero();
+        if (colour_of(l, op.n) == 0) {
+            const unsigned code = op.nbm[l];
+            x = (code & kMasked) ? F : cdf_mul(invd_df(t, op.lidx[l], conj), F);
+        }
+        __stcg(xs + l, cdf_pack(x));
+    }
+    grid_barrier(bar);
+    for (int q = 0; q < n_r; ++q) {
+        for (int colour = (q == 0 ? 1 : 0); colour < 2; ++colour) {
+            for (long long m = tid; m < M; m += nth) {
+                const long long l = 2 * m + (colour_of(2 * m, op.n) != colour);
+                if (l >= N) continue;
+                const unsigned code = op.nbm[l];
+                const Cdf F = cdf_load_cg(fs, l);
+                Cdf x;
+                if (code & kMasked) {
+                    x = F;
+                } else {
+                    const Cdf sum = nbr_sum_df_cg(op, xs, l, code);
+                    x = cdf_mul(invd_df(t, op.lidx[l], conj), cdf_sub(F, cdf_scale(t.hinv2, sum)));
+                }
+                __stcg(xs + l, cdf_pack(x));
+            }
+            grid_barrier(bar);
+        }
+    }
+    // r_red[m] = (f - A x) at the red node of pair m
+    for (long long m = tid; m < M; m += nth) {
+        const long long l = 2 * m + (colour_of(2 * m, op.n) != 0);
+        const unsigned code = op.nbm[l];
+        const Cdf x = cdf_load_cg(xs, l);
+        Cdf out;
+        if (code & kMasked) {
+            out = x;
+        } else {
+            const Cdf sum = nbr_sum_df_cg(op, xs, l, code);
+            const int mm = op.lidx[l];
+            const Cdf d = {t.dre, conj ? df_neg(t.im[mm]) : t.im[mm]};
+            out = cdf_add(cdf_scale(t.hinv2, sum), cdf_mul(d, x));
+        }
+        r_red[m] = cdf_pack(cdf_sub(cdf_load_cg(fs, l), out));
+    }
+}
+
 __global__ void k_rhs(Op<double> op, const double2* __restrict__ src, const double2* __restrict__ g,
                       double2* __restrict__ b) {
     const int i = blockIdx.x * BX + threadIdx.x;
@@ -944,6 +1065,35 @@ void launch_rbgs_df(const Op<double>& op, const DfTab& t, int colour, const floa
 void launch_residual_red_df(const Op<double>& op, const DfTab& t, const float4* fs, const float4* xs, float4* r_red,
                             int conj, cudaStream_t s) {
     k_residual_red_df<<<grid_for(op.dim, op.n, 2, 1), dim3(BX, BY), 0, s>>>(op, t, fs, xs, r_red, conj);
+}
+
+// blocks of the cooperative cycle: one per SM (at most), 0 if the device cannot
+// launch it cooperatively
+int cycle_df_blocks(long long N) {
+    static int sms = -1;
+    if (sms < 0) {
+        int dev = 0, coop = 0, occ = 0, count = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+        if (coop) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cycle_df, kCycleThreads, 0);
+        sms = (coop && occ >= 1) ? count : 0;
+    }
+    if (sms < 1) return 0;
+    const long long need = (N + kCycleThreads - 1) / kCycleThreads;
+    return (int)(need < sms ? (need < 1 ? 1 : need) : sms);
+}
+
+cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, const double2* f, float4* fs, float4* xs,
+                            float4* r_red, int n_r, int conj, unsigned* bar2, int* err, cudaStream_t s) {
+    const int nb = cycle_df_blocks(op.N);
+    if (nb < 1) return cudaErrorNotSupported;
+    GridBar b{bar2, bar2 + 1, err};
+    Op<double> opv = op;
+    DfTab tv = t;
+    const double2* fv = f;
+    void* args[] = {&opv, &tv, (void*)&fv, &fs, &xs, &r_red, &n_r, &conj, &b};
+    return cudaLaunchCooperativeKernel((const void*)k_cycle_df, dim3(nb), dim3(kCycleThreads), args, 0, s);
 }
 
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s) {
