@@ -358,18 +358,20 @@ def gpu_arm(args):
                         "peak_source": hbm_src, "traffic": None,
                         "algorithmic_bytes_per_launch": b, "avg_launch_us": avg * 1e6, "launches": n_,
                         "share_of_solve": ms_ / st_prof["ms"]})
-    # relaxation half-sweep.  FP64 kernels: per updated fluid node 10 DADD (neighbour
-    # sum), 2 DFMA (f - h^-2 s), a complex multiply (2 DMUL + 2 DFMA) = 16 FP64
-    # instructions.  The double-float red-black Gauss-Seidel of the trunk-basis cycle:
-    # 10 pair additions (11 FP32 instructions each), 2 pair products (7) for h^-2 s,
-    # 2 pair additions for f - h^-2 s and a complex pair product (4 x 7 + 2 x 11) =
-    # 196 FP32 instructions
+    # relaxation.  FP64 kernels: per updated fluid node 10 DADD (neighbour sum), 2
+    # DFMA (f - h^-2 s), a complex multiply (2 DMUL + 2 DFMA) = 16 FP64 instructions
+    # per half-sweep.  The double-float cycle of the trunk-basis correction (one
+    # cooperative launch per preconditioner application): per red/black node pair a
+    # first red update (complex pair product, 50 FP32 instructions), 2 n_r - 1
+    # half-sweeps of 196 (10 pair additions of 11 instructions, 2 pair products of 7
+    # for h^-2 s, 2 pair additions for f - h^-2 s, a complex pair product of 50) and
+    # the red residual (218)
     n_, ms_, avg = phase("n_sweep", "sweep_ms")
     df_sweep = w["relax"] == "rbgs" and w["n_r"] > 0 and w["correction"] == "tb"
     fp32_peak = 128 * 152 * sm_mhz * 1e6 / 1e12
     if avg and df_sweep:
-        ops = 196.0 * fluid / 2
-        kernels.append({"bound": "alu", "kernel": "k_rbgs_df (double-float half-sweep)",
+        ops = (50.0 + (2 * w["n_r"] - 1) * 196.0 + 218.0) * fluid / 2
+        kernels.append({"bound": "alu", "kernel": "k_cycle_df (double-float red-black cycle, one cooperative launch)",
                         "achieved": ops / avg / 1e12, "peak": fp32_peak, "unit": "T FP32 inst/s",
                         "frac": ops / avg / 1e12 / fp32_peak,
                         "peak_source": "128 FP32 instructions/clk/SM x 152 SMs x max SM clock",

@@ -282,7 +282,11 @@ helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v,
 // z = n_r sweeps on A z = r from z = 0, then z += Q A_c^-1 Q^T (r - A z), where the
 // residual is formed on the red rows only (after the black half-sweep it vanishes on
 // black and masked rows) and z is converted to FP64 once, inside the prolongation.
-helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
+// pre (0, 1, 2) and pv, pw, tol_abs: see launch_cycle_df (the BiCGStab update of
+// the preconditioner's input fused into the cycle; requires the cooperative cycle)
+helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj,
+                               int pre = 0, const double2* pv = nullptr, double2* pw = nullptr,
+                               double tol_abs = 0.0) {
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
     TRY(ensure_tmp(h, 16));
     cudaStream_t s = h->stream;
@@ -292,10 +296,12 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
     if (cycle_df_blocks(h->N) > 0) {
         // one cooperative launch for the whole red-black part and the red residual
         ev_mark(h, 2, 0);
-        CK(launch_cycle_df(h->op64, h->dft, r, fs, xs, rr, o->n_r, conj, h->counter + 2, h->dflag + 2, s));
+        CK(launch_cycle_df(h->op64, h->dft, pre, r, pv, pw, h->sc, h->fparts, tol_abs, fs, xs, rr, o->n_r, conj,
+                           h->counter + 2, h->dflag + 2, s));
         ev_mark(h, 2, 1);
         h->launches -= 2 * o->n_r;
     } else {
+        if (pre != 0) return fail(h, HELM_BAD_ARG, "fused update needs the cooperative cycle");
         launch_rbgs_df_first(h->op64, h->dft, r, fs, xs, conj, s);
         for (int q = 0; q < o->n_r; ++q) {
             if (q > 0) {
@@ -583,19 +589,33 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
     // omega, x/r update with ||r|| and the next rho/beta -- each reduction and its scalar
     // recurrence fused into the kernel that produces the vector.  The iteration ends by
     // copying the scalars into one of two pinned snapshots.
+    // the double-float cycle with a cooperative launch takes the vector updates that
+    // feed the preconditioner into its first phase
+    const bool fuse = h->precision != HELM_MIXED && o->relax == HELM_RBGS && o->n_r > 0 &&
+                      o->correction == HELM_CORR_TB && !h->k2 && h->Q && cycle_df_blocks(N) > 0;
     auto launch_iter = [&](int slot) -> helm_status {
-        launch_bicg_update_p(r, v, p, h->sc, N, s);
-        TRY(precond(h, o, p, ph, o->conj));
+        if (fuse) {
+            // p = r + beta (p - omega v) inside the preconditioner's first phase
+            TRY(precond_rbgs_tb_df(h, o, r, ph, o->conj, 1, v, p));
+        } else {
+            launch_bicg_update_p(r, v, p, h->sc, N, s);
+            TRY(precond(h, o, p, ph, o->conj));
+        }
         ev_mark(h, 3, 0);
         launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
         ev_mark(h, 3, 1);
-        launch_bicg_s_fused(r, v, sv, h->sc, N, h->fparts, h->counter, tol_abs, s);
-        TRY(precond(h, o, sv, sh, o->conj));
+        if (fuse) {
+            // s = r - alpha v and ||s|| inside the preconditioner's first phase
+            TRY(precond_rbgs_tb_df(h, o, r, sh, o->conj, 2, v, sv, tol_abs));
+        } else {
+            launch_bicg_s_fused(r, v, sv, h->sc, N, h->fparts, h->counter, tol_abs, s);
+            TRY(precond(h, o, sv, sh, o->conj));
+        }
         ev_mark(h, 3, 0);
         launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
         ev_mark(h, 3, 1);
         launch_bicg_xr_fused(x, r, ph, sh, sv, t, rh, h->sc, N, h->fparts, h->counter, o->tol, bnorm, s);
-        h->launches += 5;
+        h->launches += fuse ? 3 : 5;
         CK(cudaMemcpyAsync(h->hring + 2 * S_NSLOTS * slot, h->sc, S_NSLOTS * sizeof(double2),
                            cudaMemcpyDeviceToHost, s));
         CK(cudaEventRecord(h->evring[slot], s));

@@ -202,8 +202,12 @@ void launch_residual_red_df(const Op<double>& op, const DfTab& t, const float4* 
 // launch with grid barriers; bar2 = two zeroed counters, *err set if a barrier
 // wait times out.  Returns cudaErrorNotSupported where cooperative launch is not
 // available (the caller then uses the kernels above).
+// pre = 1: the cycle's input is the BiCGStab update p = f + beta (w - omega v),
+// written to w; pre = 2: s = f - alpha v written to w, ||s||^2 into the BiCGStab
+// scalars (parts: one double per block); pre = 0: f itself (v, w, sc, parts unused)
 int cycle_df_blocks(long long N);
-cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, const double2* f, float4* fs, float4* xs,
+cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, int pre, const double2* f, const double2* v,
+                            double2* w, double2* sc, double* parts, double tol_abs, float4* fs, float4* xs,
                             float4* r_red, int n_r, int conj, unsigned* bar2, int* err, cudaStream_t s);
 // projection of a residual given as FP32 pairs (float4 per complex entry, N rows)
 void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,

@@ -755,15 +755,37 @@ __device__ __forceinline__ Cdf nbr_sum_df_cg(const Op<double>& op, const float4*
 
 constexpr int kCycleThreads = 1024;
 
+// PRE selects where the cycle's right-hand side comes from: 0, f as given; 1, the
+// BiCGStab direction update p = r + beta (p - omega v) (p written back); 2, the
+// BiCGStab half step s = r - alpha v (written to w) with ||s||^2 summed per block
+// and, after the first barrier, in block 0 in a fixed order (scalar recurrence of
+// the BiCGStab driver, slot S_SN2 and the tolerance flag)
+template <int PRE>
 __global__ void __launch_bounds__(kCycleThreads, 1) k_cycle_df(Op<double> op, DfTab t, const double2* __restrict__ f,
-                                                               float4* fs, float4* xs, float4* r_red, int n_r, int conj,
-                                                               GridBar bar) {
+                                                               const double2* __restrict__ v, double2* w, double2* sc,
+                                                               double* parts, double tol_abs, float4* fs, float4* xs,
+                                                               float4* r_red, int n_r, int conj, GridBar bar) {
     const long long N = op.N, M = (N + 1) / 2;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nth = (long long)gridDim.x * blockDim.x;
+    double2 c1 = make_double2(0, 0), c2 = c1;
+    if (PRE == 1) { c1 = sc[S_BETA]; c2 = sc[S_OMEGA]; }
+    if (PRE == 2) c1 = sc[S_ALPHA];
+    double acc = 0.0;
     // fs = f as pairs; x = D^-1 f on red fluid nodes, f on red masked nodes, 0 on black
     for (long long l = tid; l < N; l += nth) {
-        const double2 fv = f[l];
+        double2 fv;
+        if (PRE == 0) {
+            fv = f[l];
+        } else if (PRE == 1) {
+            const double2 tt = csub(w[l], cmul(c2, v[l]));
+            fv = cadd(f[l], cmul(c1, tt));
+            w[l] = fv;
+        } else {
+            fv = csub(f[l], cmul(c1, v[l]));
+            w[l] = fv;
+            acc += fv.x * fv.x + fv.y * fv.y;
+        }
         const Cdf F = {df_split(fv.x), df_split(fv.y)};
         __stcg(fs + l, cdf_pack(F));
         Cdf x = cdf_zero();
@@ -773,7 +795,23 @@ __global__ void __launch_bounds__(kCycleThreads, 1) k_cycle_df(Op<double> op, Df
         }
         __stcg(xs + l, cdf_pack(x));
     }
+    if (PRE == 2) {
+        __shared__ double red[kCycleThreads / 32];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = 0.0;
+            for (int q = 0; q < kCycleThreads / 32; ++q) b += red[q];
+            parts[blockIdx.x] = b;
+        }
+    }
     grid_barrier(bar);
+    if (PRE == 2 && blockIdx.x == 0 && threadIdx.x == 0) {
+        double sn = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) sn += __ldcg(parts + b);
+        bicg_snorm(sc, sn, tol_abs);
+    }
     for (int q = 0; q < n_r; ++q) {
         for (int colour = (q == 0 ? 1 : 0); colour < 2; ++colour) {
             for (long long m = tid; m < M; m += nth) {
@@ -1076,7 +1114,13 @@ int cycle_df_blocks(long long N) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
-        if (coop) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cycle_df, kCycleThreads, 0);
+        if (coop) {
+            int o0 = 0, o1 = 0, o2 = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_cycle_df<0>, kCycleThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_cycle_df<1>, kCycleThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_cycle_df<2>, kCycleThreads, 0);
+            occ = std::min(o0, std::min(o1, o2));
+        }
         sms = (coop && occ >= 1) ? count : 0;
     }
     if (sms < 1) return 0;
@@ -1084,7 +1128,8 @@ int cycle_df_blocks(long long N) {
     return (int)(need < sms ? (need < 1 ? 1 : need) : sms);
 }
 
-cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, const double2* f, float4* fs, float4* xs,
+cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, int pre, const double2* f, const double2* v,
+                            double2* w, double2* sc, double* parts, double tol_abs, float4* fs, float4* xs,
                             float4* r_red, int n_r, int conj, unsigned* bar2, int* err, cudaStream_t s) {
     const int nb = cycle_df_blocks(op.N);
     if (nb < 1) return cudaErrorNotSupported;
@@ -1092,8 +1137,11 @@ cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, const double2*
     Op<double> opv = op;
     DfTab tv = t;
     const double2* fv = f;
-    void* args[] = {&opv, &tv, (void*)&fv, &fs, &xs, &r_red, &n_r, &conj, &b};
-    return cudaLaunchCooperativeKernel((const void*)k_cycle_df, dim3(nb), dim3(kCycleThreads), args, 0, s);
+    const double2* vv = v;
+    void* args[] = {&opv, &tv, (void*)&fv, (void*)&vv, &w, &sc, &parts, &tol_abs, &fs, &xs, &r_red, &n_r, &conj, &b};
+    const void* fn = pre == 0 ? (const void*)k_cycle_df<0> : pre == 1 ? (const void*)k_cycle_df<1>
+                                                                      : (const void*)k_cycle_df<2>;
+    return cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kCycleThreads), args, 0, s);
 }
 
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s) {
