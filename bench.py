@@ -188,15 +188,17 @@ def source_hash(path):
 
 
 def traffic_for(kernel, k):
-    """dram bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's source
+    file is unchanged since the capture (else None)."""
     try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "project_cube3d-64_traffic.json")))
+        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic_cube3d-64.json")))
+        e = prof["kernels"][kernel]
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2405_12380_gb300", "csrc", "tb.cu")
-    if prof.get("tb_cu_sha256_16") != source_hash(src) or prof.get("k") != k:
+    src = os.path.join(ROOT, "paper_2405_12380_gb300", "csrc", e["source"])
+    if e.get("sha256_16") != source_hash(src) or prof.get("k") != k:
         return None
-    return prof.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_launch")
 
 
 def stencil_bench(hm, torch, n=256, reps=20):
@@ -355,7 +357,7 @@ def gpu_arm(args):
         b = 8.0 * k * N + 32.0 * N
         kernels.append({"bound": "hbm", "kernel": "k_prolong_df (z += Q y, FP32-pair arithmetic)",
                         "achieved": b / avg / 1e9, "peak": hbm, "unit": "GB/s", "frac": b / avg / 1e9 / hbm,
-                        "peak_source": hbm_src, "traffic": None,
+                        "peak_source": hbm_src, "traffic": traffic_for("k_prolong_df", k),
                         "algorithmic_bytes_per_launch": b, "avg_launch_us": avg * 1e6, "launches": n_,
                         "share_of_solve": ms_ / st_prof["ms"]})
     # relaxation.  FP64 kernels: per updated fluid node 10 DADD (neighbour sum), 2
@@ -375,7 +377,8 @@ def gpu_arm(args):
                         "achieved": ops / avg / 1e12, "peak": fp32_peak, "unit": "T FP32 inst/s",
                         "frac": ops / avg / 1e12 / fp32_peak,
                         "peak_source": "128 FP32 instructions/clk/SM x 152 SMs x max SM clock",
-                        "traffic": None, "algorithmic_fp32_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
+                        "traffic": traffic_for("k_cycle_df", k), "algorithmic_fp32_inst_per_launch": ops,
+                        "avg_launch_us": avg * 1e6,
                         "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
     elif avg:
         ops = 16.0 * fluid / 2
@@ -394,7 +397,7 @@ def gpu_arm(args):
                         "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",
                         "frac": ops / avg / 1e12 / fp64_peak,
                         "peak_source": "2 FP64 instructions/clk/SM x 152 SMs x max SM clock",
-                        "traffic": None, "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
+                        "traffic": traffic_for("k_apply_bicg", k), "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
                         "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
     for e in kernels:
         e["timing"] = "CUDA events around every launch, one profiled solve after the timed solves"
