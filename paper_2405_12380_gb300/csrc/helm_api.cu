@@ -286,7 +286,7 @@ helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v,
 // the preconditioner's input fused into the cycle; requires the cooperative cycle)
 helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj,
                                int pre = 0, const double2* pv = nullptr, double2* pw = nullptr,
-                               double tol_abs = 0.0) {
+                               double tol_abs = 0.0, float4* zdf = nullptr) {
     if (!h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
     TRY(ensure_tmp(h, 16));
     cudaStream_t s = h->stream;
@@ -322,7 +322,7 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
     ev_mark(h, 0, 1);
     launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, s);
     ev_mark(h, 1, 0);
-    launch_prolong_df_base(h->Q, basis_ld(h->N), h->k, h->ybuf, xs, z, h->N, s);
+    launch_prolong_df_base(h->Q, basis_ld(h->N), h->k, h->ybuf, xs, z, zdf, h->N, s);
     ev_mark(h, 1, 1);
     h->launches += 2 * o->n_r + 5;
     CKL();
@@ -593,27 +593,41 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
     // feed the preconditioner into its first phase
     const bool fuse = h->precision != HELM_MIXED && o->relax == HELM_RBGS && o->n_r > 0 &&
                       o->correction == HELM_CORR_TB && !h->k2 && h->Q && cycle_df_blocks(N) > 0;
+    float4* phdf = nullptr;
+    float4* shdf = nullptr;
+    if (fuse) {
+        TRY(ensure_tmp(h, 18));
+        phdf = reinterpret_cast<float4*>(h->tmp[16]);
+        shdf = reinterpret_cast<float4*>(h->tmp[17]);
+    }
     auto launch_iter = [&](int slot) -> helm_status {
         if (fuse) {
-            // p = r + beta (p - omega v) inside the preconditioner's first phase
-            TRY(precond_rbgs_tb_df(h, o, r, ph, o->conj, 1, v, p));
+            // p = r + beta (p - omega v) inside the preconditioner's first phase; the
+            // preconditioned vector also as FP32 pairs, the operator's input
+            TRY(precond_rbgs_tb_df(h, o, r, ph, o->conj, 1, v, p, 0.0, phdf));
+            ev_mark(h, 3, 0);
+            launch_apply_bicg_df(h->op64, h->dft, 1, phdf, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
+            ev_mark(h, 3, 1);
         } else {
             launch_bicg_update_p(r, v, p, h->sc, N, s);
             TRY(precond(h, o, p, ph, o->conj));
+            ev_mark(h, 3, 0);
+            launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
+            ev_mark(h, 3, 1);
         }
-        ev_mark(h, 3, 0);
-        launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
-        ev_mark(h, 3, 1);
         if (fuse) {
             // s = r - alpha v and ||s|| inside the preconditioner's first phase
-            TRY(precond_rbgs_tb_df(h, o, r, sh, o->conj, 2, v, sv, tol_abs));
+            TRY(precond_rbgs_tb_df(h, o, r, sh, o->conj, 2, v, sv, tol_abs, shdf));
+            ev_mark(h, 3, 0);
+            launch_apply_bicg_df(h->op64, h->dft, 2, shdf, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
+            ev_mark(h, 3, 1);
         } else {
             launch_bicg_s_fused(r, v, sv, h->sc, N, h->fparts, h->counter, tol_abs, s);
             TRY(precond(h, o, sv, sh, o->conj));
+            ev_mark(h, 3, 0);
+            launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
+            ev_mark(h, 3, 1);
         }
-        ev_mark(h, 3, 0);
-        launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
-        ev_mark(h, 3, 1);
         launch_bicg_xr_fused(x, r, ph, sh, sv, t, rh, h->sc, N, h->fparts, h->counter, o->tol, bnorm, s);
         h->launches += fuse ? 3 : 5;
         CK(cudaMemcpyAsync(h->hring + 2 * S_NSLOTS * slot, h->sc, S_NSLOTS * sizeof(double2),

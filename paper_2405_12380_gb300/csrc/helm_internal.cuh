@@ -212,9 +212,13 @@ cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, int pre, const
 // projection of a residual given as FP32 pairs (float4 per complex entry, N rows)
 void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
                              int nblk, cudaStream_t s);
-// z = base + Q y with base given as FP32 pairs (float4 per complex entry)
+// z = base + Q y with base given as FP32 pairs (float4 per complex entry); zdf
+// (optional) receives z as FP32 pairs too
 void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
-                            long long N, cudaStream_t s);
+                            float4* zdf, long long N, cudaStream_t s);
+// k_apply_bicg for an x given as FP32 pairs: y = A x in double-float, y in FP64
+void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const float4* x, double2* y,
+                          const double2* w, int conj, double2* sc, double* parts, unsigned* counter, cudaStream_t s);
 // r_red[m] = (v - A z) at the red node of pair m (stencil.cu)
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s);

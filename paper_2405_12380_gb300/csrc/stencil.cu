@@ -690,6 +690,73 @@ __global__ void __launch_bounds__(BX * BY) k_residual_red_df(Op<double> op, DfTa
     r_red[l >> 1] = cdf_pack(cdf_sub(cdf_load(fs, l), out));
 }
 
+// y = A x with the BiCGStab reduction of k_apply_bicg, for an x given as FP32 pairs
+// (the output of the double-float hybrid cycle): the operator in double-float on
+// the FP32 pipes, y converted to FP64 once, the dots in FP64
+template <int MODE>
+__global__ void __launch_bounds__(BX * BY) k_apply_bicg_df(Op<double> op, DfTab t, const float4* __restrict__ x,
+                                                           double2* __restrict__ y, const double2* __restrict__ w,
+                                                           int conj, double2* sc, double* parts, unsigned* counter) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k0 = op.dim == 3 ? 2 * blockIdx.z : 0;
+    double a = 0, b = 0, c = 0;
+    if (i < op.n && j < op.n) {
+        for (int kk = k0; kk < (op.dim == 3 ? min(k0 + 2, op.n) : 1); ++kk) {
+            const long long l = i + (long long)op.n * (j + (long long)op.n * kk);
+            const unsigned code = node_code(op, l);
+            const Cdf X = cdf_load(x, l);
+            Cdf out;
+            if (code & kMasked) {
+                out = X;
+            } else {
+                const Cdf sum = nbr_sum_df(op, x, l, code);
+                const int m = node_lidx(op, l, i, j, kk);
+                const Cdf d = {t.dre, conj ? df_neg(t.im[m]) : t.im[m]};
+                out = cdf_add(cdf_scale(t.hinv2, sum), cdf_mul(d, X));
+            }
+            const double2 yv = make_double2((double)out.re.x + (double)out.re.y, (double)out.im.x + (double)out.im.y);
+            y[l] = yv;
+            const double2 wv = w[l];
+            if (MODE == 1) {          // conj(w) y
+                a += wv.x * yv.x + wv.y * yv.y;
+                b += wv.x * yv.y - wv.y * yv.x;
+            } else {                  // conj(y) w and |y|^2
+                a += yv.x * wv.x + yv.y * wv.y;
+                b += yv.x * wv.y - yv.y * wv.x;
+                c += yv.x * yv.x + yv.y * yv.y;
+            }
+        }
+    }
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    __shared__ double red[3][BX * BY / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((tid & 31) == 0) { red[0][tid >> 5] = a; red[1][tid >> 5] = b; red[2][tid >> 5] = c; }
+    __syncthreads();
+    if (tid == 0) {
+        double sa = 0, sb = 0, scc = 0;
+        for (int q = 0; q < BX * BY / 32; ++q) { sa += red[0][q]; sb += red[1][q]; scc += red[2][q]; }
+        parts[3 * bid + 0] = sa;
+        parts[3 * bid + 1] = sb;
+        parts[3 * bid + 2] = scc;
+    }
+    if (last_block_done(counter, nblk)) {
+        double tot[3];
+        sum_parts<3>(parts, nblk, tid, tot);
+        if (tid == 0) {
+            if (MODE == 1) bicg_alpha(sc, make_double2(tot[0], tot[1]));
+            else bicg_omega(sc, make_double2(tot[0], tot[1]), tot[2]);
+            *counter = 0;
+        }
+    }
+}
+
 // ---- the red-black part of the trunk-basis hybrid cycle in one cooperative
 // launch: f as pairs with the first red half-sweep from x = 0, the remaining
 // half-sweeps, and the red-row residual, each phase over the whole grid and the
@@ -1064,6 +1131,13 @@ void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, t
     dim3 g = grid_for(op.dim, op.n, 2, 1), b(BX, BY);
     if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj);
     else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj);
+}
+
+void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const float4* x, double2* y,
+                          const double2* w, int conj, double2* sc, double* parts, unsigned* counter, cudaStream_t s) {
+    dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
+    if (mode == 1) k_apply_bicg_df<1><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
+    else k_apply_bicg_df<2><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
 }
 
 void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2* y, const double2* w, int conj,

@@ -526,9 +526,11 @@ __global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ 
 // z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 // BASE: z_l = base_l + sum_j Q_j[l] y_j with base given as FP32 pairs
 template <bool BASE>
+// (and, given zdf, also the sum as FP32 pairs)
 __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q, long long ld, int k,
                                                     const double2* __restrict__ y, double2* __restrict__ z,
-                                                    const float4* __restrict__ base, long long N) {
+                                                    const float4* __restrict__ base, float4* __restrict__ zdf,
+                                                    long long N) {
     __shared__ float4 ys[kMaxP];
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         float4 t;
@@ -566,6 +568,10 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
             bb = s1 - b.z;
             const float e1 = (b.z - (s1 - bb)) + (a2 - bb) + (b.w + a3);
             z[l] = make_double2((double)s0 + (double)e0, (double)s1 + (double)e1);
+            if (zdf) {
+                const float h0 = s0 + e0, h1 = s1 + e1;
+                zdf[l] = make_float4(h0, e0 - (h0 - s0), h1, e1 - (h1 - s1));
+            }
         } else {
             double2 zz = z[l];
             z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
@@ -988,13 +994,13 @@ void launch_project_df(const float2* Q, long long ld, int k, const double2* r, l
 void launch_prolong_df(const float2* Q, long long ld, int k, const double2* y, double2* z, long long N,
                        cudaStream_t s) {
     long long b = (N + 255) / 256;
-    k_prolong_df<false><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, nullptr, N);
+    k_prolong_df<false><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, nullptr, nullptr, N);
 }
 
 void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
-                            long long N, cudaStream_t s) {
+                            float4* zdf, long long N, cudaStream_t s) {
     long long b = (N + 255) / 256;
-    k_prolong_df<true><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, base, N);
+    k_prolong_df<true><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, base, zdf, N);
 }
 
 void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
