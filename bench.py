@@ -226,8 +226,25 @@ def stencil_bench(hm, torch, n=256, reps=20):
         key = "c64" if dt == torch.complex64 else "c128"
         out[key] = {"us_per_apply": ms * 1e3, "GBps": gbs, "bytes_per_node": nbytes}
         del xs, y
+    # complex64 sweeps: per full sweep read x and f, write x, two table bytes (26 B per node)
+    f = torch.randn(P.N, dtype=torch.complex64, device="cuda")
+    x = torch.randn(P.N, dtype=torch.complex64, device="cuda")
+    for kind, sweeps in (("jacobi", 2), ("rbgs", 1)):
+        P.relax(kind, f, x, sweeps=sweeps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for q in range(reps):
+            P.relax(kind, f, x, sweeps=sweeps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps / sweeps
+        out[f"{kind}_c64"] = {"us_per_sweep": ms * 1e3, "GBps": 26 * P.N / (ms * 1e-3) / 1e9, "bytes_per_node": 26}
+    del f, x
     hbm = peaks().get("hbm_gbs") or 6800.0
     out["hbm_peak_GBps"] = hbm
+    out["jacobi_c64_frac_of_hbm"] = out["jacobi_c64"]["GBps"] / hbm
+    out["rbgs_c64_frac_of_hbm"] = out["rbgs_c64"]["GBps"] / hbm
     out["c64_frac_of_hbm"] = out["c64"]["GBps"] / hbm
     out["c128_frac_of_hbm"] = out["c128"]["GBps"] / hbm
     out["note"] = "c128 is bound by GB300's FP64 rate (~18 FP64 operations per node), not by HBM"
@@ -339,6 +356,7 @@ def gpu_arm(args):
         return n, ms, (ms / 1e3 / n if n else None)
 
     kernels = []
+    df_sweep = w["relax"] == "rbgs" and w["n_r"] > 0 and w["correction"] == "tb"
     # trunk-basis projection c = Q^T r: Q as FP32 pairs (8 B per entry), r as 16 B
     # per entry (complex128, or FP32 pairs after the double-float sweeps)
     n_, ms_, avg = phase("n_restrict", "restrict_ms")
@@ -369,7 +387,6 @@ def gpu_arm(args):
     # for h^-2 s, 2 pair additions for f - h^-2 s, a complex pair product of 50) and
     # the red residual (218)
     n_, ms_, avg = phase("n_sweep", "sweep_ms")
-    df_sweep = w["relax"] == "rbgs" and w["n_r"] > 0 and w["correction"] == "tb"
     fp32_peak = 128 * 152 * sm_mhz * 1e6 / 1e12
     if avg and df_sweep:
         ops = (50.0 + (2 * w["n_r"] - 1) * 196.0 + 218.0) * fluid / 2
@@ -389,11 +406,14 @@ def gpu_arm(args):
                         "traffic": None, "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
                         "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
     # BiCGStab operator with its fused reduction: 16 FP64 instructions for A x per
-    # fluid node plus 4 (<rhat, v>) or 6 (<t, s>, <t, t>): 21 on average
+    # fluid node plus 4 (<rhat, v>) or 6 (<t, s>, <t, t>): 21 on average; on the
+    # double-float input (trunk-basis red-black cycle) A x runs on the FP32 pipes and
+    # the FP64 part is the conversion of y (4 F2F + 2 DADD) and the dots: 11
     n_, ms_, avg = phase("n_apply", "apply_ms")
     if avg:
-        ops = 21.0 * fluid
-        kernels.append({"bound": "alu", "kernel": "k_apply_bicg (FP64 A x + fused dots)",
+        ops = (11.0 if df_sweep else 21.0) * fluid
+        kernels.append({"bound": "alu", "kernel": "k_apply_bicg_df (A x in double-float, FP64 y and fused dots)" if df_sweep
+                        else "k_apply_bicg (FP64 A x + fused dots)",
                         "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",
                         "frac": ops / avg / 1e12 / fp64_peak,
                         "peak_source": "2 FP64 instructions/clk/SM x 152 SMs x max SM clock",

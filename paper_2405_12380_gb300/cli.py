@@ -91,6 +91,21 @@ def stencil(n, reps):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         print(json.dumps({"dtype": str(dt), "n": n, "us": ms * 1e3, "GBps": nbytes * P.N / (ms * 1e-3) / 1e9}))
+    # complex64 sweeps: per full sweep read x and f, write x, two table bytes (26 B per node)
+    f = torch.randn(P.N, dtype=torch.complex64, device="cuda")
+    x = torch.randn(P.N, dtype=torch.complex64, device="cuda")
+    for kind, sweeps in (("jacobi", 2), ("rbgs", 1)):
+        P.relax(kind, f, x, sweeps=sweeps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for q in range(reps):
+            P.relax(kind, f, x, sweeps=sweeps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps / sweeps
+        print(json.dumps({"sweep": kind, "dtype": "complex64", "n": n, "us_per_sweep": ms * 1e3,
+                          "GBps": 26 * P.N / (ms * 1e-3) / 1e9}))
 
 
 def _emit(d):
