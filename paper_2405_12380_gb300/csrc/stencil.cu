@@ -368,6 +368,93 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
     }
 }
 
+// complex64 red-black half-sweep in 3D with the pair layout of k_march_c64: each
+// thread owns the node pair (2 i2, 2 i2 + 1) of a row, one node of each colour
+// (n even), and updates the one of the swept colour in place.  The neighbours of
+// that node are of the other colour and are not written by this launch, so the
+// z-march keeps the planes in registers as in k_march_c64.  XZERO: the first
+// half-sweep from x = 0 (no neighbours read).
+template <bool XZERO>
+__global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int colour, const float4* __restrict__ f,
+                                                      float4* x, int conj) {
+    constexpr unsigned kMM = kMasked | (kMasked << 8);
+    const int n = op.n, h = n >> 1;
+    const int i2 = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k0 = blockIdx.z * zc;
+    const int k1 = min(n, k0 + zc);
+    const bool valid = i2 < h && j < n;
+    const int sy = h, sz = h * n;
+    const int lane = threadIdx.x;
+    const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
+    const unsigned short* lidx2 = reinterpret_cast<const unsigned short*>(op.lidx);
+    const float2* x1 = reinterpret_cast<const float2*>(x);
+    float2* xw = reinterpret_cast<float2*>(x);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int l = i2 + h * (j + n * k0);
+    float4 prev = z4, cur = z4, next = z4;
+    if (!XZERO) {
+        prev = (valid && k0 > 0) ? x[l - sz] : z4;
+        cur = valid ? x[l] : z4;
+        next = (valid && k0 + 1 < n) ? x[l + sz] : z4;
+    }
+    float4 fv = valid ? f[l] : z4;
+    unsigned cc = valid ? (unsigned)code2[l] : kMM;
+    unsigned li = valid ? (unsigned)lidx2[l] : 0u;
+    for (int k = k0; k < k1; ++k, l += sz) {
+        const bool more = valid && k + 1 < k1;
+        float4 next2 = z4;
+        if (!XZERO) next2 = (more && k + 2 < n) ? x[l + 2 * sz] : z4;
+        const float4 f_n = more ? f[l + sz] : z4;
+        const unsigned cc_n = more ? (unsigned)code2[l + sz] : kMM;
+        const unsigned li_n = more ? (unsigned)lidx2[l + sz] : 0u;
+        const int a = ((j + k) & 1) ^ colour;               // swept node of the pair
+        const unsigned ca = a ? (cc >> 8) : (cc & 0xffu);
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+        if (!XZERO) {
+            float2 left, right;
+            left.x = __shfl_up_sync(0xffffffffu, cur.z, 1);
+            left.y = __shfl_up_sync(0xffffffffu, cur.w, 1);
+            right.x = __shfl_down_sync(0xffffffffu, cur.x, 1);
+            right.y = __shfl_down_sync(0xffffffffu, cur.y, 1);
+            if (lane == 0 && a == 0 && (ca & 1u)) left = x1[2 * l - 1];
+            if (lane == BX - 1 && a == 1 && (ca & 2u)) right = x1[2 * l + 2];
+            const float4 ym = (ca & 4u) ? x[l - sy] : z4;
+            const float4 yp = (ca & 8u) ? x[l + sy] : z4;
+            pair_sums(a ? 0u : ca, a ? ca : 0u, left, right, cur, ym, yp, prev, next, s0, s1);
+        }
+        if (valid) {
+            const float2 fa = a ? hi2(fv) : lo2(fv);
+            float2 out;
+            if (ca & kMasked) {
+                out = fa;
+            } else {
+                float2 id;
+                if (op.k2) {
+                    const float4 iv = reinterpret_cast<const float4*>(op.invd)[l];
+                    id = a ? hi2(iv) : lo2(iv);
+                } else {
+                    id = op.invd_tab[a ? (li >> 8) : (li & 0xffu)];
+                }
+                if (conj) id.y = -id.y;
+                if (XZERO) {
+                    out = cmul(id, fa);
+                } else {
+                    const float2 sa = a ? s1 : s0;
+                    out = cmul(id, make_float2(fa.x - op.hinv2 * sa.x, fa.y - op.hinv2 * sa.y));
+                }
+            }
+            xw[2 * l + a] = out;
+        }
+        prev = cur;
+        cur = next;
+        next = next2;
+        fv = f_n;
+        cc = cc_n;
+        li = li_n;
+    }
+}
+
 // y = A x, or y = f - A x (resid); two z-planes per thread; optional per-block ||y||^2 partials.
 template <typename R, bool RESID, bool NORM>
 __global__ void __launch_bounds__(BX * BY) k_apply(Op<R> op, int zc, const typename CT<R>::T* __restrict__ x,
@@ -1128,6 +1215,17 @@ void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f, co
 template <typename R>
 void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x, int conj,
                       bool xzero, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (pair_ok(op, f, x, nullptr)) {
+            int zc;
+            const dim3 g = pair_grid(op.n, &zc), b(BX, BY);
+            const float4* f4 = reinterpret_cast<const float4*>(f);
+            float4* x4 = reinterpret_cast<float4*>(x);
+            if (xzero) k_rbgs_c64<true><<<g, b, 0, s>>>(op, zc, colour, f4, x4, conj);
+            else k_rbgs_c64<false><<<g, b, 0, s>>>(op, zc, colour, f4, x4, conj);
+            return;
+        }
+    }
     dim3 g = grid_for(op.dim, op.n, 2, 1), b(BX, BY);
     if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj);
     else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj);
