@@ -593,6 +593,11 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
     // feed the preconditioner into its first phase
     const bool fuse = h->precision != HELM_MIXED && o->relax == HELM_RBGS && o->n_r > 0 &&
                       o->correction == HELM_CORR_TB && !h->k2 && h->Q && cycle_df_blocks(N) > 0;
+    // mixed handles: the operator reads the preconditioner's complex64 output (exact in
+    // double-float) instead of its FP64 copy (tabulated k^2 only; relaxation or
+    // correction present, so that the output comes from the complex64 cycle)
+    const bool mixed_df = h->precision == HELM_MIXED && !h->k2 &&
+                          !((o->relax == HELM_RELAX_NONE || o->n_r <= 0) && o->correction == HELM_CORR_NONE);
     float4* phdf = nullptr;
     float4* shdf = nullptr;
     if (fuse) {
@@ -612,7 +617,9 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
             launch_bicg_update_p(r, v, p, h->sc, N, s);
             TRY(precond(h, o, p, ph, o->conj));
             ev_mark(h, 3, 0);
-            launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
+            if (mixed_df) launch_apply_bicg_c64in(h->op64, h->dft, 1, h->tmp32[1], v, rh, o->conj, h->sc, h->fparts,
+                                                  h->counter, s);
+            else launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
             ev_mark(h, 3, 1);
         }
         if (fuse) {
@@ -625,7 +632,9 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
             launch_bicg_s_fused(r, v, sv, h->sc, N, h->fparts, h->counter, tol_abs, s);
             TRY(precond(h, o, sv, sh, o->conj));
             ev_mark(h, 3, 0);
-            launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
+            if (mixed_df) launch_apply_bicg_c64in(h->op64, h->dft, 2, h->tmp32[1], t, sv, o->conj, h->sc, h->fparts,
+                                                  h->counter, s);
+            else launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
             ev_mark(h, 3, 1);
         }
         launch_bicg_xr_fused(x, r, ph, sh, sv, t, rh, h->sc, N, h->fparts, h->counter, o->tol, bnorm, s);

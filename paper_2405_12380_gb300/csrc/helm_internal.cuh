@@ -216,6 +216,11 @@ void launch_project_df_split(const float2* Q, long long ld, int k, const float4*
 // (optional) receives z as FP32 pairs too
 void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
                             float4* zdf, long long N, cudaStream_t s);
+// the same for a complex64 x (mixed handles: the preconditioner's output before
+// its exact conversion to FP64)
+void launch_apply_bicg_c64in(const Op<double>& op, const DfTab& t, int mode, const float2* x, double2* y,
+                             const double2* w, int conj, double2* sc, double* parts, unsigned* counter,
+                             cudaStream_t s);
 // k_apply_bicg for an x given as FP32 pairs: y = A x in double-float, y in FP64
 void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const float4* x, double2* y,
                           const double2* w, int conj, double2* sc, double* parts, unsigned* counter, cudaStream_t s);

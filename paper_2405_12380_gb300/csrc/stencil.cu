@@ -780,8 +780,31 @@ __global__ void __launch_bounds__(BX * BY) k_residual_red_df(Op<double> op, DfTa
 // y = A x with the BiCGStab reduction of k_apply_bicg, for an x given as FP32 pairs
 // (the output of the double-float hybrid cycle): the operator in double-float on
 // the FP32 pipes, y converted to FP64 once, the dots in FP64
-template <int MODE>
-__global__ void __launch_bounds__(BX * BY) k_apply_bicg_df(Op<double> op, DfTab t, const float4* __restrict__ x,
+// (or, IN32, for a complex64 x: exact pairs with lo = 0)
+__device__ __forceinline__ Cdf cdf_load(const float2* p, long long l) {
+    const float2 v = p[l];
+    return {make_float2(v.x, 0.f), make_float2(v.y, 0.f)};
+}
+
+template <typename XT>
+__device__ __forceinline__ Cdf nbr_sum_any(const Op<double>& op, const XT* __restrict__ x, long long l,
+                                           unsigned code) {
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    const Cdf a = (code & 1u) ? cdf_load(x, l - 1) : cdf_zero();
+    const Cdf b = (code & 2u) ? cdf_load(x, l + 1) : cdf_zero();
+    const Cdf c = (code & 4u) ? cdf_load(x, l - sy) : cdf_zero();
+    const Cdf d = (code & 8u) ? cdf_load(x, l + sy) : cdf_zero();
+    Cdf s = cdf_add(cdf_add(a, b), cdf_add(c, d));
+    if (op.dim == 3) {
+        const Cdf e = (code & 16u) ? cdf_load(x, l - sz) : cdf_zero();
+        const Cdf f = (code & 32u) ? cdf_load(x, l + sz) : cdf_zero();
+        s = cdf_add(s, cdf_add(e, f));
+    }
+    return s;
+}
+
+template <int MODE, typename XT>
+__global__ void __launch_bounds__(BX * BY) k_apply_bicg_df(Op<double> op, DfTab t, const XT* __restrict__ x,
                                                            double2* __restrict__ y, const double2* __restrict__ w,
                                                            int conj, double2* sc, double* parts, unsigned* counter) {
     const int i = blockIdx.x * BX + threadIdx.x;
@@ -797,7 +820,7 @@ __global__ void __launch_bounds__(BX * BY) k_apply_bicg_df(Op<double> op, DfTab 
             if (code & kMasked) {
                 out = X;
             } else {
-                const Cdf sum = nbr_sum_df(op, x, l, code);
+                const Cdf sum = nbr_sum_any(op, x, l, code);
                 const int m = node_lidx(op, l, i, j, kk);
                 const Cdf d = {t.dre, conj ? df_neg(t.im[m]) : t.im[m]};
                 out = cdf_add(cdf_scale(t.hinv2, sum), cdf_mul(d, X));
@@ -1234,8 +1257,16 @@ void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, t
 void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const float4* x, double2* y,
                           const double2* w, int conj, double2* sc, double* parts, unsigned* counter, cudaStream_t s) {
     dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
-    if (mode == 1) k_apply_bicg_df<1><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
-    else k_apply_bicg_df<2><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
+    if (mode == 1) k_apply_bicg_df<1, float4><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
+    else k_apply_bicg_df<2, float4><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
+}
+
+void launch_apply_bicg_c64in(const Op<double>& op, const DfTab& t, int mode, const float2* x, double2* y,
+                             const double2* w, int conj, double2* sc, double* parts, unsigned* counter,
+                             cudaStream_t s) {
+    dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
+    if (mode == 1) k_apply_bicg_df<1, float2><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
+    else k_apply_bicg_df<2, float2><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
 }
 
 void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2* y, const double2* w, int conj,
