@@ -417,7 +417,7 @@ def gpu_arm(args):
                         "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",
                         "frac": ops / avg / 1e12 / fp64_peak,
                         "peak_source": "2 FP64 instructions/clk/SM x 152 SMs x max SM clock",
-                        "traffic": traffic_for("k_apply_bicg", k), "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
+                        "traffic": traffic_for("k_apply_bicg_df" if df_sweep else "k_apply_bicg", k), "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
                         "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
     for e in kernels:
         e["timing"] = "CUDA events around every launch, one profiled solve after the timed solves"
