@@ -8,7 +8,10 @@
 // reductions are segmented: one partial per tile, summed in a fixed order per
 // problem.  FGMRES runs in lockstep: every active problem takes Arnoldi step j
 // at the same time, problems that converge (or hit maxit) drop out through an
-// active mask, and each restarts with its own Krylov dimension.
+// active mask, and each restarts with its own Krylov dimension.  Each Arnoldi step
+// (about twenty kernels and two status copies) is captured once per solve as a
+// CUDA graph on a private stream and replayed; the host reads the status between
+// steps to update the active mask.
 //
 // Precision (the mixed form): complex64 hybrid cycle (damped Jacobi + trunk-basis
 // correction with each problem's BF16 basis) and complex64 Arnoldi matvec inside
@@ -630,6 +633,8 @@ struct helm_batch {
     double2 *hpart = nullptr, *H = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h2 = nullptr;
     double *cs = nullptr, *tpart = nullptr, *nrm = nullptr, *est = nullptr, *hpin = nullptr;
     int m_alloc = 0;
+    cudaStream_t cstream = nullptr;     // private non-blocking stream of the solves (graph capture)
+    cudaEvent_t join = nullptr;
     std::string err;
 };
 
@@ -767,6 +772,8 @@ helm_status helm_batch_destroy(helm_batch* B) {
     bfree(B->Z32); bfree(B->w32); bfree(B->pp32); bfree(B->y32); bfree(B->hpart); bfree(B->H); bfree(B->sn);
     bfree(B->g); bfree(B->y); bfree(B->h2); bfree(B->cs); bfree(B->tpart); bfree(B->nrm); bfree(B->est);
     if (B->hpin) cudaFreeHost(B->hpin);
+    if (B->cstream) cudaStreamDestroy(B->cstream);
+    if (B->join) cudaEventDestroy(B->join);
     delete B;
     return HELM_OK;
 }
@@ -787,7 +794,16 @@ helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const doub
     const int m = o->restart;
     helm_status st = ensure_batch_krylov(B, m);
     if (st != HELM_OK) return st;
-    cudaStream_t s = B->stream;
+    // the solve runs on a private non-blocking stream (stream capture is not allowed on
+    // the legacy default stream), ordered after the caller's stream and joined back
+    if (!B->cstream) {
+        if (cudaStreamCreateWithFlags(&B->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming) != cudaSuccess)
+            return HELM_CUDA_ERROR;
+    }
+    cudaStream_t s = B->cstream;
+    if (cudaEventRecord(B->join, B->stream) != cudaSuccess || cudaStreamWaitEvent(s, B->join, 0) != cudaSuccess)
+        return HELM_CUDA_ERROR;
     const int P = B->nprob;
     const long long NT = B->NT;
     const int TR = B->tile_rows, NTL = B->ntiles, G = B->grid;
@@ -821,6 +837,17 @@ helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const doub
     const double omega = o->omega;
     const int nr = o->relax == HELM_RELAX_NONE ? 0 : o->n_r;
     const bool tb = o->correction == HELM_CORR_TB;
+    struct Graphs {                      // instantiated Arnoldi steps, freed on every exit
+        std::vector<cudaGraphExec_t> g;
+        ~Graphs() {
+            for (auto e : g)
+                if (e) cudaGraphExecDestroy(e);
+        }
+    } graphs;
+    graphs.g.assign(m, nullptr);
+    std::vector<cudaGraphExec_t>& step_graph = graphs.g;
+    // kernels of one Arnoldi step (counted as the capture counts them)
+    const long long step_launches = (nr == 0 ? 0 : (o->relax == HELM_RBGS ? 2 * nr : nr)) + (tb ? 4 : 0) + 13;
     while (true) {
         // true residual and restart decisions
         cudaMemcpyAsync(B->active, act.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s);
@@ -847,6 +874,10 @@ helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const doub
         launches += 2;
         std::vector<int> kd(P, 0), cact = act;
         for (int j = 0; j < m; ++j) {
+          // one Arnoldi step (preconditioner, operator, CGS2, Givens, the two status
+          // copies) is captured once per solve as a CUDA graph and replayed
+          if (!step_graph[j]) {
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HELM_CUDA_ERROR;
             double2* Vj = B->V + (long long)j * NT;
             double2* w = B->V + (long long)(j + 1) * NT;
             float2* Zj = B->Z32 + (long long)j * NT;
@@ -898,6 +929,15 @@ helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const doub
             launches += 13;
             cudaMemcpyAsync(B->hpin, B->nrm + P, sizeof(double) * P, cudaMemcpyDeviceToHost, s);
             cudaMemcpyAsync(B->hpin + P, B->est, sizeof(double) * P, cudaMemcpyDeviceToHost, s);
+            cudaGraph_t gr = nullptr;
+            if (cudaStreamEndCapture(s, &gr) != cudaSuccess) return HELM_CUDA_ERROR;
+            const cudaError_t ie = cudaGraphInstantiate(&step_graph[j], gr, 0);
+            cudaGraphDestroy(gr);
+            if (ie != cudaSuccess) return HELM_CUDA_ERROR;
+          } else {
+            launches += step_launches;
+          }
+            if (cudaGraphLaunch(step_graph[j], s) != cudaSuccess) return HELM_CUDA_ERROR;
             if (cudaStreamSynchronize(s) != cudaSuccess) return HELM_CUDA_ERROR;
             int still = 0;
             for (int b = 0; b < P; ++b) {
@@ -923,6 +963,8 @@ helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const doub
         cudaMemcpyAsync(x[b], B->x + pb.off, sizeof(double2) * pb.N, cudaMemcpyDeviceToDevice, s);
     }
     cudaEventRecord(e1, s);
+    cudaEventRecord(B->join, s);
+    cudaStreamWaitEvent(B->stream, B->join, 0);
     cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
