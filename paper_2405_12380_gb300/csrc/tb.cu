@@ -19,7 +19,7 @@
 //                  FP32-pair warp reduction per block); on Q_red with the compact
 //                  r after red-black Gauss-Seidel (half the basis is read)
 //   k_coarse_*     fixed-order sum of block partials, y = A_c^-1 c (FP64, one block per row)
-//   k_prolong_df   z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per two nodes
+//   k_prolong_df   z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 #include <cuda_bf16.h>
 
 #include "helm_internal.cuh"
@@ -523,33 +523,10 @@ __global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ 
     if (threadIdx.x == 0) y[i] = make_double2(red[0].x + red[1].x, red[0].y + red[1].y);
 }
 
-// z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per two consecutive
-// nodes (16-byte loads of Q: a warp reads 512 contiguous bytes of a column per
-// load; the padded column stride keeps the last pair of an odd N inside).
-// BASE: z_l = base_l + sum_j Q_j[l] y_j with base given as FP32 pairs (and, given
-// zdf, also the sum as FP32 pairs)
-__device__ __forceinline__ void prolong_out(bool base_mode, long long l, float a0, float a1, float a2, float a3,
-                                            double2* __restrict__ z, const float4* __restrict__ base,
-                                            float4* __restrict__ zdf) {
-    if (base_mode) {
-        // (b + a) as a pair sum, then one conversion to FP64
-        const float4 b = base[l];
-        float s0 = b.x + a0, bb = s0 - b.x, e0 = (b.x - (s0 - bb)) + (a0 - bb) + (b.y + a1);
-        float s1 = b.z + a2;
-        bb = s1 - b.z;
-        const float e1 = (b.z - (s1 - bb)) + (a2 - bb) + (b.w + a3);
-        z[l] = make_double2((double)s0 + (double)e0, (double)s1 + (double)e1);
-        if (zdf) {
-            const float h0 = s0 + e0, h1 = s1 + e1;
-            zdf[l] = make_float4(h0, e0 - (h0 - s0), h1, e1 - (h1 - s1));
-        }
-    } else {
-        const double2 zz = z[l];
-        z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
-    }
-}
-
+// z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
+// BASE: z_l = base_l + sum_j Q_j[l] y_j with base given as FP32 pairs
 template <bool BASE>
+// (and, given zdf, also the sum as FP32 pairs)
 __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q, long long ld, int k,
                                                     const double2* __restrict__ y, double2* __restrict__ z,
                                                     const float4* __restrict__ base, float4* __restrict__ zdf,
@@ -562,35 +539,43 @@ __global__ void __launch_bounds__(256) k_prolong_df(const float2* __restrict__ Q
         ys[j] = t;
     }
     __syncthreads();
-    const long long M = (N + 1) / 2;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
-        float a[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-        const float4* q = reinterpret_cast<const float4*>(Q + 2 * m);
-        const long long ld4 = ld / 2;
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const float2* q = Q + l;
         int j = 0;
         for (; j + 8 <= k; j += 8) {
-            float4 qv[8];
+            float2 qv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(j + u) * ld4);
+            for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(j + u) * ld);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const float4 yy = ys[j + u];
-                pair_fma(a[0][0], a[0][1], qv[u].x, qv[u].y, yy.x, yy.y);
-                pair_fma(a[0][2], a[0][3], qv[u].x, qv[u].y, yy.z, yy.w);
-                pair_fma(a[1][0], a[1][1], qv[u].z, qv[u].w, yy.x, yy.y);
-                pair_fma(a[1][2], a[1][3], qv[u].z, qv[u].w, yy.z, yy.w);
+                pair_fma(a0, a1, qv[u].x, qv[u].y, yy.x, yy.y);
+                pair_fma(a2, a3, qv[u].x, qv[u].y, yy.z, yy.w);
             }
         }
         for (; j < k; ++j) {
-            const float4 qv = q[(long long)j * ld4];
+            const float2 qv = q[(long long)j * ld];
             const float4 yy = ys[j];
-            pair_fma(a[0][0], a[0][1], qv.x, qv.y, yy.x, yy.y);
-            pair_fma(a[0][2], a[0][3], qv.x, qv.y, yy.z, yy.w);
-            pair_fma(a[1][0], a[1][1], qv.z, qv.w, yy.x, yy.y);
-            pair_fma(a[1][2], a[1][3], qv.z, qv.w, yy.z, yy.w);
+            pair_fma(a0, a1, qv.x, qv.y, yy.x, yy.y);
+            pair_fma(a2, a3, qv.x, qv.y, yy.z, yy.w);
         }
-        prolong_out(BASE, 2 * m, a[0][0], a[0][1], a[0][2], a[0][3], z, base, zdf);
-        if (2 * m + 1 < N) prolong_out(BASE, 2 * m + 1, a[1][0], a[1][1], a[1][2], a[1][3], z, base, zdf);
+        if (BASE) {
+            // (b + a) as a pair sum, then one conversion to FP64
+            const float4 b = base[l];
+            float s0 = b.x + a0, bb = s0 - b.x, e0 = (b.x - (s0 - bb)) + (a0 - bb) + (b.y + a1);
+            float s1 = b.z + a2;
+            bb = s1 - b.z;
+            const float e1 = (b.z - (s1 - bb)) + (a2 - bb) + (b.w + a3);
+            z[l] = make_double2((double)s0 + (double)e0, (double)s1 + (double)e1);
+            if (zdf) {
+                const float h0 = s0 + e0, h1 = s1 + e1;
+                zdf[l] = make_float4(h0, e0 - (h0 - s0), h1, e1 - (h1 - s1));
+            }
+        } else {
+            double2 zz = z[l];
+            z[l] = make_double2(zz.x + ((double)a0 + (double)a1), zz.y + ((double)a2 + (double)a3));
+        }
     }
 }
 
@@ -1008,13 +993,13 @@ void launch_project_df(const float2* Q, long long ld, int k, const double2* r, l
 
 void launch_prolong_df(const float2* Q, long long ld, int k, const double2* y, double2* z, long long N,
                        cudaStream_t s) {
-    long long b = ((N + 1) / 2 + 255) / 256;
+    long long b = (N + 255) / 256;
     k_prolong_df<false><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, nullptr, nullptr, N);
 }
 
 void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
                             float4* zdf, long long N, cudaStream_t s) {
-    long long b = ((N + 1) / 2 + 255) / 256;
+    long long b = (N + 255) / 256;
     k_prolong_df<true><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, base, zdf, N);
 }
 
