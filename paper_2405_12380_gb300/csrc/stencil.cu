@@ -803,24 +803,6 @@ __device__ __forceinline__ Cdf nbr_sum_any(const Op<double>& op, const XT* __res
     return s;
 }
 
-// the same sum with the loads issued unconditionally (the node is off the ring, so
-// every neighbour exists) and masked neighbours dropped afterwards
-template <typename XT>
-__device__ __forceinline__ Cdf nbr_sum_all(const Op<double>& op, const XT* __restrict__ x, long long l,
-                                           unsigned code) {
-    const long long sy = op.n, sz = (long long)op.n * op.n;
-    const Cdf a = cdf_load(x, l - 1), b = cdf_load(x, l + 1), c = cdf_load(x, l - sy), d = cdf_load(x, l + sy);
-    Cdf e = cdf_zero(), f = cdf_zero();
-    if (op.dim == 3) {
-        e = cdf_load(x, l - sz);
-        f = cdf_load(x, l + sz);
-    }
-    auto sel = [](unsigned cd, unsigned bit, Cdf v) { return (cd & bit) ? v : cdf_zero(); };
-    Cdf s = cdf_add(cdf_add(sel(code, 1u, a), sel(code, 2u, b)), cdf_add(sel(code, 4u, c), sel(code, 8u, d)));
-    if (op.dim == 3) s = cdf_add(s, cdf_add(sel(code, 16u, e), sel(code, 32u, f)));
-    return s;
-}
-
 template <int MODE, typename XT>
 __global__ void __launch_bounds__(BX * BY) k_apply_bicg_df(Op<double> op, DfTab t, const XT* __restrict__ x,
                                                            double2* __restrict__ y, const double2* __restrict__ w,
@@ -834,15 +816,11 @@ __global__ void __launch_bounds__(BX * BY) k_apply_bicg_df(Op<double> op, DfTab 
             const long long l = i + (long long)op.n * (j + (long long)op.n * kk);
             const unsigned code = node_code(op, l);
             const Cdf X = cdf_load(x, l);
-            // off the ring (where every fluid node lies) the neighbour loads do not wait
-            // for the code; ring nodes are masked
-            const bool interior = i >= 1 && i + 2 <= op.n && j >= 1 && j + 2 <= op.n &&
-                                  (op.dim == 2 || (kk >= 1 && kk + 2 <= op.n));
-            const Cdf sum = interior ? nbr_sum_all(op, x, l, code) : cdf_zero();
             Cdf out;
             if (code & kMasked) {
                 out = X;
             } else {
+                const Cdf sum = nbr_sum_any(op, x, l, code);
                 const int m = node_lidx(op, l, i, j, kk);
                 const Cdf d = {t.dre, conj ? df_neg(t.im[m]) : t.im[m]};
                 out = cdf_add(cdf_scale(t.hinv2, sum), cdf_mul(d, X));
@@ -937,33 +915,18 @@ __device__ __forceinline__ Cdf cdf_load_cg(const float4* p, long long l) {
     return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
 
-// off the outer ring every neighbour exists, so the six loads are issued before
-// the neighbour code arrives (one L2 round trip instead of two) and masked
-// neighbours are dropped afterwards; ring nodes are masked and need no sum
-__device__ __forceinline__ bool node_interior(const Op<double>& op, long long l) {
-    const unsigned ul = (unsigned)l, un = (unsigned)op.n;
-    const unsigned r = ul / un, i = ul - r * un;
-    const unsigned k = r / un, j = r - k * un;
-    bool in = i >= 1 && i + 2 <= un && (op.dim == 3 ? (j >= 1 && j + 2 <= un && k >= 1 && k + 2 <= un)
-                                                     : (r >= 1 && r + 2 <= un));
-    return in;
-}
-
-__device__ __forceinline__ Cdf nbr_sum_df_cg(const Op<double>& op, const float4* x, long long l, unsigned code,
-                                             bool interior) {
-    if (!interior) return cdf_zero();
+__device__ __forceinline__ Cdf nbr_sum_df_cg(const Op<double>& op, const float4* x, long long l, unsigned code) {
     const long long sy = op.n, sz = (long long)op.n * op.n;
-    const float4 va = __ldcg(x + l - 1), vb = __ldcg(x + l + 1), vc = __ldcg(x + l - sy), vd = __ldcg(x + l + sy);
-    float4 ve = make_float4(0.f, 0.f, 0.f, 0.f), vf = ve;
+    const Cdf a = (code & 1u) ? cdf_load_cg(x, l - 1) : cdf_zero();
+    const Cdf b = (code & 2u) ? cdf_load_cg(x, l + 1) : cdf_zero();
+    const Cdf c = (code & 4u) ? cdf_load_cg(x, l - sy) : cdf_zero();
+    const Cdf d = (code & 8u) ? cdf_load_cg(x, l + sy) : cdf_zero();
+    Cdf s = cdf_add(cdf_add(a, b), cdf_add(c, d));
     if (op.dim == 3) {
-        ve = __ldcg(x + l - sz);
-        vf = __ldcg(x + l + sz);
+        const Cdf e = (code & 16u) ? cdf_load_cg(x, l - sz) : cdf_zero();
+        const Cdf f = (code & 32u) ? cdf_load_cg(x, l + sz) : cdf_zero();
+        s = cdf_add(s, cdf_add(e, f));
     }
-    auto sel = [](unsigned c, unsigned bit, float4 v) {
-        return (c & bit) ? Cdf{make_float2(v.x, v.y), make_float2(v.z, v.w)} : cdf_zero();
-    };
-    Cdf s = cdf_add(cdf_add(sel(code, 1u, va), sel(code, 2u, vb)), cdf_add(sel(code, 4u, vc), sel(code, 8u, vd)));
-    if (op.dim == 3) s = cdf_add(s, cdf_add(sel(code, 16u, ve), sel(code, 32u, vf)));
     return s;
 }
 
@@ -1033,11 +996,11 @@ __global__ void __launch_bounds__(kCycleThreads, 1) k_cycle_df(Op<double> op, Df
                 if (l >= N) continue;
                 const unsigned code = op.nbm[l];
                 const Cdf F = cdf_load_cg(fs, l);
-                const Cdf sum = nbr_sum_df_cg(op, xs, l, code, node_interior(op, l));
                 Cdf x;
                 if (code & kMasked) {
                     x = F;
                 } else {
+                    const Cdf sum = nbr_sum_df_cg(op, xs, l, code);
                     x = cdf_mul(invd_df(t, op.lidx[l], conj), cdf_sub(F, cdf_scale(t.hinv2, sum)));
                 }
                 __stcg(xs + l, cdf_pack(x));
@@ -1050,11 +1013,11 @@ __global__ void __launch_bounds__(kCycleThreads, 1) k_cycle_df(Op<double> op, Df
         const long long l = 2 * m + (colour_of(2 * m, op.n) != 0);
         const unsigned code = op.nbm[l];
         const Cdf x = cdf_load_cg(xs, l);
-        const Cdf sum = nbr_sum_df_cg(op, xs, l, code, node_interior(op, l));
         Cdf out;
         if (code & kMasked) {
             out = x;
         } else {
+            const Cdf sum = nbr_sum_df_cg(op, xs, l, code);
             const int mm = op.lidx[l];
             const Cdf d = {t.dre, conj ? df_neg(t.im[mm]) : t.im[mm]};
             out = cdf_add(cdf_scale(t.hinv2, sum), cdf_mul(d, x));
