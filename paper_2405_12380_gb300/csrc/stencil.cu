@@ -881,24 +881,32 @@ struct GridBar {
 };
 constexpr unsigned kBarSpinLimit = 1u << 22;
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// arrival is an acquire-release add on the counter (each block's writes, ordered
+// before it by the block barrier, are released; the last arrival acquires them all),
+// the last block resets the counter and releases the next generation, and the
+// others acquire it.  Thread 0 waits for all; the block barrier passes it on.
 __device__ __forceinline__ void grid_barrier(const GridBar& b) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = b.gen;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
-            atomicExch(b.count, 0u);
-            __threadfence();
-            atomicAdd(b.gen, 1u);
+        const unsigned g = ld_acquire_gpu(b.gen);
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(b.count) : "memory");
+        if (old == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(b.count) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(b.gen) : "memory");
         } else {
-            for (unsigned it = 0; *gen == g; ++it)
+            for (unsigned it = 0; ld_acquire_gpu(b.gen) == g; ++it)
                 if (it > kBarSpinLimit) {
                     atomicExch(b.err, 1);
                     break;
                 }
         }
-        __threadfence();
     }
     __syncthreads();
 }
