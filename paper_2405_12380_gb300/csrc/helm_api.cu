@@ -317,15 +317,14 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
     }
     const long long rows = (h->N + 1) / 2;
     const int nblk = project_blocks(rows);
-    // the projection with the coarse solve in its last block (FP32-pair arithmetic)
     ev_mark(h, 0, 0);
-    launch_project_coarse_df(h->Qr, basis_ld(rows), h->k, rr, rows, h->coarse_partials, nblk, h->Ainv_df, conj,
-                             h->ybuf, h->counter + 1, s);
+    launch_project_df_split(h->Qr, basis_ld(rows), h->k, rr, rows, h->coarse_partials, nblk, s);
     ev_mark(h, 0, 1);
+    launch_coarse_apply(h->coarse_partials, nblk, h->k, h->Ainv, conj, h->ybuf, h->cbuf, s);
     ev_mark(h, 1, 0);
     launch_prolong_df_base(h->Q, basis_ld(h->N), h->k, h->ybuf, xs, z, zdf, h->N, s);
     ev_mark(h, 1, 1);
-    h->launches += 2 * o->n_r + 3;
+    h->launches += 2 * o->n_r + 5;
     CKL();
     return HELM_OK;
 }
@@ -767,12 +766,6 @@ helm_status build_coarse(helm_handle* h, const double* Qrm, int ldq, int k) {
     launch_gram(Qrm, ldq, k, Wc, 2 * ldq, 2 * k, N, part, Cc, s);
     cudaMemsetAsync(h->dflag, 0, sizeof(int) * 8, s);
     launch_gauss_jordan(Cc, 2 * k, k, h->Ainv, gj, h->dflag, s);
-    dfree(h->Ainv_df);
-    if ((st = dalloc(h, &h->Ainv_df, (size_t)k * k)) != HELM_OK) {
-        cleanup();
-        return st;
-    }
-    launch_split_c(h->Ainv, h->Ainv_df, (long long)k * k, s);
     int flag = 0;
     cudaError_t e = cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -878,7 +871,7 @@ helm_status helm_destroy(helm_handle* h) {
         if (e) cudaEventDestroy(e);
     for (auto p : h->tmp) cudaFree(p);
     for (auto p : h->tmp32) cudaFree(p);
-    dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->Ainv_df); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
+    dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
     if (h->Qbf) cudaFree(h->Qbf);
     dfree(h->partials32); dfree(h->y32); dfree(h->Z32);
     dfree(h->Traw); dfree(h->bw); dfree(h->nl_x); dfree(h->nl_h0); dfree(h->nl_h1);
@@ -1024,7 +1017,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         for (int o = 0; o < wout; ++o) hw.push_back(b[o]);
         off += (size_t)win * wout + wout;
     }
-    dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->Ainv_df); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
+    dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
     h->k = 0;
     const long long N = h->N;
     const int ldt = round32(p);
@@ -1120,7 +1113,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     st = build_coarse(h, T, ldq, k);
     if (st != HELM_OK) {
         cleanup();
-        dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->Ainv_df);
+        dfree(h->Q); dfree(h->Qr); dfree(h->Ainv);
         return st;
     }
     STEP(dalloc(h, &h->coarse_partials, (size_t)std::max(restrict_blocks(N), project_blocks(N)) * k));

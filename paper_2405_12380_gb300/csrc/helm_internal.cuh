@@ -212,13 +212,6 @@ cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, int pre, const
 // projection of a residual given as FP32 pairs (float4 per complex entry, N rows)
 void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
                              int nblk, cudaStream_t s);
-// the projection of a pair residual with the coarse solve in its last block:
-// y = A_c^-1 Q^T r (Ainv_df: A_c^-1 as FP32 pairs, k x k; counter zero between uses)
-void launch_project_coarse_df(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
-                              int nblk, const float4* Ainv_df, int conj, double2* y, unsigned* counter,
-                              cudaStream_t s);
-// complex FP64 -> FP32 pairs (re hi, re lo, im hi, im lo)
-void launch_split_c(const double2* a, float4* b, long long n, cudaStream_t s);
 // z = base + Q y with base given as FP32 pairs (float4 per complex entry); zdf
 // (optional) receives z as FP32 pairs too
 void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
@@ -296,7 +289,6 @@ struct helm_handle {
     std::vector<int> kept;
     float2* Q = nullptr;            // FP32 pairs, k x N
     float2* Qr = nullptr;           // its red rows, k x ceil(N / 2)
-    float4* Ainv_df = nullptr;      // A_c^-1 as FP32 pairs (k x k), for the fused coarse solve
     double2* Ainv = nullptr;
     double2* coarse_partials = nullptr;
     void* Qbf = nullptr;            // BF16 basis (MIXED handles), column-major k x N

@@ -22,7 +22,6 @@
 //   k_prolong_df   z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 #include <cuda_bf16.h>
 
-#include "bicg.cuh"
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -421,83 +420,15 @@ __device__ __forceinline__ void pair_warp_sum(float& sh, float& sl) {
     }
 }
 
-// (sh, sl) += (bh, bl), two-sum of the high parts
-__device__ __forceinline__ void pair_add(float& sh, float& sl, float bh, float bl) {
-    const float s = sh + bh;
-    const float bb = s - sh;
-    const float err = (sh - (s - bb)) + (bh - bb);
-    sh = s;
-    sl += err + bl;
-}
-
-// The coarse solve in the last block of the projection, in FP32-pair arithmetic:
-// c_j = fixed-order sum of the block partials (pairs), y = A_c^-1 c (conj: with
-// conj(A_c^-1)), y written in FP64.  Threads (g, j): group g of G = blockDim / k
-// sums every G-th partial of column j (then row i of the product), the groups are
-// added in order.
-__device__ void coarse_solve_df(const float4* __restrict__ parts, int nblk, int k, const float4* __restrict__ Ainv,
-                                int conj, double2* __restrict__ y) {
-    __shared__ float4 gs[512];   // G k <= blockDim.x (= 512) entries
-    __shared__ float4 cj[kMaxP];
-    const int G = blockDim.x / k;
-    const int t = threadIdx.x, g = t / k, j = t - g * k;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g < G)
-        for (int b = g; b < nblk; b += G) {
-            const float4 q = __ldcg(parts + (long long)b * k + j);
-            pair_add(a.x, a.y, q.x, q.y);
-            pair_add(a.z, a.w, q.z, q.w);
-        }
-    if (g < G) gs[g * k + j] = a;
-    __syncthreads();
-    if (t < k) {
-        float4 c = gs[t];
-        for (int q = 1; q < G; ++q) {
-            const float4 o = gs[q * k + t];
-            pair_add(c.x, c.y, o.x, o.y);
-            pair_add(c.z, c.w, o.z, o.w);
-        }
-        cj[t] = c;
-    }
-    __syncthreads();
-    // row i = j of the product, columns jj = g, g + G, ...
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g < G)
-        for (int jj = g; jj < k; jj += G) {
-            float4 m = Ainv[(long long)j * k + jj];
-            if (conj) { m.z = -m.z; m.w = -m.w; }
-            const float4 c = cj[jj];
-            pair_fma(r.x, r.y, m.x, m.y, c.x, c.y);
-            pair_fma(r.x, r.y, -m.z, -m.w, c.z, c.w);
-            pair_fma(r.z, r.w, m.x, m.y, c.z, c.w);
-            pair_fma(r.z, r.w, m.z, m.w, c.x, c.y);
-        }
-    __syncthreads();
-    if (g < G) gs[g * k + j] = r;
-    __syncthreads();
-    if (t < k) {
-        float4 c = gs[t];
-        for (int q = 1; q < G; ++q) {
-            const float4 o = gs[q * k + t];
-            pair_add(c.x, c.y, o.x, o.y);
-            pair_add(c.z, c.w, o.z, o.w);
-        }
-        y[t] = make_double2((double)c.x + (double)c.y, (double)c.z + (double)c.w);
-    }
-}
-
 constexpr int PJ_T = 512;        // threads per projection block (16 warps), two blocks per SM
 constexpr int PJ_TILE = 512;     // rows per tile (one per thread)
 
 // partials[b][j] = sum over the rows of block b of Q_j[l] r_l (r given in FP64, or
 // SPLIT: already as FP32 pairs, one float4 per complex entry)
-template <int KPW, bool SPLIT, bool FUSE = false>
+template <int KPW, bool SPLIT>
 __global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict__ Q, long long ld, int k,
                                                      const void* __restrict__ rv_, long long N,
-                                                     double2* __restrict__ partials, long long rows_per_block,
-                                                     const float4* __restrict__ Ainv_df = nullptr, int conj = 0,
-                                                     double2* __restrict__ y = nullptr,
-                                                     unsigned* counter = nullptr) {
+                                                     double2* __restrict__ partials, long long rows_per_block) {
     __shared__ float4 rs[PJ_TILE];       // (re hi, re lo, im hi, im lo)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = PJ_T / 32;
@@ -548,18 +479,9 @@ __global__ void __launch_bounds__(PJ_T, 2) k_project_df(const float2* __restrict
         const int j = warp + NW * c;
         pair_warp_sum(acc[c][0], acc[c][1]);
         pair_warp_sum(acc[c][2], acc[c][3]);
-        if (lane == 0 && j < k) {
-            if (FUSE)
-                reinterpret_cast<float4*>(partials)[(long long)blockIdx.x * k + j] =
-                    make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
-            else
-                partials[(long long)blockIdx.x * k + j] =
-                    make_double2((double)acc[c][0] + (double)acc[c][1], (double)acc[c][2] + (double)acc[c][3]);
-        }
-    }
-    if (FUSE && last_block_done(counter, gridDim.x)) {
-        coarse_solve_df(reinterpret_cast<const float4*>(partials), gridDim.x, k, Ainv_df, conj, y);
-        if (threadIdx.x == 0) *counter = 0;
+        if (lane == 0 && j < k)
+            partials[(long long)blockIdx.x * k + j] =
+                make_double2((double)acc[c][0] + (double)acc[c][1], (double)acc[c][2] + (double)acc[c][3]);
     }
 }
 
@@ -1079,35 +1001,6 @@ void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2*
                             float4* zdf, long long N, cudaStream_t s) {
     long long b = (N + 255) / 256;
     k_prolong_df<true><<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Q, ld, k, y, z, base, zdf, N);
-}
-
-void launch_project_coarse_df(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
-                              int nblk, const float4* Ainv_df, int conj, double2* y, unsigned* counter,
-                              cudaStream_t s) {
-    long long rows = (N + nblk - 1) / nblk;
-    const int kpw = (k + 15) / 16;
-#define PJ_CASE(K) \
-    k_project_df<K, true, true><<<nblk, PJ_T, 0, s>>>(Q, ld, k, r, N, partials, rows, Ainv_df, conj, y, counter)
-    if (kpw <= 1) PJ_CASE(1);
-    else if (kpw <= 2) PJ_CASE(2);
-    else if (kpw <= 4) PJ_CASE(4);
-    else if (kpw <= 8) PJ_CASE(8);
-    else PJ_CASE(16);
-#undef PJ_CASE
-}
-
-__global__ void k_split_c(const double2* __restrict__ a, float4* __restrict__ b, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double2 v = a[i];
-        float4 t;
-        split_f64(v.x, t.x, t.y);
-        split_f64(v.y, t.z, t.w);
-        b[i] = t;
-    }
-}
-
-void launch_split_c(const double2* a, float4* b, long long n, cudaStream_t s) {
-    k_split_c<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(a, b, n);
 }
 
 void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
