@@ -109,11 +109,6 @@ __global__ void __launch_bounds__(kFinThreads) k_sum_real(const double* partials
     double v = fin_sum_d(partials, nparts);
     if (threadIdx.x == 0) *out = v;
 }
-__global__ void __launch_bounds__(kFinThreads) k_sum_cplx(const double2* partials, int nparts, double2* out) {
-    double2 v = fin_sum_c(partials, nparts);
-    if (threadIdx.x == 0) *out = v;
-}
-
 // ---------------------------------------------------------------- BiCGStab
 
 __global__ void __launch_bounds__(TB) k_bicg_p(const double2* __restrict__ r, const double2* __restrict__ v,
@@ -123,60 +118,6 @@ __global__ void __launch_bounds__(TB) k_bicg_p(const double2* __restrict__ r, co
         double2 t = csub(p[l], cmul(omega, v[l]));
         p[l] = cadd(r[l], cmul(beta, t));
     }
-}
-
-__global__ void __launch_bounds__(TB) k_bicg_s(const double2* __restrict__ r, const double2* __restrict__ v,
-                                               double2* __restrict__ s, const double2* __restrict__ sc, long long N,
-                                               double* partials) {
-    const double2 alpha = sc[S_ALPHA];
-    double acc = 0;
-    for (long long l = blockIdx.x * (long long)TB + threadIdx.x; l < N; l += (long long)gridDim.x * TB) {
-        double2 q = csub(r[l], cmul(alpha, v[l]));
-        s[l] = q;
-        acc += q.x * q.x + q.y * q.y;
-    }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
-}
-
-// partials layout: [blk] = (<t,s>.re, <t,s>.im, <t,t>, 0)
-__global__ void __launch_bounds__(TB) k_bicg_omega_dots(const double2* __restrict__ t, const double2* __restrict__ s,
-                                                        long long N, double* partials) {
-    double2 ts = make_double2(0, 0);
-    double tt = 0;
-    for (long long l = blockIdx.x * (long long)TB + threadIdx.x; l < N; l += (long long)gridDim.x * TB) {
-        double2 a = t[l], b = s[l];
-        ts.x += a.x * b.x + a.y * b.y;
-        ts.y += a.x * b.y - a.y * b.x;
-        tt += a.x * a.x + a.y * a.y;
-    }
-    ts = block_sum(ts);
-    tt = block_sum(tt);
-    if (threadIdx.x == 0) {
-        partials[4 * blockIdx.x + 0] = ts.x;
-        partials[4 * blockIdx.x + 1] = ts.y;
-        partials[4 * blockIdx.x + 2] = tt;
-        partials[4 * blockIdx.x + 3] = 0;
-    }
-}
-
-__global__ void __launch_bounds__(TB) k_bicg_xr(double2* __restrict__ x, double2* __restrict__ r,
-                                                const double2* __restrict__ phat, const double2* __restrict__ shat,
-                                                const double2* __restrict__ s, const double2* __restrict__ t,
-                                                const double2* __restrict__ sc, long long N, double* partials) {
-    const double2 alpha = sc[S_ALPHA], omega = sc[S_OMEGA];
-    double acc = 0;
-    const bool skip = sc[S_FLAGS].y == 1.0;     // breakdown before the update: leave x and r alone
-    for (long long l = blockIdx.x * (long long)TB + threadIdx.x; l < N && !skip; l += (long long)gridDim.x * TB) {
-        double2 xv = cadd(x[l], cmul(alpha, phat[l]));
-        xv = cadd(xv, cmul(omega, shat[l]));
-        x[l] = xv;
-        double2 q = csub(s[l], cmul(omega, t[l]));
-        r[l] = q;
-        acc += q.x * q.x + q.y * q.y;
-    }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
 // s = r - alpha v with ||s||^2, the scalar update in the last block
@@ -458,12 +399,6 @@ __global__ void k_init_g(double2* g, int m1, const double* beta2) {
     if (i < m1) g[i] = make_double2(i == 0 ? sqrt(*beta2) : 0.0, 0);
 }
 
-__global__ void __launch_bounds__(TB) k_axpy(double2* __restrict__ y, const double2* __restrict__ x, double2 a,
-                                             long long N) {
-    for (long long l = blockIdx.x * (long long)TB + threadIdx.x; l < N; l += (long long)gridDim.x * TB)
-        y[l] = cadd(y[l], cmul(a, x[l]));
-}
-
 __global__ void __launch_bounds__(TB) k_set_masked(double2* __restrict__ x, const double2* __restrict__ f,
                                                    const uint8_t* __restrict__ mask, long long N) {
     for (long long l = blockIdx.x * (long long)TB + threadIdx.x; l < N; l += (long long)gridDim.x * TB)
@@ -495,23 +430,9 @@ void launch_norm2(const double2* a, long long N, double* partials, cudaStream_t 
 void launch_sum_real(const double* partials, int nparts, double* out, cudaStream_t s) {
     k_sum_real<<<1, kFinThreads, 0, s>>>(partials, nparts, out);
 }
-void launch_sum_cplx(const double2* partials, int nparts, double2* out, cudaStream_t s) {
-    k_sum_cplx<<<1, kFinThreads, 0, s>>>(partials, nparts, out);
-}
 void launch_bicg_update_p(const double2* r, const double2* v, double2* p, const double2* sc, long long N,
                           cudaStream_t s) {
     k_bicg_p<<<stream_blocks(N), TB, 0, s>>>(r, v, p, sc, N);
-}
-void launch_bicg_s(const double2* r, const double2* v, double2* sv, const double2* sc, long long N,
-                   double* partials, cudaStream_t s) {
-    k_bicg_s<<<kRedBlocks, TB, 0, s>>>(r, v, sv, sc, N, partials);
-}
-void launch_bicg_omega_dots(const double2* t, const double2* sv, long long N, double* partials, cudaStream_t s) {
-    k_bicg_omega_dots<<<kRedBlocks, TB, 0, s>>>(t, sv, N, partials);
-}
-void launch_bicg_xr(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
-                    const double2* t, const double2* sc, long long N, double* partials, cudaStream_t s) {
-    k_bicg_xr<<<kRedBlocks, TB, 0, s>>>(x, r, phat, shat, sv, t, sc, N, partials);
 }
 void launch_bicg_s_fused(const double2* r, const double2* v, double2* sv, double2* sc, long long N, double* parts,
                          unsigned* counter, double tol_abs, cudaStream_t s) {
@@ -555,9 +476,6 @@ void launch_hsolve(const double2* H, int ldh, int k, const double2* g, double2* 
 }
 void launch_init_g(double2* g, int m1, const double* beta2, cudaStream_t s) {
     k_init_g<<<1, 128, 0, s>>>(g, m1, beta2);
-}
-void launch_axpy(double2* y, const double2* x, double2 a, long long N, cudaStream_t s) {
-    k_axpy<<<stream_blocks(N), TB, 0, s>>>(y, x, a, N);
 }
 void launch_set_masked(double2* x, const double2* f, const uint8_t* mask, long long N, cudaStream_t s) {
     k_set_masked<<<stream_blocks(N), TB, 0, s>>>(x, f, mask, N);

@@ -126,16 +126,9 @@ void launch_bicg_xr_fused(double2* x, double2* r, const double2* phat, const dou
 void launch_dot(const double2* a, const double2* b, long long N, double2* partials, cudaStream_t s);
 void launch_norm2(const double2* a, long long N, double* partials, cudaStream_t s);
 void launch_sum_real(const double* partials, int nparts, double* out, cudaStream_t s);
-void launch_sum_cplx(const double2* partials, int nparts, double2* out, cudaStream_t s);
 // BiCGStab pieces (scalars live in device memory, see blas.cu)
 void launch_bicg_update_p(const double2* r, const double2* v, double2* p, const double2* sc, long long N,
                           cudaStream_t s);
-void launch_bicg_s(const double2* r, const double2* v, double2* sv, const double2* sc, long long N,
-                   double* partials, cudaStream_t s);
-void launch_bicg_omega_dots(const double2* t, const double2* sv, long long N, double* partials,
-                            cudaStream_t s);
-void launch_bicg_xr(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
-                    const double2* t, const double2* sc, long long N, double* partials, cudaStream_t s);
 void launch_bicg_scalar(int recipe, const double* partials, int nparts, double2* sc, double tol_abs,
                         cudaStream_t s);
 // FGMRES pieces
@@ -150,7 +143,6 @@ void launch_givens(double2* H, int ldh, int j, double* cs, double2* sn, double2*
                    double* est, cudaStream_t s);
 void launch_hsolve(const double2* H, int ldh, int k, const double2* g, double2* y, cudaStream_t s);
 void launch_init_g(double2* g, int m1, const double* beta2, cudaStream_t s);
-void launch_axpy(double2* y, const double2* x, double2 a, long long N, cudaStream_t s);
 void launch_set_masked(double2* x, const double2* f, const uint8_t* mask, long long N, cudaStream_t s);
 void launch_cvt_f64_to_f32(const double2* a, float2* b, long long N, cudaStream_t s);
 void launch_cvt_f32_to_f64(const float2* a, double2* b, long long N, cudaStream_t s);
@@ -173,7 +165,6 @@ void launch_gauss_jordan(const double* C, int ldc, int k, double2* Ainv, double2
                          cudaStream_t s);
 void launch_coarse_apply(const double2* partials, int nblk, int k, const double2* Ainv, int conj, double2* y,
                          double2* cbuf, cudaStream_t s);
-void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s);
 // FP64 projection on FP32 pipes: Q as (hi, lo) FP32 pairs, column-major k x N
 // (N rows: the projection also runs on the compact red rows, N = ceil(N / 2))
 int project_blocks(long long N);
@@ -227,7 +218,6 @@ void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const 
 // r_red[m] = (v - A z) at the red node of pair m (stencil.cu)
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s);
-void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s);
 // nonlinear DeepONet correction: raw trunk matrix in FP32 (p x N), branch in FP32
 void launch_rm_to_cm_f32(const double* A, int ld, int p, float* B, long long N, cudaStream_t s);
 void launch_nl_pack(const double2* r, const double* s2, float* x, long long N, cudaStream_t s);
@@ -236,7 +226,6 @@ void launch_nl_prolong(const float* T, int p, const float* b, const double* s2, 
 // mixed precision: BF16 basis (column-major k x N), complex64 vectors, FP32 accumulation
 void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s);
 void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long N, cudaStream_t s);
-void launch_cm_bf16_to_rm(const void* B, int k, double* A, long long N, cudaStream_t s);
 void launch_restrict32(const Op<float>& op, const void* Q, int k, const float2* v, const float2* z, int conj,
                        float2* partials, int nblk, cudaStream_t s);
 void launch_coarse_apply32(const float2* partials, int nblk, int k, const double2* Ainv, int conj, float2* y,

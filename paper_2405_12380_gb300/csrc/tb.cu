@@ -649,42 +649,6 @@ __global__ void k_cm_pair_to_rm(const float2* __restrict__ B, long long ldb, int
     }
 }
 
-// row-major (N x ld, k used) <-> column-major (k x N)
-__global__ void k_rm_to_cm(const double* __restrict__ A, int ld, int k, double* __restrict__ B, long long N) {
-    __shared__ double tile[32][33];
-    const long long l0 = (long long)blockIdx.x * 32;
-    const int c0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        long long l = l0 + r;
-        int c = c0 + threadIdx.x;
-        tile[r][threadIdx.x] = (l < N && c < k) ? A[l * ld + c] : 0.0;
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        int c = c0 + r;
-        long long l = l0 + threadIdx.x;
-        if (c < k && l < N) B[(long long)c * N + l] = tile[threadIdx.x][r];
-    }
-}
-
-__global__ void k_cm_to_rm(const double* __restrict__ B, int k, double* __restrict__ A, long long N) {
-    __shared__ double tile[32][33];
-    const long long l0 = (long long)blockIdx.x * 32;
-    const int c0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        int c = c0 + r;
-        long long l = l0 + threadIdx.x;
-        tile[r][threadIdx.x] = (c < k && l < N) ? B[(long long)c * N + l] : 0.0;
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        long long l = l0 + r;
-        int c = c0 + threadIdx.x;
-        if (l < N && c < k) A[l * k + c] = tile[threadIdx.x][r];
-    }
-}
-
-
 // ------------------------------------------------ nonlinear DeepONet correction
 // row-major FP64 T (N x ld, p used) -> column-major FP32 (p x N)
 __global__ void k_rm_to_cm_f32(const double* __restrict__ A, int ld, int p, float* __restrict__ B, long long N) {
@@ -760,23 +724,6 @@ __global__ void k_rm_to_cm_bf16(const double* __restrict__ A, int ld, int k, __n
         int c = c0 + r;
         long long l = l0 + threadIdx.x;
         if (c < k && l < N) B[(long long)c * N + l] = __float2bfloat16_rn(tile[threadIdx.x][r]);
-    }
-}
-
-__global__ void k_cm_bf16_to_rm(const __nv_bfloat16* __restrict__ B, int k, double* __restrict__ A, long long N) {
-    __shared__ double tile[32][33];
-    const long long l0 = (long long)blockIdx.x * 32;
-    const int c0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        int c = c0 + r;
-        long long l = l0 + threadIdx.x;
-        tile[r][threadIdx.x] = (c < k && l < N) ? (double)__bfloat162float(B[(long long)c * N + l]) : 0.0;
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        long long l = l0 + r;
-        int c = c0 + threadIdx.x;
-        if (l < N && c < k) A[l * k + c] = tile[threadIdx.x][r];
     }
 }
 
@@ -1031,16 +978,6 @@ void launch_cm_pair_to_rm(const float2* B, long long ldb, int k, double* A, long
     k_cm_pair_to_rm<<<g, dim3(32, 8), 0, s>>>(B, ldb, k, A, N);
 }
 
-void launch_rm_to_cm(const double* A, int ld, int k, double* B, long long N, cudaStream_t s) {
-    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
-    k_rm_to_cm<<<g, dim3(32, 8), 0, s>>>(A, ld, k, B, N);
-}
-
-void launch_cm_to_rm(const double* B, int k, double* A, long long N, cudaStream_t s) {
-    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
-    k_cm_to_rm<<<g, dim3(32, 8), 0, s>>>(B, k, A, N);
-}
-
 void launch_rm_to_cm_f32(const double* A, int ld, int p, float* B, long long N, cudaStream_t s) {
     dim3 g((unsigned)((N + 31) / 32), (p + 31) / 32);
     k_rm_to_cm_f32<<<g, dim3(32, 8), 0, s>>>(A, ld, p, B, N);
@@ -1064,11 +1001,6 @@ void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s) {
 void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long N, cudaStream_t s) {
     dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
     k_rm_to_cm_bf16<<<g, dim3(32, 8), 0, s>>>(A, ld, k, static_cast<__nv_bfloat16*>(B), N);
-}
-
-void launch_cm_bf16_to_rm(const void* B, int k, double* A, long long N, cudaStream_t s) {
-    dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
-    k_cm_bf16_to_rm<<<g, dim3(32, 8), 0, s>>>(static_cast<const __nv_bfloat16*>(B), k, A, N);
 }
 
 void launch_restrict32(const Op<float>& op, const void* Qv, int k, const float2* v, const float2* z, int conj,
