@@ -181,14 +181,24 @@ helm_status don_load_branch(helm_handle* h, const float* weights, const int* wid
  * FP32 network).  r, z [dev] HELM_C128. */
 helm_status don_correct(helm_handle* h, int mode, const void* r, void* z, int conj, int dtype);
 
-/* z = M(r), the hybrid cycle of `opts` (Eq. 3).  r, z [dev] HELM_C128. */
+/* z = M(r), the hybrid cycle of `opts` (Eq. 3).  r, z [dev] HELM_C128.
+ * On an FP64 handle with a tabulated k^2, the red-black Gauss-Seidel cycle with
+ * the trunk-basis correction runs in double-float arithmetic (value = hi + lo,
+ * two FP32 numbers, 48-bit significand) on the FP32 pipes, the residual of the
+ * correction on the red rows only (it vanishes on the black rows after the black
+ * half-sweep); z agrees with the FP64 evaluation to about 1e-14 relative. */
 helm_status helm_precond(helm_handle* h, const helm_solve_opts* opts, const void* r, void* z);
 
 /* Solve A x = f (conj(A) x = f if opts->conj).  f [dev] complex128, x [dev]
  * complex128: initial guess in, solution out.  Masked entries of x are set to
  * f on entry (x_l = g_l).  res_hist [host] or NULL: relative true residual
  * after every restart/cycle, up to hist_len values (FGMRES: per Arnoldi step,
- * Givens estimate).  Synchronises; stats [host] may be NULL. */
+ * Givens estimate).  Synchronises; stats [host] may be NULL.  The stopping test
+ * and the final rel_res use the FP64 residual.  BiCGStab with the double-float
+ * cycle (see helm_precond) applies A to the cycle's double-float output and
+ * rounds to FP64 once; its Krylov vectors, dots and recurrences are FP64.
+ * HELM_CUDA_ERROR also reports a bounded in-kernel wait that gave up (never
+ * expected; the message says which). */
 helm_status helm_solve(helm_handle* h, const helm_solve_opts* opts, const void* f, void* x,
                        helm_stats* stats, double* res_hist, int hist_len);
 
