@@ -256,6 +256,18 @@ def stencil_bench(hm, torch, n=256, reps=20):
     return out
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """The largest value over the ranks of the job (the timing rule of multi-GPU
+    runs: the slowest replica sets the time); the value itself on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -308,11 +320,7 @@ def gpu_arm(args):
     _, st_prof = P.solve(f, None, o)
     P.set_profiling(False)
     solve_ms = [s["ms"] for s in stats]
-    mean_ms = statistics.mean(solve_ms)
-    t = torch.tensor([mean_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    mean_ms = float(t.item())
+    mean_ms = max_over_ranks(statistics.mean(solve_ms), world)
     # e2e: the same solve through helm_solve_host with pinned host buffers
     fh = f.cpu().pin_memory()
     f_np = fh.numpy()
@@ -328,11 +336,7 @@ def gpu_arm(args):
         dt = time.perf_counter() - t1
         if step >= args.warmup:
             e2e.append(dt)
-    e2e_s = statistics.mean(e2e)
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = max_over_ranks(statistics.mean(e2e), world)
     # check the converged solution with an independent FP64 residual (device, library op)
     r, nrm = P.residual(f, x)
     rel_res = float(nrm.sqrt().item() / torch.linalg.vector_norm(f).item())
