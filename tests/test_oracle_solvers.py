@@ -52,6 +52,28 @@ def test_rbgs_equals_lexicographic_gs_on_permuted_system():
     assert np.linalg.norm(y[perm] - xp) <= 1e-12 * np.linalg.norm(xp)
 
 
+def test_residual_after_black_half_sweep_lives_on_red_rows():
+    """After a red-black sweep that ends with the black half-sweep, f - A x is zero
+    (to rounding) on black rows (each was just solved given its red neighbours, the
+    only ones it couples to) and on masked rows (x = f there): the projection of
+    the hybrid cycle needs only the red rows."""
+    for dim, n, box in ((2, 13, (5, 7)), (3, 9, (3, 5))):
+        rng = np.random.default_rng(5)
+        mask = (scenes.ring_mask(dim, n) | scenes.box_mask(dim, n, *box)).reshape(-1).astype(np.uint8)
+        A = assemble.assemble(dim, n, assemble.k2_field(dim, n, 7.0, 2, 0.5), mask)
+        N = n ** dim
+        f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        col = assemble.colour(dim, n)
+        for sweeps in (1, 3):
+            x = relax.rbgs(A, f, np.zeros(N, complex), col, sweeps)
+            r = f - A @ x
+            red_fluid = (col == 0) & (mask == 0)
+            rest = ~red_fluid
+            assert np.linalg.norm(r[rest]) <= 1e-13 * np.linalg.norm(r[red_fluid]) * max(1.0, np.abs(A).max()), \
+                (dim, sweeps, np.linalg.norm(r[rest]), np.linalg.norm(r[red_fluid]))
+            assert np.linalg.norm(r[red_fluid]) > 0
+
+
 def test_colour_is_checkerboard():
     c = assemble.colour(3, 4).reshape(4, 4, 4)
     assert c[0, 0, 0] == 0 and c[0, 0, 1] == 1 and c[1, 1, 0] == 0 and c[1, 2, 3] == 0
