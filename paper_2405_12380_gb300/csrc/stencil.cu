@@ -1,10 +1,18 @@
 // Matrix-free Helmholtz operator, residual and relaxation sweeps (Eq. 1-2).
 //
-// One thread per node; blocks of 32 x 8 nodes in (x, y), one z-plane per
-// blockIdx.z.  The mask and the layer index are integers; k^2 and 1/diag come
-// from the tables in Op (or the stored field).  FP64 is the scarce pipe on
-// GB300, so per node the operator costs 2d complex adds, one scale and one
-// complex multiply-add, and the sweeps multiply by a tabulated reciprocal.
+// Blocks of 32 x 8 threads over (x, y).  Per node two byte tables (neighbour code,
+// layer index) replace the mask loads and the index arithmetic; k^2 and 1/diag
+// come from per-layer tables in Op (or the stored field).  Kernel families:
+//   k_apply_z        3D operator/residual marching in z (planes in registers,
+//                    x-neighbours by warp shuffles), complex128 and complex64
+//   k_march_c64      3D complex64 operator and damped Jacobi, two nodes per thread
+//   k_rbgs_c64       3D complex64 red-black half-sweep, two nodes per thread
+//   k_apply, k_jacobi, k_rbgs   the general forms (2D, no tables, complex128)
+//   k_apply_bicg(_df)           the BiCGStab operator with its fused reduction
+//   k_cycle_df       the red-black part of the FP64 trunk-basis hybrid cycle in
+//                    double-float arithmetic, one cooperative launch
+// FP64 is the scarce pipe on GB300 (2 instructions per clock per SM against 128
+// for FP32), so the FP64 path moves its sweeps onto FP32 pairs.
 #include <algorithm>
 #include <cstdint>
 #include <type_traits>
