@@ -54,9 +54,10 @@ typedef enum {
 
 /* dtype of the vectors passed to a call */
 enum { HELM_C128 = 0, HELM_C64 = 1 };
-/* precision mode of a handle: FP64 everywhere, or complex64 preconditioner
- * (stencil, relaxation, projection with a BF16-rounded Q) inside an FP64 outer
- * FGMRES (Arnoldi, Hessenberg/Givens, true residual in FP64). */
+/* precision mode of a handle: FP64 (see helm_precond for the double-float parts),
+ * or complex64 preconditioner (stencil, relaxation, projection with a BF16-rounded
+ * Q) inside the FP64 outer method (FGMRES: Arnoldi, Hessenberg/Givens; BiCGStab:
+ * vectors and recurrences; the true residual in FP64 for both). */
 enum { HELM_FP64 = 0, HELM_MIXED = 1 };
 /* relaxation kinds (Sec. 3.1.1: M = diag(A) -> Jacobi, lower triangle -> GS) */
 enum { HELM_RELAX_NONE = 0, HELM_JACOBI = 1, HELM_RBGS = 2 };
@@ -72,7 +73,7 @@ enum { HELM_ACT_TANH = 0 };
  * residual.  METHOD_RELAX runs that cycle as a Richardson iteration on A u = f
  * (relaxation meta-solver); FGMRES/BICGSTAB use it as a right preconditioner
  * (Krylov meta-solver).  Convergence: ||f - A x||_2 <= tol ||f||_2, true residual
- * in FP64.  `restart` is m of FGMRES(m) (<= 256).  `maxit` counts Arnoldi
+ * in FP64.  `restart` is m of FGMRES(m) (1..64).  `maxit` counts Arnoldi
  * steps / BiCGStab iterations / relaxation cycles.  conj = 1 solves with
  * conj(A) = A^H (adjoint), using the conjugated preconditioner. */
 typedef struct {
@@ -100,7 +101,9 @@ typedef struct {
     int n_prolong;       /* trunk-basis prolongations (z += Q y) */
     double restrict_ms;  /* summed CUDA-event time of the restriction kernels (profiling on) */
     double prolong_ms;   /* summed CUDA-event time of the prolongation kernels (profiling on) */
-    int n_sweep;         /* relaxation half-sweeps that read neighbours (FP64 handles, profiling on) */
+    int n_sweep;         /* relaxation launches that read neighbours: half-sweeps, or whole
+                            red-black cycles of the cooperative double-float path
+                            (FP64 handles, profiling on) */
     int n_apply;         /* operator applications of the BiCGStab loop (profiling on) */
     double sweep_ms;     /* their summed CUDA-event time */
     double apply_ms;     /* their summed CUDA-event time */
@@ -120,8 +123,10 @@ helm_status helm_destroy(helm_handle* h);
 /* stream: a cudaStream_t (NULL = legacy default stream). */
 helm_status helm_set_stream(helm_handle* h, void* stream);
 const char* helm_last_error(const helm_handle* h);
-/* on = 1: bracket every trunk-basis restriction/prolongation kernel with CUDA
- * events on the handle's stream and report their summed time in helm_stats. */
+/* on = 1: bracket every trunk-basis restriction and prolongation, every
+ * relaxation launch and every BiCGStab operator application with CUDA events on
+ * the handle's stream and report their counts and summed times in helm_stats
+ * (the event records lengthen the solve a little). */
 helm_status helm_set_profiling(helm_handle* h, int on);
 /* Grid query: N, h. */
 helm_status helm_info(const helm_handle* h, long long* N, double* hstep);
