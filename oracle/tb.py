@@ -112,8 +112,12 @@ def tb_setup(A, layers, coords, mask, p: int, Q=None, tau: float = 0.0) -> TBSet
 
 
 def tb_correct(s: TBSetup, r):
-    """M2 r = Q A_c^-1 Q^T r."""
-    return s.Q @ sla.lu_solve(s.lu, s.Q.T @ r)
+    """M2 r = Q A_c^-1 Q^T r.  Q is real, so Q^T r = Q^T Re r + i Q^T Im r and
+    Q y = Q Re y + i Q Im y: both products are taken on the two real columns."""
+    c = s.Q.T @ np.stack([r.real, r.imag], axis=1)
+    y = sla.lu_solve(s.lu, c[:, 0] + 1j * c[:, 1])
+    z = s.Q @ np.stack([y.real, y.imag], axis=1)
+    return z[:, 0] + 1j * z[:, 1]
 
 
 def mixed_setup(s: TBSetup, A) -> TBSetup:
