@@ -1,11 +1,16 @@
 #!/usr/bin/env python
 """Time-to-tolerance of the DeepONet-BiCGStab meta-solver on one GB300.
 
-Workload (scenes.BENCH_WORKLOADS["cube3d-64"]): 3D FP64 Helmholtz on 64^3 nodes,
-k = 16, 8-cell absorbing layer, centred 16^3 sound-soft cube, Gaussian source;
-trunk [3,128,128,128] (seeded), natural-order trunk basis (tau = 1e-6);
-BiCGStab right-preconditioned by the hybrid cycle (3 red-black GS sweeps, then
-the trunk-basis Galerkin correction), tolerance 1e-8 on the true residual.
+Workload (scenes.BENCH_WORKLOADS["submarine3d-128"], the mixed-precision
+configuration): 3D Helmholtz on 128^3 nodes, k = 32, 8-cell absorbing layer,
+seeded-rotation submarine scatterer, scattered-field solve for a seeded plane
+wave; seeded trunk [3,256,256,256], natural-order trunk basis (p = 256,
+tau = 1e-6); BiCGStab right-preconditioned by the hybrid cycle (3 red-black GS
+sweeps, then the trunk-basis Galerkin correction) to 1e-6 on the FP64 true
+residual.  The timed form is the mixed-precision handle (complex64 Krylov
+vectors, operator and cycle, BF16 basis, FP64 iterate and reliable updates);
+the FP64 handle solves the same inputs for comparison (`extra`), and the 64^3
+FP64 workload (cube3d-64, to 1e-8) is a second entry.
 
 One step = one complete solve from x0 = 0 (inputs resident on the device, setup
 of the trunk basis done once before the timed region).  `e2e` repeats the step
@@ -34,7 +39,7 @@ sys.path.insert(0, ROOT)
 import scenes  # noqa: E402
 
 METRIC = "time-to-1e-6 rel. residual (s) & iterations; stencil GB/s vs HBM peak, 1×GB300"
-WORKLOAD = "cube3d-64"
+WORKLOAD = "submarine3d-128"
 
 
 def parse():
@@ -147,8 +152,10 @@ def reference_arm(args):
     from oracle import assemble, krylov, tb
     A, b, _ = assemble.problem(sc)
     X = scenes.node_coords(sc.dim, sc.n)
+    t0 = time.perf_counter()
     s = tb.tb_setup(A, sc.trunk, X, sc.mask, sc.p, tau=w["tau"])
     M = tb.hybrid_preconditioner(A, s, w["relax"], w["n_r"], colours=assemble.colour(sc.dim, sc.n))
+    setup_s = time.perf_counter() - t0
     per = []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -162,44 +169,54 @@ def reference_arm(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.workload, w, sc, None),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene, seeded trunk weights)",
+        "config": workload_config(args.workload, w, sc, len(s.kept)),
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                         "sample": f"oracle DeepONet-BiCGStab, 1 iteration per step timed, scaled by the "
-                                   f"oracle's own {iters} iterations to 1e-8 (oracle/reference_counts.json); "
-                                   f"setup excluded; scipy.sparse matvecs single-threaded"},
+                         "sample": f"oracle FP64 DeepONet-BiCGStab on the same workload, one iteration per step "
+                                   f"timed ({per_iter:.3f} s/iteration), scaled by the oracle's own {iters} "
+                                   f"iterations to tol={w['tol']:g} (oracle/reference_counts.json); oracle setup "
+                                   f"({setup_s:.1f} s) excluded; scipy.sparse matvecs single-threaded"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+SCENE_TEXT = {
+    "cube3d": ("centred 16^3-node cube", "Gaussian sigma=0.04 at a seeded point", "[3,128,128,128] seeded"),
+    "submarine3d": ("submarine: ellipsoid hull 0.35/0.06/0.06, sail, four fins, seeded rotation",
+                    "plane wave in a seeded direction (scattered-field solve)", "[3,256,256,256] seeded"),
+}
+
+
 def workload_config(name, w, sc, kept):
-    return {"workload": name, "grid": f"{sc.n}^{sc.dim}", "k0": sc.k0, "layer_cells": sc.layer_cells,
-            "scatterer": "centred 16^3 cube", "source": "Gaussian sigma=0.04", "trunk": "[3,128,128,128] seeded",
-            "p": sc.p, "kept": kept, "tau": w["tau"], "method": w["method"], "relax": w["relax"],
-            "n_r": w["n_r"], "correction": w["correction"], "tol": w["tol"],
-            "l2": "256 MiB buffer written between steps (L2 is 129 MB)"}
+    scat, src, trunk = SCENE_TEXT[w["scene"]]
+    cfg = {"workload": name, "grid": f"{sc.n}^{sc.dim}", "k0": sc.k0, "layer_cells": sc.layer_cells,
+           "scatterer": scat, "source": src, "trunk": trunk,
+           "p": sc.p, "kept": kept, "tau": w["tau"], "method": w["method"], "relax": w["relax"],
+           "n_r": w["n_r"], "correction": w["correction"], "tol": w["tol"],
+           "precision": w.get("precision", "fp64"),
+           "l2": "256 MiB buffer written between steps (L2 is 129 MB)"}
+    if w["method"] == "bicgstab" and w.get("precision") == "mixed":
+        cfg["outer_method_note"] = ("BiCGStab with 3 red-black sweeps per cycle: restarted FGMRES(50) stagnates "
+                                    "near 1e-5 on this cavity with a seeded trunk")
+    return cfg
 
 
 # ------------------------------------------------------------------ GPU arm
-# the trunk-basis projection after red-black Gauss-Seidel reads the red rows only
-RED_ONLY_PROJECTION = True
-
-
 def source_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def traffic_for(kernel, k):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's source
-    file is unchanged since the capture (else None)."""
+def traffic_for(workload, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of the
+    workload, if the kernel's source file is unchanged since the capture (else None)."""
     try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic_cube3d-64.json")))
+        prof = json.load(open(os.path.join(ROOT, "profiles", f"traffic_{workload}.json")))
         e = prof["kernels"][kernel]
     except Exception:
         return None
     src = os.path.join(ROOT, "paper_2405_12380_gb300", "csrc", e["source"])
-    if e.get("sha256_16") != source_hash(src) or prof.get("k") != k:
+    if e.get("sha256_16") != source_hash(src):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -268,6 +285,49 @@ def max_over_ranks(value, world, device="cuda"):
     return float(t.item())
 
 
+def kernel_entries(w, st_prof, N, k, hbm, hbm_src, workload):
+    """Per-kernel achieved HBM bandwidth of the profiled solve: algorithmic bytes
+    per launch (per node: restriction 2k + 18 B, prolongation 2k + 16 B, red-black
+    half-sweep 13 B, operator 17 B for complex64 vectors and the BF16 basis; FP64
+    handles: FP32-pair basis 8k B per row) over the mean CUDA-event duration."""
+    mixed = w.get("precision") == "mixed"
+    out = []
+
+    def add(name, kernel, n_key, ms_key, bytes_per_launch, what):
+        n = st_prof[n_key]
+        ms = st_prof[ms_key]
+        if not n:
+            return
+        avg = ms / 1e3 / n
+        out.append({"bound": "hbm", "kernel": kernel, "what": what, "achieved": bytes_per_launch / avg / 1e9,
+                    "peak": hbm, "unit": "GB/s", "frac": bytes_per_launch / avg / 1e9 / hbm,
+                    "peak_source": hbm_src, "traffic": traffic_for(workload, kernel),
+                    "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": avg * 1e6,
+                    "launches": n, "share_of_solve": ms / st_prof["ms"],
+                    "timing": "CUDA events around every launch, one profiled solve after the timed solves"})
+
+    if mixed:
+        add("restrict", "k_restrict32", "n_restrict", "restrict_ms", (2.0 * k + 18.0) * N,
+            "c = Q^T (v - A z), BF16 Q, complex64 v and z")
+        add("prolong", "k_prolong32", "n_prolong", "prolong_ms", (2.0 * k + 16.0) * N, "z += Q y, BF16 Q")
+        add("sweep", "k_rbgs_c64", "n_sweep", "sweep_ms", 13.0 * N, "complex64 red-black half-sweep")
+        add("apply", "k_march_c64", "n_apply", "apply_ms", 17.0 * N, "complex64 y = A x")
+    else:
+        M = (N + 1) // 2
+        add("restrict", "k_project_df", "n_restrict", "restrict_ms", (8.0 * k + 16.0) * M,
+            "c = Q^T r on the red rows, FP32-pair Q")
+        add("prolong", "k_prolong_df", "n_prolong", "prolong_ms", (8.0 * k + 32.0) * N, "z += Q y, FP32-pair Q")
+        # the cooperative double-float cycle: BiCGStab input update (56 B), first
+        # red half-sweep, 2 n_r - 1 half-sweeps (24.5 B each over all nodes: f,
+        # x in/out of one colour, neighbour reads, two table bytes) and the
+        # red-row residual (40 B)
+        add("sweep", "k_cycle_df", "n_sweep", "sweep_ms", (56.0 + (2 * w["n_r"]) * 24.5 + 40.0) * N,
+            "double-float red-black cycle, one cooperative launch")
+        add("apply", "k_apply_bicg_df", "n_apply", "apply_ms", 50.0 * N,
+            "A x from FP32 pairs (16 B), y FP64 (16 B), dot operand (16 B), two table bytes")
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -278,18 +338,23 @@ def gpu_arm(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     import paper_2405_12380_gb300 as hm
-    from paper_2405_12380_gb300 import _lib as L
 
     w = scenes.BENCH_WORKLOADS[args.workload]
     sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
-    # right-hand side built on the device by the library (helm_rhs), from seeded data
-    P = hm.Problem(sc.dim, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, layer_strength=sc.layer_strength)
-    f = P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    k = P.don_load(sc.trunk, sc.p, tau=w["tau"])
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
+    prec = w.get("precision", "fp64")
+
+    def make_problem(precision):
+        P = hm.Problem(sc.dim, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells,
+                       layer_strength=sc.layer_strength, precision=precision)
+        # right-hand side built on the device by the library (helm_rhs), from seeded data
+        f = P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = P.don_load(sc.trunk, sc.p, tau=w["tau"])
+        torch.cuda.synchronize()
+        return P, f, k, time.perf_counter() - t0
+
+    P, f, k, setup_s = make_problem(prec)
     o = hm.opts(w["method"], w["relax"], w["n_r"], correction=w["correction"], tol=w["tol"],
                 restart=w["restart"], maxit=w["maxit"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -337,9 +402,36 @@ def gpu_arm(args):
         if step >= args.warmup:
             e2e.append(dt)
     e2e_s = max_over_ranks(statistics.mean(e2e), world)
-    # check the converged solution with an independent FP64 residual (device, library op)
+    # the converged solution: FP64 residual (library op) and error on the oracle's
+    # stored reference sample
     r, nrm = P.residual(f, x)
     rel_res = float(nrm.sqrt().item() / torch.linalg.vector_norm(f).item())
+    err = solution_error(args.workload, x)
+    extra = {}
+    if prec == "mixed":
+        # the same inputs on an FP64 handle (the comparison of the mixed form)
+        x64 = None
+        P64, f64, k64, setup64 = make_problem("fp64")
+        x64, _ = P64.solve(f64, None, o)
+        t64 = []
+        for _ in range(max(1, min(2, args.steps))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            x64, st64 = P64.solve(f64, None, o)
+            t64.append(st64)
+        extra["fp64_same_inputs"] = {
+            "value": statistics.mean(s["ms"] for s in t64) / 1e3, "unit": "s",
+            "iterations": statistics.mean(s["iters"] for s in t64), "status": t64[-1]["status_name"],
+            "rel_res": t64[-1]["rel_res"], "setup_s": setup64, "kept": k64,
+            "error_vs_oracle": solution_error(args.workload, x64),
+            "speedup_of_mixed": statistics.mean(s["ms"] for s in t64) / mean_ms,
+            "mixed_vs_fp64_rel_l2": float(torch.linalg.vector_norm(x - x64).item()
+                                          / torch.linalg.vector_norm(x64).item())}
+        P64.close()
+        del P64, f64, x64
+        torch.cuda.empty_cache()
+    if args.workload != "cube3d-64":
+        extra["cube3d-64"] = second_entry(hm, torch, flush)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -347,87 +439,9 @@ def gpu_arm(args):
     st0 = stats[-1]
     iters = statistics.mean(s["iters"] for s in stats)
     N = P.N
-    M = (N + 1) // 2
-    fluid = int(N - int(sc.mask.astype(bool).sum()))
     hbm = peaks().get("hbm_gbs") or 6800.0
-    hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks().get("hbm_gbs") else "fallback"
-    # FP64 issue peak: 2 FP64 instructions per clock per SM (DADD, DMUL or DFMA), 152 SMs,
-    # at the maximum SM clock seen by the clock sampler
-    sm_mhz = (clk.summary().get("sm_max_mhz") or 2070.0)
-    fp64_peak = 2 * 152 * sm_mhz * 1e6 / 1e12
-    red_only = RED_ONLY_PROJECTION and w["relax"] == "rbgs" and w["n_r"] > 0
-
-    def phase(n_key, ms_key):
-        n = st_prof[n_key]
-        ms = st_prof[ms_key]
-        return n, ms, (ms / 1e3 / n if n else None)
-
-    kernels = []
-    df_sweep = w["relax"] == "rbgs" and w["n_r"] > 0 and w["correction"] == "tb"
-    # trunk-basis projection c = Q^T r: Q as FP32 pairs (8 B per entry), r as 16 B
-    # per entry (complex128, or FP32 pairs after the double-float sweeps)
-    n_, ms_, avg = phase("n_restrict", "restrict_ms")
-    rows = M if red_only else N
-    if avg:
-        b = 8.0 * k * rows + 16.0 * rows
-        kernels.append({"bound": "hbm", "kernel": "k_project_df (Q^T r%s, FP32-pair arithmetic)" % (
-                            ", red rows" if red_only else ""),
-                        "achieved": b / avg / 1e9, "peak": hbm, "unit": "GB/s", "frac": b / avg / 1e9 / hbm,
-                        "peak_source": hbm_src, "traffic": traffic_for("k_project_df", k),
-                        "algorithmic_bytes_per_launch": b, "avg_launch_us": avg * 1e6, "launches": n_,
-                        "share_of_solve": ms_ / st_prof["ms"]})
-    # prolongation z += Q y: all of Q, z read and written
-    n_, ms_, avg = phase("n_prolong", "prolong_ms")
-    if avg:
-        b = 8.0 * k * N + 32.0 * N
-        kernels.append({"bound": "hbm", "kernel": "k_prolong_df (z += Q y, FP32-pair arithmetic)",
-                        "achieved": b / avg / 1e9, "peak": hbm, "unit": "GB/s", "frac": b / avg / 1e9 / hbm,
-                        "peak_source": hbm_src, "traffic": traffic_for("k_prolong_df", k),
-                        "algorithmic_bytes_per_launch": b, "avg_launch_us": avg * 1e6, "launches": n_,
-                        "share_of_solve": ms_ / st_prof["ms"]})
-    # relaxation.  FP64 kernels: per updated fluid node 10 DADD (neighbour sum), 2
-    # DFMA (f - h^-2 s), a complex multiply (2 DMUL + 2 DFMA) = 16 FP64 instructions
-    # per half-sweep.  The double-float cycle of the trunk-basis correction (one
-    # cooperative launch per preconditioner application): per red/black node pair a
-    # first red update (complex pair product, 50 FP32 instructions), 2 n_r - 1
-    # half-sweeps of 196 (10 pair additions of 11 instructions, 2 pair products of 7
-    # for h^-2 s, 2 pair additions for f - h^-2 s, a complex pair product of 50) and
-    # the red residual (218)
-    n_, ms_, avg = phase("n_sweep", "sweep_ms")
-    fp32_peak = 128 * 152 * sm_mhz * 1e6 / 1e12
-    if avg and df_sweep:
-        ops = (50.0 + (2 * w["n_r"] - 1) * 196.0 + 218.0) * fluid / 2
-        kernels.append({"bound": "alu", "kernel": "k_cycle_df (double-float red-black cycle, one cooperative launch)",
-                        "achieved": ops / avg / 1e12, "peak": fp32_peak, "unit": "T FP32 inst/s",
-                        "frac": ops / avg / 1e12 / fp32_peak,
-                        "peak_source": "128 FP32 instructions/clk/SM x 152 SMs x max SM clock",
-                        "traffic": traffic_for("k_cycle_df", k), "algorithmic_fp32_inst_per_launch": ops,
-                        "avg_launch_us": avg * 1e6,
-                        "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
-    elif avg:
-        ops = 16.0 * fluid / 2
-        kernels.append({"bound": "alu", "kernel": "k_%s (FP64 half-sweep)" % w["relax"],
-                        "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",
-                        "frac": ops / avg / 1e12 / fp64_peak,
-                        "peak_source": "2 FP64 instructions/clk/SM x 152 SMs x max SM clock",
-                        "traffic": None, "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
-                        "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
-    # BiCGStab operator with its fused reduction: 16 FP64 instructions for A x per
-    # fluid node plus 4 (<rhat, v>) or 6 (<t, s>, <t, t>): 21 on average; on the
-    # double-float input (trunk-basis red-black cycle) A x runs on the FP32 pipes and
-    # the FP64 part is the conversion of y (4 F2F + 2 DADD) and the dots: 11
-    n_, ms_, avg = phase("n_apply", "apply_ms")
-    if avg:
-        ops = (11.0 if df_sweep else 21.0) * fluid
-        kernels.append({"bound": "alu", "kernel": "k_apply_bicg_df (A x in double-float, FP64 y and fused dots)" if df_sweep
-                        else "k_apply_bicg (FP64 A x + fused dots)",
-                        "achieved": ops / avg / 1e12, "peak": fp64_peak, "unit": "T FP64 inst/s",
-                        "frac": ops / avg / 1e12 / fp64_peak,
-                        "peak_source": "2 FP64 instructions/clk/SM x 152 SMs x max SM clock",
-                        "traffic": traffic_for("k_apply_bicg_df" if df_sweep else "k_apply_bicg", k), "algorithmic_fp64_inst_per_launch": ops, "avg_launch_us": avg * 1e6,
-                        "launches": n_, "share_of_solve": ms_ / st_prof["ms"]})
-    for e in kernels:
-        e["timing"] = "CUDA events around every launch, one profiled solve after the timed solves"
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if peaks().get("hbm_gbs") else "fallback"
+    kernels = kernel_entries(w, st_prof, N, k, hbm, hbm_src, args.workload)
     roofline = max(kernels, key=lambda e: e["share_of_solve"]) if kernels else None
     cpu = None
     if world == 1 or args.gpus == 1:
@@ -435,8 +449,8 @@ def gpu_arm(args):
         smp = oracle_sample(w, sc, args.cpu_iters)
         cpu_value = smp["per_iter_s"] * (iters_ref or iters)
         cpu = {"value": cpu_value, "unit": "s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"oracle DeepONet-BiCGStab (scipy CSR, numpy Q), {args.cpu_iters} iterations timed "
-                         f"({smp['per_iter_s']:.3f} s/iter), scaled by "
+               "sample": f"oracle FP64 DeepONet-BiCGStab (scipy CSR, numpy Q) on the same workload, "
+                         f"{args.cpu_iters} iterations timed ({smp['per_iter_s']:.3f} s/iteration), scaled by "
                          + (f"the oracle's own {iters_ref} iterations to tol (oracle/reference_counts.json)"
                             if iters_ref else f"the GPU solve's {iters} iterations")
                          + f"; oracle setup {smp['setup_s']:.1f} s excluded; scipy.sparse single-threaded",
@@ -445,20 +459,62 @@ def gpu_arm(args):
     stencil = stencil_bench(hm, torch)
     cfg = workload_config(args.workload, w, sc, k)
     cfg.update({"iterations": iters, "rel_res": rel_res, "setup_s": setup_s, "replicas": world,
-                "solve_ms_each": solve_ms})
+                "solve_ms_each": solve_ms, "reliable_updates": "delta 0.1" if prec == "mixed" else None})
     line = {
         "metric": METRIC, "value": mean_ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene, seeded trunk weights)",
+        "vs_baseline": None, "dtype": "c64/bf16 (FP64 iterate)" if prec == "mixed" else "f64",
+        "data": "synthetic (seeded scene, seeded trunk weights)",
         "config": cfg, "iterations": iters, "status": st0["status_name"],
+        "error_vs_oracle": err,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": N * 16},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
-        "roofline": roofline, "kernels": kernels, "stencil": stencil, "cpu_baseline": cpu, "clocks": clocks,
-        "wall_s_timed_region": t_wall,
+        "roofline": roofline, "kernels": kernels, "extra": extra, "stencil": stencil, "cpu_baseline": cpu,
+        "clocks": clocks, "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def solution_error(workload, x):
+    """Relative L2 error of x on the oracle's stored reference sample (nodes drawn
+    by oracle/reference_data.py), or None if the sample is missing."""
+    try:
+        gold = np.load(os.path.join(ROOT, "tests", "golden", f"solution_{workload}.npz"))
+    except Exception:
+        return None
+    import torch
+    idx = torch.from_numpy(gold["idx"]).to(x.device)
+    xs = x[idx].cpu().numpy()
+    ref = gold["x"]
+    return {"rel_l2_on_sample": float(np.linalg.norm(xs - ref) / np.linalg.norm(ref)),
+            "sample_nodes": int(len(ref)), "oracle_rel_res": float(gold["rel_res"])}
+
+
+def second_entry(hm, torch, flush):
+    """The 64^3 FP64 workload (cube3d-64: DeepONet-BiCGStab, 3 red-black sweeps, tol
+    1e-8): mean of three solves after one warm-up."""
+    w = scenes.BENCH_WORKLOADS["cube3d-64"]
+    sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
+    P = hm.Problem(sc.dim, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, layer_strength=sc.layer_strength)
+    f = P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda())
+    k = P.don_load(sc.trunk, sc.p, tau=w["tau"])
+    o = hm.opts(w["method"], w["relax"], w["n_r"], correction=w["correction"], tol=w["tol"],
+                restart=w["restart"], maxit=w["maxit"])
+    P.solve(f, None, o)
+    sts = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        x, st = P.solve(f, None, o)
+        sts.append(st)
+    out = {"value": statistics.mean(s["ms"] for s in sts) / 1e3, "unit": "s", "tol": w["tol"],
+           "precision": "fp64", "iterations": statistics.mean(s["iters"] for s in sts), "kept": k,
+           "status": sts[-1]["status_name"], "rel_res": sts[-1]["rel_res"],
+           "error_vs_oracle": solution_error("cube3d-64", x), "config": workload_config("cube3d-64", w, sc, k)}
+    P.close()
+    return out
 
 
 def main():

@@ -20,8 +20,8 @@
  *    host pointers.  Complex data is interleaved (re, im): complex128 = 2 doubles,
  *    complex64 = 2 floats.  Vectors have N = n^d entries.
  *  - Calls are asynchronous on the handle's stream (helm_set_stream), except
- *    don_load, helm_solve and helm_solve_host, which synchronise and return
- *    statistics.
+ *    don_load, helm_precond, helm_solve and helm_solve_host, which synchronise
+ *    (the last two return statistics).
  *  - The handle owns its workspace (trunk basis, coarse operator, Krylov
  *    vectors) and frees it in helm_destroy.  It copies the mask and k^2 field.
  *  - No CPU fallback: without an sm_103a device helm_create returns HELM_NO_DEVICE.
@@ -49,7 +49,8 @@ typedef enum {
     HELM_SINGULAR_COARSE = 7,  /* zero pivot in the coarse operator A_c */
     HELM_NOT_READY = 8,        /* correction requested before don_load */
     HELM_OUT_OF_MEMORY = 9,
-    HELM_SCRATCH_TOO_SMALL = 10  /* problem exceeds the fixed scratch of helm_residual_noalloc */
+    HELM_SCRATCH_TOO_SMALL = 10, /* problem exceeds the fixed scratch of helm_residual_noalloc */
+    HELM_TIMEOUT = 11          /* a bounded in-kernel wait (grid barrier) gave up */
 } helm_status;
 
 /* dtype of the vectors passed to a call */
@@ -59,8 +60,10 @@ enum { HELM_C128 = 0, HELM_C64 = 1 };
  * Q) inside the FP64 outer method (FGMRES: Arnoldi, Hessenberg/Givens; BiCGStab:
  * vectors and recurrences; the true residual in FP64 for both). */
 enum { HELM_FP64 = 0, HELM_MIXED = 1 };
-/* relaxation kinds (Sec. 3.1.1: M = diag(A) -> Jacobi, lower triangle -> GS) */
-enum { HELM_RELAX_NONE = 0, HELM_JACOBI = 1, HELM_RBGS = 2 };
+/* relaxation kinds (Sec. 3.1.1: M = diag(A) -> Jacobi, lower triangle -> Gauss-Seidel,
+ * SOR and SSOR; Gauss-Seidel-type sweeps in red-black order).  HELM_MG (Sec. 4.3):
+ * a geometric multigrid V-cycle with damped-Jacobi smoothing (helm_mg_setup). */
+enum { HELM_RELAX_NONE = 0, HELM_JACOBI = 1, HELM_RBGS = 2, HELM_SOR = 3, HELM_SSOR = 4, HELM_MG = 5 };
 /* second-stage correction M2 (Eq. 3): none, trunk-basis Galerkin (App. C) */
 enum { HELM_CORR_NONE = 0, HELM_CORR_TB = 1, HELM_CORR_NONLINEAR = 2 };
 /* outer methods */
@@ -128,6 +131,31 @@ const char* helm_last_error(const helm_handle* h);
  * the handle's stream and report their counts and summed times in helm_stats
  * (the event records lengthen the solve a little). */
 helm_status helm_set_profiling(helm_handle* h, int on);
+/* Bounded waits of the cooperative red-black cycle (one launch whose phases are
+ * separated by grid barriers, one block per SM, co-residency checked by an
+ * occupancy query before the launch): a block polls the barrier at most `polls`
+ * times (> 0; default 2^20, about a second) before it gives up, records the
+ * timeout and goes on; the call then returns HELM_TIMEOUT and resets the barrier.
+ * extra_arrivals > 0 makes every barrier wait for that many blocks more than the
+ * launch has, so that each wait runs out: host-side fault injection for tests of
+ * the timeout path (0 for normal use).  helm_precond synchronises and checks too. */
+helm_status helm_set_wait_limit(helm_handle* h, unsigned polls, unsigned extra_arrivals);
+
+/* Multigrid hierarchy for HELM_MG (Sec. 4.3, DeepONet-MG-Krylov): `levels` grids in
+ * all (1..8), each coarser one by vertex coarsening n -> (n + 1) / 2 (so n must
+ * stay odd and >= 5 down to the coarsest), coarse node I at fine node 2I; the mask
+ * and k^2 of a coarse node are those of fine node 2I, and the operator is the
+ * stencil of Eq. 1 with the coarse h.  Restriction: full weighting (the transpose
+ * of (bi/tri)linear interpolation over 2^d); prolongation: (bi/tri)linear
+ * interpolation, added on unmasked fine nodes.  The V-cycle (HELM_MG with
+ * opts.n_r = m, opts.omega the Jacobi damping): smoother from zero, coarse-grid
+ * correction, smoother; the smoother is m damped-Jacobi sweeps, the trunk-basis
+ * correction, m sweeps (the 2-1-2 strategy for m = 2) on the finest level when
+ * opts.correction = HELM_CORR_TB, else 2 m + 1 sweeps; the coarsest level only
+ * smooths from zero.  The cycle is linear, so it preconditions FGMRES and
+ * BiCGStab.  FP64 handles; synchronises. */
+helm_status helm_mg_setup(helm_handle* h, int levels);
+
 /* Grid query: N, h. */
 helm_status helm_info(const helm_handle* h, long long* N, double* hstep);
 
@@ -202,8 +230,9 @@ helm_status helm_precond(helm_handle* h, const helm_solve_opts* opts, const void
  * and the final rel_res use the FP64 residual.  BiCGStab with the double-float
  * cycle (see helm_precond) applies A to the cycle's double-float output and
  * rounds to FP64 once; its Krylov vectors, dots and recurrences are FP64.
- * HELM_CUDA_ERROR also reports a bounded in-kernel wait that gave up (never
- * expected; the message says which). */
+ * HELM_TIMEOUT reports a bounded in-kernel wait of the cooperative red-black
+ * cycle that gave up (never expected with the default limit; see
+ * helm_set_wait_limit); the barrier state is reset, so the next call starts clean. */
 helm_status helm_solve(helm_handle* h, const helm_solve_opts* opts, const void* f, void* x,
                        helm_stats* stats, double* res_hist, int hist_len);
 
@@ -257,6 +286,17 @@ helm_status nn_rel_l2(int B, int P2, const float* pred, const float* target, flo
 helm_status nn_gather(int rows, int cols, const float* src, long long lds, const int* row_idx,
                       const int* col_idx, float* dst, void* stream);
 
+/* The same product on the tensor cores (tcgen05, sm_103a): op(A) and op(B) are
+ * rounded to BF16 (nearest even) and multiplied with FP32 accumulation, C = alpha
+ * op(A) op(B) + beta C in FP32 (dense layers of the DeepONet in mixed-precision
+ * training, App. B).  Uses a per-device BF16 workspace grown on demand (held until
+ * exit).  Asynchronous on `stream`; every wait inside the kernel is bounded, and a
+ * wait that ran out (never expected) is reported, and cleared, by
+ * nn_gemm_bf16_status (*timed_out = 1; the results since then are invalid). */
+helm_status nn_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, const float* A, int lda,
+                         const float* B, int ldb, float beta, float* C, int ldc, void* stream);
+helm_status nn_gemm_bf16_status(int* timed_out);
+
 /* ---- batched solves (many independent problems, one launch per phase) ----
  * The problems are existing HELM_MIXED handles with a loaded trunk basis; their
  * vectors are packed one after another and every phase of FGMRES runs as one
@@ -291,12 +331,13 @@ helm_status helm_batch_solve(helm_batch* b, const helm_solve_opts* opts, const d
  *    with HELM_SCRATCH_TOO_SMALL.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  *  - The first call on a device looks up the array's device address (once per
- *    device, with that device current); make that first call before any stream
- *    capture.
+ *    device, with that device current).
  *  - Synchronises `stream` (a cudaStream_t, NULL = legacy default) once to check
- *    that the outer ring is masked (HELM_BAD_ARG otherwise).
- *  - Every call shares the one array, which keeps the last call's partial sums:
- *    calls that overlap on the GPU (other streams, other host threads) race. */
+ *    that the outer ring is masked (HELM_BAD_ARG otherwise), so no call can be
+ *    made while that stream is being captured into a CUDA graph.
+ *  - Every call shares the scratch array and the ring-check flag beside it (both
+ *    keep the last call's contents): calls that overlap on the GPU (other
+ *    streams, other host threads) race on both. */
 helm_status helm_residual_noalloc(int dim, int n, double k0, int layer_cells, double layer_strength,
                                   const uint8_t* mask, const double* k2, const double* f,
                                   const double* x, double* r, double* norm2, int conj, void* stream);

@@ -13,13 +13,13 @@ LIB_PATH = os.path.join(HERE, "libhelm.so")
 
 HELM_OK, HELM_BAD_ARG, HELM_NO_DEVICE, HELM_CUDA_ERROR = 0, 1, 2, 3
 HELM_NOT_CONVERGED, HELM_DIVERGED, HELM_BREAKDOWN, HELM_SINGULAR_COARSE = 4, 5, 6, 7
-HELM_NOT_READY, HELM_OUT_OF_MEMORY, HELM_SCRATCH_TOO_SMALL = 8, 9, 10
+HELM_NOT_READY, HELM_OUT_OF_MEMORY, HELM_SCRATCH_TOO_SMALL, HELM_TIMEOUT = 8, 9, 10, 11
 STATUS_NAMES = {0: "ok", 1: "bad_arg", 2: "no_device", 3: "cuda_error", 4: "not_converged",
                 5: "diverged", 6: "breakdown", 7: "singular_coarse", 8: "not_ready", 9: "out_of_memory",
-                10: "scratch_too_small"}
+                10: "scratch_too_small", 11: "timeout"}
 HELM_C128, HELM_C64 = 0, 1
 HELM_FP64, HELM_MIXED = 0, 1
-HELM_RELAX_NONE, HELM_JACOBI, HELM_RBGS = 0, 1, 2
+HELM_RELAX_NONE, HELM_JACOBI, HELM_RBGS, HELM_SOR, HELM_SSOR, HELM_MG = 0, 1, 2, 3, 4, 5
 HELM_CORR_NONE, HELM_CORR_TB, HELM_CORR_NONLINEAR = 0, 1, 2
 HELM_METHOD_RELAX, HELM_METHOD_FGMRES, HELM_METHOD_BICGSTAB = 0, 1, 2
 HELM_ACT_TANH = 0
@@ -51,6 +51,8 @@ SIGNATURES = {
     "helm_set_stream": (i32, [H, vp]),
     "helm_last_error": (C.c_char_p, [H]),
     "helm_set_profiling": (i32, [H, i32]),
+    "helm_set_wait_limit": (i32, [H, C.c_uint, C.c_uint]),
+    "helm_mg_setup": (i32, [H, i32]),
     "helm_info": (i32, [H, C.POINTER(i64), C.POINTER(f64)]),
     "helm_layer_k2": (i32, [H, vp, vp]),
     "helm_rhs": (i32, [H, vp, vp, vp]),
@@ -73,6 +75,8 @@ SIGNATURES = {
     "helm_set_k2": (i32, [H, vp]),
     "don_load_branch": (i32, [H, vp, C.POINTER(i32), i32]),
     "nn_gemm": (i32, [i32, i32, i32, i32, i32, C.c_float, vp, i32, vp, i32, C.c_float, vp, i32, vp]),
+    "nn_gemm_bf16": (i32, [i32, i32, i32, i32, i32, C.c_float, vp, i32, vp, i32, C.c_float, vp, i32, vp]),
+    "nn_gemm_bf16_status": (i32, [C.POINTER(i32)]),
     "nn_bias_act": (i32, [i32, i32, vp, vp, i32, vp]),
     "nn_act_backward": (i32, [i64, vp, vp, i32, vp]),
     "nn_bias_grad": (i32, [i32, i32, vp, vp, vp]),

@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
-SOURCES = ["stencil.cu", "blas.cu", "tb.cu", "adjoint.cu", "nn.cu", "batch.cu", "helm_api.cu", "noalloc.cu"]
+SOURCES = ["stencil.cu", "blas.cu", "bicg32.cu", "tb.cu", "adjoint.cu", "nn.cu", "batch.cu", "helm_api.cu", "noalloc.cu",
+           "mg.cu", "gemm_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -21,9 +21,11 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
+#include "bicg.cuh"
 #include "helm_internal.cuh"
 
 using namespace helm;
@@ -48,7 +50,8 @@ struct BProb {
     const double* im;                   // Im k^2 by layer index (device, kMaxLayer)
     const float* imf;
     const float2* invdf;                // 1/diag by layer index, complex64 (device, kMaxLayer)
-    const __nv_bfloat16* Qbf;           // k x N
+    const __nv_bfloat16* Qbf;           // k columns of stride ldq
+    long long ldq;
     const double2* Ainv;                // k x k
     const double2* k2;                  // optional field (FP64) / k2f (FP32) and inverse diagonal
     const float2* k2f;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(BT) kb_project32(const BProb* __restrict__ pro
         for (int q = threadIdx.x; q < rows; q += BT) rs[q] = P.mask[T.first + q] ? make_float2(0.f, 0.f) : r[P.off + T.first + q];
         __syncthreads();
         for (int j = warp; j < P.k; j += BT / 32) {
-            const __nv_bfloat16* Qj = P.Qbf + (long long)j * P.N + T.first;
+            const __nv_bfloat16* Qj = P.Qbf + (long long)j * P.ldq + T.first;
             float ax = 0.f, ay = 0.f;
             for (int q = lane; q < rows; q += 32) {
                 const float qv = __bfloat162float(Qj[q]);
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(BT) kb_prolong32(const BProb* __restrict__ pro
             if (l >= P.N) break;
             float sx = 0.f, sy = 0.f;
             for (int j = 0; j < P.k; ++j) {
-                const float qv = __bfloat162float(P.Qbf[(long long)j * P.N + l]);
+                const float qv = __bfloat162float(P.Qbf[(long long)j * P.ldq + l]);
                 sx = fmaf(qv, ys[j].x, sx);
                 sy = fmaf(qv, ys[j].y, sy);
             }
@@ -599,6 +602,369 @@ __global__ void kb_init_g(int nprob, int m, double2* __restrict__ g, const doubl
         g[(long long)b * (m + 1) + i] = make_double2(i == 0 ? sqrt(beta2[b]) : 0.0, 0);
 }
 
+// ------------------------------------------------- batched complex64 BiCGStab
+// The BiCGStab of the single-problem mixed handles (complex64 vectors, operator
+// and hybrid cycle; FP64 iterate with reliable updates) for all problems at once.
+// Per-problem scalars are the slots of helm_internal.cuh at sc + b * S_NSLOTS; the
+// control state of a problem is a BState; every decision (reliable update,
+// convergence, restart after a breakdown, retirement) is taken on the device by
+// the per-problem finishing kernels, which also keep the active mask, so one
+// captured iteration is replayed without the host.
+struct BState {
+    double tol_abs;     // tol ||f_b||
+    double bnorm;       // ||f_b||
+    double maxrr;       // largest recursive ||r|| since the last reliable update
+    double rel_res;     // last true relative residual
+    int iters, maxit;
+    double last_true;   // true ||r|| at the last reliable update
+    int ru;             // 0; 1 reliable update; 2 update and restart (breakdown); 3 final update (maxit);
+                        // 4 reset: the increment is dropped and the method restarts (runaway growth)
+    int status;         // HELM_NOT_CONVERGED while running
+    int since_start;    // iterations since the last (re)start
+    int restarts;
+};
+
+// recipes of kb32_fin
+enum { BF_ALPHA = 0, BF_SNORM, BF_OMEGA, BF_XR, BF_RU, BF_INIT };
+// growth of the recursive residual over the last true one that counts as a runaway
+constexpr double kRunaway = 1e3;
+
+__device__ __forceinline__ double2* sc_of(double2* sc, int b) { return sc + (long long)b * S_NSLOTS; }
+__device__ __forceinline__ bool b_skip(const double2* scb) { return scb[S_STOP].x != 0.0; }
+
+// per tile: the vectors of a BiCGStab phase and its partials (up to 3 doubles per tile)
+__device__ __forceinline__ void tile_reduce3(double a0, double a1, double a2, double* part, int t) {
+    __shared__ double red[3][BT / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a0;
+        red[1][threadIdx.x >> 5] = a1;
+        red[2][threadIdx.x >> 5] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int w = 0; w < BT / 32; ++w) {
+            s0 += red[0][w];
+            s1 += red[1][w];
+            s2 += red[2][w];
+        }
+        part[3 * (long long)t] = s0;
+        part[3 * (long long)t + 1] = s1;
+        part[3 * (long long)t + 2] = s2;
+    }
+}
+
+// p = r + beta (p - omega v)
+__global__ void __launch_bounds__(BT) kb32_p(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
+                                             int tile_rows, const float2* __restrict__ r, const float2* __restrict__ v,
+                                             float2* __restrict__ p, const double2* __restrict__ sc,
+                                             const int* __restrict__ active) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        const double2* scb = sc + (long long)T.prob * S_NSLOTS;
+        if (!active[T.prob] || b_skip(scb)) continue;
+        const BProb& P = probs[T.prob];
+        const float2 beta = make_float2((float)scb[S_BETA].x, (float)scb[S_BETA].y);
+        const float2 om = make_float2((float)scb[S_OMEGA].x, (float)scb[S_OMEGA].y);
+        for (int rr = threadIdx.x; rr < tile_rows; rr += BT) {
+            const long long l = T.first + rr;
+            if (l >= P.N) break;
+            const long long g = P.off + l;
+            p[g] = cadd(r[g], cmul(beta, csub(p[g], cmul(om, v[g]))));
+        }
+    }
+}
+
+// partials of <a, b> (conj(a) b) per tile
+__global__ void __launch_bounds__(BT) kb32_dot(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
+                                               int tile_rows, const float2* __restrict__ a, const float2* __restrict__ b,
+                                               double* __restrict__ part, const double2* __restrict__ sc,
+                                               const int* __restrict__ active) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        const double2* scb = sc + (long long)T.prob * S_NSLOTS;
+        float re = 0.f, im = 0.f;
+        if (active[T.prob] && !b_skip(scb)) {
+            const BProb& P = probs[T.prob];
+            for (int rr = threadIdx.x; rr < tile_rows; rr += BT) {
+                const long long l = T.first + rr;
+                if (l >= P.N) break;
+                const float2 x = a[P.off + l], y = b[P.off + l];
+                re = fmaf(x.x, y.x, fmaf(x.y, y.y, re));
+                im = fmaf(x.x, y.y, fmaf(-x.y, y.x, im));
+            }
+        }
+        tile_reduce3(re, im, 0.0, part, t);
+    }
+}
+
+// s = r - alpha v, partials of ||s||^2
+__global__ void __launch_bounds__(BT) kb32_s(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
+                                             int tile_rows, const float2* __restrict__ r, const float2* __restrict__ v,
+                                             float2* __restrict__ sv, double* __restrict__ part,
+                                             const double2* __restrict__ sc, const int* __restrict__ active) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        const double2* scb = sc + (long long)T.prob * S_NSLOTS;
+        float acc = 0.f;
+        if (active[T.prob] && !b_skip(scb)) {
+            const BProb& P = probs[T.prob];
+            const float2 al = make_float2((float)scb[S_ALPHA].x, (float)scb[S_ALPHA].y);
+            for (int rr = threadIdx.x; rr < tile_rows; rr += BT) {
+                const long long l = T.first + rr;
+                if (l >= P.N) break;
+                const long long g = P.off + l;
+                const float2 q = csub(r[g], cmul(al, v[g]));
+                sv[g] = q;
+                acc = fmaf(q.x, q.x, fmaf(q.y, q.y, acc));
+            }
+        }
+        tile_reduce3(acc, 0.0, 0.0, part, t);
+    }
+}
+
+// partials of <t, s> and <t, t>
+__global__ void __launch_bounds__(BT) kb32_ts(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
+                                              int tile_rows, const float2* __restrict__ tv, const float2* __restrict__ sv,
+                                              double* __restrict__ part, const double2* __restrict__ sc,
+                                              const int* __restrict__ active) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        const double2* scb = sc + (long long)T.prob * S_NSLOTS;
+        float re = 0.f, im = 0.f, tt = 0.f;
+        if (active[T.prob] && !b_skip(scb)) {
+            const BProb& P = probs[T.prob];
+            for (int rr = threadIdx.x; rr < tile_rows; rr += BT) {
+                const long long l = T.first + rr;
+                if (l >= P.N) break;
+                const float2 x = tv[P.off + l], y = sv[P.off + l];
+                re = fmaf(x.x, y.x, fmaf(x.y, y.y, re));
+                im = fmaf(x.x, y.y, fmaf(-x.y, y.x, im));
+                tt = fmaf(x.x, x.x, fmaf(x.y, x.y, tt));
+            }
+        }
+        tile_reduce3(re, im, tt, part, t);
+    }
+}
+
+// xl += alpha phat + omega shat; r = s - omega t; partials of ||r||^2 and <rhat, r>
+__global__ void __launch_bounds__(BT) kb32_xr(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
+                                              int tile_rows, float2* __restrict__ xl, float2* __restrict__ r,
+                                              const float2* __restrict__ ph, const float2* __restrict__ sh,
+                                              const float2* __restrict__ sv, const float2* __restrict__ tv,
+                                              const float2* __restrict__ rh, double* __restrict__ part,
+                                              const double2* __restrict__ sc, const int* __restrict__ active) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        const double2* scb = sc + (long long)T.prob * S_NSLOTS;
+        float rn = 0.f, re = 0.f, im = 0.f;
+        if (active[T.prob] && !b_skip(scb) && scb[S_FLAGS].y != 1.0) {
+            const BProb& P = probs[T.prob];
+            const float2 al = make_float2((float)scb[S_ALPHA].x, (float)scb[S_ALPHA].y);
+            const float2 om = make_float2((float)scb[S_OMEGA].x, (float)scb[S_OMEGA].y);
+            for (int rr = threadIdx.x; rr < tile_rows; rr += BT) {
+                const long long l = T.first + rr;
+                if (l >= P.N) break;
+                const long long g = P.off + l;
+                xl[g] = cadd(cadd(xl[g], cmul(al, ph[g])), cmul(om, sh[g]));
+                const float2 q = csub(sv[g], cmul(om, tv[g]));
+                r[g] = q;
+                rn = fmaf(q.x, q.x, fmaf(q.y, q.y, rn));
+                const float2 h = rh[g];
+                re = fmaf(h.x, q.x, fmaf(h.y, q.y, re));
+                im = fmaf(h.x, q.y, fmaf(-h.y, q.x, im));
+            }
+        }
+        tile_reduce3(rn, re, im, part, t);
+    }
+}
+
+// reliable update, first half, for problems with st.ru != 0: x += xl, xl = 0 (a reset,
+// ru = 4, drops the increment: xl = 0 with x unchanged)
+__global__ void __launch_bounds__(BT) kb32_fold(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
+                                                int tile_rows, double2* __restrict__ x, float2* __restrict__ xl,
+                                                const int* __restrict__ ruflag) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        if (!ruflag[T.prob]) continue;
+        const BProb& P = probs[T.prob];
+        for (int rr = threadIdx.x; rr < tile_rows; rr += BT) {
+            const long long l = T.first + rr;
+            if (l >= P.N) break;
+            const long long g = P.off + l;
+            const float2 d = xl[g];
+            if (ruflag[T.prob] != 4) x[g] = make_double2(x[g].x + (double)d.x, x[g].y + (double)d.y);
+            xl[g] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// reliable update, second half: r = complex64(r64) (restart: rhat = r, p = v = 0);
+// partials of <rhat, r>
+__global__ void __launch_bounds__(BT) kb32_replace(const BProb* __restrict__ probs, const Tile* __restrict__ tiles,
+                                                   int ntiles, int tile_rows, const double2* __restrict__ r64,
+                                                   float2* __restrict__ r, float2* __restrict__ rh,
+                                                   float2* __restrict__ p, float2* __restrict__ v,
+                                                   double* __restrict__ part, const int* __restrict__ ruflag) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        const int ru = ruflag[T.prob];
+        float re = 0.f, im = 0.f;
+        if (ru) {
+            const BProb& P = probs[T.prob];
+            for (int rr = threadIdx.x; rr < tile_rows; rr += BT) {
+                const long long l = T.first + rr;
+                if (l >= P.N) break;
+                const long long g = P.off + l;
+                const float2 q = make_float2((float)r64[g].x, (float)r64[g].y);
+                r[g] = q;
+                float2 h;
+                if (ru == 2 || ru == 4) {
+                    rh[g] = q;
+                    p[g] = make_float2(0.f, 0.f);
+                    v[g] = make_float2(0.f, 0.f);
+                    h = q;
+                } else {
+                    h = rh[g];
+                }
+                re = fmaf(h.x, q.x, fmaf(h.y, q.y, re));
+                im = fmaf(h.x, q.y, fmaf(-h.y, q.x, im));
+            }
+        }
+        tile_reduce3(re, im, 0.0, part, t);
+    }
+}
+
+// One block per problem: the problem's tile partials summed in a fixed order, then
+// the recurrence of `recipe` on its scalars and its control state.  `nrm` holds the
+// true ||r||^2 of BF_RU / BF_INIT (from kb_resid64 + kb_seg_sum); ruflag mirrors
+// BState.ru for the tile kernels and active the running problems.
+__global__ void __launch_bounds__(64) kb32_fin(int recipe, const BProb* __restrict__ probs, int nprob,
+                                               const double* __restrict__ part, double2* __restrict__ sc,
+                                               BState* __restrict__ st, int* __restrict__ active,
+                                               int* __restrict__ ruflag, const double* __restrict__ nrm, double delta) {
+    const int b = blockIdx.x;
+    if (b >= nprob) return;
+    const BProb& P = probs[b];
+    __shared__ double red[3][2];
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int q = threadIdx.x; q < P.ntiles; q += 64) {
+        const long long t = P.tile0 + q;
+        a0 += part[3 * t];
+        a1 += part[3 * t + 1];
+        a2 += part[3 * t + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a0;
+        red[1][threadIdx.x >> 5] = a1;
+        red[2][threadIdx.x >> 5] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double t0 = red[0][0] + red[0][1], t1 = red[1][0] + red[1][1], t2 = red[2][0] + red[2][1];
+    double2* scb = sc + (long long)b * S_NSLOTS;
+    BState& S = st[b];
+    if (recipe == BF_INIT) {
+        // initial true residual (x0 given): converged already, or a fresh start
+        S.rel_res = S.bnorm > 0 ? sqrt(nrm[b]) / S.bnorm : 0.0;
+        if (S.bnorm == 0 || sqrt(nrm[b]) <= S.tol_abs) {
+            S.status = HELM_OK;
+            active[b] = 0;
+        } else {
+            scb[S_RHO_OLD] = make_double2(1, 0);
+            scb[S_ALPHA] = make_double2(1, 0);
+            scb[S_OMEGA] = make_double2(1, 0);
+            scb[S_FLAGS] = make_double2(0, 0);
+            scb[S_STOP] = make_double2(0, 0);
+            bicg_rho_beta(scb, make_double2(t0, t1), 1.0);
+            S.maxrr = sqrt(nrm[b]);
+            S.last_true = S.maxrr;
+            S.since_start = 0;
+        }
+        ruflag[b] = 0;
+        S.ru = 0;
+        return;
+    }
+    if (recipe == BF_RU) {
+        if (!S.ru) return;
+        const double rt = sqrt(nrm[b]);
+        S.rel_res = rt / S.bnorm;
+        const int ru = S.ru;
+        S.ru = 0;
+        ruflag[b] = 0;
+        if (rt <= S.tol_abs) {
+            S.status = HELM_OK;
+            active[b] = 0;
+        } else if (!isfinite(rt)) {
+            S.status = HELM_DIVERGED;
+            active[b] = 0;
+        } else if (ru == 3) {
+            S.status = HELM_NOT_CONVERGED;
+            active[b] = 0;
+        } else if (ru == 2 && S.since_start <= 1) {
+            S.status = HELM_BREAKDOWN;
+            active[b] = 0;
+        } else {
+            if (ru == 2 || ru == 4) {
+                scb[S_RHO_OLD] = make_double2(1, 0);
+                scb[S_ALPHA] = make_double2(1, 0);
+                scb[S_OMEGA] = make_double2(1, 0);
+                S.since_start = 0;
+                ++S.restarts;
+            }
+            scb[S_FLAGS] = make_double2(0, 0);
+            scb[S_STOP] = make_double2(0, 0);
+            bicg_rho_beta(scb, make_double2(t0, t1), 1.0);
+            S.maxrr = rt;
+            S.last_true = rt;
+        }
+        return;
+    }
+    if (!active[b] || b_skip(scb)) return;
+    if (recipe == BF_ALPHA) {
+        bicg_alpha(scb, make_double2(t0, t1));
+    } else if (recipe == BF_SNORM) {
+        bicg_snorm(scb, t0, S.tol_abs);
+    } else if (recipe == BF_OMEGA) {
+        bicg_omega(scb, make_double2(t0, t1), t2);
+    } else {   // BF_XR
+        const bool skip = scb[S_FLAGS].y == 1.0;
+        if (!skip) {
+            bicg_rnorm(scb, t0);
+            bicg_rho_beta(scb, make_double2(t1, t2), 3.0);
+        }
+        ++S.iters;
+        ++S.since_start;
+        const double rn = sqrt(scb[S_RN2].x);
+        const bool brk = scb[S_FLAGS].y != 0.0;
+        if (brk || !isfinite(rn) || rn <= S.tol_abs) {
+            scb[S_STOP].x = 1.0;
+            S.ru = brk ? 2 : (!isfinite(rn) ? 4 : 1);
+        } else if (rn > kRunaway * S.last_true) {
+            // the complex64 recursion ran away: drop the increment, restart from x
+            scb[S_STOP].x = 1.0;
+            S.ru = 4;
+        } else if (rn < delta * S.maxrr) {
+            S.ru = 1;
+        } else if (rn > S.maxrr) {
+            S.maxrr = rn;
+        }
+        if (S.iters >= S.maxit && S.ru == 0) S.ru = 3;
+        ruflag[b] = S.ru;
+    }
+}
+
 __global__ void kb_cvt64to32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
     for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < n; l += (long long)gridDim.x * blockDim.x)
         b[l] = make_float2((float)a[l].x, (float)a[l].y);
@@ -633,6 +999,15 @@ struct helm_batch {
     double2 *hpart = nullptr, *H = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h2 = nullptr;
     double *cs = nullptr, *tpart = nullptr, *nrm = nullptr, *est = nullptr, *hpin = nullptr;
     int m_alloc = 0;
+    // batched complex64 BiCGStab: r, rhat, p, v, s, t, phat, shat, xl (complex64), the
+    // FP64 residual, per-problem scalars and control states, tile partials (3 each)
+    float2* b32 = nullptr;
+    double2* r64 = nullptr;
+    double2* bsc = nullptr;
+    BState* bst = nullptr;
+    BState* hbst = nullptr;             // pinned mirror
+    int* ruflag = nullptr;
+    double* part3 = nullptr;
     cudaStream_t cstream = nullptr;     // private non-blocking stream of the solves (graph capture)
     cudaEvent_t join = nullptr;
     std::string err;
@@ -698,6 +1073,245 @@ helm_status ensure_batch_krylov(helm_batch* B, int m) {
     return HELM_OK;
 }
 
+// ---------------------------------------------- batched complex64 BiCGStab
+constexpr double kBatchReliableDelta = 0.1;
+
+helm_status ensure_batch_b32(helm_batch* B) {
+    if (B->b32) return HELM_OK;
+    helm_status st;
+    const int P = B->nprob;
+    if ((st = balloc(B, &B->b32, (size_t)9 * B->NT)) != HELM_OK) return st;
+    if ((st = balloc(B, &B->r64, (size_t)B->NT)) != HELM_OK) return st;
+    if ((st = balloc(B, &B->bsc, (size_t)P * S_NSLOTS)) != HELM_OK) return st;
+    if ((st = balloc(B, &B->bst, (size_t)P)) != HELM_OK) return st;
+    if ((st = balloc(B, &B->ruflag, (size_t)P)) != HELM_OK) return st;
+    if (cudaMallocHost((void**)&B->hbst, sizeof(BState) * P) != cudaSuccess) return HELM_OUT_OF_MEMORY;
+    return HELM_OK;
+}
+
+// the hybrid cycle z = M(v) of every active problem (complex64, each problem's BF16 basis)
+void batch_precond32(helm_batch* B, const helm_solve_opts* o, const float2* v, float2* z, cudaStream_t s,
+                     long long& launches) {
+    const int G = B->grid, NTL = B->ntiles, TR = B->tile_rows, P = B->nprob;
+    const int nr = o->relax == HELM_RELAX_NONE ? 0 : o->n_r;
+    if (nr == 0) {
+        cudaMemsetAsync(z, 0, sizeof(float2) * B->NT, s);
+    } else if (o->relax == HELM_RBGS) {
+        for (int q = 0; q < nr; ++q) {
+            kb_rbgs32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, 0, q == 0, v, z, B->active);
+            kb_rbgs32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, 1, 0, v, z, B->active);
+        }
+        launches += 2 * nr;
+    } else {
+        float2* a = (nr % 2 == 1) ? z : B->z32tmp;
+        float2* bb = (nr % 2 == 1) ? B->z32tmp : z;
+        kb_jacobi32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, (float)o->omega, v, nullptr, a, B->active);
+        for (int q = 1; q < nr; ++q) {
+            kb_jacobi32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, (float)o->omega, v, a, bb, B->active);
+            std::swap(a, bb);
+        }
+        launches += nr;
+    }
+    if (o->correction == HELM_CORR_TB) {
+        const size_t smem32 = (size_t)TR * sizeof(float2);
+        kb_resid32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, v, z, B->r32, B->active);
+        kb_project32<<<G, BT, smem32, s>>>(B->probs, B->tiles, NTL, TR, B->r32, B->pp32, B->kmax, B->active);
+        kb_coarse<<<P, 128, 0, s>>>(B->probs, P, B->pp32, B->kmax, B->y32, B->active);
+        kb_prolong32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->y32, B->kmax, z, B->active);
+        launches += 4;
+    }
+}
+
+// BiCGStab with the hybrid-cycle preconditioner on every problem at once, in lockstep
+// (helm_batch_solve with HELM_METHOD_BICGSTAB): one iteration of all problems, with the
+// per-problem reliable updates, is one captured CUDA graph; the host replays it and
+// polls the problems' states a few iterations behind.
+helm_status batch_bicgstab(helm_batch* B, const helm_solve_opts* o, const double* const* f, double* const* x,
+                           helm_stats* stats) {
+    if (o->conj || o->correction == HELM_CORR_NONLINEAR || (o->relax != HELM_RELAX_NONE && o->relax != HELM_JACOBI &&
+                                                            o->relax != HELM_RBGS) || o->maxit < 0 || !(o->tol >= 0))
+        return HELM_BAD_ARG;
+    helm_status st0 = ensure_batch_b32(B);
+    if (st0 != HELM_OK) return st0;
+    if (!B->part3 && balloc(B, &B->part3, (size_t)3 * B->ntiles) != HELM_OK) return HELM_OUT_OF_MEMORY;
+    if (!B->cstream) {
+        if (cudaStreamCreateWithFlags(&B->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming) != cudaSuccess)
+            return HELM_CUDA_ERROR;
+    }
+    cudaStream_t s = B->cstream;
+    if (cudaEventRecord(B->join, B->stream) != cudaSuccess || cudaStreamWaitEvent(s, B->join, 0) != cudaSuccess)
+        return HELM_CUDA_ERROR;
+    const int P = B->nprob, G = B->grid, NTL = B->ntiles, TR = B->tile_rows;
+    const long long NT = B->NT;
+    float2 *r = B->b32, *rh = r + NT, *p = rh + NT, *v = p + NT, *sv = v + NT, *tv = sv + NT, *ph = tv + NT,
+           *sh = ph + NT, *xl = sh + NT;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    for (int b = 0; b < P; ++b) {
+        const BProb& pb = B->hprobs[b];
+        cudaMemcpyAsync(B->f + pb.off, f[b], sizeof(double2) * pb.N, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(B->x + pb.off, x[b], sizeof(double2) * pb.N, cudaMemcpyDeviceToDevice, s);
+        launch_set_masked(B->x + pb.off, B->f + pb.off, pb.mask, pb.N, s);
+    }
+    long long launches = 0;
+    // ||f_b||: the residual of x = 0
+    std::vector<int> ones(P, 1);
+    cudaMemcpyAsync(B->active, ones.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(B->w, 0, sizeof(double2) * NT, s);
+    kb_resid64<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->f, B->w, B->r64, B->tpart, B->active);
+    kb_seg_sum<<<(P + 127) / 128, 128, 0, s>>>(B->probs, P, B->tpart, B->nrm);
+    cudaMemcpyAsync(B->hpin, B->nrm, sizeof(double) * P, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HELM_CUDA_ERROR;
+    for (int b = 0; b < P; ++b) {
+        BState& S = B->hbst[b];
+        S = BState{};
+        S.bnorm = std::sqrt(B->hpin[b]);
+        S.tol_abs = o->tol * S.bnorm;
+        S.maxit = o->maxit;
+        S.status = HELM_NOT_CONVERGED;
+    }
+    cudaMemcpyAsync(B->bst, B->hbst, sizeof(BState) * P, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(B->ruflag, 0, sizeof(int) * P, s);
+    cudaMemsetAsync(B->bsc, 0, sizeof(double2) * P * S_NSLOTS, s);
+    cudaMemsetAsync(xl, 0, sizeof(float2) * NT, s);
+    // initial true residual, a fresh start everywhere (ruflag = 2 for the replace kernel)
+    std::vector<int> twos(P, 2);
+    kb_resid64<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->f, B->x, B->r64, B->tpart, B->active);
+    kb_seg_sum<<<(P + 127) / 128, 128, 0, s>>>(B->probs, P, B->tpart, B->nrm);
+    cudaMemcpyAsync(B->ruflag, twos.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s);
+    kb32_replace<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->r64, r, rh, p, v, B->part3, B->ruflag);
+    kb32_fin<<<P, 64, 0, s>>>(BF_INIT, B->probs, P, B->part3, B->bsc, B->bst, B->active, B->ruflag, B->nrm,
+                              kBatchReliableDelta);
+    launches += 6;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HELM_CUDA_ERROR;
+    // one iteration of every active problem, with the reliable updates the iteration asks for
+    auto enqueue = [&]() {
+        kb32_p<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, r, v, p, B->bsc, B->active);
+        batch_precond32(B, o, p, ph, s, launches);
+        kb_apply32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, ph, v, B->active);
+        kb32_dot<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, rh, v, B->part3, B->bsc, B->active);
+        kb32_fin<<<P, 64, 0, s>>>(BF_ALPHA, B->probs, P, B->part3, B->bsc, B->bst, B->active, B->ruflag, B->nrm,
+                                  kBatchReliableDelta);
+        kb32_s<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, r, v, sv, B->part3, B->bsc, B->active);
+        kb32_fin<<<P, 64, 0, s>>>(BF_SNORM, B->probs, P, B->part3, B->bsc, B->bst, B->active, B->ruflag, B->nrm,
+                                  kBatchReliableDelta);
+        batch_precond32(B, o, sv, sh, s, launches);
+        kb_apply32<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, sh, tv, B->active);
+        kb32_ts<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, tv, sv, B->part3, B->bsc, B->active);
+        kb32_fin<<<P, 64, 0, s>>>(BF_OMEGA, B->probs, P, B->part3, B->bsc, B->bst, B->active, B->ruflag, B->nrm,
+                                  kBatchReliableDelta);
+        kb32_xr<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, xl, r, ph, sh, sv, tv, rh, B->part3, B->bsc, B->active);
+        kb32_fin<<<P, 64, 0, s>>>(BF_XR, B->probs, P, B->part3, B->bsc, B->bst, B->active, B->ruflag, B->nrm,
+                                  kBatchReliableDelta);
+        kb32_fold<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->x, xl, B->ruflag);
+        kb_resid64<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->f, B->x, B->r64, B->tpart, B->ruflag);
+        kb_seg_sum<<<(P + 127) / 128, 128, 0, s>>>(B->probs, P, B->tpart, B->nrm);
+        kb32_replace<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->r64, r, rh, p, v, B->part3, B->ruflag);
+        kb32_fin<<<P, 64, 0, s>>>(BF_RU, B->probs, P, B->part3, B->bsc, B->bst, B->active, B->ruflag, B->nrm,
+                                  kBatchReliableDelta);
+        launches += 17;
+    };
+    cudaGraphExec_t gexec = nullptr;
+    const long long l0 = launches;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HELM_CUDA_ERROR;
+    enqueue();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamEndCapture(s, &graph) != cudaSuccess) return HELM_CUDA_ERROR;
+    const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return HELM_CUDA_ERROR;
+    const long long per_iter = launches - l0;
+    launches = l0;
+    // replay in rounds of kRound iterations; the states of round i are read while
+    // round i + 1 runs (a finished problem makes every later kernel skip its tiles)
+    constexpr int kRound = 8;
+    cudaEvent_t rev[2];
+    cudaEventCreateWithFlags(&rev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&rev[1], cudaEventDisableTiming);
+    std::vector<BState> snap[2] = {std::vector<BState>(P), std::vector<BState>(P)};
+    BState* stage = B->hbst;            // pinned staging of one snapshot
+    int rounds = 0, pending = -1;
+    bool done = false;
+    cudaError_t err = cudaSuccess;
+    const int max_rounds = o->maxit / kRound + 2;
+    while (!done && rounds <= max_rounds) {
+        for (int q = 0; q < kRound && err == cudaSuccess; ++q) {
+            err = cudaGraphLaunch(gexec, s);
+            launches += per_iter;
+        }
+        if (err != cudaSuccess) break;
+        // wait for the previous round's snapshot before reusing the staging buffer
+        if (pending >= 0) {
+            if ((err = cudaEventSynchronize(rev[pending])) != cudaSuccess) break;
+            std::memcpy(snap[pending].data(), stage, sizeof(BState) * P);
+            done = true;
+            for (int b = 0; b < P; ++b)
+                if (snap[pending][b].status == HELM_NOT_CONVERGED && snap[pending][b].iters < o->maxit) done = false;
+        }
+        const int slot = rounds & 1;
+        cudaMemcpyAsync(stage, B->bst, sizeof(BState) * P, cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(rev[slot], s);
+        pending = slot;
+        ++rounds;
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(gexec);
+    cudaEventDestroy(rev[0]);
+    cudaEventDestroy(rev[1]);
+    if (err != cudaSuccess) return HELM_CUDA_ERROR;
+    // final states; problems still running (maxit reached mid-round) fold their increment
+    std::memcpy(snap[0].data(), stage, sizeof(BState) * P);
+    std::vector<int> still(P, 0);
+    bool any = false;
+    for (int b = 0; b < P; ++b)
+        if (snap[0][b].status == HELM_NOT_CONVERGED) { still[b] = 1; any = true; }
+    if (any) {
+        cudaMemcpyAsync(B->ruflag, still.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s);
+        kb32_fold<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->x, xl, B->ruflag);
+        kb_resid64<<<G, BT, 0, s>>>(B->probs, B->tiles, NTL, TR, B->f, B->x, B->r64, B->tpart, B->ruflag);
+        kb_seg_sum<<<(P + 127) / 128, 128, 0, s>>>(B->probs, P, B->tpart, B->nrm);
+        cudaMemcpyAsync(B->hpin, B->nrm, sizeof(double) * P, cudaMemcpyDeviceToHost, s);
+        launches += 3;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return HELM_CUDA_ERROR;
+        for (int b = 0; b < P; ++b)
+            if (still[b] && snap[0][b].bnorm > 0) snap[0][b].rel_res = std::sqrt(B->hpin[b]) / snap[0][b].bnorm;
+    }
+    for (int b = 0; b < P; ++b) {
+        const BProb& pb = B->hprobs[b];
+        cudaMemcpyAsync(x[b], B->x + pb.off, sizeof(double2) * pb.N, cudaMemcpyDeviceToDevice, s);
+    }
+    cudaEventRecord(e1, s);
+    cudaEventRecord(B->join, s);
+    cudaStreamWaitEvent(B->stream, B->join, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int worst = HELM_OK;
+    for (int b = 0; b < P; ++b) {
+        const BState& S = snap[0][b];
+        if (stats) {
+            helm_stats& sb = stats[b];
+            sb = helm_stats{};
+            sb.status = S.status;
+            sb.iters = S.iters;
+            sb.cycles = S.restarts;
+            sb.rel_res = S.rel_res;
+            sb.ms = ms;
+            sb.launches = launches;
+            sb.precond_applies = 2 * S.iters;
+            sb.matvecs = 2 * S.iters;
+        }
+        if (S.status != HELM_OK) worst = S.status;
+    }
+    if (cudaGetLastError() != cudaSuccess) return HELM_CUDA_ERROR;
+    return (helm_status)worst;
+}
+
 }  // namespace
 
 extern "C" {
@@ -742,6 +1356,7 @@ helm_status helm_batch_create(int nprob, helm_handle** hs, helm_batch** out) {
         P.imf = B->tablesf + (size_t)b * kTabF;
         P.invdf = reinterpret_cast<const float2*>(B->tablesf + (size_t)b * kTabF + kTabPad);
         P.Qbf = static_cast<const __nv_bfloat16*>(h->Qbf);
+        P.ldq = basis_ld(h->N);
         P.Ainv = h->Ainv;
         P.k2 = h->k2; P.k2f = h->k2f; P.invd_field = h->invdf;
         B->hprobs.push_back(P);
@@ -771,6 +1386,8 @@ helm_status helm_batch_destroy(helm_batch* B) {
     bfree(B->f); bfree(B->x); bfree(B->V); bfree(B->w); bfree(B->v32); bfree(B->z32tmp); bfree(B->r32);
     bfree(B->Z32); bfree(B->w32); bfree(B->pp32); bfree(B->y32); bfree(B->hpart); bfree(B->H); bfree(B->sn);
     bfree(B->g); bfree(B->y); bfree(B->h2); bfree(B->cs); bfree(B->tpart); bfree(B->nrm); bfree(B->est);
+    bfree(B->b32); bfree(B->r64); bfree(B->bsc); bfree(B->bst); bfree(B->ruflag); bfree(B->part3);
+    if (B->hbst) cudaFreeHost(B->hbst);
     if (B->hpin) cudaFreeHost(B->hpin);
     if (B->cstream) cudaStreamDestroy(B->cstream);
     if (B->join) cudaEventDestroy(B->join);
@@ -788,6 +1405,7 @@ helm_status helm_batch_set_tile(helm_batch* B, int tile_rows, int grid) {
 helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const double* const* f, double* const* x,
                              helm_stats* stats) {
     if (!B || !o || !f || !x) return HELM_BAD_ARG;
+    if (o->method == HELM_METHOD_BICGSTAB) return batch_bicgstab(B, o, f, x, stats);
     if (o->method != HELM_METHOD_FGMRES || o->restart < 1 || o->restart > kMaxRestart || o->conj ||
         o->correction == HELM_CORR_NONLINEAR)
         return HELM_BAD_ARG;

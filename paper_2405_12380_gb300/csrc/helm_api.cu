@@ -64,6 +64,13 @@ void dfree(T*& p) {
 
 int round32(int k) { return ((k + 31) / 32) * 32; }
 
+// drop the captured iterations (their kernels name buffers and operator tables that
+// are about to change)
+void drop_graphs(helm_handle* h) {
+    if (h->g32) cudaGraphExecDestroy(h->g32);
+    h->g32 = nullptr;
+}
+
 helm_status ensure_tmp(helm_handle* h, size_t count) {
     while (h->tmp.size() < count) {
         double2* p = nullptr;
@@ -84,12 +91,17 @@ helm_status ensure_tmp32(helm_handle* h, size_t count) {
 
 double* scal(helm_handle* h, int slot) { return reinterpret_cast<double*>(h->sc + slot); }
 
+bool red_black(int kind) { return kind == HELM_RBGS || kind == HELM_SOR || kind == HELM_SSOR; }
+
+
 helm_status poll(helm_handle* h) {
     CK(cudaMemcpyAsync(h->hpin, h->sc, S_NSLOTS * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return HELM_OK;
 }
 double hs(const helm_handle* h, int slot, int im = 0) { return h->hpin[2 * slot + im]; }
+// a grid-barrier wait of the cooperative cycle gave up (flag 4 in S_FLAGS.y, read by poll)
+bool barrier_timed_out(const helm_handle* h) { return hs(h, S_FLAGS, 1) == 4.0; }
 
 // ||f - A x||^2 into slot (FP64)
 helm_status residual_norm(helm_handle* h, const double2* f, const double2* x, double2* r, int conj, int slot) {
@@ -132,6 +144,28 @@ double ev_sum(helm_handle* h, int ph) {
     return t;
 }
 
+// `sweeps` red-black sweeps in place (Eq. 2 with M = the lower triangle of the
+// red-black ordered A): HELM_RBGS red then black half-sweeps; HELM_SOR the same with
+// each node moved by omega times its Gauss-Seidel step; HELM_SSOR the forward sweep
+// (red, black) then the backward one (black, red).  from_zero: x = 0 on entry (the
+// first half-sweep reads no neighbours; its other colour must already be zero).
+template <typename R>
+void red_black_sweeps(helm_handle* h, const Op<R>& op, int kind, double omega, int sweeps,
+                      const typename CT<R>::T* f, typename CT<R>::T* x, int conj, bool from_zero) {
+    const double w = kind == HELM_RBGS ? 1.0 : omega;
+    static const int fwd[2] = {0, 1}, sym[4] = {0, 1, 1, 0};
+    const int* order = kind == HELM_SSOR ? sym : fwd;
+    const int per = kind == HELM_SSOR ? 4 : 2;
+    for (int q = 0; q < sweeps; ++q)
+        for (int c = 0; c < per; ++c) {
+            const bool first = from_zero && q == 0 && c == 0;
+            if (!first) ev_mark(h, 2, 0);
+            launch_rbgs_half<R>(op, order[c], f, x, conj, first, h->stream, w);
+            if (!first) ev_mark(h, 2, 1);
+        }
+    h->launches += (long long)per * sweeps;
+}
+
 // z = n sweeps of the relaxation on A z = r from z = 0 (FP64)
 helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, const double2* r, double2* z,
                             int conj) {
@@ -156,17 +190,9 @@ helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, 
         CKL();
         return HELM_OK;
     }
-    if (kind == HELM_RBGS) {
+    if (red_black(kind)) {
         CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
-        for (int q = 0; q < sweeps; ++q) {
-            if (q > 0) ev_mark(h, 2, 0);
-            launch_rbgs_half<double>(h->op64, 0, r, z, conj, q == 0, s);
-            if (q > 0) ev_mark(h, 2, 1);
-            ev_mark(h, 2, 0);
-            launch_rbgs_half<double>(h->op64, 1, r, z, conj, false, s);
-            ev_mark(h, 2, 1);
-        }
-        h->launches += 2 * sweeps;
+        red_black_sweeps<double>(h, h->op64, kind, omega, sweeps, r, z, conj, true);
         CKL();
         return HELM_OK;
     }
@@ -255,23 +281,27 @@ helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v,
         h->launches += o->n_r;
     } else {
         CK(cudaMemsetAsync(z, 0, sizeof(float2) * h->N, s));
-        for (int q = 0; q < o->n_r; ++q) {
-            launch_rbgs_half<float>(h->op32, 0, v, z, conj, q == 0, s);
-            launch_rbgs_half<float>(h->op32, 1, v, z, conj, false, s);
-        }
-        h->launches += 2 * o->n_r;
+        red_black_sweeps<float>(h, h->op32, o->relax, o->omega, o->n_r, v, z, conj, true);
     }
     if (o->correction == HELM_CORR_TB) {
         if (!h->Qbf) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
-        const int nblk = restrict_blocks(h->N);
+        int nblk = restrict_blocks(h->N);
         ev_mark(h, 0, 0);
-        launch_restrict32(h->op32, h->Qbf, h->k, v, no_relax ? nullptr : z, conj, h->partials32, nblk, s);
+        if (!no_relax && o->relax == HELM_RBGS && h->Qbr) {
+            // after the black half-sweep v - A z vanishes on black and masked rows:
+            // project the red rows only
+            nblk = launch_restrict32_red(h->op32, h->Qbr, basis_ld((h->N + 1) / 2), h->k, v, z, conj,
+                                         h->partials32, s);
+        } else {
+            launch_restrict32(h->op32, h->Qbf, basis_ld(h->N), h->k, v, no_relax ? nullptr : z, conj,
+                              h->partials32, nblk, s);
+        }
         ev_mark(h, 0, 1);
-        launch_coarse_apply32(h->partials32, nblk, h->k, h->Ainv, conj, h->y32, s);
+        launch_coarse_apply32(h->partials32, nblk, h->k, h->Ainv, conj, h->y32, h->cbuf, s);
         ev_mark(h, 1, 0);
-        launch_prolong32(h->Qbf, h->k, h->y32, z, h->N, s);
+        launch_prolong32(h->Qbf, basis_ld(h->N), h->k, h->y32, z, h->N, s);
         ev_mark(h, 1, 1);
-        h->launches += 3;
+        h->launches += 4;
     }
     CKL();
     return HELM_OK;
@@ -297,7 +327,7 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
         // one cooperative launch for the whole red-black part and the red residual
         ev_mark(h, 2, 0);
         CK(launch_cycle_df(h->op64, h->dft, pre, r, pv, pw, h->sc, h->fparts, tol_abs, fs, xs, rr, o->n_r, conj,
-                           h->counter + 2, h->dflag + 2, s));
+                           h->counter + 2, h->dflag + 2, h->bar_spin, h->bar_extra, s));
         ev_mark(h, 2, 1);
         h->launches -= 2 * o->n_r;
     } else {
@@ -329,7 +359,77 @@ helm_status precond_rbgs_tb_df(helm_handle* h, const helm_solve_opts* o, const d
     return HELM_OK;
 }
 
+// ---------------------------------------------------------------- multigrid
+// `sweeps` damped-Jacobi sweeps on A z = r on handle H, z from zero if `zero`; the
+// sweeps alternate between z and jt so that the last one lands in z
+helm_status jacobi_sweeps(helm_handle* h, double omega, int sweeps, const double2* r, double2* z, double2* jt,
+                          int conj, bool zero, cudaStream_t s) {
+    if (sweeps <= 0) {
+        if (zero) CK(cudaMemsetAsync(z, 0, sizeof(double2) * h->N, s));
+        return HELM_OK;
+    }
+    double2* bufs[2] = {z, jt};
+    int src = zero ? -1 : 0;
+    for (int q = 0; q < sweeps; ++q) {
+        const int dst = ((sweeps - 1 - q) % 2 == 0) ? 0 : 1;
+        if (src == dst) {
+            CK(cudaMemcpyAsync(bufs[1 - src], bufs[src], sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, s));
+            src = 1 - src;
+        }
+        launch_jacobi<double>(h->op64, omega, r, src < 0 ? nullptr : bufs[src], bufs[dst], conj, src < 0, s);
+        src = dst;
+    }
+    CKL();
+    return HELM_OK;
+}
+
+// z = V(r) on level `level` (handle H; level 0 is h itself), Sec. 4.3 DeepONet-MG:
+// smoother from zero, coarse-grid correction z += P V_c(R (r - A z)) (zero on masked
+// nodes), smoother again; the smoother is n_r damped-Jacobi sweeps, the trunk-basis
+// correction, n_r sweeps (the 2-1-2 strategy for n_r = 2) on level 0 when the
+// correction is the trunk basis, else 2 n_r + 1 sweeps; the coarsest level only
+// smooths from zero
+helm_status vcycle(helm_handle* h, int level, helm_handle* H, const helm_solve_opts* o, const double2* r, double2* z,
+                   int conj) {
+    const cudaStream_t s = h->stream;
+    double2 *jt, *t;
+    if (level == 0) {
+        TRY(ensure_tmp(h, 20));
+        jt = h->tmp[18];
+        t = h->tmp[19];
+    } else {
+        TRY(ensure_tmp(H, 4));
+        jt = H->tmp[0];
+        t = H->tmp[3];
+    }
+    const bool with_tb = level == 0 && o->correction == HELM_CORR_TB;
+    auto smooth = [&](bool zero) -> helm_status {
+        if (with_tb) {
+            TRY(jacobi_sweeps(H, o->omega, o->n_r, r, z, jt, conj, zero, s));
+            TRY(tb_correct(H, r, z, z, conj, false));
+            return jacobi_sweeps(H, o->omega, o->n_r, r, z, jt, conj, false, s);
+        }
+        return jacobi_sweeps(H, o->omega, 2 * o->n_r + 1, r, z, jt, conj, zero, s);
+    };
+    TRY(smooth(true));
+    if (level == (int)h->mg.size()) return HELM_OK;
+    helm_handle* Cc = h->mg[level];
+    TRY(ensure_tmp(Cc, 4));
+    Cc->stream = s;
+    launch_apply<double>(H->op64, z, r, t, nullptr, conj, true, s);
+    launch_restrict_fw<double>(H->dim, H->n, t, Cc->mask, Cc->tmp[1], s);
+    h->launches += 2;
+    CKL();
+    TRY(vcycle(h, level + 1, Cc, o, Cc->tmp[1], Cc->tmp[2], conj));
+    launch_prolong_add<double>(H->dim, H->n, Cc->tmp[2], H->mask, z, s);
+    h->launches += 1;
+    CKL();
+    return smooth(false);
+}
+
 helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
+    if (h->precision == HELM_MIXED && o->relax == HELM_MG)
+        return fail(h, HELM_BAD_ARG, "the multigrid cycle runs on FP64 handles");
     if (h->precision == HELM_MIXED) {
         TRY(ensure_tmp32(h, 4));
         launch_cvt_f64_to_f32(r, h->tmp32[0], h->N, h->stream);
@@ -345,6 +445,7 @@ helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, 
         CK(cudaMemcpyAsync(z, r, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, h->stream));
         return HELM_OK;
     }
+    if (o->relax == HELM_MG) return vcycle(h, 0, h, o, r, z, conj);
     if (o->relax == HELM_RBGS && o->n_r > 0 && o->correction == HELM_CORR_TB && !h->k2) return precond_rbgs_tb_df(h, o, r, z, conj);
     TRY(relax_from_zero(h, o->relax, o->omega, o->n_r, r, z, conj));
     if (o->correction == HELM_CORR_TB) {
@@ -368,7 +469,12 @@ helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, 
 helm_status check_opts(helm_handle* h, const helm_solve_opts* o) {
     if (!o) return fail(h, HELM_BAD_ARG, "opts is NULL");
     if (o->method < 0 || o->method > 2) return fail(h, HELM_BAD_ARG, "unknown method");
-    if (o->relax < 0 || o->relax > 2) return fail(h, HELM_BAD_ARG, "unknown relaxation");
+    if (o->relax < 0 || o->relax > HELM_MG) return fail(h, HELM_BAD_ARG, "unknown relaxation");
+    if ((o->relax == HELM_SOR || o->relax == HELM_SSOR || o->relax == HELM_JACOBI || o->relax == HELM_MG) &&
+        !(o->omega > 0.0 && o->omega < 2.0))
+        return fail(h, HELM_BAD_ARG, "omega must be in (0, 2)");
+    if (o->relax == HELM_MG && !h->mg_levels)
+        return fail(h, HELM_NOT_READY, "multigrid hierarchy not set up (helm_mg_setup)");
     if (o->correction < 0 || o->correction > 2) return fail(h, HELM_BAD_ARG, "unknown correction");
     if (o->correction == HELM_CORR_TB && !h->Q) return fail(h, HELM_NOT_READY, "trunk basis not loaded");
     if (o->correction == HELM_CORR_NONLINEAR) {
@@ -403,6 +509,7 @@ helm_status solve_relax(helm_handle* h, const helm_solve_opts* o, const double2*
         TRY(residual_norm(h, f, x, r, o->conj, S_RN2));
         ++st->matvecs;
         TRY(poll(h));
+        if (barrier_timed_out(h)) { st->status = HELM_TIMEOUT; break; }
         const double res = std::sqrt(hs(h, S_RN2)) / bnorm;
         hist.push(res);
         st->rel_res = res;
@@ -419,12 +526,8 @@ helm_status solve_relax(helm_handle* h, const helm_solve_opts* o, const double2*
             }
             h->launches += o->n_r;
             if (a != x) CK(cudaMemcpyAsync(x, a, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, h->stream));
-        } else if (o->relax == HELM_RBGS) {
-            for (int q = 0; q < o->n_r; ++q) {
-                launch_rbgs_half<double>(h->op64, 0, f, x, o->conj, false, h->stream);
-                launch_rbgs_half<double>(h->op64, 1, f, x, o->conj, false, h->stream);
-            }
-            h->launches += 2 * o->n_r;
+        } else if (red_black(o->relax)) {
+            red_black_sweeps<double>(h, h->op64, o->relax, o->omega, o->n_r, f, x, o->conj, false);
         }
         CKL();
         if (o->correction == HELM_CORR_TB) {
@@ -531,12 +634,14 @@ helm_status solve_fgmres(helm_handle* h, const helm_solve_opts* o, const double2
             ++iters;
             kdim = j + 1;
             TRY(poll(h));
+            if (barrier_timed_out(h)) { st->status = HELM_TIMEOUT; break; }
             const double est = hs(h, S_EST) / bnorm;
             hist.push(est);
             const double wn2 = hs(h, S_WN2);
             if (!std::isfinite(est)) break;
             if (wn2 == 0.0 || est <= o->tol || iters >= o->maxit) break;
         }
+        if (st->status == HELM_TIMEOUT) break;
         launch_hsolve(h->Hm, ldh, kdim, h->g, h->y, s);
         if (mixed)
             launch_mupdate32(h->Z32, kdim, h->y, 1.0, x, N, s);
@@ -593,11 +698,6 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
     // feed the preconditioner into its first phase
     const bool fuse = h->precision != HELM_MIXED && o->relax == HELM_RBGS && o->n_r > 0 &&
                       o->correction == HELM_CORR_TB && !h->k2 && h->Q && cycle_df_blocks(N) > 0;
-    // mixed handles: the operator reads the preconditioner's complex64 output (exact in
-    // double-float) instead of its FP64 copy (tabulated k^2 only; relaxation or
-    // correction present, so that the output comes from the complex64 cycle)
-    const bool mixed_df = h->precision == HELM_MIXED && !h->k2 &&
-                          !((o->relax == HELM_RELAX_NONE || o->n_r <= 0) && o->correction == HELM_CORR_NONE);
     float4* phdf = nullptr;
     float4* shdf = nullptr;
     if (fuse) {
@@ -617,9 +717,7 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
             launch_bicg_update_p(r, v, p, h->sc, N, s);
             TRY(precond(h, o, p, ph, o->conj));
             ev_mark(h, 3, 0);
-            if (mixed_df) launch_apply_bicg_c64in(h->op64, h->dft, 1, h->tmp32[1], v, rh, o->conj, h->sc, h->fparts,
-                                                  h->counter, s);
-            else launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
+            launch_apply_bicg(h->op64, 1, ph, v, rh, o->conj, h->sc, h->fparts, h->counter, s);
             ev_mark(h, 3, 1);
         }
         if (fuse) {
@@ -632,9 +730,7 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
             launch_bicg_s_fused(r, v, sv, h->sc, N, h->fparts, h->counter, tol_abs, s);
             TRY(precond(h, o, sv, sh, o->conj));
             ev_mark(h, 3, 0);
-            if (mixed_df) launch_apply_bicg_c64in(h->op64, h->dft, 2, h->tmp32[1], t, sv, o->conj, h->sc, h->fparts,
-                                                  h->counter, s);
-            else launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
+            launch_apply_bicg(h->op64, 2, sh, t, sv, o->conj, h->sc, h->fparts, h->counter, s);
             ev_mark(h, 3, 1);
         }
         launch_bicg_xr_fused(x, r, ph, sh, sv, t, rh, h->sc, N, h->fparts, h->counter, o->tol, bnorm, s);
@@ -669,6 +765,7 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
         st->matvecs += 2;
         ++iters;
         const double brk = snap[2 * S_FLAGS + 1];
+        if (brk == 4.0) { st->status = HELM_TIMEOUT; break; }
         if (brk == 1.0) { st->status = HELM_BREAKDOWN; break; }
         res = std::sqrt(snap[2 * S_RN2]) / bnorm;
         hist.push(res);
@@ -697,6 +794,211 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
     TRY(residual_norm(h, f, x, t, o->conj, S_RN2));
     TRY(poll(h));
     st->rel_res = std::sqrt(hs(h, S_RN2)) / bnorm;
+    st->iters = iters;
+    st->cycles = restarts;
+    return HELM_OK;
+}
+
+// ------------------------------------------- complex64 BiCGStab (MIXED handles)
+// BiCGStab with right preconditioning whose vectors, operator and preconditioner are
+// complex64, with reliable updates of an FP64 iterate (bicg32.cu): when the recursive
+// residual has dropped below kReliableDelta times its largest value since the last
+// update, or met the tolerance, the host folds the increment into x, recomputes the
+// true residual in FP64 and replaces the recursive one by it (keeping the search
+// direction); a breakdown restarts from the true residual (rhat = r, p = v = 0).
+// Convergence is decided on the FP64 true residual only.
+constexpr double kReliableDelta = 0.1;
+// growth of the recursive residual over the last true one that counts as a runaway
+constexpr double kRunaway = 1e3;
+
+helm_status ensure_b32(helm_handle* h) {
+    while (h->b32.size() < 9) {
+        float2* p = nullptr;
+        TRY(dalloc(h, &p, (size_t)h->N));
+        h->b32.push_back(p);
+    }
+    if (!h->b32parts) TRY(dalloc(h, &h->b32parts, (size_t)3 * bicg32_blocks()));
+    return HELM_OK;
+}
+
+helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const double2* f, double2* x,
+                             helm_stats* st, Hist& hist, double bnorm) {
+    TRY(ensure_tmp(h, 2));
+    TRY(ensure_tmp32(h, 4));
+    TRY(ensure_b32(h));
+    const long long N = h->N;
+    cudaStream_t s = h->stream;
+    double2* r64 = h->tmp[1];
+    float2 *r = h->b32[0], *rh = h->b32[1], *p = h->b32[2], *v = h->b32[3], *sv = h->b32[4], *t = h->b32[5],
+           *ph = h->b32[6], *sh = h->b32[7], *xl = h->b32[8];
+    double* parts = h->b32parts;
+    const double tol_abs = o->tol * bnorm;
+    TRY(residual_norm(h, f, x, r64, o->conj, S_RN2));
+    ++st->matvecs;
+    TRY(poll(h));
+    double res = std::sqrt(hs(h, S_RN2)) / bnorm;
+    hist.push(res);
+    st->rel_res = res;
+    if (res <= o->tol) {
+        st->status = HELM_OK;
+        st->iters = 0;
+        return HELM_OK;
+    }
+    CK(cudaMemsetAsync(xl, 0, sizeof(float2) * N, s));
+    launch_b32_set_tol(h->sc, tol_abs, s);
+    launch_b32_replace(r64, r, rh, p, v, 1, h->sc, N, parts, h->counter, s);
+    h->launches += 2;
+    CKL();
+    // the kernels of one iteration, on h->stream
+    auto enqueue_iter = [&]() -> helm_status {
+        const cudaStream_t q = h->stream;
+        launch_b32_update_p(r, v, p, h->sc, N, q);
+        TRY(precond32(h, o, p, ph, o->conj));
+        ev_mark(h, 3, 0);
+        launch_apply<float>(h->op32, ph, nullptr, v, nullptr, o->conj, false, q);
+        ev_mark(h, 3, 1);
+        launch_b32_alpha(rh, v, h->sc, N, parts, h->counter, q);
+        launch_b32_s(r, v, sv, h->sc, N, parts, h->counter, q);
+        TRY(precond32(h, o, sv, sh, o->conj));
+        ev_mark(h, 3, 0);
+        launch_apply<float>(h->op32, sh, nullptr, t, nullptr, o->conj, false, q);
+        ev_mark(h, 3, 1);
+        launch_b32_omega(t, sv, h->sc, N, parts, h->counter, q);
+        launch_b32_xr(xl, r, ph, sh, sv, t, rh, h->sc, N, parts, h->counter, q);
+        h->launches += 7;
+        CKL();
+        return HELM_OK;
+    };
+    // without per-launch profiling the iteration is captured once as a CUDA graph (on a
+    // private stream: the legacy default stream cannot be captured) and replayed
+    const bool use_graph = !h->profile;
+    const int key[5] = {o->relax, o->n_r, o->correction, o->conj, 1};
+    if (use_graph && (!h->g32 || std::memcmp(key, h->g32_key, sizeof(key)) != 0 || h->g32_omega != o->omega)) {
+        drop_graphs(h);
+        if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        const cudaStream_t saved = h->stream;
+        const long long l0 = h->launches;
+        h->stream = h->cap_stream;
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const helm_status cst = enqueue_iter();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+        h->stream = saved;
+        if (cst != HELM_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cst != HELM_OK ? cst : fail(h, HELM_CUDA_ERROR, "capture of the BiCGStab iteration failed");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&h->g32, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            h->g32 = nullptr;
+            return fail(h, HELM_CUDA_ERROR, std::string("graph instantiation: ") + cudaGetErrorString(ie));
+        }
+        h->g32_launches = h->launches - l0;
+        h->launches = l0;
+        std::memcpy(h->g32_key, key, sizeof(key));
+        h->g32_omega = o->omega;
+    }
+    auto launch_iter = [&](int slot) -> helm_status {
+        if (use_graph) {
+            CK(cudaGraphLaunch(h->g32, s));
+            h->launches += h->g32_launches;
+        } else {
+            TRY(enqueue_iter());
+        }
+        CK(cudaMemcpyAsync(h->hring + 2 * S_NSLOTS * slot, h->sc, S_NSLOTS * sizeof(double2),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(h->evring[slot], s));
+        CKL();
+        return HELM_OK;
+    };
+    // x += xl; r64 = f - A x (FP64, its norm in S_BETA2); r = complex64(r64) with rho,
+    // beta (restart: also rhat = r, p = v = 0); the host waits for the result
+    auto reliable_update = [&](int restart, int drop = 0) -> helm_status {
+        launch_b32_fold(x, xl, N, s, drop);
+        TRY(residual_norm(h, f, x, r64, o->conj, S_BETA2));
+        launch_b32_replace(r64, r, rh, p, v, restart, h->sc, N, parts, h->counter, s);
+        h->launches += 2;
+        ++st->matvecs;
+        CKL();
+        return poll(h);
+    };
+    st->status = HELM_NOT_CONVERGED;
+    double maxrr = res, last_true = res;
+    int iters = 0, restarts = 0, inflight = 0, head = 0, since_start = 0;
+    while (true) {
+        if (inflight == 0) {
+            if (iters >= o->maxit) break;
+            TRY(launch_iter(head));
+            inflight = 1;
+        }
+        if (inflight == 1 && iters + 1 < o->maxit) {
+            TRY(launch_iter(head ^ 1));
+            inflight = 2;
+        }
+        CK(cudaEventSynchronize(h->evring[head]));
+        const double* snap = h->hring + 2 * S_NSLOTS * head;
+        head ^= 1;
+        --inflight;
+        st->precond_applies += 2;
+        st->matvecs += 2;
+        ++iters;
+        ++since_start;
+        const double brk = snap[2 * S_FLAGS + 1];
+        const bool stop = snap[2 * S_STOP] != 0.0;
+        if (brk == 4.0) { st->status = HELM_TIMEOUT; break; }
+        const double rn = std::sqrt(snap[2 * S_RN2]) / bnorm;
+        hist.push(rn);
+        // a runaway of the complex64 recursion (or a non-finite value): drop the
+        // increment and restart from the FP64 iterate
+        const bool reset = !std::isfinite(rn) || rn > kRunaway * last_true;
+        if (!stop && !reset && rn >= kReliableDelta * maxrr) {
+            maxrr = std::max(maxrr, rn);
+            continue;
+        }
+        // drain the queued iteration: a no-op if this one stopped, else a real one
+        if (inflight) {
+            CK(cudaEventSynchronize(h->evring[head]));
+            if (!stop) {
+                st->precond_applies += 2;
+                st->matvecs += 2;
+                ++iters;
+                ++since_start;
+            }
+            inflight = 0;
+        }
+        head = 0;
+        TRY(reliable_update(reset ? 1 : 0, reset ? 1 : 0));
+        const double rt = std::sqrt(hs(h, S_BETA2)) / bnorm;
+        res = rt;
+        if (rt <= o->tol) { st->status = HELM_OK; break; }
+        if (!std::isfinite(rt)) { st->status = HELM_DIVERGED; break; }
+        if (reset) {
+            ++restarts;
+            since_start = 0;
+            maxrr = last_true = rt;
+            continue;
+        }
+        if (stop && brk != 0.0) {
+            // breakdown (rho, <rhat, v> or <t, t> zero, or omega zero): restart from
+            // the true residual just computed, unless the (re)start itself broke down
+            if (since_start <= 1) { st->status = HELM_BREAKDOWN; break; }
+            since_start = 0;
+            launch_b32_replace(r64, r, rh, p, v, 1, h->sc, N, parts, h->counter, s);
+            h->launches += 1;
+            CKL();
+            ++restarts;
+        }
+        maxrr = last_true = rt;
+    }
+    // fold what is left of the increment and take the final true residual
+    launch_b32_fold(x, xl, N, s);
+    h->launches += 1;
+    TRY(residual_norm(h, f, x, r64, o->conj, S_RN2));
+    TRY(poll(h));
+    st->rel_res = std::sqrt(hs(h, S_RN2)) / bnorm;
+    if (st->status == HELM_NOT_CONVERGED && st->rel_res <= o->tol) st->status = HELM_OK;
     st->iters = iters;
     st->cycles = restarts;
     return HELM_OK;
@@ -773,6 +1075,19 @@ helm_status build_coarse(helm_handle* h, const double* Qrm, int ldq, int k) {
     if (e != cudaSuccess) return fail(h, HELM_CUDA_ERROR, cudaGetErrorString(e));
     if (flag) return fail(h, HELM_SINGULAR_COARSE, "coarse operator A_c is singular");
     return HELM_OK;
+}
+
+// after a synchronised solve or preconditioner call: HELM_TIMEOUT (with the barrier
+// state reset) if a grid-barrier wait of the cooperative cycle gave up
+helm_status clear_barrier_timeout(helm_handle* h) {
+    int waited_out = 0;
+    CK(cudaMemcpy(&waited_out, h->dflag + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!waited_out) return HELM_OK;
+    CK(cudaMemset(h->dflag + 2, 0, sizeof(int)));
+    CK(cudaMemset(h->counter + 2, 0, 2 * sizeof(unsigned)));
+    CK(cudaMemset(h->sc + S_FLAGS, 0, sizeof(double2)));
+    CK(cudaMemset(h->sc + S_STOP, 0, sizeof(double2)));
+    return fail(h, HELM_TIMEOUT, "a grid-barrier wait of the red-black cycle timed out");
 }
 
 }  // namespace
@@ -863,6 +1178,10 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
 
 helm_status helm_destroy(helm_handle* h) {
     if (!h) return HELM_BAD_ARG;
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (helm_handle* c : h->mg) helm_destroy(c);
+    h->mg.clear();
     dfree(h->mask); dfree(h->lidx); dfree(h->nbm); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
     dfree(h->red); dfree(h->sc); dfree(h->dflag); dfree(h->counter); dfree(h->fparts);
     if (h->hpin) cudaFreeHost(h->hpin);
@@ -871,8 +1190,11 @@ helm_status helm_destroy(helm_handle* h) {
         if (e) cudaEventDestroy(e);
     for (auto p : h->tmp) cudaFree(p);
     for (auto p : h->tmp32) cudaFree(p);
+    for (auto p : h->b32) cudaFree(p);
+    dfree(h->b32parts);
     dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
     if (h->Qbf) cudaFree(h->Qbf);
+    if (h->Qbr) cudaFree(h->Qbr);
     dfree(h->partials32); dfree(h->y32); dfree(h->Z32);
     dfree(h->Traw); dfree(h->bw); dfree(h->nl_x); dfree(h->nl_h0); dfree(h->nl_h1);
     dfree(h->V); dfree(h->Z); dfree(h->Hm); dfree(h->cs); dfree(h->sn); dfree(h->g); dfree(h->y); dfree(h->hpart);
@@ -953,7 +1275,7 @@ helm_status helm_residual(helm_handle* h, const void* f, const void* x, void* r,
 helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const void* f, void* x, int conj,
                        int dtype) {
     if (!h || !f || !x || sweeps < 0) return fail(h, HELM_BAD_ARG, "bad argument");
-    if (kind != HELM_JACOBI && kind != HELM_RBGS) return fail(h, HELM_BAD_ARG, "kind");
+    if (kind != HELM_JACOBI && !red_black(kind)) return fail(h, HELM_BAD_ARG, "kind");
     cudaStream_t s = h->stream;
     if (dtype == HELM_C128) {
         if (kind == HELM_JACOBI) {
@@ -966,10 +1288,7 @@ helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const
             }
             if (a != x) CK(cudaMemcpyAsync(x, a, sizeof(double2) * h->N, cudaMemcpyDeviceToDevice, s));
         } else {
-            for (int q = 0; q < sweeps; ++q) {
-                launch_rbgs_half<double>(h->op64, 0, (const double2*)f, (double2*)x, conj, false, s);
-                launch_rbgs_half<double>(h->op64, 1, (const double2*)f, (double2*)x, conj, false, s);
-            }
+            red_black_sweeps<double>(h, h->op64, kind, omega, sweeps, (const double2*)f, (double2*)x, conj, false);
         }
     } else if (dtype == HELM_C64) {
         if (kind == HELM_JACOBI) {
@@ -982,10 +1301,7 @@ helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const
             }
             if (a != x) CK(cudaMemcpyAsync(x, a, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, s));
         } else {
-            for (int q = 0; q < sweeps; ++q) {
-                launch_rbgs_half<float>(h->op32, 0, (const float2*)f, (float2*)x, conj, false, s);
-                launch_rbgs_half<float>(h->op32, 1, (const float2*)f, (float2*)x, conj, false, s);
-            }
+            red_black_sweeps<float>(h, h->op32, kind, omega, sweeps, (const float2*)f, (float2*)x, conj, false);
         }
     } else {
         return fail(h, HELM_BAD_ARG, "dtype");
@@ -998,6 +1314,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
                      double tau) {
     if (!h || !weights || !widths) return fail(h, HELM_BAD_ARG, "null argument");
     if (act != HELM_ACT_TANH) return fail(h, HELM_BAD_ARG, "activation");
+    drop_graphs(h);
     if (n_layers < 1 || n_layers > 7) return fail(h, HELM_BAD_ARG, "n_layers must be 1..7");
     if (widths[0] != h->dim) return fail(h, HELM_BAD_ARG, "widths[0] must equal dim");
     for (int i = 1; i <= n_layers; ++i)
@@ -1096,8 +1413,14 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
         // the coarse operator is built from the same rounded basis the kernels use
         launch_round_bf16(T, ldq, k, N, s);
         dfree(h->Qbf);
-        STEPC(cudaMalloc(&h->Qbf, (size_t)N * k * 2));
-        launch_rm_to_cm_bf16(T, ldq, k, h->Qbf, N, s);
+        dfree(h->Qbr);
+        const long long ldb = basis_ld(N), ldr = basis_ld((N + 1) / 2);
+        STEPC(cudaMalloc(&h->Qbf, (size_t)ldb * k * 2));
+        STEPC(cudaMemsetAsync(h->Qbf, 0, (size_t)ldb * k * 2, s));
+        launch_rm_to_cm_bf16(T, ldq, k, h->Qbf, ldb, N, s);
+        STEPC(cudaMalloc(&h->Qbr, (size_t)ldr * k * 2));
+        STEPC(cudaMemsetAsync(h->Qbr, 0, (size_t)ldr * k * 2, s));
+        launch_red_rows_bf16(h->Qbf, ldb, k, N, h->n, h->Qbr, ldr, s);
     }
     // column-major FP32-pair Q for the per-iteration kernels; T becomes hi + lo so that
     // A_c is built from exactly the basis the kernels apply
@@ -1119,7 +1442,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     STEP(dalloc(h, &h->coarse_partials, (size_t)std::max(restrict_blocks(N), project_blocks(N)) * k));
     if (h->precision == HELM_MIXED) {
         dfree(h->partials32); dfree(h->y32);
-        STEP(dalloc(h, &h->partials32, (size_t)restrict_blocks(N) * k));
+        STEP(dalloc(h, &h->partials32, (size_t)std::max(restrict_blocks(N), restrict32_red_blocks(N)) * k));
         STEP(dalloc(h, &h->y32, (size_t)kMaxP));
     }
     STEP(dalloc(h, &h->cbuf, (size_t)kMaxP));
@@ -1195,7 +1518,68 @@ helm_status don_correct(helm_handle* h, int mode, const void* r, void* z, int co
 helm_status helm_precond(helm_handle* h, const helm_solve_opts* opts, const void* r, void* z) {
     if (!h || !r || !z) return fail(h, HELM_BAD_ARG, "null argument");
     TRY(check_opts(h, opts));
-    return precond(h, opts, (const double2*)r, (double2*)z, opts->conj);
+    TRY(precond(h, opts, (const double2*)r, (double2*)z, opts->conj));
+    CK(cudaStreamSynchronize(h->stream));
+    return clear_barrier_timeout(h);
+}
+
+helm_status helm_mg_setup(helm_handle* h, int levels) {
+    if (!h) return HELM_BAD_ARG;
+    if (levels < 1 || levels > 8) return fail(h, HELM_BAD_ARG, "levels must be 1..8");
+    if (h->precision != HELM_FP64) return fail(h, HELM_BAD_ARG, "the multigrid cycle runs on FP64 handles");
+    for (helm_handle* c : h->mg) helm_destroy(c);
+    h->mg.clear();
+    h->mg_levels = 0;
+    int n = h->n;
+    for (int l = 1; l < levels; ++l) {
+        if (n % 2 == 0 || n < 5) return fail(h, HELM_BAD_ARG, "vertex coarsening needs an odd n >= 5 on every level");
+        n = (n + 1) / 2;
+    }
+    helm_handle* parent = h;
+    cudaStream_t s = h->stream;
+    for (int l = 1; l < levels; ++l) {
+        const int nf = parent->n, nc = (nf + 1) / 2;
+        const long long Nf = parent->N, Nc = h->dim == 3 ? (long long)nc * nc * nc : (long long)nc * nc;
+        uint8_t* mc = nullptr;
+        double2 *kf = nullptr, *kc = nullptr;
+        auto cleanup = [&]() { dfree(mc); dfree(kf); dfree(kc); };
+        helm_status st;
+        if ((st = dalloc(h, &mc, (size_t)Nc)) != HELM_OK || (st = dalloc(h, &kc, (size_t)Nc)) != HELM_OK) {
+            cleanup();
+            return st;
+        }
+        const double2* kfine = parent->k2;
+        if (!kfine) {
+            if ((st = dalloc(h, &kf, (size_t)Nf)) != HELM_OK) {
+                cleanup();
+                return st;
+            }
+            launch_layer_k2(parent->op64, parent->k0, parent->strength, nullptr, kf, s);
+            kfine = kf;
+        }
+        launch_inject_mask(h->dim, nf, parent->mask, mc, s);
+        launch_inject_c128(h->dim, nf, kfine, kc, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cleanup();
+            return fail(h, HELM_CUDA_ERROR, "injection to the coarse level");
+        }
+        helm_handle* c = nullptr;
+        st = helm_create(h->dim, nc, h->k0, 0, 0.0, mc, reinterpret_cast<const double*>(kc), HELM_FP64, &c);
+        cleanup();
+        if (st != HELM_OK) return fail(h, st, "coarse level handle");
+        c->stream = s;
+        h->mg.push_back(c);
+        parent = c;
+    }
+    h->mg_levels = levels;
+    return HELM_OK;
+}
+
+helm_status helm_set_wait_limit(helm_handle* h, unsigned polls, unsigned extra_arrivals) {
+    if (!h || polls == 0) return fail(h, HELM_BAD_ARG, "bad argument");
+    h->bar_spin = polls;
+    h->bar_extra = extra_arrivals;
+    return HELM_OK;
 }
 
 helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv, void* xv, helm_stats* stats,
@@ -1210,6 +1594,7 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     h->launches = 0;
     for (int& e : h->evn) e = 0;
     CK(cudaEventRecord(h->ev0, h->stream));
+    CK(cudaMemsetAsync(h->sc + S_FLAGS, 0, sizeof(double2), h->stream));
     launch_set_masked(x, f, h->mask, h->N, h->stream);
     h->launches += 1;
     TRY(norm2_into(h, f, S_BN2));
@@ -1223,18 +1608,19 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
         TRY(solve_relax(h, o, f, x, &st, hist, bnorm));
     } else if (o->method == HELM_METHOD_FGMRES) {
         TRY(solve_fgmres(h, o, f, x, &st, hist, bnorm));
+    } else if (h->precision == HELM_MIXED) {
+        TRY(solve_bicgstab32(h, o, f, x, &st, hist, bnorm));
     } else {
         TRY(solve_bicgstab(h, o, f, x, &st, hist, bnorm));
     }
     CK(cudaEventRecord(h->ev1, h->stream));
     CK(cudaEventSynchronize(h->ev1));
-    // a grid-barrier wait that gave up leaves a flag (never expected)
-    int waited_out = 0;
-    CK(cudaMemcpy(&waited_out, h->dflag + 2, sizeof(int), cudaMemcpyDeviceToHost));
-    if (waited_out) {
-        CK(cudaMemset(h->dflag + 2, 0, sizeof(int)));
-        return fail(h, HELM_CUDA_ERROR, "a grid-barrier wait of the red-black cycle timed out");
-    }
+    // a grid-barrier wait that gave up leaves a flag: the blocks that gave up went on
+    // unsynchronised, so the barrier's arrival counter and generation are reset before
+    // the next launch and the solve reports HELM_TIMEOUT
+    const helm_status bst = clear_barrier_timeout(h);
+    if (bst == HELM_TIMEOUT) st.status = HELM_TIMEOUT;
+    else if (bst != HELM_OK) return bst;
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     st.ms = ms;
@@ -1287,6 +1673,7 @@ helm_status helm_k2_gradient(helm_handle* h, const double* lambda, const double*
 
 helm_status helm_set_k2(helm_handle* h, const double* k2) {
     if (!h || !k2) return fail(h, HELM_BAD_ARG, "null argument");
+    drop_graphs(h);
     const long long N = h->N;
     if (!h->k2) {
         TRY(dalloc(h, &h->k2, (size_t)N));

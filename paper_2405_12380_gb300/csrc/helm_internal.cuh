@@ -83,8 +83,10 @@ struct DfTab {
 
 // device scalar slots of the Krylov drivers (double2 each, in helm_handle::sc)
 enum { S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_SN2, S_RN2, S_FLAGS, S_TS, S_TT,
-       S_BETA2, S_WN2, S_EST, S_BN2, S_STOP, S_NSLOTS };
+       S_BETA2, S_WN2, S_EST, S_BN2, S_STOP, S_TOLS, S_NSLOTS };
 // S_FLAGS.x = 1: ||s|| met the tolerance this iteration; S_FLAGS.y = 1: breakdown
+// S_TOLS.x: the absolute tolerance tol ||f|| of the complex64 BiCGStab (set per solve,
+// so that its captured iteration does not depend on the solve)
 // S_STOP.x = 1: the BiCGStab iteration that set it ended the loop (converged, broke
 // down or diverged); later x/r updates are no-ops until the next reset
 
@@ -98,9 +100,10 @@ template <typename R>
 void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f,
                    const typename CT<R>::T* xin, typename CT<R>::T* xout, int conj, bool xzero,
                    cudaStream_t s);
+// omega: 1 = Gauss-Seidel; otherwise SOR (each node moves by omega times its GS step)
 template <typename R>
 void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x,
-                      int conj, bool xzero, cudaStream_t s);
+                      int conj, bool xzero, cudaStream_t s, double omega = 1.0);
 int apply_grid_blocks(int dim, int n);
 int bicg_grid_blocks(int dim, int n);
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s);
@@ -120,6 +123,23 @@ void launch_bicg_s_fused(const double2* r, const double2* v, double2* sv, double
 void launch_bicg_xr_fused(double2* x, double2* r, const double2* phat, const double2* shat, const double2* sv,
                           const double2* t, const double2* rhat, double2* sc, long long N, double* parts,
                           unsigned* counter, double tol, double bnorm, cudaStream_t s);
+
+// bicg32.cu: complex64 BiCGStab with reliable updates (HELM_MIXED handles); each
+// reduction finishes in the last block of its kernel (parts: 3 doubles per block)
+int bicg32_blocks();
+void launch_b32_update_p(const float2* r, const float2* v, float2* p, const double2* sc, long long N, cudaStream_t s);
+void launch_b32_alpha(const float2* rhat, const float2* v, double2* sc, long long N, double* parts, unsigned* counter,
+                      cudaStream_t s);
+void launch_b32_s(const float2* r, const float2* v, float2* sv, double2* sc, long long N, double* parts,
+                  unsigned* counter, cudaStream_t s);
+void launch_b32_set_tol(double2* sc, double tol_abs, cudaStream_t s);
+void launch_b32_omega(const float2* t, const float2* sv, double2* sc, long long N, double* parts, unsigned* counter,
+                      cudaStream_t s);
+void launch_b32_xr(float2* xl, float2* r, const float2* phat, const float2* shat, const float2* sv, const float2* t,
+                   const float2* rhat, double2* sc, long long N, double* parts, unsigned* counter, cudaStream_t s);
+void launch_b32_fold(double2* x, float2* xl, long long N, cudaStream_t s, int drop = 0);
+void launch_b32_replace(const double2* r64, float2* r, float2* rhat, float2* p, float2* v, int restart, double2* sc,
+                        long long N, double* parts, unsigned* counter, cudaStream_t s);
 
 // blas.cu
 // partial reductions over a fixed grid of kRedBlocks blocks
@@ -199,7 +219,8 @@ void launch_residual_red_df(const Op<double>& op, const DfTab& t, const float4* 
 int cycle_df_blocks(long long N);
 cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, int pre, const double2* f, const double2* v,
                             double2* w, double2* sc, double* parts, double tol_abs, float4* fs, float4* xs,
-                            float4* r_red, int n_r, int conj, unsigned* bar2, int* err, cudaStream_t s);
+                            float4* r_red, int n_r, int conj, unsigned* bar2, int* err, unsigned spin_limit,
+                            unsigned extra_arrivals, cudaStream_t s);
 // projection of a residual given as FP32 pairs (float4 per complex entry, N rows)
 void launch_project_df_split(const float2* Q, long long ld, int k, const float4* r, long long N, double2* partials,
                              int nblk, cudaStream_t s);
@@ -207,11 +228,6 @@ void launch_project_df_split(const float2* Q, long long ld, int k, const float4*
 // (optional) receives z as FP32 pairs too
 void launch_prolong_df_base(const float2* Q, long long ld, int k, const double2* y, const float4* base, double2* z,
                             float4* zdf, long long N, cudaStream_t s);
-// the same for a complex64 x (mixed handles: the preconditioner's output before
-// its exact conversion to FP64)
-void launch_apply_bicg_c64in(const Op<double>& op, const DfTab& t, int mode, const float2* x, double2* y,
-                             const double2* w, int conj, double2* sc, double* parts, unsigned* counter,
-                             cudaStream_t s);
 // k_apply_bicg for an x given as FP32 pairs: y = A x in double-float, y in FP64
 void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const float4* x, double2* y,
                           const double2* w, int conj, double2* sc, double* parts, unsigned* counter, cudaStream_t s);
@@ -223,15 +239,34 @@ void launch_rm_to_cm_f32(const double* A, int ld, int p, float* B, long long N, 
 void launch_nl_pack(const double2* r, const double* s2, float* x, long long N, cudaStream_t s);
 void launch_nl_prolong(const float* T, int p, const float* b, const double* s2, double2* z, long long N,
                        cudaStream_t s);
-// mixed precision: BF16 basis (column-major k x N), complex64 vectors, FP32 accumulation
+// mixed precision: BF16 basis (column-major k columns of stride basis_ld(N), zero
+// padding), complex64 vectors, FP32 accumulation
 void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s);
-void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long N, cudaStream_t s);
-void launch_restrict32(const Op<float>& op, const void* Q, int k, const float2* v, const float2* z, int conj,
-                       float2* partials, int nblk, cudaStream_t s);
+void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long ldb, long long N, cudaStream_t s);
+void launch_restrict32(const Op<float>& op, const void* Q, long long ldq, int k, const float2* v, const float2* z,
+                       int conj, float2* partials, int nblk, cudaStream_t s);
 void launch_coarse_apply32(const float2* partials, int nblk, int k, const double2* Ainv, int conj, float2* y,
-                           cudaStream_t s);
-void launch_prolong32(const void* Q, int k, const float2* y, float2* z, long long N, cudaStream_t s);
+                           double2* cbuf, cudaStream_t s);
+void launch_prolong32(const void* Q, long long ldq, int k, const float2* y, float2* z, long long N, cudaStream_t s);
+// the red rows of the BF16 basis (k x ceil(N / 2), stride basis_ld(ceil(N / 2)))
+void launch_red_rows_bf16(const void* Q, long long ldq, int k, long long N, int n, void* Qr, long long ldr,
+                          cudaStream_t s);
+// c = Q_red^T (v - A z) over the red rows (the residual after a red-black sweep that
+// ends with the black half-sweep); returns the number of block partials written
+int restrict32_red_blocks(long long N);
+int launch_restrict32_red(const Op<float>& op, const void* Qr, long long ldr, int k, const float2* v,
+                          const float2* z, int conj, float2* partials, cudaStream_t s);
 int restrict_blocks(long long N);
+
+// mg.cu: grid transfers of the multigrid V-cycle (n_f = 2 n_c - 1, coarse node I at fine 2I)
+void launch_inject_mask(int dim, int nf, const uint8_t* fine, uint8_t* coarse, cudaStream_t s);
+void launch_inject_c128(int dim, int nf, const double2* fine, double2* coarse, cudaStream_t s);
+template <typename R>
+void launch_restrict_fw(int dim, int nf, const typename CT<R>::T* rf, const uint8_t* mask_c, typename CT<R>::T* rc,
+                        cudaStream_t s);
+template <typename R>
+void launch_prolong_add(int dim, int nf, const typename CT<R>::T* zc, const uint8_t* mask_f, typename CT<R>::T* zf,
+                        cudaStream_t s);
 
 // adjoint.cu
 void launch_receivers_setup(int n, int nrec, const double* xyz, int* idx, double* w, cudaStream_t s);
@@ -280,7 +315,8 @@ struct helm_handle {
     float2* Qr = nullptr;           // its red rows, k x ceil(N / 2)
     double2* Ainv = nullptr;
     double2* coarse_partials = nullptr;
-    void* Qbf = nullptr;            // BF16 basis (MIXED handles), column-major k x N
+    void* Qbf = nullptr;            // BF16 basis (MIXED handles), column-major k x basis_ld(N)
+    void* Qbr = nullptr;            // its red rows, k x basis_ld(ceil(N / 2))
     float2* partials32 = nullptr;
     float2* y32 = nullptr;
     float2* Z32 = nullptr;          // FGMRES preconditioned vectors in complex64 (MIXED)
@@ -306,10 +342,27 @@ struct helm_handle {
     double2* hpart = nullptr;
     // mixed precision buffers
     std::vector<float2*> tmp32;
+    std::vector<float2*> b32;       // complex64 BiCGStab vectors (MIXED handles)
+    double* b32parts = nullptr;     // their reduction partials
+    // one iteration of the complex64 BiCGStab captured as a CUDA graph (replayed per
+    // iteration; rebuilt when the cycle's options change, dropped when the basis,
+    // the k^2 field or a workspace buffer changes)
+    cudaGraphExec_t g32 = nullptr;
+    long long g32_launches = 0;
+    int g32_key[5] = {0, 0, 0, 0, 0};
+    double g32_omega = 0.0;
+    cudaStream_t cap_stream = nullptr;
+    // multigrid hierarchy (helm_mg_setup): the coarser levels as handles of their own
+    std::vector<helm_handle*> mg;
+    int mg_levels = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // launch accounting and per-kernel event timing (helm_set_profiling)
     int profile = 0;
     long long launches = 0;
+    // bounded waits of the cooperative cycle's grid barriers: polls before a wait
+    // gives up, and arrivals added to the barrier target (0; > 0 injects a timeout)
+    unsigned bar_spin = 1u << 20;
+    unsigned bar_extra = 0;
     // phases: 0 restriction, 1 prolongation, 2 relaxation half-sweeps that read
     // neighbours, 3 operator applications of the Krylov loop
     std::vector<cudaEvent_t> evpool[4];

@@ -381,10 +381,11 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
 // (n even), and updates the one of the swept colour in place.  The neighbours of
 // that node are of the other colour and are not written by this launch, so the
 // z-march keeps the planes in registers as in k_march_c64.  XZERO: the first
-// half-sweep from x = 0 (no neighbours read).
+// half-sweep from x = 0 (no neighbours read).  SOR (omega != 1): the node moves by
+// omega times its Gauss-Seidel step.
 template <bool XZERO>
 __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int colour, const float4* __restrict__ f,
-                                                      float4* x, int conj) {
+                                                      float4* x, int conj, float omega) {
     constexpr unsigned kMM = kMasked | (kMasked << 8);
     const int n = op.n, h = n >> 1;
     const int i2 = blockIdx.x * BX + threadIdx.x;
@@ -450,6 +451,14 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
                 } else {
                     const float2 sa = a ? s1 : s0;
                     out = cmul(id, make_float2(fa.x - op.hinv2 * sa.x, fa.y - op.hinv2 * sa.y));
+                }
+            }
+            if (omega != 1.f) {
+                if (XZERO) {
+                    out = cscale(omega, out);
+                } else {
+                    const float2 xo = a ? hi2(cur) : lo2(cur);
+                    out = cadd(xo, cscale(omega, csub(out, xo)));
                 }
             }
             xw[2 * l + a] = out;
@@ -590,10 +599,11 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(Op<R> op, R omega, const typ
 
 // red-black Gauss-Seidel update of one node of the swept colour, in place:
 // x_l = D_l^-1 (f_l - h^-2 sum of fluid neighbours) on fluid nodes (the Gauss-Seidel
-// value x + D^-1 (f - A x) with the diagonal term cancelled), f_l on masked nodes
+// value x + D^-1 (f - A x) with the diagonal term cancelled), f_l on masked nodes;
+// SOR (omega != 1): x_l + omega (that value - x_l)
 template <typename R, bool XZERO>
 __device__ __forceinline__ void rbgs_point(const Op<R>& op, const typename CT<R>::T* __restrict__ f,
-                                           typename CT<R>::T* x, int conj, int i, int j, int k) {
+                                           typename CT<R>::T* x, int conj, int i, int j, int k, R omega) {
     using C = typename CT<R>::T;
     const long long l = i + (long long)op.n * (j + (long long)op.n * k);
     const C fl = f[l];
@@ -613,17 +623,25 @@ __device__ __forceinline__ void rbgs_point(const Op<R>& op, const typename CT<R>
             out = cmul(id, g);
         }
     }
+    if (omega != (R)1) {
+        if (XZERO) {
+            out = cscale(omega, out);
+        } else {
+            const C xo = x[l];
+            out = cadd(xo, cscale(omega, csub(out, xo)));
+        }
+    }
     x[l] = out;
 }
 
 template <typename R, bool XZERO>
 __global__ void __launch_bounds__(BX * BY) k_rbgs(Op<R> op, int colour, const typename CT<R>::T* __restrict__ f,
-                                                  typename CT<R>::T* x, int conj) {
+                                                  typename CT<R>::T* x, int conj, R omega) {
     const int j = blockIdx.y * BY + threadIdx.y;
     const int k = op.dim == 3 ? blockIdx.z : 0;
     if (j >= op.n) return;
     const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + colour) & 1);
-    if (i < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i, j, k);
+    if (i < op.n) rbgs_point<R, XZERO>(op, f, x, conj, i, j, k, omega);
 }
 
 // r_red[l / 2] = (v - A z)_l at the red nodes l (one per node pair (2m, 2m + 1))
@@ -885,9 +903,11 @@ __global__ void __launch_bounds__(BX * BY) k_apply_bicg_df(Op<double> op, DfTab 
 struct GridBar {
     unsigned* count;        // arrivals in the current barrier
     unsigned* gen;          // barrier generation
-    int* err;
+    int* err;               // set to 1 when a wait gives up
+    double2* sc;            // Krylov scalars or null: a timeout also stops the BiCGStab loop
+    unsigned spin_limit;    // polls of the generation word before a wait gives up
+    unsigned target;        // arrivals that complete a barrier (gridDim.x; more only to inject a timeout)
 };
-constexpr unsigned kBarSpinLimit = 1u << 22;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
@@ -905,13 +925,20 @@ __device__ __forceinline__ void grid_barrier(const GridBar& b) {
         const unsigned g = ld_acquire_gpu(b.gen);
         unsigned old;
         asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(b.count) : "memory");
-        if (old == gridDim.x - 1) {
+        if (old == b.target - 1) {
             asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(b.count) : "memory");
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(b.gen) : "memory");
         } else {
             for (unsigned it = 0; ld_acquire_gpu(b.gen) == g; ++it)
-                if (it > kBarSpinLimit) {
+                if (it >= b.spin_limit) {
+                    // give up: record it and mark the BiCGStab iteration as stopped
+                    // (flag 4 = timeout); the block goes on with its phases, reading
+                    // and writing only in-range entries
                     atomicExch(b.err, 1);
+                    if (b.sc) {
+                        b.sc[S_FLAGS].y = 4.0;
+                        b.sc[S_STOP].x = 1.0;
+                    }
                     break;
                 }
         }
@@ -1075,7 +1102,7 @@ __global__ void k_layer_k2(Op<double> op, double k0sq, double strength, const do
     if (i >= op.n || j >= op.n) return;
     const long long l = i + (long long)op.n * (j + (long long)op.n * k);
     const int m = node_layer(op, i, j, k);
-    const double eta = (double)m / (double)op.L;
+    const double eta = op.L > 0 ? (double)m / (double)op.L : 0.0;
     const double base = scale ? k0sq * scale[l] : k0sq;
     k2[l] = make_double2(base, base * (strength * eta * eta));
 }
@@ -1253,21 +1280,21 @@ void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f, co
 
 template <typename R>
 void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x, int conj,
-                      bool xzero, cudaStream_t s) {
+                      bool xzero, cudaStream_t s, double omega) {
     if constexpr (std::is_same<R, float>::value) {
         if (pair_ok(op, f, x, nullptr)) {
             int zc;
             const dim3 g = pair_grid(op.n, &zc), b(BX, BY);
             const float4* f4 = reinterpret_cast<const float4*>(f);
             float4* x4 = reinterpret_cast<float4*>(x);
-            if (xzero) k_rbgs_c64<true><<<g, b, 0, s>>>(op, zc, colour, f4, x4, conj);
-            else k_rbgs_c64<false><<<g, b, 0, s>>>(op, zc, colour, f4, x4, conj);
+            if (xzero) k_rbgs_c64<true><<<g, b, 0, s>>>(op, zc, colour, f4, x4, conj, (float)omega);
+            else k_rbgs_c64<false><<<g, b, 0, s>>>(op, zc, colour, f4, x4, conj, (float)omega);
             return;
         }
     }
     dim3 g = grid_for(op.dim, op.n, 2, 1), b(BX, BY);
-    if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj);
-    else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj);
+    if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj, (R)omega);
+    else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj, (R)omega);
 }
 
 void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const float4* x, double2* y,
@@ -1275,14 +1302,6 @@ void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const 
     dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
     if (mode == 1) k_apply_bicg_df<1, float4><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
     else k_apply_bicg_df<2, float4><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
-}
-
-void launch_apply_bicg_c64in(const Op<double>& op, const DfTab& t, int mode, const float2* x, double2* y,
-                             const double2* w, int conj, double2* sc, double* parts, unsigned* counter,
-                             cudaStream_t s) {
-    dim3 g = grid_for(op.dim, op.n, 1, 2), b(BX, BY);
-    if (mode == 1) k_apply_bicg_df<1, float2><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
-    else k_apply_bicg_df<2, float2><<<g, b, 0, s>>>(op, t, x, y, w, conj, sc, parts, counter);
 }
 
 void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2* y, const double2* w, int conj,
@@ -1301,8 +1320,9 @@ template void launch_jacobi<double>(const Op<double>&, double, const double2*, c
 template void launch_jacobi<float>(const Op<float>&, double, const float2*, const float2*, float2*, int, bool,
                                    cudaStream_t);
 template void launch_rbgs_half<double>(const Op<double>&, int, const double2*, double2*, int, bool,
-                                       cudaStream_t);
-template void launch_rbgs_half<float>(const Op<float>&, int, const float2*, float2*, int, bool, cudaStream_t);
+                                       cudaStream_t, double);
+template void launch_rbgs_half<float>(const Op<float>&, int, const float2*, float2*, int, bool, cudaStream_t,
+                                      double);
 
 void launch_residual_red(const Op<double>& op, const double2* z, const double2* v, double2* r_red, int conj,
                          cudaStream_t s) {
@@ -1349,10 +1369,11 @@ int cycle_df_blocks(long long N) {
 
 cudaError_t launch_cycle_df(const Op<double>& op, const DfTab& t, int pre, const double2* f, const double2* v,
                             double2* w, double2* sc, double* parts, double tol_abs, float4* fs, float4* xs,
-                            float4* r_red, int n_r, int conj, unsigned* bar2, int* err, cudaStream_t s) {
+                            float4* r_red, int n_r, int conj, unsigned* bar2, int* err, unsigned spin_limit,
+                            unsigned extra_arrivals, cudaStream_t s) {
     const int nb = cycle_df_blocks(op.N);
     if (nb < 1) return cudaErrorNotSupported;
-    GridBar b{bar2, bar2 + 1, err};
+    GridBar b{bar2, bar2 + 1, err, sc, spin_limit, (unsigned)nb + extra_arrivals};
     Op<double> opv = op;
     DfTab tv = t;
     const double2* fv = f;

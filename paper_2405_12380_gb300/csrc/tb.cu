@@ -523,6 +523,45 @@ __global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ 
     if (threadIdx.x == 0) y[i] = make_double2(red[0].x + red[1].x, red[0].y + red[1].y);
 }
 
+// complex64 partials of the BF16-basis restriction: c_j = sum over blocks (FP64, fixed
+// order), one block per column; then y (complex64) = A_c^-1 c, one block per row --
+// spread over k SMs like the FP64 pair above
+__global__ void __launch_bounds__(64) k_coarse32_reduce(const float2* __restrict__ partials, int nblk, int k,
+                                                        double2* __restrict__ c) {
+    __shared__ double2 red[2];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double sx = 0, sy = 0;
+    for (int b = threadIdx.x; b < nblk; b += 64) {
+        const float2 q = partials[(long long)b * k + j];
+        sx += q.x;
+        sy += q.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) red[w] = make_double2(sx, sy);
+    __syncthreads();
+    if (threadIdx.x == 0) c[j] = make_double2(red[0].x + red[1].x, red[0].y + red[1].y);
+}
+
+__global__ void __launch_bounds__(64) k_coarse32_gemv(const double2* __restrict__ Ainv, int k, int conj,
+                                                      const double2* __restrict__ c, float2* __restrict__ y) {
+    __shared__ double2 red[2];
+    const int i = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double sx = 0, sy = 0;
+    for (int j = threadIdx.x; j < k; j += 64) {
+        double2 a = Ainv[(long long)i * k + j];
+        if (conj) a.y = -a.y;
+        const double2 cj = c[j];
+        sx += a.x * cj.x - a.y * cj.y;
+        sy += a.x * cj.y + a.y * cj.x;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) red[w] = make_double2(sx, sy);
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = make_float2((float)(red[0].x + red[1].x), (float)(red[0].y + red[1].y));
+}
+
 // z_l += sum_j Q_j[l] y_j in FP32-pair arithmetic, one thread per node
 // BASE: z_l = base_l + sum_j Q_j[l] y_j with base given as FP32 pairs
 template <bool BASE>
@@ -709,8 +748,9 @@ __global__ void k_round_bf16(double* __restrict__ A, int ld, int k, long long N)
     }
 }
 
-// row-major FP64 (N x ld) -> column-major BF16 (k x N)
-__global__ void k_rm_to_cm_bf16(const double* __restrict__ A, int ld, int k, __nv_bfloat16* __restrict__ B, long long N) {
+// row-major FP64 (N x ld) -> column-major BF16 (k columns of stride ldb)
+__global__ void k_rm_to_cm_bf16(const double* __restrict__ A, int ld, int k, __nv_bfloat16* __restrict__ B, long long ldb,
+                                long long N) {
     __shared__ float tile[32][33];
     const long long l0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -723,13 +763,13 @@ __global__ void k_rm_to_cm_bf16(const double* __restrict__ A, int ld, int k, __n
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         int c = c0 + r;
         long long l = l0 + threadIdx.x;
-        if (c < k && l < N) B[(long long)c * N + l] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+        if (c < k && l < N) B[(long long)c * ldb + l] = __float2bfloat16_rn(tile[threadIdx.x][r]);
     }
 }
 
 // complex64 restriction with a BF16 basis, FP32 accumulation: same structure as k_restrict
 template <int KPW>
-__global__ void __launch_bounds__(RS_T) k_restrict32(Op<float> op, const __nv_bfloat16* __restrict__ Q, int k,
+__global__ void __launch_bounds__(RS_T) k_restrict32(Op<float> op, const __nv_bfloat16* __restrict__ Q, long long ldq, int k,
                                                      const float2* __restrict__ v, const float2* __restrict__ z,
                                                      int conj, float2* __restrict__ partials,
                                                      long long rows_per_block) {
@@ -780,7 +820,7 @@ __global__ void __launch_bounds__(RS_T) k_restrict32(Op<float> op, const __nv_bf
         for (int c = 0; c < KPW; ++c) {
             const int j = warp + NW * c;
             if (j < k) {
-                const __nv_bfloat16* Qj = Q + (long long)j * N + t0;
+                const __nv_bfloat16* Qj = Q + (long long)j * ldq + t0;
                 float ax = acc[c].x, ay = acc[c].y;
                 for (int q = lane; q < rows; q += 32) {
                     const float qv = __bfloat162float(Qj[q]);
@@ -805,40 +845,9 @@ __global__ void __launch_bounds__(RS_T) k_restrict32(Op<float> op, const __nv_bf
     }
 }
 
-// y (complex64) = A_c^-1 c, partial sums added in FP64
-__global__ void __launch_bounds__(1024) k_coarse32(const float2* __restrict__ partials, int nblk, int k,
-                                                   const double2* __restrict__ Ainv, int conj, float2* __restrict__ y) {
-    __shared__ double2 c[kMaxP];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < k; j += nw) {
-        double sx = 0, sy = 0;
-        for (int b = lane; b < nblk; b += 32) {
-            float2 q = partials[(long long)b * k + j];
-            sx += q.x;
-            sy += q.y;
-        }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) c[j] = make_double2(sx, sy);
-    }
-    __syncthreads();
-    for (int i = warp; i < k; i += nw) {
-        double sx = 0, sy = 0;
-        for (int j = lane; j < k; j += 32) {
-            double2 a = Ainv[(long long)i * k + j];
-            if (conj) a.y = -a.y;
-            double2 cj = c[j];
-            sx += a.x * cj.x - a.y * cj.y;
-            sy += a.x * cj.y + a.y * cj.x;
-        }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) y[i] = make_float2((float)sx, (float)sy);
-    }
-}
 
-__global__ void __launch_bounds__(256) k_prolong32(const __nv_bfloat16* __restrict__ Q, int k, const float2* __restrict__ y,
-                                                   float2* __restrict__ z, long long N) {
+__global__ void __launch_bounds__(256) k_prolong32(const __nv_bfloat16* __restrict__ Q, long long ldq, int k,
+                                                   const float2* __restrict__ y, float2* __restrict__ z, long long N) {
     __shared__ float2 ys[kMaxP];
     for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
     __syncthreads();
@@ -847,12 +856,200 @@ __global__ void __launch_bounds__(256) k_prolong32(const __nv_bfloat16* __restri
         const __nv_bfloat16* q = Q + l;
 #pragma unroll 8
         for (int j = 0; j < k; ++j) {
-            const float qv = __bfloat162float(q[(long long)j * N]);
+            const float qv = __bfloat162float(q[(long long)j * ldq]);
             sx = fmaf(qv, ys[j].x, sx);
             sy = fmaf(qv, ys[j].y, sy);
         }
         float2 zz = z[l];
         z[l] = make_float2(zz.x + sx, zz.y + sy);
+    }
+}
+
+// ---- the trunk-basis correction of the complex64 red-black cycle ---------------
+// BF16 basis columns have a stride that is a multiple of 64 entries with zero
+// padding, so that a thread reads eight consecutive rows of a column with one
+// 16-byte load.  Eight BF16 values of a uint4, in memory order (BF16 is the top
+// half of an FP32 number).
+__device__ __forceinline__ void bf16x8(const uint4 u, float* q) {
+    q[0] = __uint_as_float(u.x << 16); q[1] = __uint_as_float(u.x & 0xffff0000u);
+    q[2] = __uint_as_float(u.y << 16); q[3] = __uint_as_float(u.y & 0xffff0000u);
+    q[4] = __uint_as_float(u.z << 16); q[5] = __uint_as_float(u.z & 0xffff0000u);
+    q[6] = __uint_as_float(u.w << 16); q[7] = __uint_as_float(u.w & 0xffff0000u);
+}
+
+// Qr[j][m] = Q[j][red node of pair m] (BF16; the red node of pair (2m, 2m + 1) is
+// 2m + colour(2m); an odd N's last pair may name node N, a zero padding row)
+__global__ void k_red_rows_bf16(const __nv_bfloat16* __restrict__ Q, long long ldq, int k, long long N, int n,
+                                __nv_bfloat16* __restrict__ Qr, long long ldr) {
+    const long long M = (N + 1) / 2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < M * k;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long j = idx / M, m = idx - j * M;
+        const long long l = 2 * m + node_colour(2 * m, n);
+        Qr[j * ldr + m] = Q[j * ldq + l];
+    }
+}
+
+// (v - A z) at the red node of pair m (complex64); zero on masked nodes and past N
+__device__ __forceinline__ float2 red_residual32(const Op<float>& op, const float2* __restrict__ v,
+                                                 const float2* __restrict__ z, long long m, int conj) {
+    const long long l = 2 * m + node_colour(2 * m, op.n);
+    if (l >= op.N) return make_float2(0.f, 0.f);
+    const unsigned code = op.nbm[l];
+    if (code & 0x80u) return make_float2(0.f, 0.f);
+    const long long sy = op.n, sz = (long long)op.n * op.n;
+    float2 s = make_float2(0.f, 0.f);
+    if (code & 1u) s = cadd(s, z[l - 1]);
+    if (code & 2u) s = cadd(s, z[l + 1]);
+    if (code & 4u) s = cadd(s, z[l - sy]);
+    if (code & 8u) s = cadd(s, z[l + sy]);
+    if (op.dim == 3) {
+        if (code & 16u) s = cadd(s, z[l - sz]);
+        if (code & 32u) s = cadd(s, z[l + sz]);
+    }
+    float2 d;
+    if (op.k2) {
+        d = op.k2[l];
+        d.x -= 2.0f * op.dim * op.hinv2;
+    } else {
+        d = make_float2(op.dre, op.im[op.lidx[l]]);
+    }
+    if (conj) d.y = -d.y;
+    const float2 zc = z[l], vv = v[l];
+    return make_float2(vv.x - (op.hinv2 * s.x + (d.x * zc.x - d.y * zc.y)),
+                       vv.y - (op.hinv2 * s.y + (d.x * zc.y + d.y * zc.x)));
+}
+
+constexpr int RR_T = 256;     // threads of the red-row restriction
+constexpr int RR_ROWS = 8;    // consecutive red rows per thread (one 16-byte basis load per column)
+constexpr int RR_KC = 8;      // columns per chunk (registers)
+
+// c = Q_red^T r with r = v - A z on the red rows (after a red-black sweep that ends
+// with the black half-sweep the residual vanishes on black and masked rows).  A
+// warp takes 32 x 8 consecutive red rows; per chunk of 8 columns each lane sums its
+// 8 rows in FP32, the warp adds its lanes (fixed butterfly) and lane 0 adds the
+// chunk into the warp's row of shared memory; at the end the block sums its warps
+// in a fixed order into partials[block][j].  Deterministic.
+__global__ void __launch_bounds__(RR_T, 4) k_restrict32_red(Op<float> op, const __nv_bfloat16* __restrict__ Qr,
+                                                         long long ldr, int k, const float2* __restrict__ v,
+                                                         const float2* __restrict__ z, int conj,
+                                                         float2* __restrict__ partials, long long M) {
+    constexpr int NW = RR_T / 32;
+    constexpr int WROWS = 32 * RR_ROWS;            // red rows of one warp tile
+    __shared__ float2 sacc[NW][kMaxP];
+    // the warp tile's residuals, 8 rows per lane with one padding slot per lane
+    __shared__ float2 rsm[NW][32 * (RR_ROWS + 1)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = lane; j < k; j += 32) sacc[warp][j] = make_float2(0.f, 0.f);
+    __syncwarp();
+    const long long groups = (M + RR_ROWS - 1) / RR_ROWS;
+    const long long wtiles = (groups + 31) / 32;
+    for (long long wt = blockIdx.x * (long long)NW + warp; wt < wtiles; wt += (long long)gridDim.x * NW) {
+        // residuals of the tile's rows computed with consecutive rows on consecutive
+        // lanes (coalesced neighbour loads), then read back eight consecutive rows per lane
+        const long long mt = wt * WROWS;
+#pragma unroll
+        for (int q = 0; q < RR_ROWS; ++q) {
+            const int row = lane + 32 * q;
+            const long long m = mt + row;
+            rsm[warp][row + row / RR_ROWS] = (m < M) ? red_residual32(op, v, z, m, conj) : make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+        const long long m0 = mt + (long long)lane * RR_ROWS;
+        float2 r[RR_ROWS];
+#pragma unroll
+        for (int q = 0; q < RR_ROWS; ++q) r[q] = rsm[warp][lane * (RR_ROWS + 1) + q];
+        __syncwarp();
+        for (int c0 = 0; c0 < k; c0 += RR_KC) {
+            float ax[RR_KC], ay[RR_KC];
+#pragma unroll
+            for (int c = 0; c < RR_KC; ++c) {
+                ax[c] = 0.f;
+                ay[c] = 0.f;
+                if (c0 + c < k && m0 < M) {
+                    const uint4 u = __ldcs(reinterpret_cast<const uint4*>(Qr + (long long)(c0 + c) * ldr + m0));
+                    float qv[8];
+                    bf16x8(u, qv);
+#pragma unroll
+                    for (int q = 0; q < RR_ROWS; ++q) {
+                        ax[c] = fmaf(qv[q], r[q].x, ax[c]);
+                        ay[c] = fmaf(qv[q], r[q].y, ay[c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RR_KC; ++c)
+                for (int o = 16; o > 0; o >>= 1) {
+                    ax[c] += __shfl_xor_sync(0xffffffffu, ax[c], o);
+                    ay[c] += __shfl_xor_sync(0xffffffffu, ay[c], o);
+                }
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < RR_KC; ++c)
+                    if (c0 + c < k) {
+                        sacc[warp][c0 + c].x += ax[c];
+                        sacc[warp][c0 + c].y += ay[c];
+                    }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += RR_T) {
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t = cadd(t, sacc[w][j]);
+        partials[(long long)blockIdx.x * k + j] = t;
+    }
+}
+
+// z += Q y, eight consecutive rows per thread (16-byte basis loads, 64-byte z
+// accesses); z must be 16-byte aligned
+__global__ void __launch_bounds__(256) k_prolong32v(const __nv_bfloat16* __restrict__ Q, long long ldq, int k,
+                                                    const float2* __restrict__ y, float2* __restrict__ z,
+                                                    long long N) {
+    __shared__ float2 ys[kMaxP];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
+    const long long groups = (N + 7) / 8;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long l0 = g * 8;
+        float ax[8], ay[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            ax[q] = 0.f;
+            ay[q] = 0.f;
+        }
+        const __nv_bfloat16* Qg = Q + l0;
+#pragma unroll 8
+        for (int j = 0; j < k; ++j) {
+            const uint4 u = __ldcs(reinterpret_cast<const uint4*>(Qg + (long long)j * ldq));
+            float qv[8];
+            bf16x8(u, qv);
+            const float2 yj = ys[j];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                ax[q] = fmaf(qv[q], yj.x, ax[q]);
+                ay[q] = fmaf(qv[q], yj.y, ay[q]);
+            }
+        }
+        if (l0 + 8 <= N) {
+            float4* z4 = reinterpret_cast<float4*>(z + l0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4 t = z4[q];
+                t.x += ax[2 * q];
+                t.y += ay[2 * q];
+                t.z += ax[2 * q + 1];
+                t.w += ay[2 * q + 1];
+                z4[q] = t;
+            }
+        } else {
+            for (int q = 0; q < 8; ++q)
+                if (l0 + q < N) {
+                    float2 t = z[l0 + q];
+                    z[l0 + q] = make_float2(t.x + ax[q], t.y + ay[q]);
+                }
+        }
     }
 }
 
@@ -998,17 +1195,38 @@ void launch_round_bf16(double* A, int ld, int k, long long N, cudaStream_t s) {
     k_round_bf16<<<4 * 152, 256, 0, s>>>(A, ld, k, N);
 }
 
-void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long N, cudaStream_t s) {
+void launch_rm_to_cm_bf16(const double* A, int ld, int k, void* B, long long ldb, long long N, cudaStream_t s) {
     dim3 g((unsigned)((N + 31) / 32), (k + 31) / 32);
-    k_rm_to_cm_bf16<<<g, dim3(32, 8), 0, s>>>(A, ld, k, static_cast<__nv_bfloat16*>(B), N);
+    k_rm_to_cm_bf16<<<g, dim3(32, 8), 0, s>>>(A, ld, k, static_cast<__nv_bfloat16*>(B), ldb, N);
 }
 
-void launch_restrict32(const Op<float>& op, const void* Qv, int k, const float2* v, const float2* z, int conj,
-                       float2* partials, int nblk, cudaStream_t s) {
+void launch_red_rows_bf16(const void* Q, long long ldq, int k, long long N, int n, void* Qr, long long ldr,
+                          cudaStream_t s) {
+    k_red_rows_bf16<<<4 * 152, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(Q), ldq, k, N, n,
+                                            static_cast<__nv_bfloat16*>(Qr), ldr);
+}
+
+int restrict32_red_blocks(long long N) {
+    const long long M = (N + 1) / 2;
+    const long long wtiles = ((M + RR_ROWS - 1) / RR_ROWS + 31) / 32;
+    const long long b = (wtiles + RR_T / 32 - 1) / (RR_T / 32);
+    return (int)(b < 4 * 152 ? (b < 1 ? 1 : b) : 4 * 152);
+}
+
+int launch_restrict32_red(const Op<float>& op, const void* Qr, long long ldr, int k, const float2* v,
+                          const float2* z, int conj, float2* partials, cudaStream_t s) {
+    const int nb = restrict32_red_blocks(op.N);
+    k_restrict32_red<<<nb, RR_T, 0, s>>>(op, static_cast<const __nv_bfloat16*>(Qr), ldr, k, v, z, conj, partials,
+                                         (op.N + 1) / 2);
+    return nb;
+}
+
+void launch_restrict32(const Op<float>& op, const void* Qv, long long ldq, int k, const float2* v, const float2* z,
+                       int conj, float2* partials, int nblk, cudaStream_t s) {
     const __nv_bfloat16* Q = static_cast<const __nv_bfloat16*>(Qv);
     long long rows = (op.N + nblk - 1) / nblk;
     const int kpw = (k + 7) / 8;
-#define RS_CASE(K) k_restrict32<K><<<nblk, RS_T, 0, s>>>(op, Q, k, v, z, conj, partials, rows)
+#define RS_CASE(K) k_restrict32<K><<<nblk, RS_T, 0, s>>>(op, Q, ldq, k, v, z, conj, partials, rows)
     if (kpw <= 1) RS_CASE(1);
     else if (kpw <= 2) RS_CASE(2);
     else if (kpw <= 4) RS_CASE(4);
@@ -1019,13 +1237,20 @@ void launch_restrict32(const Op<float>& op, const void* Qv, int k, const float2*
 }
 
 void launch_coarse_apply32(const float2* partials, int nblk, int k, const double2* Ainv, int conj, float2* y,
-                           cudaStream_t s) {
-    k_coarse32<<<1, 1024, 0, s>>>(partials, nblk, k, Ainv, conj, y);
+                           double2* cbuf, cudaStream_t s) {
+    k_coarse32_reduce<<<k, 64, 0, s>>>(partials, nblk, k, cbuf);
+    k_coarse32_gemv<<<k, 64, 0, s>>>(Ainv, k, conj, cbuf, y);
 }
 
-void launch_prolong32(const void* Q, int k, const float2* y, float2* z, long long N, cudaStream_t s) {
+void launch_prolong32(const void* Q, long long ldq, int k, const float2* y, float2* z, long long N, cudaStream_t s) {
+    const __nv_bfloat16* Qb = static_cast<const __nv_bfloat16*>(Q);
+    if ((reinterpret_cast<uintptr_t>(z) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Q) & 15u) == 0 && ldq % 8 == 0) {
+        const long long b = ((N + 7) / 8 + 255) / 256;
+        k_prolong32v<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Qb, ldq, k, y, z, N);
+        return;
+    }
     long long b = (N + 255) / 256;
-    k_prolong32<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(Q), k, y, z, N);
+    k_prolong32<<<(unsigned)(b < 8 * 152 ? b : 8 * 152), 256, 0, s>>>(Qb, ldq, k, y, z, N);
 }
 
 }  // namespace helm

@@ -25,7 +25,8 @@ def opts(method="fgmres", relax="jacobi", n_r=1, omega=0.6, correction="tb", tol
          restart=30, maxit=1000, conj=False) -> SolveOpts:
     m = {"relax": L.HELM_METHOD_RELAX, "fgmres": L.HELM_METHOD_FGMRES,
          "bicgstab": L.HELM_METHOD_BICGSTAB}[method]
-    r = {"none": L.HELM_RELAX_NONE, "jacobi": L.HELM_JACOBI, "rbgs": L.HELM_RBGS}[relax]
+    r = {"none": L.HELM_RELAX_NONE, "jacobi": L.HELM_JACOBI, "rbgs": L.HELM_RBGS, "sor": L.HELM_SOR,
+         "ssor": L.HELM_SSOR, "mg": L.HELM_MG}[relax]
     c = {"none": L.HELM_CORR_NONE, "tb": L.HELM_CORR_TB, "nonlinear": L.HELM_CORR_NONLINEAR}[correction]
     return SolveOpts(m, r, int(n_r), float(omega), c, float(tol), int(restart), int(maxit), int(bool(conj)))
 
@@ -75,6 +76,17 @@ class Problem:
     def set_profiling(self, on=True):
         self._check(self.lib.helm_set_profiling(self.h, int(bool(on))), "set_profiling")
 
+    def mg_setup(self, levels):
+        """Multigrid hierarchy of `levels` grids for the HELM_MG cycle (n odd down
+        to the coarsest level)."""
+        self._check(self.lib.helm_mg_setup(self.h, int(levels)), "mg_setup")
+
+    def set_wait_limit(self, polls=1 << 20, extra_arrivals=0):
+        """Bounded grid-barrier waits of the cooperative red-black cycle: polls
+        before a wait gives up, and arrivals added to every barrier's target
+        (> 0 injects a timeout for tests)."""
+        self._check(self.lib.helm_set_wait_limit(self.h, int(polls), int(extra_arrivals)), "set_wait_limit")
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.helm_destroy(self.h)
@@ -114,7 +126,7 @@ class Problem:
         return (r, nrm) if want_norm else r
 
     def relax(self, kind, f, x, sweeps=1, omega=0.6, conj=False):
-        k = {"jacobi": L.HELM_JACOBI, "rbgs": L.HELM_RBGS}[kind]
+        k = {"jacobi": L.HELM_JACOBI, "rbgs": L.HELM_RBGS, "sor": L.HELM_SOR, "ssor": L.HELM_SSOR}[kind]
         self._check(self.lib.helm_relax(self.h, k, float(omega), int(sweeps), _ptr(f), _ptr(x), int(conj),
                                         _dtype_code(x)), "relax")
         return x
@@ -239,6 +251,16 @@ class Problem:
         return st.as_dict()
 
 
+def _driver_version():
+    """CUDA driver version (e.g. 13000), the tile cache key's driver part."""
+    v = C.c_int(0)
+    try:
+        C.CDLL("libcuda.so.1").cuDriverGetVersion(C.byref(v))
+    except OSError:
+        return "unknown"
+    return v.value
+
+
 class Batch:
     """Many independent problems (HELM_MIXED Problems with a loaded trunk basis)
     solved together by batched FGMRES: one launch per phase over all problems."""
@@ -279,15 +301,17 @@ class Batch:
 
     def autotune(self, fs, o: SolveOpts | None = None, candidates=(256, 512, 1024, 2048, 4096), trial_iters=6,
                  cache=None):
-        """Pick the tile length by timing a few FGMRES steps for each candidate;
-        results are cached per GPU, driver, problem count and total size."""
+        """Pick the tile length by timing a few iterations of the given method for each
+        candidate; results are cached per GPU, driver version, method, problem count
+        and total size."""
         import json
         import os
         import time
         key = None
         if cache:
             prop = torch.cuda.get_device_properties(0)
-            key = f"{prop.name}|{torch.version.cuda}|{len(self.problems)}|{sum(P.N for P in self.problems)}"
+            key = (f"{prop.name}|driver {_driver_version()}|{o.method if o is not None else 1}|"
+                   f"{len(self.problems)}|{sum(P.N for P in self.problems)}")
             try:
                 table = json.load(open(cache))
                 if key in table:

@@ -60,6 +60,48 @@ def test_training_step_matches_oracle():
         assert np.allclose(moved[g > 1e-4], 1e-3, rtol=1e-2)
 
 
+def test_three_training_steps_match_oracle_adam():
+    """Three forward/backward/Adam steps on the same batch: after each step the
+    device parameters equal the oracle's (FP64 gradients of the oracle network at
+    the device's current parameters, then oracle Adam with bias correction at
+    t = 1, 2, 3; moments carried over)."""
+    from paper_2405_12380_gb300 import train
+    rng = np.random.default_rng(31)
+    net = train.DeepONet.init([30, 20, 12], [2, 10, 10, 6], seed=6)
+    X = rng.standard_normal((5, 30)).astype(np.float32)
+    Xc = rng.random((17, 2)).astype(np.float32)
+    Y = rng.standard_normal((5, 34)).astype(np.float32)
+    layers = net.branch + net.trunk
+    params = [[l.W.double().cpu().numpy(), l.b.double().cpu().numpy()] for l in layers]
+    moments = [[np.zeros_like(a) for a in pr] + [np.zeros_like(a) for a in pr] for pr in params]
+    lr = 2e-3
+    # entries whose oracle gradient stays clear of zero (an FP32 gradient of a
+    # near-zero FP64 one may have the other sign, and Adam moves both by ~lr)
+    clear = [[np.ones(a.shape, bool) for a in pr] for pr in params]
+    for t in (1, 2, 3):
+        nb = len(net.branch)
+        branch = [(w, b) for w, b in params[:nb]]
+        trunk = [(w, b) for w, b in params[nb:]]
+        pred, ba, ta_ = mlp.deeponet_forward(branch, trunk, X, Xc)
+        _, dpred = mlp.rel_l2(pred, Y.astype(np.float64))
+        gb, gt = mlp.deeponet_backward(branch, trunk, ba, ta_, dpred)
+        for q, (dW, db) in enumerate(gb + gt):
+            clear[q][0] &= np.abs(dW) > 1e-4
+            clear[q][1] &= np.abs(db) > 1e-4
+            mW, mb, vW, vb = moments[q]
+            params[q][0], mW, vW = mlp.adam_step(params[q][0], dW, mW, vW, t, lr=lr)
+            params[q][1], mb, vb = mlp.adam_step(params[q][1], db, mb, vb, t, lr=lr)
+            moments[q] = [mW, mb, vW, vb]
+        train.train_step(net, to_dev(X), to_dev(Xc), to_dev(Y), lr=lr)
+        torch.cuda.synchronize()
+        for l, (W, b), (cW, cb) in zip(layers, params, clear):
+            # a slip in Adam (betas swapped, a bias correction dropped) moves an
+            # entry by several percent of lr at t = 2
+            assert np.max(np.abs(l.W.double().cpu().numpy() - W)[cW]) < 5e-3 * lr, t
+            assert np.max(np.abs(l.b.double().cpu().numpy() - b)[cb], initial=0) < 5e-3 * lr, t
+            assert cW.mean() > 0.5
+
+
 def test_nonlinear_correction_matches_oracle():
     s = small_scene(3, 21)
     rng = np.random.default_rng(7)

@@ -91,3 +91,28 @@ def test_adjoint_96_against_oracle_data_and_central_differences():
             fd = (vals[0] - vals[1]) / (2 * eps)
             an = g[l].real if part == "re" else g[l].imag
             assert abs(fd - an) <= 2e-3 * max(abs(fd), 1e-2 * gmax), (l, part, fd, an)
+
+
+def test_batched_bicgstab_config4_problems_at_full_size():
+    """The first eight problems of the batched workload (uneven grids 48^3-128^3, k in
+    [8, 32], cube / sphere / submarine scatterers, p = 32), solved together by the
+    batched complex64 BiCGStab (3 red-black sweeps + trunk basis) to 1e-6; each
+    solution is checked on the oracle's own FP64 residual."""
+    import paper_2405_12380_gb300 as hm
+    scs = scenes.batch_scenes(0, count=64)[:8]
+    probs, fs = [], []
+    for sc in scs:
+        P = hm.Problem(3, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, precision="mixed")
+        P.don_load(sc.trunk, sc.p, tau=1e-6)
+        probs.append(P)
+        fs.append(P.rhs(to_dev(sc.src), to_dev(sc.g)))
+    B = hm.Batch(probs)
+    xs, st = B.solve(fs, None, hm.opts("bicgstab", "rbgs", 3, tol=1e-6, maxit=20000))
+    for sc, x, s in zip(scs, xs, st):
+        assert s["status"] == 0, (sc.n, sc.k0, s["status_name"], s["iters"], s["rel_res"])
+        A = assemble.assemble(3, sc.n, assemble.k2_field(3, sc.n, sc.k0, sc.layer_cells, sc.layer_strength),
+                              sc.mask)
+        b = assemble.rhs(3, sc.n, sc.mask, sc.src, sc.g)
+        res = np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b)
+        assert res <= 1.0001e-6, (sc.n, res)
+    B.close()

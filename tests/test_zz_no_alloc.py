@@ -2,7 +2,10 @@
 allocate device memory (no handle, scratch in a fixed device array).
 
 Checked through the C ABI against helm_residual, the handle-based entry point,
-on two calls in a row (the second call reuses the scratch the first one left)."""
+and against the oracle's b - A x, on two calls in a row (the second call reuses
+the scratch the first one left): with the layer formula (2D, odd and even 3D n,
+so that both 3D kernel families of the handle run) and with a stored k^2 field
+(scaled layer profile)."""
 import ctypes
 
 import numpy as np
@@ -13,13 +16,23 @@ from tests.gpu_common import need_gpu, problem_for, rel, small_scene, to_dev, to
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dim,n", [(2, 45), (3, 37)])
-def test_noalloc_residual_matches_handle_residual(dim, n):
+@pytest.mark.parametrize("dim,n,field", [(2, 45, False), (3, 37, False), (3, 36, False), (2, 45, True),
+                                         (3, 36, True)])
+def test_noalloc_residual_matches_handle_and_oracle(dim, n, field):
     need_gpu()
+    from oracle import assemble
     from paper_2405_12380_gb300 import _lib as L
     lib = L.lib()
     s = small_scene(dim, n)
-    P = problem_for(s)
+    A = s["A"]
+    k2 = k2d = None
+    if field:
+        # stored k^2: the layer profile scaled per node by 1 + 5% of a seeded field
+        scale = 1.0 + 0.05 * s["rng"].uniform(-1, 1, n ** dim)
+        k2 = assemble.k2_field(dim, n, s["k0"], s["cells"], 0.5, scale)
+        A = assemble.assemble(dim, n, k2, s["mask"])
+        k2d = to_dev(k2)
+    P = problem_for(s, k2=k2d)
     stream = torch.cuda.current_stream().cuda_stream
     mask = to_dev(s["mask"])
     for call in range(2):
@@ -30,13 +43,19 @@ def test_noalloc_residual_matches_handle_residual(dim, n):
             r = torch.empty_like(xd)
             nrm = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
             st = lib.helm_residual_noalloc(dim, n, s["k0"], s["cells"], 0.5, ctypes.c_void_p(mask.data_ptr()),
-                                           None, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(xd.data_ptr()),
+                                           None if k2d is None else ctypes.c_void_p(k2d.data_ptr()),
+                                           ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(xd.data_ptr()),
                                            ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
                                            conj, ctypes.c_void_p(stream))
             assert st == 0, L.STATUS_NAMES.get(st, st)
             torch.cuda.synchronize()
-            assert rel(r.cpu().numpy(), r_ref.cpu().numpy()) <= 1e-13
+            rh = r.cpu().numpy()
+            assert rel(rh, r_ref.cpu().numpy()) <= 1e-13
             assert abs(nrm.item() - n_ref.item()) <= 1e-13 * n_ref.item()
+            Ac = A.conj() if conj else A
+            ro = s["b"] - Ac @ x
+            assert rel(rh, ro) <= 1e-13, rel(rh, ro)
+            assert abs(nrm.item() - np.vdot(ro, ro).real) <= 1e-12 * np.vdot(ro, ro).real
 
 
 def test_noalloc_rejects_oversized_and_unmasked():
