@@ -122,6 +122,24 @@ typedef struct {
 helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer_strength,
                         const uint8_t* mask, const double* k2, int precision,
                         helm_handle** out);
+/* The paper's own boundary-value problem (Eq. 1): no absorbing layer and no
+ * Dirichlet ring; every outer-boundary node is an unknown whose row comes from
+ * eliminating the ghost node of a central difference -- first-order Sommerfeld
+ * condition du/dn - i k0 u = 0 on every face, except, with neumann_top, the top
+ * face (y = 1 in 2D, z = 1 in 3D) where du/dn = g (incoming wave, data g passed to
+ * helm_rhs).  A row of a node on b faces is scaled by 2^-b, which keeps A complex
+ * symmetric: fluid neighbours couple with weight h^-2 2^-|F(l) and F(m)| (F the set
+ * of faces a node lies on), and the diagonal is 2^-b (k^2 - 2d h^-2 + 2 i k0 a / h)
+ * with a the node's Sommerfeld faces.  mask [dev] N bytes, 1 = Dirichlet (the
+ * scatterer; the outer ring is NOT masked); k2 [dev] N complex128 or NULL (k0^2).
+ * helm_rhs on such a handle gives b_l = g_l on masked nodes and, on fluid nodes,
+ * 2^-b (src_l - (2/h) g_l [l on the Neumann face]) minus the weighted Dirichlet
+ * values of masked neighbours.  FP64 handles; the trunk-basis, relaxation and
+ * Krylov calls work as on helm_create handles (through the generic kernels);
+ * helm_layer_k2, helm_set_k2, helm_k2_gradient and helm_mg_setup return
+ * HELM_BAD_ARG. */
+helm_status helm_create_bvp(int dim, int n, double k0, const uint8_t* mask, const double* k2, int neumann_top,
+                            helm_handle** out);
 helm_status helm_destroy(helm_handle* h);
 /* stream: a cudaStream_t (NULL = legacy default stream). */
 helm_status helm_set_stream(helm_handle* h, void* stream);

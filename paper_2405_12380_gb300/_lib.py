@@ -47,6 +47,7 @@ H = C.c_void_p
 
 SIGNATURES = {
     "helm_create": (i32, [i32, i32, f64, i32, f64, vp, vp, i32, C.POINTER(H)]),
+    "helm_create_bvp": (i32, [i32, i32, f64, vp, vp, i32, C.POINTER(H)]),
     "helm_destroy": (i32, [H]),
     "helm_set_stream": (i32, [H, vp]),
     "helm_last_error": (C.c_char_p, [H]),

@@ -1404,6 +1404,7 @@ helm_status helm_batch_set_tile(helm_batch* B, int tile_rows, int grid) {
 
 helm_status helm_batch_solve(helm_batch* B, const helm_solve_opts* o, const double* const* f, double* const* x,
                              helm_stats* stats) {
+    NvtxRange nvtx("helm_batch_solve");
     if (!B || !o || !f || !x) return HELM_BAD_ARG;
     if (o->method == HELM_METHOD_BICGSTAB) return batch_bicgstab(B, o, f, x, stats);
     if (o->method != HELM_METHOD_FGMRES || o->restart < 1 || o->restart > kMaxRestart || o->conj ||

@@ -428,6 +428,7 @@ helm_status vcycle(helm_handle* h, int level, helm_handle* H, const helm_solve_o
 }
 
 helm_status precond(helm_handle* h, const helm_solve_opts* o, const double2* r, double2* z, int conj) {
+    NvtxRange nvtx("hybrid cycle");
     if (h->precision == HELM_MIXED && o->relax == HELM_MG)
         return fail(h, HELM_BAD_ARG, "the multigrid cycle runs on FP64 handles");
     if (h->precision == HELM_MIXED) {
@@ -620,6 +621,7 @@ helm_status solve_fgmres(helm_handle* h, const helm_solve_opts* o, const double2
             ++st->precond_applies;
             ++st->matvecs;
             // CGS2: h = V^H w, w -= V h, h2 = V^H w, w -= V h2, h += h2
+            NvtxRange nvtx_a("Arnoldi CGS2 + Givens");
             launch_mdot(h->V, j + 1, w, N, h->hpart, s);
             launch_mdot_finalize(h->hpart, kRedBlocks, j + 1, Hcol, 0, nullptr, s);
             launch_mupdate(h->V, j + 1, Hcol, -1.0, w, N, nullptr, s);
@@ -1018,6 +1020,7 @@ void fill_tables(helm_handle* h) {
     o.mask = f.mask = h->mask;
     o.lidx = f.lidx = h->lidx;
     o.nbm = f.nbm = h->nbm;
+    o.face = f.face = h->face;
     for (int m = 0; m <= kMaxLayerCells; ++m) {
         double eta = (h->L > 0 && m <= h->L) ? (double)m / (double)h->L : 0.0;
         double im = h->k0 * h->k0 * ((h->strength * eta) * eta);
@@ -1176,13 +1179,86 @@ helm_status helm_create(int dim, int n, double k0, int layer_cells, double layer
     return HELM_OK;
 }
 
+helm_status helm_create_bvp(int dim, int n, double k0, const uint8_t* mask, const double* k2, int neumann_top,
+                            helm_handle** out) {
+    helm_handle* h = nullptr;
+    if (!out) return HELM_BAD_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || n < 4 || !mask || !std::isfinite(k0) || k0 < 0) return HELM_BAD_ARG;
+    long long N = 1;
+    for (int a = 0; a < dim; ++a) N *= n;
+    if (N >= (1LL << 31) || n > 65535) return HELM_BAD_ARG;
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return HELM_NO_DEVICE;
+    }
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return HELM_NO_DEVICE;
+    if (prop.major * 10 + prop.minor != 103) return HELM_NO_DEVICE;
+    h = new helm_handle();
+    h->dim = dim;
+    h->n = n;
+    h->N = N;
+    h->L = 0;
+    h->k0 = k0;
+    h->strength = 0.0;
+    h->precision = HELM_FP64;
+    h->bvp = 1;
+    h->neumann_top = neumann_top ? 1 : 0;
+    h->h = 1.0 / (n - 1);
+    h->hinv2 = 1.0 / (h->h * h->h);
+    auto bail = [&](helm_status st) {
+        helm_destroy(h);
+        return st;
+    };
+    if (dalloc(h, &h->mask, (size_t)N) != HELM_OK) return bail(HELM_OUT_OF_MEMORY);
+    if (cudaMemcpy(h->mask, mask, (size_t)N, cudaMemcpyDefault) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    h->red_len = std::max<long long>(apply_grid_blocks(dim, n), 4LL * kRedBlocks) * 2;
+    if (dalloc(h, &h->red, (size_t)h->red_len) != HELM_OK || dalloc(h, &h->sc, (size_t)S_NSLOTS) != HELM_OK ||
+        dalloc(h, &h->dflag, 8) != HELM_OK || dalloc(h, &h->counter, 4) != HELM_OK ||
+        dalloc(h, &h->fparts, (size_t)4 * std::max<long long>(std::max(apply_grid_blocks(dim, n),
+                                                                        bicg_grid_blocks(dim, n)),
+                                                               kRedBlocks)) != HELM_OK)
+        return bail(HELM_OUT_OF_MEMORY);
+    if (cudaMemset(h->counter, 0, 4 * sizeof(unsigned)) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    if (cudaMemset(h->dflag, 0, 8 * sizeof(int)) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    if (cudaMallocHost((void**)&h->hpin, sizeof(double2) * S_NSLOTS) != cudaSuccess ||
+        cudaMallocHost((void**)&h->hring, 2 * sizeof(double2) * S_NSLOTS) != cudaSuccess)
+        return bail(HELM_OUT_OF_MEMORY);
+    for (auto& e : h->evring)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    if (cudaMemset(h->sc, 0, sizeof(double2) * S_NSLOTS) != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    if (dalloc(h, &h->k2, (size_t)N) != HELM_OK || dalloc(h, &h->invd, (size_t)N) != HELM_OK ||
+        dalloc(h, &h->k2f, (size_t)N) != HELM_OK || dalloc(h, &h->invdf, (size_t)N) != HELM_OK ||
+        dalloc(h, &h->lidx, (size_t)N) != HELM_OK || dalloc(h, &h->nbm, (size_t)N) != HELM_OK ||
+        dalloc(h, &h->face, (size_t)N) != HELM_OK)
+        return bail(HELM_OUT_OF_MEMORY);
+    fill_tables(h);
+    launch_face_code(h->op64, h->face, nullptr);
+    launch_layer_index(h->op64, h->lidx, nullptr);
+    launch_nbr_code(h->op64, h->nbm, nullptr);
+    // the scaled boundary diagonals as an effective k^2 field, then 1/diag
+    launch_bvp_k2(h->op64, reinterpret_cast<const double2*>(k2), k0, h->neumann_top, h->k2, nullptr);
+    launch_invd_field(h->op64, h->invd, nullptr);
+    launch_cvt_f64_to_f32(h->k2, h->k2f, N, nullptr);
+    launch_cvt_f64_to_f32(h->invd, h->invdf, N, nullptr);
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(HELM_CUDA_ERROR);
+    cudaEventCreate(&h->ev0);
+    cudaEventCreate(&h->ev1);
+    *out = h;
+    return HELM_OK;
+}
+
 helm_status helm_destroy(helm_handle* h) {
     if (!h) return HELM_BAD_ARG;
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (helm_handle* c : h->mg) helm_destroy(c);
     h->mg.clear();
-    dfree(h->mask); dfree(h->lidx); dfree(h->nbm); dfree(h->k2); dfree(h->invd); dfree(h->k2f); dfree(h->invdf);
+    dfree(h->mask); dfree(h->lidx); dfree(h->nbm); dfree(h->face); dfree(h->k2); dfree(h->invd); dfree(h->k2f);
+    dfree(h->invdf);
     dfree(h->red); dfree(h->sc); dfree(h->dflag); dfree(h->counter); dfree(h->fparts);
     if (h->hpin) cudaFreeHost(h->hpin);
     if (h->hring) cudaFreeHost(h->hring);
@@ -1229,12 +1305,18 @@ helm_status helm_info(const helm_handle* h, long long* N, double* hstep) {
 
 helm_status helm_layer_k2(helm_handle* h, const double* scale, double* k2_out) {
     if (!h || !k2_out) return fail(h, HELM_BAD_ARG, "null argument");
+    if (h->bvp) return fail(h, HELM_BAD_ARG, "no absorbing layer on an outer-boundary (helm_create_bvp) handle");
     launch_layer_k2(h->op64, h->k0, h->strength, scale, reinterpret_cast<double2*>(k2_out), h->stream);
     CKL();
     return HELM_OK;
 }
 
 helm_status helm_rhs(helm_handle* h, const double* src, const double* g, double* b) {
+    if (h && h->bvp && src && g && b) {
+        launch_rhs_bvp(h->op64, (const double2*)src, (const double2*)g, h->neumann_top, (double2*)b, h->stream);
+        CKL();
+        return HELM_OK;
+    }
     if (!h || !src || !g || !b) return fail(h, HELM_BAD_ARG, "null argument");
     launch_rhs(h->op64, reinterpret_cast<const double2*>(src), reinterpret_cast<const double2*>(g),
                reinterpret_cast<double2*>(b), h->stream);
@@ -1312,6 +1394,7 @@ helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const
 
 helm_status don_load(helm_handle* h, const double* weights, const int* widths, int n_layers, int act, int p,
                      double tau) {
+    NvtxRange nvtx("don_load: trunk basis setup");
     if (!h || !weights || !widths) return fail(h, HELM_BAD_ARG, "null argument");
     if (act != HELM_ACT_TANH) return fail(h, HELM_BAD_ARG, "activation");
     drop_graphs(h);
@@ -1524,8 +1607,10 @@ helm_status helm_precond(helm_handle* h, const helm_solve_opts* opts, const void
 }
 
 helm_status helm_mg_setup(helm_handle* h, int levels) {
+    NvtxRange nvtx("helm_mg_setup");
     if (!h) return HELM_BAD_ARG;
     if (levels < 1 || levels > 8) return fail(h, HELM_BAD_ARG, "levels must be 1..8");
+    if (h->bvp) return fail(h, HELM_BAD_ARG, "the multigrid hierarchy needs the Dirichlet-ring operator");
     if (h->precision != HELM_FP64) return fail(h, HELM_BAD_ARG, "the multigrid cycle runs on FP64 handles");
     for (helm_handle* c : h->mg) helm_destroy(c);
     h->mg.clear();
@@ -1584,6 +1669,9 @@ helm_status helm_set_wait_limit(helm_handle* h, unsigned polls, unsigned extra_a
 
 helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv, void* xv, helm_stats* stats,
                        double* res_hist, int hist_len) {
+    NvtxRange nvtx(o && o->method == HELM_METHOD_FGMRES ? "helm_solve: FGMRES"
+                   : o && o->method == HELM_METHOD_BICGSTAB ? "helm_solve: BiCGStab"
+                                                            : "helm_solve: relaxation");
     if (!h || !fv || !xv) return fail(h, HELM_BAD_ARG, "null argument");
     TRY(check_opts(h, o));
     const double2* f = (const double2*)fv;
@@ -1666,6 +1754,7 @@ helm_status helm_receivers_adjoint(helm_handle* h, int nrec, const int* idx, con
 
 helm_status helm_k2_gradient(helm_handle* h, const double* lambda, const double* u, double* grad) {
     if (!h || !lambda || !u || !grad) return fail(h, HELM_BAD_ARG, "null argument");
+    if (h->bvp) return fail(h, HELM_BAD_ARG, "k^2 gradients need the Dirichlet-ring operator");
     launch_k2_gradient(h->N, h->mask, (const double2*)lambda, (const double2*)u, (double2*)grad, h->stream);
     CKL();
     return HELM_OK;
@@ -1673,6 +1762,7 @@ helm_status helm_k2_gradient(helm_handle* h, const double* lambda, const double*
 
 helm_status helm_set_k2(helm_handle* h, const double* k2) {
     if (!h || !k2) return fail(h, HELM_BAD_ARG, "null argument");
+    if (h->bvp) return fail(h, HELM_BAD_ARG, "an outer-boundary handle takes its k^2 at creation");
     drop_graphs(h);
     const long long N = h->N;
     if (!h->k2) {

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -18,6 +19,15 @@
 #include "../../include/helm.h"
 
 namespace helm {
+
+// NVTX range for the phases of a call (setup, solve, preconditioner, Arnoldi step);
+// free when no profiler is attached
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxLayerCells = 64;
 constexpr int kMaxP = 256;          // trunk basis functions
@@ -68,6 +78,11 @@ struct Op {
     const uint8_t* nbm;      // per-node neighbour code: bit q = neighbour q fluid, 0x80 = masked node
     const C* k2;             // stored k^2 field or nullptr
     const C* invd;           // per-node 1/diag for the stored field, or nullptr
+    // Sommerfeld / Neumann outer boundary (helm_create_bvp) or nullptr: per node
+    // (number of boundary faces b << 4) | (bit a: the node lies on a face normal to
+    // axis a); the row is scaled by 2^-b and a neighbour across axis a weighs
+    // 2^-(b - [node on an axis-a face]) (symmetric scaling of the ghost-point rows)
+    const uint8_t* face;
     R im[kMaxLayerCells + 1];        // Im k^2 by layer index
     C invd_tab[kMaxLayerCells + 1];  // 1/(diag) by layer index (fluid nodes)
 };
@@ -113,6 +128,13 @@ void launch_invd_field(const Op<double>& op, double2* invd, cudaStream_t s);
 void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s);
 void launch_layer_index(const Op<double>& op, uint8_t* lidx, cudaStream_t s);
 void launch_nbr_code(const Op<double>& op, uint8_t* code, cudaStream_t s);
+// outer-boundary problem: face bytes (see Op::face), the effective k^2 field that
+// makes diag_of return the scaled boundary diagonal, and the right-hand side
+void launch_face_code(const Op<double>& op, uint8_t* face, cudaStream_t s);
+void launch_bvp_k2(const Op<double>& op, const double2* k2phys, double k0, int neumann_top, double2* k2eff,
+                   cudaStream_t s);
+void launch_rhs_bvp(const Op<double>& op, const double2* src, const double2* g, int neumann_top, double2* b,
+                    cudaStream_t s);
 // BiCGStab fused kernels (reduction + scalar update in the last block; counter zero between uses)
 void launch_apply_bicg(const Op<double>& op, int mode, const double2* x, double2* y, const double2* w, int conj,
                        double2* sc, double* parts, unsigned* counter, cudaStream_t s);
@@ -292,6 +314,8 @@ struct helm_handle {
     uint8_t* mask = nullptr;
     uint8_t* lidx = nullptr;
     uint8_t* nbm = nullptr;
+    uint8_t* face = nullptr;        // outer-boundary problem (helm_create_bvp): face bytes
+    int bvp = 0, neumann_top = 0;
     double2* k2 = nullptr;
     double2* invd = nullptr;
     float2* k2f = nullptr;

@@ -74,6 +74,20 @@ __device__ __forceinline__ typename CT<R>::T nbr_sum(const Op<R>& op, const type
     const C b = (code & 2u) ? x[l + 1] : z;
     const C c = (code & 4u) ? x[l - sy] : z;
     const C d = (code & 8u) ? x[l + sy] : z;
+    if (op.face) {
+        // Sommerfeld / Neumann boundary rows: axis a weighs 2^-(b - [on an axis-a face])
+        const unsigned fc = op.face[l];
+        const int nb = (int)(fc >> 4);
+        const R wx = ldexp((R)1, -(nb - (int)(fc & 1u))), wy = ldexp((R)1, -(nb - (int)((fc >> 1) & 1u)));
+        C s = cadd(cscale(wx, cadd(a, b)), cscale(wy, cadd(c, d)));
+        if (op.dim == 3) {
+            const R wz = ldexp((R)1, -(nb - (int)((fc >> 2) & 1u)));
+            const C e = (code & 16u) ? x[l - sz] : z;
+            const C f = (code & 32u) ? x[l + sz] : z;
+            s = cadd(s, cscale(wz, cadd(e, f)));
+        }
+        return s;
+    }
     C s = cadd(cadd(a, b), cadd(c, d));
     if (op.dim == 3) {
         const C e = (code & 16u) ? x[l - sz] : z;
@@ -1137,6 +1151,17 @@ __global__ void k_nbr_code(Op<double> op, uint8_t* __restrict__ code) {
     unsigned c = 0;
     if (op.mask[l]) {
         c = kMasked;
+    } else if (op.face) {
+        // outer-boundary problem: a neighbour counts if it is in the grid and unmasked
+        const int n = op.n;
+        if (i > 0 && !op.mask[l - 1]) c |= 1u;
+        if (i < n - 1 && !op.mask[l + 1]) c |= 2u;
+        if (j > 0 && !op.mask[l - sy]) c |= 4u;
+        if (j < n - 1 && !op.mask[l + sy]) c |= 8u;
+        if (op.dim == 3) {
+            if (k > 0 && !op.mask[l - sz]) c |= 16u;
+            if (k < n - 1 && !op.mask[l + sz]) c |= 32u;
+        }
     } else {
         // fluid nodes are interior (the outer ring is masked), so all neighbours exist
         if (!op.mask[l - 1]) c |= 1u;
@@ -1149,6 +1174,84 @@ __global__ void k_nbr_code(Op<double> op, uint8_t* __restrict__ code) {
         }
     }
     code[l] = (uint8_t)c;
+}
+
+// face byte of a node: (number of boundary faces << 4) | axis bits
+__global__ void k_face_code(Op<double> op, uint8_t* __restrict__ face) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const int n = op.n;
+    const unsigned ax = (i == 0 || i == n - 1) ? 1u : 0u, ay = (j == 0 || j == n - 1) ? 1u : 0u;
+    const unsigned az = (op.dim == 3 && (k == 0 || k == n - 1)) ? 1u : 0u;
+    face[l] = (uint8_t)(((ax + ay + az) << 4) | ax | (ay << 1) | (az << 2));
+}
+
+// effective k^2 of the outer-boundary problem: with it diag_of returns the scaled
+// boundary diagonal 2^-b (k^2 - 2d h^-2 + 2 i k0 a / h), a = number of Sommerfeld
+// faces of the node (all its faces but the Neumann top face y = 1 in 2D, z = 1 in 3D)
+__global__ void k_bvp_k2(Op<double> op, const double2* __restrict__ k2phys, double k0, int neumann_top,
+                         double2* __restrict__ k2eff) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    const int n = op.n;
+    const int top = op.dim == 3 ? (k == n - 1) : (j == n - 1);
+    const int nb = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (op.dim == 3 ? (k == 0) + (k == n - 1) : 0);
+    const int a = nb - (neumann_top && top ? 1 : 0);
+    const double sigma = ldexp(1.0, -nb), h = sqrt(1.0 / op.hinv2), two_d = 2.0 * op.dim * op.hinv2;
+    const double2 kp = k2phys ? k2phys[l] : make_double2(k0 * k0, 0.0);
+    // K - 2d h^-2 = sigma (k^2 - 2d h^-2) + i sigma 2 k0 a / h
+    k2eff[l] = make_double2(sigma * (kp.x - two_d) + two_d, sigma * (kp.y + 2.0 * k0 * a / h));
+}
+
+// right-hand side of the outer-boundary problem: masked nodes carry the Dirichlet
+// value g; a fluid node gets 2^-b (src - (2 / h) g [on the Neumann top face]) minus the
+// weighted Dirichlet values of its masked neighbours
+__global__ void k_rhs_bvp(Op<double> op, const double2* __restrict__ src, const double2* __restrict__ g,
+                          int neumann_top, double2* __restrict__ b) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= op.n || j >= op.n) return;
+    const long long l = i + (long long)op.n * (j + (long long)op.n * k);
+    if (op.mask[l]) {
+        b[l] = g[l];
+        return;
+    }
+    const int n = op.n;
+    const unsigned fc = op.face[l];
+    const int nb = (int)(fc >> 4);
+    const double sigma = ldexp(1.0, -nb), h = sqrt(1.0 / op.hinv2);
+    const int top = op.dim == 3 ? (k == n - 1) : (j == n - 1);
+    double2 v = src[l];
+    if (neumann_top && top) {
+        v.x -= 2.0 / h * g[l].x;
+        v.y -= 2.0 / h * g[l].y;
+    }
+    v = cscale(sigma, v);
+    const long long sy = n, sz = (long long)n * n;
+    const double wx = ldexp(1.0, -(nb - (int)(fc & 1u))), wy = ldexp(1.0, -(nb - (int)((fc >> 1) & 1u)));
+    const double wz = ldexp(1.0, -(nb - (int)((fc >> 2) & 1u)));
+    auto lift = [&](bool exists, long long m, double w) {
+        if (exists && op.mask[m]) {
+            v.x -= op.hinv2 * w * g[m].x;
+            v.y -= op.hinv2 * w * g[m].y;
+        }
+    };
+    lift(i > 0, l - 1, wx);
+    lift(i < n - 1, l + 1, wx);
+    lift(j > 0, l - sy, wy);
+    lift(j < n - 1, l + sy, wy);
+    if (op.dim == 3) {
+        lift(k > 0, l - sz, wz);
+        lift(k < n - 1, l + sz, wz);
+    }
+    b[l] = v;
 }
 
 __global__ void k_check_ring(Op<double> op, int* bad) {
@@ -1199,7 +1302,7 @@ bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr
 
 // the complex64 pair kernels apply: 3D, tables present, n even, 16-byte aligned vectors
 bool pair_ok(const Op<float>& op, const void* a, const void* b, const void* c) {
-    return op.dim == 3 && op.nbm && op.lidx && (op.n % 2) == 0 && aligned16(a) && aligned16(b) && aligned16(c) &&
+    return op.dim == 3 && op.nbm && op.lidx && !op.face && (op.n % 2) == 0 && aligned16(a) && aligned16(b) && aligned16(c) &&
            aligned16(op.k2) && aligned16(op.invd);
 }
 
@@ -1237,7 +1340,7 @@ int launch_apply(const Op<R>& op, const typename CT<R>::T* x, const typename CT<
     }
     const int zc = apply_zc(op.dim, op.n);
     dim3 g = grid_for(op.dim, op.n, 1, zc), b(BX, BY);
-    if (op.dim == 3 && op.nbm && op.lidx) {
+    if (op.dim == 3 && op.nbm && op.lidx && !op.face) {
         if (resid) {
             if (partials) k_apply_z<R, true, true><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
             else k_apply_z<R, true, false><<<g, b, 0, s>>>(op, zc, x, f, y, partials, conj);
@@ -1403,6 +1506,18 @@ void launch_layer_index(const Op<double>& op, uint8_t* lidx, cudaStream_t s) {
 
 void launch_nbr_code(const Op<double>& op, uint8_t* code, cudaStream_t s) {
     k_nbr_code<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, code);
+}
+
+void launch_face_code(const Op<double>& op, uint8_t* face, cudaStream_t s) {
+    k_face_code<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, face);
+}
+void launch_bvp_k2(const Op<double>& op, const double2* k2phys, double k0, int neumann_top, double2* k2eff,
+                   cudaStream_t s) {
+    k_bvp_k2<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, k2phys, k0, neumann_top, k2eff);
+}
+void launch_rhs_bvp(const Op<double>& op, const double2* src, const double2* g, int neumann_top, double2* b,
+                    cudaStream_t s) {
+    k_rhs_bvp<<<grid_for(op.dim, op.n), dim3(BX, BY), 0, s>>>(op, src, g, neumann_top, b);
 }
 
 void launch_check_ring(const Op<double>& op, int* bad, cudaStream_t s) {

@@ -275,13 +275,30 @@ __global__ void __launch_bounds__(256) k_apply_columns(Op<double> op, const doub
         double re = 0, im = 0;
         if (!op.mask[l]) {
             double s = 0;
-            if (!op.mask[l - 1]) s += Q[(l - 1) * ldq + c];
-            if (!op.mask[l + 1]) s += Q[(l + 1) * ldq + c];
-            if (!op.mask[l - sy]) s += Q[(l - sy) * ldq + c];
-            if (!op.mask[l + sy]) s += Q[(l + sy) * ldq + c];
-            if (op.dim == 3) {
-                if (!op.mask[l - sz]) s += Q[(l - sz) * ldq + c];
-                if (!op.mask[l + sz]) s += Q[(l + sz) * ldq + c];
+            if (op.face) {
+                // Sommerfeld / Neumann outer boundary: neighbour code of the handle and
+                // the symmetric face weights (see Op::face)
+                const unsigned code = op.nbm[l], fc = op.face[l];
+                const int nb = (int)(fc >> 4);
+                const double wx = ldexp(1.0, -(nb - (int)(fc & 1u))), wy = ldexp(1.0, -(nb - (int)((fc >> 1) & 1u)));
+                const double wz = ldexp(1.0, -(nb - (int)((fc >> 2) & 1u)));
+                if (code & 1u) s += wx * Q[(l - 1) * ldq + c];
+                if (code & 2u) s += wx * Q[(l + 1) * ldq + c];
+                if (code & 4u) s += wy * Q[(l - sy) * ldq + c];
+                if (code & 8u) s += wy * Q[(l + sy) * ldq + c];
+                if (op.dim == 3) {
+                    if (code & 16u) s += wz * Q[(l - sz) * ldq + c];
+                    if (code & 32u) s += wz * Q[(l + sz) * ldq + c];
+                }
+            } else {
+                if (!op.mask[l - 1]) s += Q[(l - 1) * ldq + c];
+                if (!op.mask[l + 1]) s += Q[(l + 1) * ldq + c];
+                if (!op.mask[l - sy]) s += Q[(l - sy) * ldq + c];
+                if (!op.mask[l + sy]) s += Q[(l + sy) * ldq + c];
+                if (op.dim == 3) {
+                    if (!op.mask[l - sz]) s += Q[(l - sz) * ldq + c];
+                    if (!op.mask[l + sz]) s += Q[(l + sz) * ldq + c];
+                }
             }
             double dre, dim_;
             if (op.k2) {

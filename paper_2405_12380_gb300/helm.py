@@ -46,7 +46,12 @@ def _dtype_code(t):
 class Problem:
     """One discretised Helmholtz problem (helm_create) on the current CUDA device."""
 
-    def __init__(self, dim, n, k0, mask, layer_cells=8, layer_strength=0.5, k2=None, precision="fp64"):
+    def __init__(self, dim, n, k0, mask, layer_cells=8, layer_strength=0.5, k2=None, precision="fp64",
+                 boundary="dirichlet", neumann_top=True):
+        """boundary "dirichlet": the outer ring is masked and an absorbing layer of
+        layer_cells cells damps the waves (helm_create); "sommerfeld": the paper's
+        first-order absorbing condition on the outer faces, with the Neumann
+        incoming-wave face on top when neumann_top (helm_create_bvp)."""
         self.lib = L.lib()
         self.dim, self.n = int(dim), int(n)
         self.N = self.n ** self.dim
@@ -57,8 +62,12 @@ class Problem:
             k2t = torch.as_tensor(k2).to(dev, torch.complex128).reshape(-1).contiguous()
         prec = {"fp64": L.HELM_FP64, "mixed": L.HELM_MIXED}[precision]
         h = C.c_void_p()
-        st = self.lib.helm_create(self.dim, self.n, float(k0), int(layer_cells), float(layer_strength),
-                                  _ptr(self.mask), _ptr(k2t), prec, C.byref(h))
+        if boundary == "sommerfeld":
+            st = self.lib.helm_create_bvp(self.dim, self.n, float(k0), _ptr(self.mask), _ptr(k2t),
+                                          int(bool(neumann_top)), C.byref(h))
+        else:
+            st = self.lib.helm_create(self.dim, self.n, float(k0), int(layer_cells), float(layer_strength),
+                                      _ptr(self.mask), _ptr(k2t), prec, C.byref(h))
         if st != 0:
             raise HelmError(st, "helm_create")
         self.h = h

@@ -9,9 +9,12 @@ normalised by ||f|| (the correction is applied as s * DeepONet(r / s)).
 Network: branch [2N, hidden..., 2p] with ReLU, trunk [d, hidden..., p] with
 tanh, output u_l = sum_j b_re,j T_j(x_l) + i sum_j b_im,j T_j(x_l); loss: relative
 L2 on a random subset of nodes per step; Adam (App. B: constant learning rate).
-Every forward, backward and optimiser step runs in libhelm's FP32 kernels
-(nn_gemm, nn_bias_act, nn_act_backward, nn_bias_grad, nn_rel_l2, nn_adam,
-nn_gather); torch only provides device buffers.
+Every forward, backward and optimiser step runs in libhelm's kernels (nn_gemm,
+nn_bias_act, nn_act_backward, nn_bias_grad, nn_rel_l2, nn_adam, nn_gather);
+torch only provides device buffers.  The dense-layer products run in FP32 on the
+CUDA cores, or -- set_tensor_cores(True) -- with BF16 operands and FP32
+accumulation on the tcgen05 tensor cores (nn_gemm_bf16; master weights, Adam and
+the loss stay FP32).
 """
 from __future__ import annotations
 
@@ -28,6 +31,20 @@ from . import _lib as L
 
 def _p(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+_TENSOR_CORES = False
+
+
+def set_tensor_cores(on: bool):
+    """Dense-layer products of training on the tcgen05 tensor cores (BF16 operands,
+    FP32 accumulation) instead of the FP32 CUDA-core GEMM."""
+    global _TENSOR_CORES
+    _TENSOR_CORES = bool(on)
+
+
+def _gemm(lib, *args):
+    return (lib.nn_gemm_bf16 if _TENSOR_CORES else lib.nn_gemm)(*args)
 
 
 def _ck(st, what):
@@ -100,7 +117,7 @@ def _forward_mlp(layers, X, act, stream):
     for i, l in enumerate(layers):
         rows, fin = acts[-1].shape
         H = torch.empty(rows, l.W.shape[0], dtype=torch.float32, device="cuda")
-        _ck(lib.nn_gemm(0, 1, rows, l.W.shape[0], fin, 1.0, _p(acts[-1]), fin, _p(l.W), fin, 0.0, _p(H),
+        _ck(_gemm(lib, 0, 1, rows, l.W.shape[0], fin, 1.0, _p(acts[-1]), fin, _p(l.W), fin, 0.0, _p(H),
                         l.W.shape[0], stream), "nn_gemm")
         _ck(lib.nn_bias_act(rows, l.W.shape[0], _p(H), _p(l.b), act if i < len(layers) - 1 else 0, stream),
             "nn_bias_act")
@@ -117,11 +134,11 @@ def _backward_mlp(layers, acts, dout, act, stream, need_input_grad=False):
         fout, fin = l.W.shape
         if i < len(layers) - 1:
             _ck(lib.nn_act_backward(d.numel(), _p(d), _p(acts[i + 1]), act, stream), "nn_act_backward")
-        _ck(lib.nn_gemm(1, 0, fout, fin, rows, 1.0, _p(d), fout, _p(acts[i]), fin, 0.0, _p(l.gW), fin, stream), "dW")
+        _ck(_gemm(lib, 1, 0, fout, fin, rows, 1.0, _p(d), fout, _p(acts[i]), fin, 0.0, _p(l.gW), fin, stream), "dW")
         _ck(lib.nn_bias_grad(rows, fout, _p(d), _p(l.gb), stream), "db")
         if i > 0 or need_input_grad:
             dn = torch.empty(rows, fin, dtype=torch.float32, device="cuda")
-            _ck(lib.nn_gemm(0, 0, rows, fin, fout, 1.0, _p(d), fout, _p(l.W), fin, 0.0, _p(dn), fin, stream), "dX")
+            _ck(_gemm(lib, 0, 0, rows, fin, fout, 1.0, _p(d), fout, _p(l.W), fin, 0.0, _p(dn), fin, stream), "dX")
             d = dn
 
 
@@ -137,19 +154,19 @@ def train_step(net, X, Xc, Y, lr=1e-4, stream=None):
     Bo, T = ba[-1], ta[-1]
     p = T.shape[1]
     pred = torch.empty(B, 2 * P, dtype=torch.float32, device="cuda")
-    _ck(lib.nn_gemm(0, 1, B, P, p, 1.0, _p(Bo), 2 * p, _p(T), p, 0.0, _p(pred), 2 * P, s), "pred re")
-    _ck(lib.nn_gemm(0, 1, B, P, p, 1.0, C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, _p(T), p, 0.0,
+    _ck(_gemm(lib, 0, 1, B, P, p, 1.0, _p(Bo), 2 * p, _p(T), p, 0.0, _p(pred), 2 * P, s), "pred re")
+    _ck(_gemm(lib, 0, 1, B, P, p, 1.0, C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, _p(T), p, 0.0,
                     C.c_void_p(pred.data_ptr() + 4 * P), 2 * P, s), "pred im")
     dpred = torch.empty_like(pred)
     loss = torch.empty(B, dtype=torch.float32, device="cuda")
     _ck(lib.nn_rel_l2(B, 2 * P, _p(pred), _p(Y), _p(dpred), _p(loss), s), "nn_rel_l2")
     dBo = torch.empty_like(Bo)
-    _ck(lib.nn_gemm(0, 0, B, p, P, 1.0, _p(dpred), 2 * P, _p(T), p, 0.0, _p(dBo), 2 * p, s), "dB re")
-    _ck(lib.nn_gemm(0, 0, B, p, P, 1.0, C.c_void_p(dpred.data_ptr() + 4 * P), 2 * P, _p(T), p, 0.0,
+    _ck(_gemm(lib, 0, 0, B, p, P, 1.0, _p(dpred), 2 * P, _p(T), p, 0.0, _p(dBo), 2 * p, s), "dB re")
+    _ck(_gemm(lib, 0, 0, B, p, P, 1.0, C.c_void_p(dpred.data_ptr() + 4 * P), 2 * P, _p(T), p, 0.0,
                     C.c_void_p(dBo.data_ptr() + 4 * p), 2 * p, s), "dB im")
     dT = torch.empty_like(T)
-    _ck(lib.nn_gemm(1, 0, P, p, B, 1.0, _p(dpred), 2 * P, _p(Bo), 2 * p, 0.0, _p(dT), p, s), "dT re")
-    _ck(lib.nn_gemm(1, 0, P, p, B, 1.0, C.c_void_p(dpred.data_ptr() + 4 * P), 2 * P,
+    _ck(_gemm(lib, 1, 0, P, p, B, 1.0, _p(dpred), 2 * P, _p(Bo), 2 * p, 0.0, _p(dT), p, s), "dT re")
+    _ck(_gemm(lib, 1, 0, P, p, B, 1.0, C.c_void_p(dpred.data_ptr() + 4 * P), 2 * P,
                     C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, 1.0, _p(dT), p, s), "dT im")
     _backward_mlp(net.branch, ba, dBo, 1, s)
     _backward_mlp(net.trunk, ta, dT, 2, s)
@@ -247,8 +264,8 @@ def evaluate(net, X, Y, coords, rows):
         ba = _forward_mlp(net.branch, X[r:r + 1], 1, s)
         Bo = ba[-1]
         pred = torch.empty(1, 2 * N, dtype=torch.float32, device="cuda")
-        _ck(lib.nn_gemm(0, 1, 1, N, p, 1.0, _p(Bo), 2 * p, _p(T), p, 0.0, _p(pred), 2 * N, s), "pred re")
-        _ck(lib.nn_gemm(0, 1, 1, N, p, 1.0, C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, _p(T), p, 0.0,
+        _ck(_gemm(lib, 0, 1, 1, N, p, 1.0, _p(Bo), 2 * p, _p(T), p, 0.0, _p(pred), 2 * N, s), "pred re")
+        _ck(_gemm(lib, 0, 1, 1, N, p, 1.0, C.c_void_p(Bo.data_ptr() + 4 * p), 2 * p, _p(T), p, 0.0,
                         C.c_void_p(pred.data_ptr() + 4 * N), 2 * N, s), "pred im")
         d = torch.empty_like(pred)
         lo = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -330,8 +347,10 @@ if __name__ == "__main__":
     ap.add_argument("--lr", type=float, default=1e-4)
     ap.add_argument("--out", default=None)
     ap.add_argument("--full", default=None, help="also save the full network and Adam state (.npz)")
+    ap.add_argument("--tensor-cores", action="store_true", help="BF16 dense-layer products on tcgen05")
     a = ap.parse_args()
     torch.cuda.set_device(0)
+    set_tensor_cores(a.tensor_cores)
     net, info = train_workload(a.workload, a.samples, a.steps, a.batch, a.nodes, a.lr, out=a.out)
     if a.full:
         net.save(a.full)

@@ -159,3 +159,70 @@ def test_training_reduces_loss_on_scatterer_free_problem():
     train.train(net, X[:40], Y[:40], coords, fluid, steps=400, batch=16, nodes=512, lr=1e-3, log=lambda *a: None)
     after_train = train.evaluate(net, X, Y, coords, range(0, 8))
     assert after_train < 0.5 * before
+
+
+def _bf16_reference_step(branch, trunk, X, Xc, Y):
+    """Loss and gradients of one DeepONet training step in FP64 with every operand of
+    every product rounded to BF16 first (oracle/tb.py bf16_round), in the order of
+    the products train_step forms; ReLU / tanh, biases and the loss in FP64."""
+    from oracle.tb import bf16_round as bf
+    acts_b, acts_t = [np.asarray(X, np.float64)], [np.asarray(Xc, np.float64)]
+    for li, (W, b) in enumerate(branch):
+        H = bf(acts_b[-1]) @ bf(W).T + b
+        acts_b.append(np.maximum(H, 0) if li < len(branch) - 1 else H)
+    for li, (W, b) in enumerate(trunk):
+        H = bf(acts_t[-1]) @ bf(W).T + b
+        acts_t.append(np.tanh(H) if li < len(trunk) - 1 else H)
+    Bo, T = acts_b[-1], acts_t[-1]
+    p = T.shape[1]
+    pred = np.concatenate([bf(Bo[:, :p]) @ bf(T).T, bf(Bo[:, p:]) @ bf(T).T], axis=1)
+    loss, dpred = mlp.rel_l2(pred, np.asarray(Y, np.float64))
+    P = T.shape[0]
+    dBo = np.concatenate([bf(dpred[:, :P]) @ bf(T), bf(dpred[:, P:]) @ bf(T)], axis=1)
+    dT = bf(dpred[:, :P]).T @ bf(Bo[:, :p]) + bf(dpred[:, P:]).T @ bf(Bo[:, p:])
+
+    def back(layers, acts, d, deriv):
+        grads = [None] * len(layers)
+        for li in range(len(layers) - 1, -1, -1):
+            if li < len(layers) - 1:
+                d = d * deriv(acts[li + 1])
+            grads[li] = (bf(d).T @ bf(acts[li]), d.sum(axis=0))
+            d = bf(d) @ bf(layers[li][0])
+        return grads
+    gb = back(branch, acts_b, dBo, lambda H: (H > 0).astype(np.float64))
+    gt = back(trunk, acts_t, dT, lambda H: 1.0 - H * H)
+    return loss, gb, gt
+
+
+def test_training_step_on_tensor_cores():
+    """The same training step with the dense-layer products on the tcgen05 tensor
+    cores (BF16 operands, FP32 accumulation) against the oracle's FP64 arithmetic
+    with the operands of every product rounded to BF16 (what remains is the FP32
+    accumulation and BF16 ties of nearly equal FP32 / FP64 values: 1e-2), and the
+    loss falls over a short run."""
+    from paper_2405_12380_gb300 import train
+    rng = np.random.default_rng(23)
+    net = train.DeepONet.init([64, 48, 32, 20], [3, 24, 24, 10], seed=5)
+    X = rng.standard_normal((8, 64)).astype(np.float32)
+    Xc = rng.random((40, 3)).astype(np.float32)
+    Y = rng.standard_normal((8, 80)).astype(np.float32)
+    branch, trunk = net.numpy_layers("branch"), net.numpy_layers("trunk")
+    loss_o, gb, gt = _bf16_reference_step(branch, trunk, X, Xc, Y)
+    train.set_tensor_cores(True)
+    try:
+        loss = train.train_step(net, to_dev(X), to_dev(Xc), to_dev(Y), lr=1e-3)
+        torch.cuda.synchronize()
+        assert rel(loss.cpu().numpy(), loss_o) < 1e-2
+        for l, (dW, db) in zip(net.branch + net.trunk, gb + gt):
+            assert rel(l.gW.cpu().numpy(), dW) < 1e-2, rel(l.gW.cpu().numpy(), dW)
+            assert rel(l.gb.cpu().numpy(), db) < 1e-2, rel(l.gb.cpu().numpy(), db)
+        l0 = float(loss.mean())
+        for _ in range(60):
+            loss = train.train_step(net, to_dev(X), to_dev(Xc), to_dev(Y), lr=1e-3)
+        assert float(loss.mean()) < 0.7 * l0
+    finally:
+        train.set_tensor_cores(False)
+    import ctypes as C
+    from paper_2405_12380_gb300 import _lib as L
+    flag = C.c_int(-1)
+    assert L.lib().nn_gemm_bf16_status(C.byref(flag)) == 0 and flag.value == 0
