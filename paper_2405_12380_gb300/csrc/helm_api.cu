@@ -878,27 +878,28 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
     if (use_graph && (!h->g32 || std::memcmp(key, h->g32_key, sizeof(key)) != 0 || h->g32_omega != o->omega)) {
         drop_graphs(h);
         if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-        const cudaStream_t saved = h->stream;
-        const long long l0 = h->launches;
-        h->stream = h->cap_stream;
-        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        const helm_status cst = enqueue_iter();
-        cudaGraph_t graph = nullptr;
-        const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
-        h->stream = saved;
-        if (cst != HELM_OK || ce != cudaSuccess) {
+        {
+            const cudaStream_t saved = h->stream;
+            const long long l0 = h->launches;
+            const std::string err0 = h->err;
+            h->stream = h->cap_stream;
+            CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            const helm_status cst = enqueue_iter();
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+            h->stream = saved;
+            cudaError_t ie = cudaErrorUnknown;
+            if (cst == HELM_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&h->g32, graph, 0);
             if (graph) cudaGraphDestroy(graph);
-            cudaGetLastError();
-            return cst != HELM_OK ? cst : fail(h, HELM_CUDA_ERROR, "capture of the BiCGStab iteration failed");
+            h->g32_launches = h->launches - l0;
+            h->launches = l0;
+            if (ie != cudaSuccess) {
+                h->g32 = nullptr;
+                cudaGetLastError();
+                h->err = err0;
+                return cst != HELM_OK ? cst : fail(h, HELM_CUDA_ERROR, "capture of the BiCGStab iteration failed");
+            }
         }
-        const cudaError_t ie = cudaGraphInstantiate(&h->g32, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ie != cudaSuccess) {
-            h->g32 = nullptr;
-            return fail(h, HELM_CUDA_ERROR, std::string("graph instantiation: ") + cudaGetErrorString(ie));
-        }
-        h->g32_launches = h->launches - l0;
-        h->launches = l0;
         std::memcpy(h->g32_key, key, sizeof(key));
         h->g32_omega = o->omega;
     }
@@ -1662,6 +1663,7 @@ helm_status helm_mg_setup(helm_handle* h, int levels) {
 
 helm_status helm_set_wait_limit(helm_handle* h, unsigned polls, unsigned extra_arrivals) {
     if (!h || polls == 0) return fail(h, HELM_BAD_ARG, "bad argument");
+    drop_graphs(h);         // the captured iteration holds the old limits
     h->bar_spin = polls;
     h->bar_extra = extra_arrivals;
     return HELM_OK;
