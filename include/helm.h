@@ -159,6 +159,17 @@ helm_status helm_set_profiling(helm_handle* h, int on);
  * the timeout path (0 for normal use).  helm_precond synchronises and checks too. */
 helm_status helm_set_wait_limit(helm_handle* h, unsigned polls, unsigned extra_arrivals);
 
+/* Reliable updates of the complex64 BiCGStab of HELM_MIXED handles (Sleijpen and
+ * van der Vorst's reliable updating of the residual): the FP32 increment is folded
+ * into the FP64 iterate and the residual recomputed in FP64 when the recursive
+ * residual falls below delta times its largest value since the last update
+ * (default 0.1); a recursive residual above runaway times the last true residual
+ * (default 1e3) drops the increment and restarts; guard > 0 tries each fold first
+ * and takes the increment back out (and restarts) when the true residual would
+ * exceed guard times the last true residual (default 0: no guard).
+ * HELM_BAD_ARG unless 0 < delta < 1, runaway > 1, guard >= 0. */
+helm_status helm_set_reliable(helm_handle* h, double delta, double runaway, double guard);
+
 /* Multigrid hierarchy for HELM_MG (Sec. 4.3, DeepONet-MG-Krylov): `levels` grids in
  * all (1..8), each coarser one by vertex coarsening n -> (n + 1) / 2 (so n must
  * stay odd and >= 5 down to the coarsest), coarse node I at fine node 2I; the mask

@@ -53,6 +53,7 @@ SIGNATURES = {
     "helm_last_error": (C.c_char_p, [H]),
     "helm_set_profiling": (i32, [H, i32]),
     "helm_set_wait_limit": (i32, [H, C.c_uint, C.c_uint]),
+    "helm_set_reliable": (i32, [H, C.c_double, C.c_double, C.c_double]),
     "helm_mg_setup": (i32, [H, i32]),
     "helm_info": (i32, [H, C.POINTER(i64), C.POINTER(f64)]),
     "helm_layer_k2": (i32, [H, vp, vp]),

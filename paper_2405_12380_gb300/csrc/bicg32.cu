@@ -222,16 +222,19 @@ __global__ void __launch_bounds__(kB32Threads) k32_xr(float2* __restrict__ xl, f
 }
 
 // reliable update, first half: x += xl (FP64), xl = 0; drop = 1 discards the increment
+// mode 0: x += xl, xl = 0 (fold); 1: xl = 0 (drop); 2: x += xl, xl kept (trial
+// fold); 3: x -= xl, xl = 0 (undo a trial fold)
 __global__ void __launch_bounds__(kB32Threads) k32_fold(double2* __restrict__ x, float2* __restrict__ xl, long long N,
-                                                        int drop) {
+                                                        int mode) {
     for (long long l = blockIdx.x * (long long)kB32Threads + threadIdx.x; l < N;
          l += (long long)gridDim.x * kB32Threads) {
-        if (!drop) {
+        if (mode != 1) {
             const float2 d = xl[l];
             const double2 xv = x[l];
-            x[l] = make_double2(xv.x + (double)d.x, xv.y + (double)d.y);
+            x[l] = mode == 3 ? make_double2(xv.x - (double)d.x, xv.y - (double)d.y)
+                             : make_double2(xv.x + (double)d.x, xv.y + (double)d.y);
         }
-        xl[l] = make_float2(0.f, 0.f);
+        if (mode != 2) xl[l] = make_float2(0.f, 0.f);
     }
 }
 
@@ -315,8 +318,8 @@ void launch_b32_xr(float2* xl, float2* r, const float2* phat, const float2* shat
                    const float2* rhat, double2* sc, long long N, double* parts, unsigned* counter, cudaStream_t s) {
     k32_xr<<<bicg32_blocks(), kB32Threads, 0, s>>>(xl, r, phat, shat, sv, t, rhat, sc, N, parts, counter);
 }
-void launch_b32_fold(double2* x, float2* xl, long long N, cudaStream_t s, int drop) {
-    k32_fold<<<bicg32_blocks(), kB32Threads, 0, s>>>(x, xl, N, drop);
+void launch_b32_fold(double2* x, float2* xl, long long N, cudaStream_t s, int mode) {
+    k32_fold<<<bicg32_blocks(), kB32Threads, 0, s>>>(x, xl, N, mode);
 }
 void launch_b32_replace(const double2* r64, float2* r, float2* rhat, float2* p, float2* v, int restart, double2* sc,
                         long long N, double* parts, unsigned* counter, cudaStream_t s) {

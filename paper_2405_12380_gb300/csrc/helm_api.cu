@@ -166,6 +166,37 @@ void red_black_sweeps(helm_handle* h, const Op<R>& op, int kind, double omega, i
     h->launches += (long long)per * sweeps;
 }
 
+// complex64 Gauss-Seidel-type sweeps as fused full sweeps (one launch each, out of
+// place): the launches alternate between x and tmp so that the last one writes x.
+// SSOR is a forward sweep (colour 0 first) and a backward one (colour 1 first).
+// From zero the first launch reads nothing; otherwise an odd launch count first
+// copies x to tmp.  Returns false (nothing launched) where the fused kernel does
+// not apply.
+bool fused_sweeps32(helm_handle* h, int kind, double omega, int sweeps, const float2* f, float2* x, float2* tmp,
+                    int conj, bool from_zero) {
+    const double w = kind == HELM_RBGS ? 1.0 : omega;
+    const int per = kind == HELM_SSOR ? 2 : 1;
+    const int L = per * sweeps;
+    if (L <= 0) return false;
+    if (!rbgs_sweep32_ok(h->op32, f, x, tmp)) return false;
+    const float2* in = from_zero ? nullptr : x;
+    if (!from_zero && L % 2 == 1) {
+        if (cudaMemcpyAsync(tmp, x, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            return false;
+        in = tmp;
+    }
+    for (int i = 0; i < L; ++i) {
+        float2* out = ((L - 1 - i) % 2 == 0) ? x : tmp;
+        const int c0 = (kind == HELM_SSOR && i % 2 == 1) ? 1 : 0;
+        ev_mark(h, 2, 0);
+        launch_rbgs_sweep32(h->op32, c0, f, in, out, conj, w, h->stream);
+        ev_mark(h, 2, 1);
+        in = out;
+    }
+    h->launches += L;
+    return true;
+}
+
 // z = n sweeps of the relaxation on A z = r from z = 0 (FP64)
 helm_status relax_from_zero(helm_handle* h, int kind, double omega, int sweeps, const double2* r, double2* z,
                             int conj) {
@@ -280,8 +311,11 @@ helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v,
         }
         h->launches += o->n_r;
     } else {
-        CK(cudaMemsetAsync(z, 0, sizeof(float2) * h->N, s));
-        red_black_sweeps<float>(h, h->op32, o->relax, o->omega, o->n_r, v, z, conj, true);
+        TRY(ensure_tmp32(h, 4));
+        if (!fused_sweeps32(h, o->relax, o->omega, o->n_r, v, z, h->tmp32[3], conj, true)) {
+            CK(cudaMemsetAsync(z, 0, sizeof(float2) * h->N, s));
+            red_black_sweeps<float>(h, h->op32, o->relax, o->omega, o->n_r, v, z, conj, true);
+        }
     }
     if (o->correction == HELM_CORR_TB) {
         if (!h->Qbf) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
@@ -808,10 +842,12 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
 // update, or met the tolerance, the host folds the increment into x, recomputes the
 // true residual in FP64 and replaces the recursive one by it (keeping the search
 // direction); a breakdown restarts from the true residual (rhat = r, p = v = 0).
-// Convergence is decided on the FP64 true residual only.
-constexpr double kReliableDelta = 0.1;
-// growth of the recursive residual over the last true one that counts as a runaway
-constexpr double kRunaway = 1e3;
+// A recursive residual that grows past rel_runaway times the last true one (a
+// runaway of the complex64 recursion) drops the increment and restarts from the
+// FP64 iterate.  With rel_guard > 0 a fold is first tried: if the true residual of
+// x + xl exceeds rel_guard times the last true one the increment is taken back out
+// and the iteration restarts from x.  Convergence is decided on the FP64 true
+// residual only.
 
 helm_status ensure_b32(helm_handle* h) {
     while (h->b32.size() < 9) {
@@ -918,11 +954,36 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
     };
     // x += xl; r64 = f - A x (FP64, its norm in S_BETA2); r = complex64(r64) with rho,
     // beta (restart: also rhat = r, p = v = 0); the host waits for the result
-    auto reliable_update = [&](int restart, int drop = 0) -> helm_status {
-        launch_b32_fold(x, xl, N, s, drop);
+    bool rejected = false;
+    auto reliable_update = [&](int restart, int drop, double last) -> helm_status {
+        rejected = false;
+        if (drop || !(h->rel_guard > 0.0)) {
+            launch_b32_fold(x, xl, N, s, drop ? 1 : 0);
+            TRY(residual_norm(h, f, x, r64, o->conj, S_BETA2));
+            launch_b32_replace(r64, r, rh, p, v, restart, h->sc, N, parts, h->counter, s);
+            h->launches += 2;
+            ++st->matvecs;
+            CKL();
+            return poll(h);
+        }
+        launch_b32_fold(x, xl, N, s, 2);
         TRY(residual_norm(h, f, x, r64, o->conj, S_BETA2));
-        launch_b32_replace(r64, r, rh, p, v, restart, h->sc, N, parts, h->counter, s);
-        h->launches += 2;
+        ++st->matvecs;
+        TRY(poll(h));
+        const double rt = std::sqrt(hs(h, S_BETA2)) / bnorm;
+        if (std::isfinite(rt) && rt <= h->rel_guard * last) {
+            launch_b32_fold(x, xl, N, s, 1);
+            launch_b32_replace(r64, r, rh, p, v, restart, h->sc, N, parts, h->counter, s);
+            h->launches += 3;
+            CKL();
+            return poll(h);
+        }
+        // the increment made the iterate worse: take it back out and start afresh
+        rejected = true;
+        launch_b32_fold(x, xl, N, s, 3);
+        TRY(residual_norm(h, f, x, r64, o->conj, S_BETA2));
+        launch_b32_replace(r64, r, rh, p, v, 1, h->sc, N, parts, h->counter, s);
+        h->launches += 4;
         ++st->matvecs;
         CKL();
         return poll(h);
@@ -955,8 +1016,8 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
         hist.push(rn);
         // a runaway of the complex64 recursion (or a non-finite value): drop the
         // increment and restart from the FP64 iterate
-        const bool reset = !std::isfinite(rn) || rn > kRunaway * last_true;
-        if (!stop && !reset && rn >= kReliableDelta * maxrr) {
+        const bool reset = !std::isfinite(rn) || rn > h->rel_runaway * last_true;
+        if (!stop && !reset && rn >= h->rel_delta * maxrr) {
             maxrr = std::max(maxrr, rn);
             continue;
         }
@@ -972,12 +1033,12 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
             inflight = 0;
         }
         head = 0;
-        TRY(reliable_update(reset ? 1 : 0, reset ? 1 : 0));
+        TRY(reliable_update(reset ? 1 : 0, reset ? 1 : 0, last_true));
         const double rt = std::sqrt(hs(h, S_BETA2)) / bnorm;
         res = rt;
         if (rt <= o->tol) { st->status = HELM_OK; break; }
         if (!std::isfinite(rt)) { st->status = HELM_DIVERGED; break; }
-        if (reset) {
+        if (reset || rejected) {
             ++restarts;
             since_start = 0;
             maxrr = last_true = rt;
@@ -1048,6 +1109,9 @@ void fill_tables(helm_handle* h) {
         const float2 re = split(o.invd_tab[m].x), im = split(o.invd_tab[m].y);
         t.invd[m] = make_float4(re.x, re.y, im.x, im.y);
     }
+    // the fused sweep's launch shape queries the occupancy once per row width: here,
+    // outside any stream capture
+    (void)rbgs_sweep32_ok(f, nullptr, nullptr, nullptr);
 }
 
 // A_c = Q^T (A Q) and its inverse from a node-major copy of Q (N x ldq)
@@ -1384,7 +1448,9 @@ helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const
             }
             if (a != x) CK(cudaMemcpyAsync(x, a, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, s));
         } else {
-            red_black_sweeps<float>(h, h->op32, kind, omega, sweeps, (const float2*)f, (float2*)x, conj, false);
+            TRY(ensure_tmp32(h, 1));
+            if (!fused_sweeps32(h, kind, omega, sweeps, (const float2*)f, (float2*)x, h->tmp32[0], conj, false))
+                red_black_sweeps<float>(h, h->op32, kind, omega, sweeps, (const float2*)f, (float2*)x, conj, false);
         }
     } else {
         return fail(h, HELM_BAD_ARG, "dtype");
@@ -1658,6 +1724,15 @@ helm_status helm_mg_setup(helm_handle* h, int levels) {
         parent = c;
     }
     h->mg_levels = levels;
+    return HELM_OK;
+}
+
+helm_status helm_set_reliable(helm_handle* h, double delta, double runaway, double guard) {
+    if (!h || !(delta > 0.0 && delta < 1.0) || !(runaway > 1.0) || !(guard >= 0.0))
+        return fail(h, HELM_BAD_ARG, "bad argument");
+    h->rel_delta = delta;
+    h->rel_runaway = runaway;
+    h->rel_guard = guard;
     return HELM_OK;
 }
 

@@ -119,6 +119,13 @@ void launch_jacobi(const Op<R>& op, double omega, const typename CT<R>::T* f,
 template <typename R>
 void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, typename CT<R>::T* x,
                       int conj, bool xzero, cudaStream_t s, double omega = 1.0);
+// one full red-black sweep, colour c0 on every node then colour 1 - c0, from xin
+// (nullptr: from zero) into xout (a different buffer) in one launch; returns false
+// without launching where the fused kernel does not apply (2D, odd n, n > 256,
+// outer-boundary rows, unaligned vectors)
+bool launch_rbgs_sweep32(const Op<float>& op, int c0, const float2* f, const float2* xin, float2* xout, int conj,
+                         double omega, cudaStream_t s);
+bool rbgs_sweep32_ok(const Op<float>& op, const void* f, const void* x, const void* tmp);
 int apply_grid_blocks(int dim, int n);
 int bicg_grid_blocks(int dim, int n);
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s);
@@ -159,7 +166,8 @@ void launch_b32_omega(const float2* t, const float2* sv, double2* sc, long long 
                       cudaStream_t s);
 void launch_b32_xr(float2* xl, float2* r, const float2* phat, const float2* shat, const float2* sv, const float2* t,
                    const float2* rhat, double2* sc, long long N, double* parts, unsigned* counter, cudaStream_t s);
-void launch_b32_fold(double2* x, float2* xl, long long N, cudaStream_t s, int drop = 0);
+// mode 0: x += xl, xl = 0; 1: xl = 0; 2: x += xl (xl kept); 3: x -= xl, xl = 0
+void launch_b32_fold(double2* x, float2* xl, long long N, cudaStream_t s, int mode = 0);
 void launch_b32_replace(const double2* r64, float2* r, float2* rhat, float2* p, float2* v, int restart, double2* sc,
                         long long N, double* parts, unsigned* counter, cudaStream_t s);
 
@@ -387,6 +395,8 @@ struct helm_handle {
     // gives up, and arrivals added to the barrier target (0; > 0 injects a timeout)
     unsigned bar_spin = 1u << 20;
     unsigned bar_extra = 0;
+    // reliable updates of the complex64 BiCGStab (helm_set_reliable)
+    double rel_delta = 0.1, rel_runaway = 1e3, rel_guard = 0.0;
     // phases: 0 restriction, 1 prolongation, 2 relaxation half-sweeps that read
     // neighbours, 3 operator applications of the Krylov loop
     std::vector<cudaEvent_t> evpool[4];

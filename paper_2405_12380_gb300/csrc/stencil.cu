@@ -390,6 +390,23 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
     }
 }
 
+// new value of a swept node (Gauss-Seidel, or SOR for omega != 1): a masked node
+// takes f, a fluid node D^-1 (f - h^-2 s) from its neighbour sum s (D^-1 f when the
+// old iterate is zero); SOR moves the old value xo by omega times the step
+__device__ __forceinline__ float2 gs_value(const Op<float>& op, unsigned c, float2 fa, float2 s, float2 id,
+                                           float2 xo, float omega, bool xzero) {
+    float2 out;
+    if (c & kMasked) {
+        out = fa;
+    } else if (xzero) {
+        out = cmul(id, fa);
+    } else {
+        out = cmul(id, make_float2(fa.x - op.hinv2 * s.x, fa.y - op.hinv2 * s.y));
+    }
+    if (omega != 1.f) out = xzero ? cscale(omega, out) : cadd(xo, cscale(omega, csub(out, xo)));
+    return out;
+}
+
 // complex64 red-black half-sweep in 3D with the pair layout of k_march_c64: each
 // thread owns the node pair (2 i2, 2 i2 + 1) of a row, one node of each colour
 // (n even), and updates the one of the swept colour in place.  The neighbours of
@@ -447,12 +464,8 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
             pair_sums(a ? 0u : ca, a ? ca : 0u, left, right, cur, ym, yp, prev, next, s0, s1);
         }
         if (valid) {
-            const float2 fa = a ? hi2(fv) : lo2(fv);
-            float2 out;
-            if (ca & kMasked) {
-                out = fa;
-            } else {
-                float2 id;
+            float2 id = make_float2(0.f, 0.f);
+            if (!(ca & kMasked)) {
                 if (op.k2) {
                     const float4 iv = reinterpret_cast<const float4*>(op.invd)[l];
                     id = a ? hi2(iv) : lo2(iv);
@@ -460,21 +473,9 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
                     id = op.invd_tab[a ? (li >> 8) : (li & 0xffu)];
                 }
                 if (conj) id.y = -id.y;
-                if (XZERO) {
-                    out = cmul(id, fa);
-                } else {
-                    const float2 sa = a ? s1 : s0;
-                    out = cmul(id, make_float2(fa.x - op.hinv2 * sa.x, fa.y - op.hinv2 * sa.y));
-                }
             }
-            if (omega != 1.f) {
-                if (XZERO) {
-                    out = cscale(omega, out);
-                } else {
-                    const float2 xo = a ? hi2(cur) : lo2(cur);
-                    out = cadd(xo, cscale(omega, csub(out, xo)));
-                }
-            }
+            const float2 out = gs_value(op, ca, a ? hi2(fv) : lo2(fv), a ? s1 : s0, id, a ? hi2(cur) : lo2(cur),
+                                        omega, XZERO);
             xw[2 * l + a] = out;
         }
         prev = cur;
@@ -484,6 +485,155 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
         cc = cc_n;
         li = li_n;
     }
+}
+
+// ---- one full red-black sweep per launch (complex64, 3D, n even, pair layout)
+//
+// Colour c0 on every node, then colour 1 - c0, read from xin and written to xout
+// (out of place).  A block owns whole x-rows: blockDim.x threads over the n/2
+// pairs of a row (a multiple of 32), blockDim.y = BYI + 2 rows, of which the first
+// and last are halo rows: they compute the colour-c0 values of the rows just
+// outside the block, which the block's own second-colour nodes need, instead of
+// waiting for the neighbouring block.  Each thread marches in z over its pair: at
+// step t it updates colour c0 at plane t (old values: the other node of the pair and
+// the z-planes in registers, x-neighbours by shuffles, y-neighbours from xin) and
+// puts the new value in a ring of three shared planes; after one barrier it updates
+// colour 1 - c0 at plane t - 1 from the new colour-c0 values (x and y neighbours
+// from the shared plane, z neighbours from its registers) and writes the pair.
+// Blocks split z into chunks and recompute the colour-c0 planes just outside their
+// chunk.  Every node value comes from the arithmetic of k_rbgs_c64 (gs_value) with
+// the neighbour sums in the same order, so one launch equals two half-sweeps.
+__device__ __forceinline__ float2 pair_node(float4 v, int a) { return a ? hi2(v) : lo2(v); }
+
+__device__ __forceinline__ float2 sweep_invd(const Op<float>& op, int l, int a, unsigned li, int conj) {
+    float2 id;
+    if (op.k2) {
+        const float4 iv = reinterpret_cast<const float4*>(op.invd)[l];
+        id = a ? hi2(iv) : lo2(iv);
+    } else {
+        id = op.invd_tab[a ? (li >> 8) : (li & 0xffu)];
+    }
+    if (conj) id.y = -id.y;
+    return id;
+}
+
+// neighbour sum of one node from its six neighbour values (code bits select the
+// fluid ones), in the order of pair_sums
+__device__ __forceinline__ float2 six_sum(unsigned c, float2 xm, float2 xp, float2 ym, float2 yp, float2 zm,
+                                          float2 zp) {
+    return cadd(cadd(cadd(pick(c, 1u, xm), pick(c, 2u, xp)), cadd(pick(c, 4u, ym), pick(c, 8u, yp))),
+                cadd(pick(c, 16u, zm), pick(c, 32u, zp)));
+}
+
+constexpr int kSweepMaxThreads = 1024;
+
+// the block (by, bz) of the sweep grid of one problem (shared by the batched form)
+template <bool XZERO>
+__device__ __forceinline__ void sweep_c64_block(const Op<float>& op, int by, int bz, int zc, int c0,
+                                                const float4* __restrict__ f, const float4* __restrict__ xin,
+                                                float4* __restrict__ xout, int conj, float omega, float2* ring) {
+    constexpr unsigned kMM = kMasked | (kMasked << 8);
+    const int n = op.n, h = n >> 1;
+    const int TXT = blockDim.x, BYI = blockDim.y - 2;
+    const int i2 = threadIdx.x, ty = threadIdx.y, lane = i2 & 31;
+    const int j = by * BYI - 1 + ty;
+    const int k0 = bz * zc, k1 = min(n, k0 + zc);
+    const bool row_ok = i2 < h && j >= 0 && j < n;
+    const bool inner = row_ok && ty >= 1 && ty <= BYI;
+    const int sy = h, sz = h * n;
+    const int plane = blockDim.y * TXT, me = ty * TXT + i2;
+    const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
+    const unsigned short* lidx2 = reinterpret_cast<const unsigned short*>(op.lidx);
+    const float2* x1 = reinterpret_cast<const float2*>(xin);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 z2 = make_float2(0.f, 0.f);
+    const int lrow = i2 + h * j;
+    int t = k0 - 1;
+    auto in_t = [&](int q) { return row_ok && q >= 0 && q < n; };
+    float4 om = z4, oc = z4, on = z4;                      // old pairs at planes t-1, t, t+1
+    if (!XZERO) {
+        if (in_t(t - 1)) om = xin[lrow + sz * (t - 1)];
+        if (in_t(t)) oc = xin[lrow + sz * t];
+        if (in_t(t + 1)) on = xin[lrow + sz * (t + 1)];
+    }
+    float4 fc = in_t(t) ? f[lrow + sz * t] : z4, fm = z4;
+    unsigned cc = in_t(t) ? (unsigned)code2[lrow + sz * t] : kMM, cm = kMM;
+    unsigned lc = in_t(t) ? (unsigned)lidx2[lrow + sz * t] : 0u, lm = 0u;
+    float2 rm2 = z2, rm = z2;                              // new colour-c0 values at planes t-2, t-1
+    int slot = 0, slot_m = 2;
+    for (; t <= k1; ++t) {
+        const int l = lrow + sz * t;
+        const bool tin = in_t(t);
+        float4 onn = z4, fn = z4;
+        unsigned cn = kMM, ln = 0u;
+        if (in_t(t + 1)) {
+            fn = f[l + sz];
+            cn = code2[l + sz];
+            ln = lidx2[l + sz];
+        }
+        if (!XZERO && in_t(t + 2)) onn = xin[l + 2 * sz];
+        // colour c0 at plane t (old neighbours)
+        float2 rc = z2;
+        {
+            const int a = c0 ^ ((j + t) & 1);
+            const unsigned ca = a ? (cc >> 8) : (cc & 0xffu);
+            float2 sa = z2;
+            if (!XZERO) {
+                float2 left, right;
+                left.x = __shfl_up_sync(0xffffffffu, oc.z, 1);
+                left.y = __shfl_up_sync(0xffffffffu, oc.w, 1);
+                right.x = __shfl_down_sync(0xffffffffu, oc.x, 1);
+                right.y = __shfl_down_sync(0xffffffffu, oc.y, 1);
+                if (tin && lane == 0 && a == 0 && (ca & 1u)) left = x1[2 * l - 1];
+                if (tin && lane == 31 && a == 1 && (ca & 2u)) right = x1[2 * l + 2];
+                const float2 ym = (tin && (ca & 4u)) ? pair_node(xin[l - sy], a) : z2;
+                const float2 yp = (tin && (ca & 8u)) ? pair_node(xin[l + sy], a) : z2;
+                sa = six_sum(ca, a ? lo2(oc) : left, a ? right : hi2(oc), ym, yp, pair_node(om, a), pair_node(on, a));
+            }
+            if (tin) {
+                const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, l, a, lc, conj);
+                rc = gs_value(op, ca, pair_node(fc, a), sa, id, pair_node(oc, a), omega, XZERO);
+            }
+        }
+        ring[slot * plane + me] = rc;
+        __syncthreads();
+        // colour 1 - c0 at plane t - 1 (new colour-c0 neighbours)
+        if (inner && t - 1 >= k0 && t - 1 < k1) {
+            const int lmi = l - sz;
+            const int a = (c0 ^ 1) ^ ((j + t - 1) & 1);
+            const unsigned ca = a ? (cm >> 8) : (cm & 0xffu);
+            const float2* P = ring + slot_m * plane;
+            const float2 xm = a ? rm : ((ca & 1u) ? P[me - 1] : z2);
+            const float2 xp = a ? ((ca & 2u) ? P[me + 1] : z2) : rm;
+            const float2 ym = (ca & 4u) ? P[me - TXT] : z2;
+            const float2 yp = (ca & 8u) ? P[me + TXT] : z2;
+            const float2 sb = six_sum(ca, xm, xp, ym, yp, rm2, rc);
+            const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, lmi, a, lm, conj);
+            const float2 b = gs_value(op, ca, pair_node(fm, a), sb, id, pair_node(om, a), omega, false);
+            xout[lmi] = a ? make_float4(rm.x, rm.y, b.x, b.y) : make_float4(b.x, b.y, rm.x, rm.y);
+        }
+        rm2 = rm;
+        rm = rc;
+        om = oc;
+        oc = on;
+        on = onn;
+        fm = fc;
+        fc = fn;
+        cm = cc;
+        cc = cn;
+        lm = lc;
+        lc = ln;
+        slot_m = slot;
+        slot = slot == 2 ? 0 : slot + 1;
+    }
+}
+
+template <bool XZERO>
+__global__ void __launch_bounds__(kSweepMaxThreads, 1)
+    k_sweep_c64(Op<float> op, int zc, int c0, const float4* __restrict__ f, const float4* __restrict__ xin,
+                float4* __restrict__ xout, int conj, float omega) {
+    extern __shared__ float2 ring[];                       // [3][blockDim.y][blockDim.x] colour-c0 values
+    sweep_c64_block<XZERO>(op, blockIdx.y, blockIdx.z, zc, c0, f, xin, xout, conj, omega, ring);
 }
 
 // y = A x, or y = f - A x (resid); two z-planes per thread; optional per-block ||y||^2 partials.
@@ -1398,6 +1548,67 @@ void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, t
     dim3 g = grid_for(op.dim, op.n, 2, 1), b(BX, BY);
     if (xzero) k_rbgs<R, true><<<g, b, 0, s>>>(op, colour, f, x, conj, (R)omega);
     else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj, (R)omega);
+}
+
+namespace {
+
+// launch shape of k_sweep_c64 on an n^3 grid: whole rows per block (n/2 pairs, at
+// most 128), 16 rows (8 for rows wider than one warp) including the two halo rows;
+// z chunks of 4..16 planes, as many as fill the resident block slots once
+struct SweepShape {
+    dim3 g, b;
+    int zc;
+    size_t smem;
+};
+
+bool sweep_shape(int n, SweepShape& sh) {
+    const int h = n / 2;
+    if (n % 2 != 0 || h < 1 || h > 128) return false;
+    const int txt = (h + 31) / 32 * 32;
+    const int tyt = txt <= 32 ? 16 : 8;
+    const int byi = tyt - 2;
+    sh.b = dim3(txt, tyt);
+    sh.smem = (size_t)3 * txt * tyt * sizeof(float2);
+    static int sms = 0;
+    static int occ[5] = {0, 0, 0, 0, 0};
+    const int w = txt / 32;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (occ[w] == 0) {
+        int o0 = 0, o1 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_sweep_c64<false>, txt * tyt, sh.smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_sweep_c64<true>, txt * tyt, sh.smem);
+        occ[w] = std::max(1, std::min(o0, o1));
+    }
+    const int gy = (n + byi - 1) / byi;
+    const long long slots = (long long)std::max(sms, 1) * occ[w];
+    const int chunks = (int)std::max<long long>(1, slots / gy);
+    sh.zc = std::max(4, std::min(16, (n + chunks - 1) / chunks));
+    sh.g = dim3(1, gy, (n + sh.zc - 1) / sh.zc);
+    return true;
+}
+
+}  // namespace
+
+bool rbgs_sweep32_ok(const Op<float>& op, const void* f, const void* x, const void* tmp) {
+    SweepShape sh;
+    const bool shape = op.dim == 3 && sweep_shape(op.n, sh);      // (also fills the occupancy cache)
+    return shape && pair_ok(op, f, x, tmp) && x != tmp;
+}
+
+bool launch_rbgs_sweep32(const Op<float>& op, int c0, const float2* f, const float2* xin, float2* xout, int conj,
+                         double omega, cudaStream_t s) {
+    SweepShape sh;
+    if (!pair_ok(op, f, xin, xout) || !sweep_shape(op.n, sh) || xin == xout) return false;
+    const float4* f4 = reinterpret_cast<const float4*>(f);
+    const float4* x4 = reinterpret_cast<const float4*>(xin);
+    float4* y4 = reinterpret_cast<float4*>(xout);
+    if (xin) k_sweep_c64<false><<<sh.g, sh.b, sh.smem, s>>>(op, sh.zc, c0, f4, x4, y4, conj, (float)omega);
+    else k_sweep_c64<true><<<sh.g, sh.b, sh.smem, s>>>(op, sh.zc, c0, f4, x4, y4, conj, (float)omega);
+    return true;
 }
 
 void launch_apply_bicg_df(const Op<double>& op, const DfTab& t, int mode, const float4* x, double2* y,

@@ -96,6 +96,10 @@ class Problem:
         (> 0 injects a timeout for tests)."""
         self._check(self.lib.helm_set_wait_limit(self.h, int(polls), int(extra_arrivals)), "set_wait_limit")
 
+    def set_reliable(self, delta=0.1, runaway=1e3, guard=0.0):
+        """Reliable-update parameters of the complex64 BiCGStab (helm_set_reliable)."""
+        self._check(self.lib.helm_set_reliable(self.h, float(delta), float(runaway), float(guard)), "set_reliable")
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.helm_destroy(self.h)
