@@ -144,6 +144,15 @@ helm_status helm_destroy(helm_handle* h);
 /* stream: a cudaStream_t (NULL = legacy default stream). */
 helm_status helm_set_stream(helm_handle* h, void* stream);
 const char* helm_last_error(const helm_handle* h);
+
+/* Bounds-checked build (the library compiled with -DHELM_CHECKED, which replaces a
+ * sanitizer here): its kernels check the indices of their vector, table and basis
+ * accesses, and an index out of range is recorded (the source line << 8 | the
+ * translation unit's id + 1, first one only) and replaced by 0 instead of being
+ * used; nothing traps.  Synchronises the device, then sets *checked = 1 in a
+ * checked build (0 otherwise) and *first to the first recorded violation since the
+ * previous call (0: none), and clears the records. */
+helm_status helm_checked_status(int* checked, unsigned long long* first);
 /* on = 1: bracket every trunk-basis restriction and prolongation, every
  * relaxation launch and every BiCGStab operator application with CUDA events on
  * the handle's stream and report their counts and summed times in helm_stats

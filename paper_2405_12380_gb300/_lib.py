@@ -9,7 +9,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhelm.so")
+# HELM_LIBRARY=checked loads the bounds-checked variant (built by build(checked=True))
+LIB_PATH = os.path.join(HERE, "libhelm_checked.so" if os.environ.get("HELM_LIBRARY") == "checked" else "libhelm.so")
 
 HELM_OK, HELM_BAD_ARG, HELM_NO_DEVICE, HELM_CUDA_ERROR = 0, 1, 2, 3
 HELM_NOT_CONVERGED, HELM_DIVERGED, HELM_BREAKDOWN, HELM_SINGULAR_COARSE = 4, 5, 6, 7
@@ -54,6 +55,7 @@ SIGNATURES = {
     "helm_set_profiling": (i32, [H, i32]),
     "helm_set_wait_limit": (i32, [H, C.c_uint, C.c_uint]),
     "helm_set_reliable": (i32, [H, C.c_double, C.c_double, C.c_double]),
+    "helm_checked_status": (i32, [C.POINTER(i32), C.POINTER(C.c_ulonglong)]),
     "helm_mg_setup": (i32, [H, i32]),
     "helm_info": (i32, [H, C.POINTER(i64), C.POINTER(f64)]),
     "helm_layer_k2": (i32, [H, vp, vp]),

@@ -25,28 +25,43 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
+    tu = ["-DHELM_TU_ID=%d" % SOURCES.index(src)] if src in SOURCES else []
+    cmd = [nvcc(), *ARCH, *FLAGS, *tu, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(LIB + ".tmp", LIB)
-    if verbose:
-        print("built", LIB)
+LIB_CHECKED = os.path.join(HERE, "libhelm_checked.so")
+
+
+def build(verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """libhelm.so; with checked=True also libhelm_checked.so, the bounds-checked
+    variant (-DHELM_CHECKED), compiled in the same parallel pass."""
+    variants = [(BUILD, LIB, list(extra))]
+    if checked:
+        variants.append((BUILD + "_checked", LIB_CHECKED, list(extra) + ["-DHELM_CHECKED"]))
+    jobs = []
+    for bdir, _, ex_flags in variants:
+        os.makedirs(bdir, exist_ok=True)
+        jobs += [(src, ex_flags, bdir) for src in SOURCES]
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(lambda j: _compile(*j), jobs))
+    for vi, (bdir, lib, _) in enumerate(variants):
+        vobjs = objs[vi * len(SOURCES):(vi + 1) * len(SOURCES)]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *vobjs, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(lib + ".tmp", lib)
+        if verbose:
+            print("built", lib)
     return LIB
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    args = [a for a in sys.argv[1:] if a != "--checked"]
+    build(verbose=True, extra=args, checked="--checked" in sys.argv[1:])

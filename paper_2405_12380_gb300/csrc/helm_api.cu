@@ -16,6 +16,12 @@
 
 using namespace helm;
 
+// the per-unit violation records of the bounds-checked build
+std::vector<unsigned long long (*)()>& helm::checked_units() {
+    static std::vector<unsigned long long (*)()> units;
+    return units;
+}
+
 namespace {
 
 helm_status fail(helm_handle* h, helm_status st, const std::string& msg) {
@@ -321,7 +327,15 @@ helm_status precond32(helm_handle* h, const helm_solve_opts* o, const float2* v,
         if (!h->Qbf) return fail(h, HELM_NOT_READY, "trunk basis not loaded (don_load)");
         int nblk = restrict_blocks(h->N);
         ev_mark(h, 0, 0);
-        if (!no_relax && o->relax == HELM_RBGS && h->Qbr) {
+        // after the black half-sweep v - A z vanishes on black and masked rows: with
+        // the pair layout the red rows' residual is stored compactly (in the sweep
+        // buffer, free again) and projected by a plain tall-skinny product
+        if (!no_relax && o->relax == HELM_RBGS && h->Qbr &&
+            launch_red_residual32(h->op32, v, z, h->tmp32[3], conj, s)) {
+            nblk = launch_restrict32_rr(h->Qbr, basis_ld((h->N + 1) / 2), h->k, h->tmp32[3], (h->N + 1) / 2,
+                                        h->partials32, h->N, s);
+            h->launches += 1;
+        } else if (!no_relax && o->relax == HELM_RBGS && h->Qbr) {
             // after the black half-sweep v - A z vanishes on black and masked rows:
             // project the red rows only
             nblk = launch_restrict32_red(h->op32, h->Qbr, basis_ld((h->N + 1) / 2), h->k, v, z, conj,
@@ -1355,6 +1369,22 @@ helm_status helm_set_stream(helm_handle* h, void* stream) {
 
 const char* helm_last_error(const helm_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
+helm_status helm_checked_status(int* checked, unsigned long long* first) {
+    if (!checked || !first) return HELM_BAD_ARG;
+#ifdef HELM_CHECKED
+    *checked = 1;
+#else
+    *checked = 0;
+#endif
+    *first = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HELM_CUDA_ERROR;
+    for (auto take : checked_units()) {
+        const unsigned long long v = take();
+        if (v && !*first) *first = v;
+    }
+    return HELM_OK;
+}
+
 helm_status helm_set_profiling(helm_handle* h, int on) {
     if (!h) return HELM_BAD_ARG;
     h->profile = on ? 1 : 0;
@@ -1592,7 +1622,8 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     STEP(dalloc(h, &h->coarse_partials, (size_t)std::max(restrict_blocks(N), project_blocks(N)) * k));
     if (h->precision == HELM_MIXED) {
         dfree(h->partials32); dfree(h->y32);
-        STEP(dalloc(h, &h->partials32, (size_t)std::max(restrict_blocks(N), restrict32_red_blocks(N)) * k));
+        STEP(dalloc(h, &h->partials32,
+                    (size_t)std::max({restrict_blocks(N), restrict32_red_blocks(N), restrict32_rr_ranges(N)}) * k));
         STEP(dalloc(h, &h->y32, (size_t)kMaxP));
     }
     STEP(dalloc(h, &h->cbuf, (size_t)kMaxP));

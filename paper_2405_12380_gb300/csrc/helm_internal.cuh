@@ -20,6 +20,40 @@
 
 namespace helm {
 
+// ------------------------------------------------ bounds-checked build (HELM_CHECKED)
+// Compiled with -DHELM_CHECKED, HCHK(i, n) checks 0 <= i < n before an access: an
+// index out of range is recorded in a device word of the translation unit (the
+// first one wins: its source line and the unit's id) and replaced by 0, so the
+// access stays inside the buffer and nothing traps.  helm_checked_status reads and
+// clears the words of every unit.  In the normal build HCHK(i, n) is just i.
+std::vector<unsigned long long (*)()>& checked_units();
+#ifdef HELM_CHECKED
+#ifndef HELM_TU_ID
+#define HELM_TU_ID 0
+#endif
+static __device__ unsigned long long g_helm_oob = 0ull;
+__device__ __forceinline__ long long helm_chk(long long i, long long n, int line) {
+    if ((unsigned long long)i >= (unsigned long long)n) {
+        atomicCAS(&g_helm_oob, 0ull, ((unsigned long long)line << 8) | (unsigned long long)(HELM_TU_ID + 1));
+        return 0;
+    }
+    return i;
+}
+#define HCHK(i, n) (::helm::helm_chk((long long)(i), (long long)(n), __LINE__))
+static unsigned long long checked_take_unit() {
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_helm_oob, sizeof(v)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_helm_oob, &z, sizeof(z));
+    return v;
+}
+struct CheckedUnitRegistration {
+    explicit CheckedUnitRegistration(unsigned long long (*take)()) { checked_units().push_back(take); }
+};
+static CheckedUnitRegistration checked_unit_registration(&checked_take_unit);
+#else
+#define HCHK(i, n) (i)
+#endif
+
 // NVTX range for the phases of a call (setup, solve, preconditioner, Arnoldi step);
 // free when no profiler is attached
 struct NvtxRange {
@@ -126,6 +160,11 @@ void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, t
 bool launch_rbgs_sweep32(const Op<float>& op, int c0, const float2* f, const float2* xin, float2* xout, int conj,
                          double omega, cudaStream_t s);
 bool rbgs_sweep32_ok(const Op<float>& op, const void* f, const void* x, const void* tmp);
+// r_red[q] = (f - A x) at the red node of pair q (the pair layout: 3D, n even; the
+// red rows in the order of the red-row basis copy), zero on masked nodes; false
+// without launching where the pair layout does not apply
+bool launch_red_residual32(const Op<float>& op, const float2* f, const float2* x, float2* r_red, int conj,
+                           cudaStream_t s);
 int apply_grid_blocks(int dim, int n);
 int bicg_grid_blocks(int dim, int n);
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s);
@@ -284,6 +323,11 @@ void launch_red_rows_bf16(const void* Q, long long ldq, int k, long long N, int 
 // c = Q_red^T (v - A z) over the red rows (the residual after a red-black sweep that
 // ends with the black half-sweep); returns the number of block partials written
 int restrict32_red_blocks(long long N);
+// c partials = Q_red^T r_red from a stored red-row residual (M = red rows): returns
+// the number of partial rows written (restrict32_rr_ranges(N))
+int restrict32_rr_ranges(long long N);
+int launch_restrict32_rr(const void* Qr, long long ldr, int k, const float2* r_red, long long M, float2* partials,
+                         long long N, cudaStream_t s);
 int launch_restrict32_red(const Op<float>& op, const void* Qr, long long ldr, int k, const float2* v,
                           const float2* z, int conj, float2* partials, cudaStream_t s);
 int restrict_blocks(long long N);

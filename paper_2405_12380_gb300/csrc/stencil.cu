@@ -70,10 +70,10 @@ __device__ __forceinline__ typename CT<R>::T nbr_sum(const Op<R>& op, const type
     C z;
     z.x = 0; z.y = 0;
     // pairwise (tree) sum: three independent adds, then two -- shorter FP64 dependency chains
-    const C a = (code & 1u) ? x[l - 1] : z;
-    const C b = (code & 2u) ? x[l + 1] : z;
-    const C c = (code & 4u) ? x[l - sy] : z;
-    const C d = (code & 8u) ? x[l + sy] : z;
+    const C a = (code & 1u) ? x[HCHK(l - 1, op.N)] : z;
+    const C b = (code & 2u) ? x[HCHK(l + 1, op.N)] : z;
+    const C c = (code & 4u) ? x[HCHK(l - sy, op.N)] : z;
+    const C d = (code & 8u) ? x[HCHK(l + sy, op.N)] : z;
     if (op.face) {
         // Sommerfeld / Neumann boundary rows: axis a weighs 2^-(b - [on an axis-a face])
         const unsigned fc = op.face[l];
@@ -82,16 +82,16 @@ __device__ __forceinline__ typename CT<R>::T nbr_sum(const Op<R>& op, const type
         C s = cadd(cscale(wx, cadd(a, b)), cscale(wy, cadd(c, d)));
         if (op.dim == 3) {
             const R wz = ldexp((R)1, -(nb - (int)((fc >> 2) & 1u)));
-            const C e = (code & 16u) ? x[l - sz] : z;
-            const C f = (code & 32u) ? x[l + sz] : z;
+            const C e = (code & 16u) ? x[HCHK(l - sz, op.N)] : z;
+            const C f = (code & 32u) ? x[HCHK(l + sz, op.N)] : z;
             s = cadd(s, cscale(wz, cadd(e, f)));
         }
         return s;
     }
     C s = cadd(cadd(a, b), cadd(c, d));
     if (op.dim == 3) {
-        const C e = (code & 16u) ? x[l - sz] : z;
-        const C f = (code & 32u) ? x[l + sz] : z;
+        const C e = (code & 16u) ? x[HCHK(l - sz, op.N)] : z;
+        const C f = (code & 32u) ? x[HCHK(l + sz, op.N)] : z;
         s = cadd(s, cadd(e, f));
     }
     return s;
@@ -264,13 +264,15 @@ __device__ __forceinline__ void pair_sums(unsigned c0, unsigned c1, float2 left,
 }
 
 // KIND 0: y = A x (FLAG: y = f - A x); KIND 1: damped-Jacobi sweep y = x + omega
-// D^-1 (f - A x) (FLAG: from x = 0, x not read)
+// D^-1 (f - A x) (FLAG: from x = 0, x not read); KIND 2: the residual f - A x of the
+// red node of each pair (colour 0), written compactly as one float2 per pair
+// (zero on masked nodes)
 template <int KIND, bool FLAG, bool NORM>
 __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, float omega,
                                                        const float4* __restrict__ x, const float4* __restrict__ f,
                                                        float4* __restrict__ y, double* partials, int conj) {
     constexpr bool NBR = !(KIND == 1 && FLAG);             // neighbours (and x) are read
-    constexpr bool RHS = KIND == 1 || FLAG;                // f is read
+    constexpr bool RHS = KIND >= 1 || FLAG;                // f is read
     constexpr unsigned kMM = kMasked | (kMasked << 8);
     const int n = op.n, h = n >> 1;
     const int i2 = blockIdx.x * BX + threadIdx.x;          // pair index within the row
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
     const int k1 = min(n, k0 + zc);
     const bool valid = i2 < h && j < n;
     const int sy = h, sz = h * n;                          // strides in pairs (N < 2^31)
+    [[maybe_unused]] const long long NP = op.N >> 1;       // pairs (bounds of the checked build)
     const int lane = threadIdx.x;
     const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
     const unsigned short* lidx2 = reinterpret_cast<const unsigned short*>(op.lidx);
@@ -287,21 +290,21 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
     int l = i2 + h * (j + n * k0);
     float4 prev = z4, cur = z4, next = z4, fv = z4;
     if (NBR) {
-        prev = (valid && k0 > 0) ? x[l - sz] : z4;
-        cur = valid ? x[l] : z4;
-        next = (valid && k0 + 1 < n) ? x[l + sz] : z4;
+        prev = (valid && k0 > 0) ? x[HCHK(l - sz, NP)] : z4;
+        cur = valid ? x[HCHK(l, NP)] : z4;
+        next = (valid && k0 + 1 < n) ? x[HCHK(l + sz, NP)] : z4;
     }
-    if (RHS) fv = valid ? f[l] : z4;
-    unsigned cc = valid ? (unsigned)code2[l] : kMM;
-    unsigned li = valid ? (unsigned)lidx2[l] : 0u;
+    if (RHS) fv = valid ? f[HCHK(l, NP)] : z4;
+    unsigned cc = valid ? (unsigned)code2[HCHK(l, NP)] : kMM;
+    unsigned li = valid ? (unsigned)lidx2[HCHK(l, NP)] : 0u;
     float acc = 0.f;
     for (int k = k0; k < k1; ++k, l += sz) {
         const bool more = valid && k + 1 < k1;
         float4 next2 = z4, f_n = z4;
-        if (NBR) next2 = (more && k + 2 < n) ? x[l + 2 * sz] : z4;
-        if (RHS) f_n = more ? f[l + sz] : z4;
-        const unsigned cc_n = more ? (unsigned)code2[l + sz] : kMM;
-        const unsigned li_n = more ? (unsigned)lidx2[l + sz] : 0u;
+        if (NBR) next2 = (more && k + 2 < n) ? x[HCHK(l + 2 * sz, NP)] : z4;
+        if (RHS) f_n = more ? f[HCHK(l + sz, NP)] : z4;
+        const unsigned cc_n = more ? (unsigned)code2[HCHK(l + sz, NP)] : kMM;
+        const unsigned li_n = more ? (unsigned)lidx2[HCHK(l + sz, NP)] : 0u;
         const unsigned c0 = cc & 0xffu, c1 = cc >> 8;
         float2 s0 = make_float2(0.f, 0.f), s1 = s0;
         if (NBR) {
@@ -312,23 +315,23 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
             right.y = __shfl_down_sync(0xffffffffu, cur.y, 1);
             // the row-segment ends: node i-1 of lane 0 and node i+2 of the last lane
             // (fluid nodes are interior, so these exist whenever the bit is set)
-            if (lane == 0 && (c0 & 1u)) left = x1[2 * l - 1];
-            if (lane == BX - 1 && (c1 & 2u)) right = x1[2 * l + 2];
+            if (lane == 0 && (c0 & 1u)) left = x1[HCHK(2 * l - 1, op.N)];
+            if (lane == BX - 1 && (c1 & 2u)) right = x1[HCHK(2 * l + 2, op.N)];
             const unsigned any = c0 | c1;                  // a masked code has no neighbour bits
-            const float4 ym = (any & 4u) ? x[l - sy] : z4;
-            const float4 yp = (any & 8u) ? x[l + sy] : z4;
+            const float4 ym = (any & 4u) ? x[HCHK(l - sy, NP)] : z4;
+            const float4 yp = (any & 8u) ? x[HCHK(l + sy, NP)] : z4;
             pair_sums(c0, c1, left, right, cur, ym, yp, prev, next, s0, s1);
         }
         float2 o0, o1;
-        if (KIND == 0) {
+        if (KIND != 1) {
             float2 d0, d1;
             if (op.k2) {
-                const float4 kk = reinterpret_cast<const float4*>(op.k2)[l];
+                const float4 kk = reinterpret_cast<const float4*>(op.k2)[HCHK(l, NP)];
                 d0 = make_float2(kk.x - 6.f * op.hinv2, kk.y);
                 d1 = make_float2(kk.z - 6.f * op.hinv2, kk.w);
             } else {
-                d0 = make_float2(op.dre, op.im[li & 0xffu]);
-                d1 = make_float2(op.dre, op.im[li >> 8]);
+                d0 = make_float2(op.dre, op.im[HCHK(li & 0xffu, kMaxLayerCells + 1)]);
+                d1 = make_float2(op.dre, op.im[HCHK(li >> 8, kMaxLayerCells + 1)]);
             }
             if (conj) { d0.y = -d0.y; d1.y = -d1.y; }
             const float2 x0 = lo2(cur), xh = hi2(cur);
@@ -338,19 +341,19 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
             o1 = (c1 & kMasked) ? xh
                                 : make_float2(op.hinv2 * s1.x + (d1.x * xh.x - d1.y * xh.y),
                                               op.hinv2 * s1.y + (d1.x * xh.y + d1.y * xh.x));
-            if (FLAG) {
+            if (FLAG || KIND == 2) {
                 o0 = csub(lo2(fv), o0);
                 o1 = csub(hi2(fv), o1);
             }
         } else {
             float2 id0, id1;
             if (op.k2) {
-                const float4 iv = reinterpret_cast<const float4*>(op.invd)[l];
+                const float4 iv = reinterpret_cast<const float4*>(op.invd)[HCHK(l, NP)];
                 id0 = lo2(iv);
                 id1 = hi2(iv);
             } else {
-                id0 = op.invd_tab[li & 0xffu];
-                id1 = op.invd_tab[li >> 8];
+                id0 = op.invd_tab[HCHK(li & 0xffu, kMaxLayerCells + 1)];
+                id1 = op.invd_tab[HCHK(li >> 8, kMaxLayerCells + 1)];
             }
             if (conj) { id0.y = -id0.y; id1.y = -id1.y; }
             const float2 f0 = lo2(fv), fh = hi2(fv);
@@ -375,8 +378,14 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
             }
         }
         if (valid) {
-            y[l] = make_float4(o0.x, o0.y, o1.x, o1.y);
-            if (NORM) acc += (o0.x * o0.x + o0.y * o0.y) + (o1.x * o1.x + o1.y * o1.y);
+            if (KIND == 2) {
+                const int a = (j + k) & 1;                 // the red node of the pair
+                const unsigned ca = a ? c1 : c0;
+                reinterpret_cast<float2*>(y)[HCHK(l, NP)] = (ca & kMasked) ? make_float2(0.f, 0.f) : (a ? o1 : o0);
+            } else {
+                y[HCHK(l, NP)] = make_float4(o0.x, o0.y, o1.x, o1.y);
+                if (NORM) acc += (o0.x * o0.x + o0.y * o0.y) + (o1.x * o1.x + o1.y * o1.y);
+            }
         }
         prev = cur;
         cur = next;
@@ -424,6 +433,7 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
     const int k0 = blockIdx.z * zc;
     const int k1 = min(n, k0 + zc);
     const bool valid = i2 < h && j < n;
+    [[maybe_unused]] const long long NP = op.N >> 1;
     const int sy = h, sz = h * n;
     const int lane = threadIdx.x;
     const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
@@ -434,20 +444,20 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
     int l = i2 + h * (j + n * k0);
     float4 prev = z4, cur = z4, next = z4;
     if (!XZERO) {
-        prev = (valid && k0 > 0) ? x[l - sz] : z4;
-        cur = valid ? x[l] : z4;
-        next = (valid && k0 + 1 < n) ? x[l + sz] : z4;
+        prev = (valid && k0 > 0) ? x[HCHK(l - sz, NP)] : z4;
+        cur = valid ? x[HCHK(l, NP)] : z4;
+        next = (valid && k0 + 1 < n) ? x[HCHK(l + sz, NP)] : z4;
     }
-    float4 fv = valid ? f[l] : z4;
-    unsigned cc = valid ? (unsigned)code2[l] : kMM;
-    unsigned li = valid ? (unsigned)lidx2[l] : 0u;
+    float4 fv = valid ? f[HCHK(l, NP)] : z4;
+    unsigned cc = valid ? (unsigned)code2[HCHK(l, NP)] : kMM;
+    unsigned li = valid ? (unsigned)lidx2[HCHK(l, NP)] : 0u;
     for (int k = k0; k < k1; ++k, l += sz) {
         const bool more = valid && k + 1 < k1;
         float4 next2 = z4;
-        if (!XZERO) next2 = (more && k + 2 < n) ? x[l + 2 * sz] : z4;
-        const float4 f_n = more ? f[l + sz] : z4;
-        const unsigned cc_n = more ? (unsigned)code2[l + sz] : kMM;
-        const unsigned li_n = more ? (unsigned)lidx2[l + sz] : 0u;
+        if (!XZERO) next2 = (more && k + 2 < n) ? x[HCHK(l + 2 * sz, NP)] : z4;
+        const float4 f_n = more ? f[HCHK(l + sz, NP)] : z4;
+        const unsigned cc_n = more ? (unsigned)code2[HCHK(l + sz, NP)] : kMM;
+        const unsigned li_n = more ? (unsigned)lidx2[HCHK(l + sz, NP)] : 0u;
         const int a = ((j + k) & 1) ^ colour;               // swept node of the pair
         const unsigned ca = a ? (cc >> 8) : (cc & 0xffu);
         float2 s0 = make_float2(0.f, 0.f), s1 = s0;
@@ -457,26 +467,26 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
             left.y = __shfl_up_sync(0xffffffffu, cur.w, 1);
             right.x = __shfl_down_sync(0xffffffffu, cur.x, 1);
             right.y = __shfl_down_sync(0xffffffffu, cur.y, 1);
-            if (lane == 0 && a == 0 && (ca & 1u)) left = x1[2 * l - 1];
-            if (lane == BX - 1 && a == 1 && (ca & 2u)) right = x1[2 * l + 2];
-            const float4 ym = (ca & 4u) ? x[l - sy] : z4;
-            const float4 yp = (ca & 8u) ? x[l + sy] : z4;
+            if (lane == 0 && a == 0 && (ca & 1u)) left = x1[HCHK(2 * l - 1, op.N)];
+            if (lane == BX - 1 && a == 1 && (ca & 2u)) right = x1[HCHK(2 * l + 2, op.N)];
+            const float4 ym = (ca & 4u) ? x[HCHK(l - sy, NP)] : z4;
+            const float4 yp = (ca & 8u) ? x[HCHK(l + sy, NP)] : z4;
             pair_sums(a ? 0u : ca, a ? ca : 0u, left, right, cur, ym, yp, prev, next, s0, s1);
         }
         if (valid) {
             float2 id = make_float2(0.f, 0.f);
             if (!(ca & kMasked)) {
                 if (op.k2) {
-                    const float4 iv = reinterpret_cast<const float4*>(op.invd)[l];
+                    const float4 iv = reinterpret_cast<const float4*>(op.invd)[HCHK(l, NP)];
                     id = a ? hi2(iv) : lo2(iv);
                 } else {
-                    id = op.invd_tab[a ? (li >> 8) : (li & 0xffu)];
+                    id = op.invd_tab[HCHK(a ? (li >> 8) : (li & 0xffu), kMaxLayerCells + 1)];
                 }
                 if (conj) id.y = -id.y;
             }
             const float2 out = gs_value(op, ca, a ? hi2(fv) : lo2(fv), a ? s1 : s0, id, a ? hi2(cur) : lo2(cur),
                                         omega, XZERO);
-            xw[2 * l + a] = out;
+            xw[HCHK(2 * l + a, op.N)] = out;
         }
         prev = cur;
         cur = next;
@@ -508,10 +518,10 @@ __device__ __forceinline__ float2 pair_node(float4 v, int a) { return a ? hi2(v)
 __device__ __forceinline__ float2 sweep_invd(const Op<float>& op, int l, int a, unsigned li, int conj) {
     float2 id;
     if (op.k2) {
-        const float4 iv = reinterpret_cast<const float4*>(op.invd)[l];
+        const float4 iv = reinterpret_cast<const float4*>(op.invd)[HCHK(l, op.N >> 1)];
         id = a ? hi2(iv) : lo2(iv);
     } else {
-        id = op.invd_tab[a ? (li >> 8) : (li & 0xffu)];
+        id = op.invd_tab[HCHK(a ? (li >> 8) : (li & 0xffu), kMaxLayerCells + 1)];
     }
     if (conj) id.y = -id.y;
     return id;
@@ -541,6 +551,7 @@ __device__ __forceinline__ void sweep_c64_block(const Op<float>& op, int by, int
     const bool row_ok = i2 < h && j >= 0 && j < n;
     const bool inner = row_ok && ty >= 1 && ty <= BYI;
     const int sy = h, sz = h * n;
+    [[maybe_unused]] const long long NP = op.N >> 1;
     const int plane = blockDim.y * TXT, me = ty * TXT + i2;
     const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
     const unsigned short* lidx2 = reinterpret_cast<const unsigned short*>(op.lidx);
@@ -552,13 +563,13 @@ __device__ __forceinline__ void sweep_c64_block(const Op<float>& op, int by, int
     auto in_t = [&](int q) { return row_ok && q >= 0 && q < n; };
     float4 om = z4, oc = z4, on = z4;                      // old pairs at planes t-1, t, t+1
     if (!XZERO) {
-        if (in_t(t - 1)) om = xin[lrow + sz * (t - 1)];
-        if (in_t(t)) oc = xin[lrow + sz * t];
-        if (in_t(t + 1)) on = xin[lrow + sz * (t + 1)];
+        if (in_t(t - 1)) om = xin[HCHK(lrow + sz * (t - 1), NP)];
+        if (in_t(t)) oc = xin[HCHK(lrow + sz * t, NP)];
+        if (in_t(t + 1)) on = xin[HCHK(lrow + sz * (t + 1), NP)];
     }
-    float4 fc = in_t(t) ? f[lrow + sz * t] : z4, fm = z4;
-    unsigned cc = in_t(t) ? (unsigned)code2[lrow + sz * t] : kMM, cm = kMM;
-    unsigned lc = in_t(t) ? (unsigned)lidx2[lrow + sz * t] : 0u, lm = 0u;
+    float4 fc = in_t(t) ? f[HCHK(lrow + sz * t, NP)] : z4, fm = z4;
+    unsigned cc = in_t(t) ? (unsigned)code2[HCHK(lrow + sz * t, NP)] : kMM, cm = kMM;
+    unsigned lc = in_t(t) ? (unsigned)lidx2[HCHK(lrow + sz * t, NP)] : 0u, lm = 0u;
     float2 rm2 = z2, rm = z2;                              // new colour-c0 values at planes t-2, t-1
     int slot = 0, slot_m = 2;
     for (; t <= k1; ++t) {
@@ -567,11 +578,11 @@ __device__ __forceinline__ void sweep_c64_block(const Op<float>& op, int by, int
         float4 onn = z4, fn = z4;
         unsigned cn = kMM, ln = 0u;
         if (in_t(t + 1)) {
-            fn = f[l + sz];
-            cn = code2[l + sz];
-            ln = lidx2[l + sz];
+            fn = f[HCHK(l + sz, NP)];
+            cn = code2[HCHK(l + sz, NP)];
+            ln = lidx2[HCHK(l + sz, NP)];
         }
-        if (!XZERO && in_t(t + 2)) onn = xin[l + 2 * sz];
+        if (!XZERO && in_t(t + 2)) onn = xin[HCHK(l + 2 * sz, NP)];
         // colour c0 at plane t (old neighbours)
         float2 rc = z2;
         {
@@ -584,10 +595,10 @@ __device__ __forceinline__ void sweep_c64_block(const Op<float>& op, int by, int
                 left.y = __shfl_up_sync(0xffffffffu, oc.w, 1);
                 right.x = __shfl_down_sync(0xffffffffu, oc.x, 1);
                 right.y = __shfl_down_sync(0xffffffffu, oc.y, 1);
-                if (tin && lane == 0 && a == 0 && (ca & 1u)) left = x1[2 * l - 1];
-                if (tin && lane == 31 && a == 1 && (ca & 2u)) right = x1[2 * l + 2];
-                const float2 ym = (tin && (ca & 4u)) ? pair_node(xin[l - sy], a) : z2;
-                const float2 yp = (tin && (ca & 8u)) ? pair_node(xin[l + sy], a) : z2;
+                if (tin && lane == 0 && a == 0 && (ca & 1u)) left = x1[HCHK(2 * l - 1, op.N)];
+                if (tin && lane == 31 && a == 1 && (ca & 2u)) right = x1[HCHK(2 * l + 2, op.N)];
+                const float2 ym = (tin && (ca & 4u)) ? pair_node(xin[HCHK(l - sy, NP)], a) : z2;
+                const float2 yp = (tin && (ca & 8u)) ? pair_node(xin[HCHK(l + sy, NP)], a) : z2;
                 sa = six_sum(ca, a ? lo2(oc) : left, a ? right : hi2(oc), ym, yp, pair_node(om, a), pair_node(on, a));
             }
             if (tin) {
@@ -610,7 +621,7 @@ __device__ __forceinline__ void sweep_c64_block(const Op<float>& op, int by, int
             const float2 sb = six_sum(ca, xm, xp, ym, yp, rm2, rc);
             const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, lmi, a, lm, conj);
             const float2 b = gs_value(op, ca, pair_node(fm, a), sb, id, pair_node(om, a), omega, false);
-            xout[lmi] = a ? make_float4(rm.x, rm.y, b.x, b.y) : make_float4(b.x, b.y, rm.x, rm.y);
+            xout[HCHK(lmi, NP)] = a ? make_float4(rm.x, rm.y, b.x, b.y) : make_float4(b.x, b.y, rm.x, rm.y);
         }
         rm2 = rm;
         rm = rc;
@@ -889,14 +900,14 @@ __device__ __forceinline__ Cdf invd_df(const DfTab& t, int m, int conj) {
 __device__ __forceinline__ Cdf nbr_sum_df(const Op<double>& op, const float4* __restrict__ x, long long l,
                                           unsigned code) {
     const long long sy = op.n, sz = (long long)op.n * op.n;
-    const Cdf a = (code & 1u) ? cdf_load(x, l - 1) : cdf_zero();
-    const Cdf b = (code & 2u) ? cdf_load(x, l + 1) : cdf_zero();
-    const Cdf c = (code & 4u) ? cdf_load(x, l - sy) : cdf_zero();
-    const Cdf d = (code & 8u) ? cdf_load(x, l + sy) : cdf_zero();
+    const Cdf a = (code & 1u) ? cdf_load(x, HCHK(l - 1, op.N)) : cdf_zero();
+    const Cdf b = (code & 2u) ? cdf_load(x, HCHK(l + 1, op.N)) : cdf_zero();
+    const Cdf c = (code & 4u) ? cdf_load(x, HCHK(l - sy, op.N)) : cdf_zero();
+    const Cdf d = (code & 8u) ? cdf_load(x, HCHK(l + sy, op.N)) : cdf_zero();
     Cdf s = cdf_add(cdf_add(a, b), cdf_add(c, d));
     if (op.dim == 3) {
-        const Cdf e = (code & 16u) ? cdf_load(x, l - sz) : cdf_zero();
-        const Cdf f = (code & 32u) ? cdf_load(x, l + sz) : cdf_zero();
+        const Cdf e = (code & 16u) ? cdf_load(x, HCHK(l - sz, op.N)) : cdf_zero();
+        const Cdf f = (code & 32u) ? cdf_load(x, HCHK(l + sz, op.N)) : cdf_zero();
         s = cdf_add(s, cdf_add(e, f));
     }
     return s;
@@ -980,14 +991,14 @@ template <typename XT>
 __device__ __forceinline__ Cdf nbr_sum_any(const Op<double>& op, const XT* __restrict__ x, long long l,
                                            unsigned code) {
     const long long sy = op.n, sz = (long long)op.n * op.n;
-    const Cdf a = (code & 1u) ? cdf_load(x, l - 1) : cdf_zero();
-    const Cdf b = (code & 2u) ? cdf_load(x, l + 1) : cdf_zero();
-    const Cdf c = (code & 4u) ? cdf_load(x, l - sy) : cdf_zero();
-    const Cdf d = (code & 8u) ? cdf_load(x, l + sy) : cdf_zero();
+    const Cdf a = (code & 1u) ? cdf_load(x, HCHK(l - 1, op.N)) : cdf_zero();
+    const Cdf b = (code & 2u) ? cdf_load(x, HCHK(l + 1, op.N)) : cdf_zero();
+    const Cdf c = (code & 4u) ? cdf_load(x, HCHK(l - sy, op.N)) : cdf_zero();
+    const Cdf d = (code & 8u) ? cdf_load(x, HCHK(l + sy, op.N)) : cdf_zero();
     Cdf s = cdf_add(cdf_add(a, b), cdf_add(c, d));
     if (op.dim == 3) {
-        const Cdf e = (code & 16u) ? cdf_load(x, l - sz) : cdf_zero();
-        const Cdf f = (code & 32u) ? cdf_load(x, l + sz) : cdf_zero();
+        const Cdf e = (code & 16u) ? cdf_load(x, HCHK(l - sz, op.N)) : cdf_zero();
+        const Cdf f = (code & 32u) ? cdf_load(x, HCHK(l + sz, op.N)) : cdf_zero();
         s = cdf_add(s, cdf_add(e, f));
     }
     return s;
@@ -1124,14 +1135,14 @@ __device__ __forceinline__ Cdf cdf_load_cg(const float4* p, long long l) {
 
 __device__ __forceinline__ Cdf nbr_sum_df_cg(const Op<double>& op, const float4* x, long long l, unsigned code) {
     const long long sy = op.n, sz = (long long)op.n * op.n;
-    const Cdf a = (code & 1u) ? cdf_load_cg(x, l - 1) : cdf_zero();
-    const Cdf b = (code & 2u) ? cdf_load_cg(x, l + 1) : cdf_zero();
-    const Cdf c = (code & 4u) ? cdf_load_cg(x, l - sy) : cdf_zero();
-    const Cdf d = (code & 8u) ? cdf_load_cg(x, l + sy) : cdf_zero();
+    const Cdf a = (code & 1u) ? cdf_load_cg(x, HCHK(l - 1, op.N)) : cdf_zero();
+    const Cdf b = (code & 2u) ? cdf_load_cg(x, HCHK(l + 1, op.N)) : cdf_zero();
+    const Cdf c = (code & 4u) ? cdf_load_cg(x, HCHK(l - sy, op.N)) : cdf_zero();
+    const Cdf d = (code & 8u) ? cdf_load_cg(x, HCHK(l + sy, op.N)) : cdf_zero();
     Cdf s = cdf_add(cdf_add(a, b), cdf_add(c, d));
     if (op.dim == 3) {
-        const Cdf e = (code & 16u) ? cdf_load_cg(x, l - sz) : cdf_zero();
-        const Cdf f = (code & 32u) ? cdf_load_cg(x, l + sz) : cdf_zero();
+        const Cdf e = (code & 16u) ? cdf_load_cg(x, HCHK(l - sz, op.N)) : cdf_zero();
+        const Cdf f = (code & 32u) ? cdf_load_cg(x, HCHK(l + sz, op.N)) : cdf_zero();
         s = cdf_add(s, cdf_add(e, f));
     }
     return s;
@@ -1550,10 +1561,21 @@ void launch_rbgs_half(const Op<R>& op, int colour, const typename CT<R>::T* f, t
     else k_rbgs<R, false><<<g, b, 0, s>>>(op, colour, f, x, conj, (R)omega);
 }
 
+bool launch_red_residual32(const Op<float>& op, const float2* f, const float2* x, float2* r_red, int conj,
+                           cudaStream_t s) {
+    if (!pair_ok(op, f, x, r_red)) return false;
+    int zc;
+    const dim3 g = pair_grid(op.n, &zc), b(BX, BY);
+    k_march_c64<2, false, false><<<g, b, 0, s>>>(op, zc, 0.f, reinterpret_cast<const float4*>(x),
+                                                 reinterpret_cast<const float4*>(f), reinterpret_cast<float4*>(r_red),
+                                                 nullptr, conj);
+    return true;
+}
+
 namespace {
 
 // launch shape of k_sweep_c64 on an n^3 grid: whole rows per block (n/2 pairs, at
-// most 128), 16 rows (8 for rows wider than one warp) including the two halo rows;
+// most 128), as many rows as fill 1024 threads (8 to 32) including the two halo rows;
 // z chunks of 4..16 planes, as many as fill the resident block slots once
 struct SweepShape {
     dim3 g, b;
@@ -1565,7 +1587,7 @@ bool sweep_shape(int n, SweepShape& sh) {
     const int h = n / 2;
     if (n % 2 != 0 || h < 1 || h > 128) return false;
     const int txt = (h + 31) / 32 * 32;
-    const int tyt = txt <= 32 ? 16 : 8;
+    const int tyt = std::max(8, std::min(32, kSweepMaxThreads / txt));
     const int byi = tyt - 2;
     sh.b = dim3(txt, tyt);
     sh.smem = (size_t)3 * txt * tyt * sizeof(float2);

@@ -916,13 +916,13 @@ __device__ __forceinline__ float2 red_residual32(const Op<float>& op, const floa
     if (code & 0x80u) return make_float2(0.f, 0.f);
     const long long sy = op.n, sz = (long long)op.n * op.n;
     float2 s = make_float2(0.f, 0.f);
-    if (code & 1u) s = cadd(s, z[l - 1]);
-    if (code & 2u) s = cadd(s, z[l + 1]);
-    if (code & 4u) s = cadd(s, z[l - sy]);
-    if (code & 8u) s = cadd(s, z[l + sy]);
+    if (code & 1u) s = cadd(s, z[HCHK(l - 1, op.N)]);
+    if (code & 2u) s = cadd(s, z[HCHK(l + 1, op.N)]);
+    if (code & 4u) s = cadd(s, z[HCHK(l - sy, op.N)]);
+    if (code & 8u) s = cadd(s, z[HCHK(l + sy, op.N)]);
     if (op.dim == 3) {
-        if (code & 16u) s = cadd(s, z[l - sz]);
-        if (code & 32u) s = cadd(s, z[l + sz]);
+        if (code & 16u) s = cadd(s, z[HCHK(l - sz, op.N)]);
+        if (code & 32u) s = cadd(s, z[HCHK(l + sz, op.N)]);
     }
     float2 d;
     if (op.k2) {
@@ -1018,6 +1018,71 @@ __global__ void __launch_bounds__(RR_T, 4) k_restrict32_red(Op<float> op, const 
     }
 }
 
+// c = Q_red^T r_red from a stored red-row residual: a tall-skinny product.  A warp
+// owns RQ_COLS columns and one range of RQ_RANGE rows; per 256 rows each lane loads
+// its 8 consecutive residual rows and then all its 16-byte basis pieces (one per
+// column, issued together) before the FMAs, and keeps the complex sums in
+// registers over the range; the lanes are added once at the end (fixed butterfly)
+// and lane 0 writes partials[range][j].  Deterministic.
+constexpr int RQ_COLS = 8;
+constexpr int RQ_RANGE = 1024;
+__global__ void __launch_bounds__(256) k_restrict32_rr(const __nv_bfloat16* __restrict__ Qr, long long ldr, int k,
+                                                       const float2* __restrict__ r, long long M,
+                                                       float2* __restrict__ partials, int S) {
+    const int lane = threadIdx.x & 31;
+    const int rg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int c0 = blockIdx.y * RQ_COLS;
+    if (rg >= S) return;
+    const int nc = min(RQ_COLS, k - c0);
+    float ax[RQ_COLS], ay[RQ_COLS];
+#pragma unroll
+    for (int c = 0; c < RQ_COLS; ++c) ax[c] = ay[c] = 0.f;
+#pragma unroll 1
+    for (int it = 0; it < RQ_RANGE / 256; ++it) {
+        const long long m0 = (long long)rg * RQ_RANGE + it * 256 + lane * 8;
+        if (m0 >= M) break;
+        uint4 u[RQ_COLS];
+#pragma unroll
+        for (int c = 0; c < RQ_COLS; ++c)
+            u[c] = c < nc ? __ldcs(reinterpret_cast<const uint4*>(
+                                Qr + HCHK((long long)(c0 + c) * ldr + m0, (long long)k * ldr - 7)))
+                          : make_uint4(0u, 0u, 0u, 0u);
+        float2 rv[8];
+        if (m0 + 8 <= M) {
+            const float4* r4 = reinterpret_cast<const float4*>(r + HCHK(m0, M - 7));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 t = r4[q];
+                rv[2 * q] = make_float2(t.x, t.y);
+                rv[2 * q + 1] = make_float2(t.z, t.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) rv[q] = (m0 + q < M) ? r[m0 + q] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int c = 0; c < RQ_COLS; ++c) {
+            float qv[8];
+            bf16x8(u[c], qv);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                ax[c] = fmaf(qv[q], rv[q].x, ax[c]);
+                ay[c] = fmaf(qv[q], rv[q].y, ay[c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < RQ_COLS; ++c)
+        for (int o = 16; o > 0; o >>= 1) {
+            ax[c] += __shfl_xor_sync(0xffffffffu, ax[c], o);
+            ay[c] += __shfl_xor_sync(0xffffffffu, ay[c], o);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < RQ_COLS; ++c)
+            if (c < nc) partials[(long long)rg * k + c0 + c] = make_float2(ax[c], ay[c]);
+}
+
 // z += Q y, eight consecutive rows per thread (16-byte basis loads, 64-byte z
 // accesses); z must be 16-byte aligned
 __global__ void __launch_bounds__(256) k_prolong32v(const __nv_bfloat16* __restrict__ Q, long long ldq, int k,
@@ -1039,7 +1104,8 @@ __global__ void __launch_bounds__(256) k_prolong32v(const __nv_bfloat16* __restr
         const __nv_bfloat16* Qg = Q + l0;
 #pragma unroll 8
         for (int j = 0; j < k; ++j) {
-            const uint4 u = __ldcs(reinterpret_cast<const uint4*>(Qg + (long long)j * ldq));
+            const uint4 u =
+                __ldcs(reinterpret_cast<const uint4*>(Q + HCHK((long long)j * ldq + l0, (long long)k * ldq - 7)));
             float qv[8];
             bf16x8(u, qv);
             const float2 yj = ys[j];
@@ -1050,7 +1116,7 @@ __global__ void __launch_bounds__(256) k_prolong32v(const __nv_bfloat16* __restr
             }
         }
         if (l0 + 8 <= N) {
-            float4* z4 = reinterpret_cast<float4*>(z + l0);
+            float4* z4 = reinterpret_cast<float4*>(z + HCHK(l0, N - 7));
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float4 t = z4[q];
@@ -1236,6 +1302,19 @@ int launch_restrict32_red(const Op<float>& op, const void* Qr, long long ldr, in
     k_restrict32_red<<<nb, RR_T, 0, s>>>(op, static_cast<const __nv_bfloat16*>(Qr), ldr, k, v, z, conj, partials,
                                          (op.N + 1) / 2);
     return nb;
+}
+
+int restrict32_rr_ranges(long long N) {
+    const long long M = (N + 1) / 2;
+    return (int)std::max<long long>(1, (M + RQ_RANGE - 1) / RQ_RANGE);
+}
+
+int launch_restrict32_rr(const void* Qr, long long ldr, int k, const float2* r_red, long long M, float2* partials,
+                         long long N, cudaStream_t s) {
+    const int S = restrict32_rr_ranges(N);
+    const dim3 g((S + 7) / 8, (k + RQ_COLS - 1) / RQ_COLS);
+    k_restrict32_rr<<<g, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(Qr), ldr, k, r_red, M, partials, S);
+    return S;
 }
 
 void launch_restrict32(const Op<float>& op, const void* Qv, long long ldq, int k, const float2* v, const float2* z,

@@ -64,10 +64,11 @@ def test_singular_coarse_operator():
     assert e.value.status == 7, e.value                                # HELM_SINGULAR_COARSE
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64"])
 def test_barrier_timeout_returns_timeout_and_handle_recovers(precision):
-    """FP64: the double-float cooperative cycle inside BiCGStab; mixed: the same
-    handle's preconditioner call (helm_precond) and the complex64 BiCGStab."""
+    """The double-float cooperative cycle of FP64 handles inside BiCGStab, and the
+    same handle's preconditioner call (helm_precond).  (The complex64 cycle of
+    mixed handles has no grid-wide wait: its sweeps are separate launches.)"""
     import paper_2405_12380_gb300 as hm
     import time
     s = small_scene(3, 25)

@@ -52,3 +52,14 @@ def test_no_gpu_means_no_device(libpath):
     mask = (ctypes.c_uint8 * 27)(*([1] * 27))
     st = L.helm_create(3, 3, 1.0, 0, 0.5, ctypes.cast(mask, ctypes.c_void_p), None, 0, ctypes.byref(h))
     assert st == _lib.HELM_NO_DEVICE
+
+
+def test_checked_build_exports_the_same_boundary():
+    """The bounds-checked variant (-DHELM_CHECKED) builds and exports every declared
+    symbol as well."""
+    from paper_2405_12380_gb300 import build
+    if not os.path.exists(build.LIB_CHECKED):
+        build.build(checked=True)
+    lib = ctypes.CDLL(build.LIB_CHECKED)
+    for name in _declared():
+        assert hasattr(lib, name), name
