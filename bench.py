@@ -287,9 +287,13 @@ def max_over_ranks(value, world, device="cuda"):
 
 def kernel_entries(w, st_prof, N, k, hbm, hbm_src, workload):
     """Per-kernel achieved HBM bandwidth of the profiled solve: algorithmic bytes
-    per launch (per node: restriction 2k + 18 B, prolongation 2k + 16 B, red-black
-    half-sweep 13 B, operator 17 B for complex64 vectors and the BF16 basis; FP64
-    handles: FP32-pair basis 8k B per row) over the mean CUDA-event duration."""
+    per launch over the mean CUDA-event duration.  Mixed handles, per node:
+    restriction k + 26 B (red-row residual: v and z in, 2 table bytes, the red
+    residual out and in again; BF16 Q_red k B), prolongation 2k + 16 B (BF16 Q,
+    z in and out), fused red-black sweep 26 B from x (x and f in, x out, 2 table
+    bytes) and 18 B from zero, operator with the fused BiCGStab reduction 26 B (x and
+    the dot operand in, y out, 2 table bytes).  FP64 handles: FP32-pair basis 8k B
+    per row."""
     mixed = w.get("precision") == "mixed"
     out = []
 
@@ -307,11 +311,14 @@ def kernel_entries(w, st_prof, N, k, hbm, hbm_src, workload):
                     "timing": "CUDA events around every launch, one profiled solve after the timed solves"})
 
     if mixed:
-        add("restrict", "k_restrict32", "n_restrict", "restrict_ms", (2.0 * k + 18.0) * N,
-            "c = Q^T (v - A z), BF16 Q, complex64 v and z")
-        add("prolong", "k_prolong32", "n_prolong", "prolong_ms", (2.0 * k + 16.0) * N, "z += Q y, BF16 Q")
-        add("sweep", "k_rbgs_c64", "n_sweep", "sweep_ms", 13.0 * N, "complex64 red-black half-sweep")
-        add("apply", "k_march_c64", "n_apply", "apply_ms", 17.0 * N, "complex64 y = A x")
+        add("restrict", "k_march_c64<2> + k_restrict32_rr", "n_restrict", "restrict_ms", (k + 26.0) * N,
+            "c = Q_red^T (v - A z) on the red rows: red residual, then BF16 tall-skinny product")
+        add("prolong", "k_prolong32v", "n_prolong", "prolong_ms", (2.0 * k + 16.0) * N, "z += Q y, BF16 Q")
+        nr = max(1, w["n_r"])
+        add("sweep", "k_sweep_c64", "n_sweep", "sweep_ms", (18.0 + 26.0 * (nr - 1)) / nr * N,
+            "complex64 red-black full sweep (one launch), the first of each cycle from zero")
+        add("apply", "k_march_c64<0,DOT>", "n_apply", "apply_ms", 26.0 * N,
+            "complex64 y = A x with the BiCGStab reduction (alpha or omega) in its epilogue")
     else:
         M = (N + 1) // 2
         add("restrict", "k_project_df", "n_restrict", "restrict_ms", (8.0 * k + 16.0) * M,

@@ -1,6 +1,6 @@
 """Command-line runner: set up a named workload and solve it on cuda:0.
 
-    python -m paper_2405_12380_gb300.cli --workload cube3d-64 [--maxit M] [--solves S]
+    python -m paper_2405_12380_gb300.cli --workload cube3d-64 [--maxit M] [--solves S] [--precision P]
     python -m paper_2405_12380_gb300.cli --stencil N          # operator bandwidth on N^3
     python -m paper_2405_12380_gb300.cli --experiment mixed   # 128^3 submarine, mixed vs FP64
     python -m paper_2405_12380_gb300.cli --experiment batch [--count C]
@@ -41,6 +41,7 @@ def main(argv=None):
     ap.add_argument("--relax", default=None, help="experiments: jacobi | rbgs (default: the workload's)")
     ap.add_argument("--n-r", type=int, default=None, help="experiments: sweeps per preconditioner application")
     ap.add_argument("--method", default=None, help="experiments: fgmres | bicgstab")
+    ap.add_argument("--precision", default=None, help="fp64 | mixed (default: the workload's)")
     a = ap.parse_args(argv)
     if a.stencil:
         return stencil(a.stencil, a.reps)
@@ -56,7 +57,9 @@ def main(argv=None):
         w["maxit"] = a.maxit
     sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
     torch.cuda.set_device(0)
-    P = hm.Problem(sc.dim, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, layer_strength=sc.layer_strength)
+    prec = a.precision or w.get("precision", "fp64")
+    P = hm.Problem(sc.dim, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells, layer_strength=sc.layer_strength,
+                   precision=prec)
     f = P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda())
     k = P.don_load(sc.trunk, sc.p, tau=w["tau"]) if w["correction"] == "tb" else 0
     o = hm.opts(w["method"], w["relax"], w["n_r"], correction=w["correction"], tol=w["tol"],
@@ -65,6 +68,7 @@ def main(argv=None):
         x, st = P.solve(f, None, o)
         st.pop("hist", None)
         st["kept"] = k
+        st["precision"] = prec
         print(json.dumps(st), flush=True)
 
 

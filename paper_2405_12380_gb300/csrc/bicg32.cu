@@ -28,16 +28,50 @@ constexpr int kB32Threads = kFusedThreads;   // 256
 
 __device__ __forceinline__ bool stopped(const double2* sc) { return sc[S_STOP].x != 0.0; }
 
-__device__ __forceinline__ double block_sum32(double v) {
-    __shared__ double red[kB32Threads / 32];
+// block sum of a per-thread FP32 value: an FP32 butterfly within each warp, then the
+// warps' sums in a fixed order; valid in thread 0.  (FP64 adds and shuffles run at a
+// small fraction of the FP32 rate on this GPU; the per-thread sums are FP32 already.)
+__device__ __forceinline__ double block_sum32(float v) {
+    __shared__ float red[kB32Threads / 32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double s = 0.0;
+    float s = 0.f;
     if (threadIdx.x == 0)
         for (int q = 0; q < kB32Threads / 32; ++q) s += red[q];
-    return s;
+    return (double)s;
+}
+
+// the sum of nparts FP32 partials of W values (stride W), taken by every block in
+// the same fixed order (so every block gets the same value bit for bit) -- a strided
+// sum per thread, a butterfly per warp, the warps in order -- and returned to all
+// threads of the block
+template <int W>
+__device__ __forceinline__ void all_blocks_sum(const float* parts, int nparts, float* out) {
+    __shared__ float red[W][kB32Threads / 32];
+    __shared__ float res[W];
+    float v[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) v[q] = 0.f;
+    for (int b = threadIdx.x; b < nparts; b += kB32Threads)
+#pragma unroll
+        for (int q = 0; q < W; ++q) v[q] += __ldcg(parts + (long long)b * W + q);
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < W; ++q) red[q][threadIdx.x >> 5] = v[q];
+    __syncthreads();
+    if (threadIdx.x < W) {
+        float t = 0.f;
+        for (int w = 0; w < kB32Threads / 32; ++w) t += red[threadIdx.x][w];
+        res[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < W; ++q) out[q] = res[q];
 }
 
 // complex64 as float2; two entries per float4
@@ -116,12 +150,33 @@ __global__ void __launch_bounds__(kB32Threads) k32_alpha(const float2* __restric
     }
 }
 
-// s = r - alpha v, ||s||^2 (||s|| <= tol ||f||, slot S_TOLS: the iteration ends after x += alpha phat)
+// s = r - alpha v, ||s||^2 (||s|| <= tol ||f||, slot S_TOLS: the iteration ends after x += alpha phat).
+// DOT: alpha = rho / <rhat, v> from the operator's partial sums (aparts, na blocks),
+// computed by every block (bicg_alpha's arithmetic), stored by block 0
+template <bool DOT>
 __global__ void __launch_bounds__(kB32Threads) k32_s(const float2* __restrict__ r, const float2* __restrict__ v,
                                                      float2* __restrict__ s, double2* sc, long long N, double* parts,
-                                                     unsigned* counter) {
+                                                     unsigned* counter, const float* aparts, int na) {
     if (stopped(sc)) return;
-    const float2 alpha = tof(sc[S_ALPHA]);
+    // the scalar in one thread, shared with the block (FP64 division is slow here)
+    __shared__ float2 s_alpha;
+    if (DOT) {
+        float d[2];
+        all_blocks_sum<2>(aparts, na, d);
+        if (threadIdx.x == 0) {
+            const bool brk = d[0] == 0.f && d[1] == 0.f;
+            const double2 a64 = brk ? make_double2(0.0, 0.0) : cdiv(sc[S_RHO], make_double2(d[0], d[1]));
+            s_alpha = tof(a64);
+            if (blockIdx.x == 0) {
+                sc[S_ALPHA] = a64;
+                if (brk) sc[S_FLAGS].y = 1;
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        s_alpha = tof(sc[S_ALPHA]);
+    }
+    __syncthreads();
+    const float2 alpha = s_alpha;
     float acc = 0.f;
     for_pairs(N, [&](long long q, bool half) {
         const float4 rr = ld2(r, q, half), vv = ld2(v, q, half);
@@ -173,16 +228,54 @@ __global__ void __launch_bounds__(kB32Threads) k32_omega(const float2* __restric
 
 // xl += alpha phat + omega shat; r = s - omega t; ||r||^2 and the next rho = <rhat, r>
 // with beta; the last block sets S_STOP on ||r|| <= tol ||f|| (slot S_TOLS), a
-// breakdown flag or a non-finite residual
+// breakdown flag or a non-finite residual.  DOT: omega = <t, s> / <t, t> from the
+// operator's partial sums (oparts, no blocks), computed by every block with
+// bicg_omega's arithmetic and stored (with its flags) by block 0
+template <bool DOT>
 __global__ void __launch_bounds__(kB32Threads) k32_xr(float2* __restrict__ xl, float2* __restrict__ r,
                                                       const float2* __restrict__ phat, const float2* __restrict__ shat,
                                                       const float2* __restrict__ s, const float2* __restrict__ t,
                                                       const float2* __restrict__ rhat, double2* sc, long long N,
-                                                      double* parts, unsigned* counter) {
-    const bool skip = stopped(sc) || sc[S_FLAGS].y == 1.0;
+                                                      double* parts, unsigned* counter, const float* oparts, int no) {
+    // the scalars in one thread, shared with the block (FP64 division is slow here)
+    __shared__ float2 s_alpha, s_omega;
+    __shared__ int s_skip;
+    float d[3] = {0.f, 0.f, 0.f};
+    const bool stop = stopped(sc);
+    if (DOT && !stop) all_blocks_sum<3>(oparts, no, d);
+    if (threadIdx.x == 0) {
+        bool skip = stop || sc[S_FLAGS].y == 1.0;
+        double2 omega64 = sc[S_OMEGA];
+        if (DOT && !stop) {
+            const double2 ts = make_double2(d[0], d[1]);
+            const double tt = d[2];
+            double flag = 0.0;
+            if (sc[S_FLAGS].x != 0) {
+                omega64 = make_double2(0, 0);
+            } else if (tt == 0) {
+                flag = 1.0;
+                omega64 = make_double2(0, 0);
+            } else {
+                omega64 = make_double2(ts.x / tt, ts.y / tt);
+                if (omega64.x == 0 && omega64.y == 0) flag = 2.0;   // breakdown after this update
+            }
+            if (flag == 1.0) skip = true;
+            if (blockIdx.x == 0) {
+                sc[S_TS] = ts;
+                sc[S_TT] = make_double2(tt, 0);
+                sc[S_OMEGA] = omega64;
+                if (flag != 0.0) sc[S_FLAGS].y = flag;
+            }
+        }
+        s_alpha = tof(sc[S_ALPHA]);
+        s_omega = tof(omega64);
+        s_skip = skip ? 1 : 0;
+    }
+    __syncthreads();
+    const bool skip = s_skip != 0;
     float rn = 0.f, re = 0.f, im = 0.f;
     if (!skip) {
-        const float2 alpha = tof(sc[S_ALPHA]), omega = tof(sc[S_OMEGA]);
+        const float2 alpha = s_alpha, omega = s_omega;
         for_pairs(N, [&](long long q, bool half) {
             const float4 xx = ld2(xl, q, half), ph = ld2(phat, q, half), sh = ld2(shat, q, half);
             const float4 ss = ld2(s, q, half), tt = ld2(t, q, half), rh = ld2(rhat, q, half);
@@ -307,7 +400,11 @@ void launch_b32_alpha(const float2* rhat, const float2* v, double2* sc, long lon
 }
 void launch_b32_s(const float2* r, const float2* v, float2* sv, double2* sc, long long N, double* parts,
                   unsigned* counter, cudaStream_t s) {
-    k32_s<<<bicg32_blocks(), kB32Threads, 0, s>>>(r, v, sv, sc, N, parts, counter);
+    k32_s<false><<<bicg32_blocks(), kB32Threads, 0, s>>>(r, v, sv, sc, N, parts, counter, nullptr, 0);
+}
+void launch_b32_s_dot(const float2* r, const float2* v, float2* sv, double2* sc, long long N, double* parts,
+                      unsigned* counter, const float* aparts, int na, cudaStream_t s) {
+    k32_s<true><<<bicg32_blocks(), kB32Threads, 0, s>>>(r, v, sv, sc, N, parts, counter, aparts, na);
 }
 void launch_b32_set_tol(double2* sc, double tol_abs, cudaStream_t s) { k32_set_tol<<<1, 1, 0, s>>>(sc, tol_abs); }
 void launch_b32_omega(const float2* t, const float2* sv, double2* sc, long long N, double* parts, unsigned* counter,
@@ -316,7 +413,14 @@ void launch_b32_omega(const float2* t, const float2* sv, double2* sc, long long 
 }
 void launch_b32_xr(float2* xl, float2* r, const float2* phat, const float2* shat, const float2* sv, const float2* t,
                    const float2* rhat, double2* sc, long long N, double* parts, unsigned* counter, cudaStream_t s) {
-    k32_xr<<<bicg32_blocks(), kB32Threads, 0, s>>>(xl, r, phat, shat, sv, t, rhat, sc, N, parts, counter);
+    k32_xr<false><<<bicg32_blocks(), kB32Threads, 0, s>>>(xl, r, phat, shat, sv, t, rhat, sc, N, parts, counter,
+                                                          nullptr, 0);
+}
+void launch_b32_xr_dot(float2* xl, float2* r, const float2* phat, const float2* shat, const float2* sv,
+                       const float2* t, const float2* rhat, double2* sc, long long N, double* parts, unsigned* counter,
+                       const float* oparts, int no, cudaStream_t s) {
+    k32_xr<true><<<bicg32_blocks(), kB32Threads, 0, s>>>(xl, r, phat, shat, sv, t, rhat, sc, N, parts, counter,
+                                                         oparts, no);
 }
 void launch_b32_fold(double2* x, float2* xl, long long N, cudaStream_t s, int mode) {
     k32_fold<<<bicg32_blocks(), kB32Threads, 0, s>>>(x, xl, N, mode);

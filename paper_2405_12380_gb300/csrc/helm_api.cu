@@ -870,6 +870,7 @@ helm_status ensure_b32(helm_handle* h) {
         h->b32.push_back(p);
     }
     if (!h->b32parts) TRY(dalloc(h, &h->b32parts, (size_t)3 * bicg32_blocks()));
+    if (!h->a32parts) TRY(dalloc(h, &h->a32parts, (size_t)5 * apply_grid_blocks(h->op32.dim, h->n)));
     return HELM_OK;
 }
 
@@ -906,18 +907,34 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
         const cudaStream_t q = h->stream;
         launch_b32_update_p(r, v, p, h->sc, N, q);
         TRY(precond32(h, o, p, ph, o->conj));
+        // v = A phat with the partial sums of <rhat, v> in its epilogue where the pair
+        // kernels apply (k32_s then forms alpha itself); else the operator, then the
+        // reduction kernel.  The two parts buffers keep both sets of partials apart.
         ev_mark(h, 3, 0);
-        launch_apply<float>(h->op32, ph, nullptr, v, nullptr, o->conj, false, q);
+        const int na = launch_apply32_bicg(h->op32, 1, ph, v, rh, o->conj, h->sc, h->a32parts, q);
+        if (!na) launch_apply<float>(h->op32, ph, nullptr, v, nullptr, o->conj, false, q);
         ev_mark(h, 3, 1);
-        launch_b32_alpha(rh, v, h->sc, N, parts, h->counter, q);
-        launch_b32_s(r, v, sv, h->sc, N, parts, h->counter, q);
+        if (na) {
+            launch_b32_s_dot(r, v, sv, h->sc, N, parts, h->counter, h->a32parts, na, q);
+        } else {
+            launch_b32_alpha(rh, v, h->sc, N, parts, h->counter, q);
+            launch_b32_s(r, v, sv, h->sc, N, parts, h->counter, q);
+        }
         TRY(precond32(h, o, sv, sh, o->conj));
+        // t = A shat with the partial sums of <t, s> and <t, t> (omega, formed by k32_xr)
         ev_mark(h, 3, 0);
-        launch_apply<float>(h->op32, sh, nullptr, t, nullptr, o->conj, false, q);
+        const int no = launch_apply32_bicg(h->op32, 2, sh, t, sv, o->conj, h->sc, h->a32parts + 2 * (size_t)na, q);
+        if (!no) launch_apply<float>(h->op32, sh, nullptr, t, nullptr, o->conj, false, q);
         ev_mark(h, 3, 1);
-        launch_b32_omega(t, sv, h->sc, N, parts, h->counter, q);
-        launch_b32_xr(xl, r, ph, sh, sv, t, rh, h->sc, N, parts, h->counter, q);
-        h->launches += 7;
+        if (no) {
+            launch_b32_xr_dot(xl, r, ph, sh, sv, t, rh, h->sc, N, parts, h->counter, h->a32parts + 2 * (size_t)na, no,
+                              q);
+        } else {
+            launch_b32_omega(t, sv, h->sc, N, parts, h->counter, q);
+            launch_b32_xr(xl, r, ph, sh, sv, t, rh, h->sc, N, parts, h->counter, q);
+        }
+        const bool fa = na != 0, fo = no != 0;
+        h->launches += 5 + (fa ? 0 : 1) + (fo ? 0 : 1);
         CKL();
         return HELM_OK;
     };
@@ -1347,6 +1364,7 @@ helm_status helm_destroy(helm_handle* h) {
     for (auto p : h->tmp32) cudaFree(p);
     for (auto p : h->b32) cudaFree(p);
     dfree(h->b32parts);
+    dfree(h->a32parts);
     dfree(h->Q); dfree(h->Qr); dfree(h->Ainv); dfree(h->coarse_partials); dfree(h->cbuf); dfree(h->ybuf);
     if (h->Qbf) cudaFree(h->Qbf);
     if (h->Qbr) cudaFree(h->Qbr);

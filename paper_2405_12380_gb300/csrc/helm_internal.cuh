@@ -165,6 +165,13 @@ bool rbgs_sweep32_ok(const Op<float>& op, const void* f, const void* x, const vo
 // without launching where the pair layout does not apply
 bool launch_red_residual32(const Op<float>& op, const float2* f, const float2* x, float2* r_red, int conj,
                            cudaStream_t s);
+// complex64 y = A x with the partial sums of a BiCGStab reduction in the epilogue
+// (mode 1: <w, y> with w = rhat, for alpha; mode 2: <y, w> and <y, y> with w = s,
+// for omega), 2 or 3 floats per block in parts (the block count is at most
+// apply_grid_blocks); nothing is written once S_STOP is set.  Returns the number of blocks, or 0 without
+// launching where the pair kernels do not apply.
+int launch_apply32_bicg(const Op<float>& op, int mode, const float2* x, float2* y, const float2* w, int conj,
+                        const double2* sc, float* parts, cudaStream_t s);
 int apply_grid_blocks(int dim, int n);
 int bicg_grid_blocks(int dim, int n);
 void launch_rhs(const Op<double>& op, const double2* src, const double2* g, double2* b, cudaStream_t s);
@@ -201,6 +208,14 @@ void launch_b32_alpha(const float2* rhat, const float2* v, double2* sc, long lon
 void launch_b32_s(const float2* r, const float2* v, float2* sv, double2* sc, long long N, double* parts,
                   unsigned* counter, cudaStream_t s);
 void launch_b32_set_tol(double2* sc, double tol_abs, cudaStream_t s);
+// k32_s / k32_xr taking alpha / omega from the partial sums of launch_apply32_bicg
+// (na, no blocks): every block sums them in the same fixed order, block 0 stores the
+// scalar and its flags
+void launch_b32_s_dot(const float2* r, const float2* v, float2* sv, double2* sc, long long N, double* parts,
+                      unsigned* counter, const float* aparts, int na, cudaStream_t s);
+void launch_b32_xr_dot(float2* xl, float2* r, const float2* phat, const float2* shat, const float2* sv,
+                       const float2* t, const float2* rhat, double2* sc, long long N, double* parts, unsigned* counter,
+                       const float* oparts, int no, cudaStream_t s);
 void launch_b32_omega(const float2* t, const float2* sv, double2* sc, long long N, double* parts, unsigned* counter,
                       cudaStream_t s);
 void launch_b32_xr(float2* xl, float2* r, const float2* phat, const float2* shat, const float2* sv, const float2* t,
@@ -420,6 +435,7 @@ struct helm_handle {
     std::vector<float2*> tmp32;
     std::vector<float2*> b32;       // complex64 BiCGStab vectors (MIXED handles)
     double* b32parts = nullptr;     // their reduction partials
+    float* a32parts = nullptr;      // partials of the operator launches with a fused reduction
     // one iteration of the complex64 BiCGStab captured as a CUDA graph (replayed per
     // iteration; rebuilt when the cycle's options change, dropped when the basis,
     // the k^2 field or a workspace buffer changes)

@@ -267,10 +267,21 @@ __device__ __forceinline__ void pair_sums(unsigned c0, unsigned c1, float2 left,
 // D^-1 (f - A x) (FLAG: from x = 0, x not read); KIND 2: the residual f - A x of the
 // red node of each pair (colour 0), written compactly as one float2 per pair
 // (zero on masked nodes)
-template <int KIND, bool FLAG, bool NORM>
+// DOT (KIND 0 only): the BiCGStab reduction of launch_apply32_bicg in the epilogue,
+// 1: conj(w) y (for alpha), 2: conj(y) w and |y|^2 (for omega); FP32 sums per
+// thread and across the block in a fixed order, one partial per block
+struct Dot32 {
+    const float4* w;
+    double2* sc;
+    float* parts;
+};
+
+template <int KIND, bool FLAG, bool NORM, int DOT = 0>
 __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, float omega,
                                                        const float4* __restrict__ x, const float4* __restrict__ f,
-                                                       float4* __restrict__ y, double* partials, int conj) {
+                                                       float4* __restrict__ y, double* partials, int conj,
+                                                       Dot32 dot = Dot32{}) {
+    static_assert(DOT == 0 || (KIND == 0 && !FLAG && !NORM), "the fused reduction follows y = A x only");
     constexpr bool NBR = !(KIND == 1 && FLAG);             // neighbours (and x) are read
     constexpr bool RHS = KIND >= 1 || FLAG;                // f is read
     constexpr unsigned kMM = kMasked | (kMasked << 8);
@@ -298,9 +309,13 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
     unsigned cc = valid ? (unsigned)code2[HCHK(l, NP)] : kMM;
     unsigned li = valid ? (unsigned)lidx2[HCHK(l, NP)] : 0u;
     float acc = 0.f;
+    float dre = 0.f, dim = 0.f, dtt = 0.f;                 // DOT sums
+    float4 wv = z4;                                        // DOT operand, prefetched one plane ahead
+    if (DOT) wv = valid ? dot.w[HCHK(l, NP)] : z4;
     for (int k = k0; k < k1; ++k, l += sz) {
         const bool more = valid && k + 1 < k1;
-        float4 next2 = z4, f_n = z4;
+        float4 next2 = z4, f_n = z4, w_n = z4;
+        if (DOT) w_n = more ? dot.w[HCHK(l + sz, NP)] : z4;
         if (NBR) next2 = (more && k + 2 < n) ? x[HCHK(l + 2 * sz, NP)] : z4;
         if (RHS) f_n = more ? f[HCHK(l + sz, NP)] : z4;
         const unsigned cc_n = more ? (unsigned)code2[HCHK(l + sz, NP)] : kMM;
@@ -377,25 +392,62 @@ __global__ void __launch_bounds__(BX * BY) k_march_c64(Op<float> op, int zc, flo
                 }
             }
         }
-        if (valid) {
-            if (KIND == 2) {
-                const int a = (j + k) & 1;                 // the red node of the pair
-                const unsigned ca = a ? c1 : c0;
-                reinterpret_cast<float2*>(y)[HCHK(l, NP)] = (ca & kMasked) ? make_float2(0.f, 0.f) : (a ? o1 : o0);
-            } else {
-                y[HCHK(l, NP)] = make_float4(o0.x, o0.y, o1.x, o1.y);
-                if (NORM) acc += (o0.x * o0.x + o0.y * o0.y) + (o1.x * o1.x + o1.y * o1.y);
+        if (valid && KIND == 2) {
+            const int a = (j + k) & 1;                     // the red node of the pair
+            const unsigned ca = a ? c1 : c0;
+            reinterpret_cast<float2*>(y)[HCHK(l, NP)] = (ca & kMasked) ? make_float2(0.f, 0.f) : (a ? o1 : o0);
+        } else if (valid) {
+            y[HCHK(l, NP)] = make_float4(o0.x, o0.y, o1.x, o1.y);
+            if (NORM) acc += (o0.x * o0.x + o0.y * o0.y) + (o1.x * o1.x + o1.y * o1.y);
+            if (DOT == 1) {                                // conj(w) y
+                const float2 w0 = lo2(wv), w1 = hi2(wv);
+                dre = fmaf(w0.x, o0.x, fmaf(w0.y, o0.y, dre));
+                dim = fmaf(w0.x, o0.y, fmaf(-w0.y, o0.x, dim));
+                dre = fmaf(w1.x, o1.x, fmaf(w1.y, o1.y, dre));
+                dim = fmaf(w1.x, o1.y, fmaf(-w1.y, o1.x, dim));
+            } else if (DOT == 2) {                         // conj(y) w, |y|^2
+                const float2 w0 = lo2(wv), w1 = hi2(wv);
+                dre = fmaf(o0.x, w0.x, fmaf(o0.y, w0.y, dre));
+                dim = fmaf(o0.x, w0.y, fmaf(-o0.y, w0.x, dim));
+                dre = fmaf(o1.x, w1.x, fmaf(o1.y, w1.y, dre));
+                dim = fmaf(o1.x, w1.y, fmaf(-o1.y, w1.x, dim));
+                dtt = fmaf(o0.x, o0.x, fmaf(o0.y, o0.y, dtt));
+                dtt = fmaf(o1.x, o1.x, fmaf(o1.y, o1.y, dtt));
             }
         }
         prev = cur;
         cur = next;
         next = next2;
         fv = f_n;
+        wv = w_n;
         cc = cc_n;
         li = li_n;
     }
     if (NORM) {
         block_reduce_store<float>((double)acc, partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    }
+    if (DOT) {
+        // S_STOP was set, if at all, by an earlier launch: every block takes the same
+        // branch.  The block's partial sums only: the kernel that needs the scalar
+        // (k32_s for alpha, k32_xr for omega) sums them itself.
+        if (dot.sc[S_STOP].x != 0.0) return;
+        // (FP32 butterflies and the warps in order: FP64 adds and shuffles run at a
+        // small fraction of the FP32 rate on this GPU)
+        constexpr int W = DOT == 1 ? 2 : 3;
+        const int tid = threadIdx.x + BX * threadIdx.y;
+        const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        float v[3] = {dre, dim, dtt};
+        __shared__ float red[3][BX * BY / 32];
+        for (int q = 0; q < W; ++q)
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if ((tid & 31) == 0)
+            for (int q = 0; q < W; ++q) red[q][tid >> 5] = v[q];
+        __syncthreads();
+        if (tid < W) {
+            float t = 0.f;
+            for (int w = 0; w < BX * BY / 32; ++w) t += red[tid][w];
+            dot.parts[W * bid + tid] = t;
+        }
     }
 }
 
@@ -504,147 +556,207 @@ __global__ void __launch_bounds__(BX * BY) k_rbgs_c64(Op<float> op, int zc, int 
 // pairs of a row (a multiple of 32), blockDim.y = BYI + 2 rows, of which the first
 // and last are halo rows: they compute the colour-c0 values of the rows just
 // outside the block, which the block's own second-colour nodes need, instead of
-// waiting for the neighbouring block.  Each thread marches in z over its pair: at
-// step t it updates colour c0 at plane t (old values: the other node of the pair and
-// the z-planes in registers, x-neighbours by shuffles, y-neighbours from xin) and
-// puts the new value in a ring of three shared planes; after one barrier it updates
-// colour 1 - c0 at plane t - 1 from the new colour-c0 values (x and y neighbours
-// from the shared plane, z neighbours from its registers) and writes the pair.
-// Blocks split z into chunks and recompute the colour-c0 planes just outside their
-// chunk.  Every node value comes from the arithmetic of k_rbgs_c64 (gs_value) with
-// the neighbour sums in the same order, so one launch equals two half-sweeps.
+// waiting for the neighbouring block.  Each thread marches in z over its pair.
+//
+// Old values are staged in shared memory: a ring of five z-planes of the block's rows
+// plus one more row on each side (the y-neighbours of the halo rows), filled by
+// asynchronous copies (cp.async, 16 bytes per thread and row) issued two planes
+// ahead, so that no neighbour read waits on global memory and the staging holds no
+// registers.  At step t a thread updates colour c0 at plane t from the staged planes
+// t - 1, t, t + 1 and puts the new value in a ring of three shared planes; after one
+// barrier it updates colour 1 - c0 at plane t - 1 from the new colour-c0 values
+// (x and y neighbours from the shared plane, z neighbours from its registers) and
+// writes the pair.  Blocks split z into chunks and recompute the colour-c0 planes
+// just outside their chunk.  1/diag of the layer comes from a shared copy of the
+// per-layer table.  Every node value comes from the arithmetic of k_rbgs_c64
+// (gs_value) with the neighbour sums in the same order, so one launch equals two
+// half-sweeps.
 __device__ __forceinline__ float2 pair_node(float4 v, int a) { return a ? hi2(v) : lo2(v); }
-
-__device__ __forceinline__ float2 sweep_invd(const Op<float>& op, int l, int a, unsigned li, int conj) {
-    float2 id;
-    if (op.k2) {
-        const float4 iv = reinterpret_cast<const float4*>(op.invd)[HCHK(l, op.N >> 1)];
-        id = a ? hi2(iv) : lo2(iv);
-    } else {
-        id = op.invd_tab[HCHK(a ? (li >> 8) : (li & 0xffu), kMaxLayerCells + 1)];
-    }
-    if (conj) id.y = -id.y;
-    return id;
-}
 
 // neighbour sum of one node from its six neighbour values (code bits select the
 // fluid ones), in the order of pair_sums
 __device__ __forceinline__ float2 six_sum(unsigned c, float2 xm, float2 xp, float2 ym, float2 yp, float2 zm,
                                           float2 zp) {
+    if ((c & 0x3Fu) == 0x3Fu) return cadd(cadd(cadd(xm, xp), cadd(ym, yp)), cadd(zm, zp));
     return cadd(cadd(cadd(pick(c, 1u, xm), pick(c, 2u, xp)), cadd(pick(c, 4u, ym), pick(c, 8u, yp))),
                 cadd(pick(c, 16u, zm), pick(c, 32u, zp)));
 }
 
-constexpr int kSweepMaxThreads = 1024;
+// 16-byte asynchronous copy global -> shared (L2 only); valid = false fills zeros
+// without reading (src must still be a mapped address)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's copy groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
-// the block (by, bz) of the sweep grid of one problem (shared by the batched form)
-template <bool XZERO>
-__device__ __forceinline__ void sweep_c64_block(const Op<float>& op, int by, int bz, int zc, int c0,
-                                                const float4* __restrict__ f, const float4* __restrict__ xin,
-                                                float4* __restrict__ xout, int conj, float omega, float2* ring) {
-    constexpr unsigned kMM = kMasked | (kMasked << 8);
-    const int n = op.n, h = n >> 1;
-    const int TXT = blockDim.x, BYI = blockDim.y - 2;
-    const int i2 = threadIdx.x, ty = threadIdx.y, lane = i2 & 31;
-    const int j = by * BYI - 1 + ty;
-    const int k0 = bz * zc, k1 = min(n, k0 + zc);
-    const bool row_ok = i2 < h && j >= 0 && j < n;
-    const bool inner = row_ok && ty >= 1 && ty <= BYI;
-    const int sy = h, sz = h * n;
-    [[maybe_unused]] const long long NP = op.N >> 1;
-    const int plane = blockDim.y * TXT, me = ty * TXT + i2;
-    const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
-    const unsigned short* lidx2 = reinterpret_cast<const unsigned short*>(op.lidx);
-    const float2* x1 = reinterpret_cast<const float2*>(xin);
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float2 z2 = make_float2(0.f, 0.f);
-    const int lrow = i2 + h * j;
-    int t = k0 - 1;
-    auto in_t = [&](int q) { return row_ok && q >= 0 && q < n; };
-    float4 om = z4, oc = z4, on = z4;                      // old pairs at planes t-1, t, t+1
-    if (!XZERO) {
-        if (in_t(t - 1)) om = xin[HCHK(lrow + sz * (t - 1), NP)];
-        if (in_t(t)) oc = xin[HCHK(lrow + sz * t, NP)];
-        if (in_t(t + 1)) on = xin[HCHK(lrow + sz * (t + 1), NP)];
+constexpr int kSweepMaxThreads = 1024;
+constexpr int kSweepXPlanes = 5;     // staged old-value planes: t - 1, t, t + 1, and two in flight
+
+// 1/diag of node a of the pair at pair index l with layer byte m: the stored field's
+// per-node value, or the shared copy of the layer table (conjugated already)
+__device__ __forceinline__ float2 sweep_invd(const Op<float>& op, const float2* stab, int l, int a, unsigned m,
+                                             int conj) {
+    if (op.k2) {
+        const float4 iv = reinterpret_cast<const float4*>(op.invd)[HCHK(l, op.N >> 1)];
+        float2 id = a ? hi2(iv) : lo2(iv);
+        if (conj) id.y = -id.y;
+        return id;
     }
-    float4 fc = in_t(t) ? f[HCHK(lrow + sz * t, NP)] : z4, fm = z4;
-    unsigned cc = in_t(t) ? (unsigned)code2[HCHK(lrow + sz * t, NP)] : kMM, cm = kMM;
-    unsigned lc = in_t(t) ? (unsigned)lidx2[HCHK(lrow + sz * t, NP)] : 0u, lm = 0u;
-    float2 rm2 = z2, rm = z2;                              // new colour-c0 values at planes t-2, t-1
-    int slot = 0, slot_m = 2;
-    for (; t <= k1; ++t) {
-        const int l = lrow + sz * t;
-        const bool tin = in_t(t);
-        float4 onn = z4, fn = z4;
-        unsigned cn = kMM, ln = 0u;
-        if (in_t(t + 1)) {
-            fn = f[HCHK(l + sz, NP)];
-            cn = code2[HCHK(l + sz, NP)];
-            ln = lidx2[HCHK(l + sz, NP)];
-        }
-        if (!XZERO && in_t(t + 2)) onn = xin[HCHK(l + 2 * sz, NP)];
-        // colour c0 at plane t (old neighbours)
-        float2 rc = z2;
-        {
-            const int a = c0 ^ ((j + t) & 1);
-            const unsigned ca = a ? (cc >> 8) : (cc & 0xffu);
-            float2 sa = z2;
-            if (!XZERO) {
-                float2 left, right;
-                left.x = __shfl_up_sync(0xffffffffu, oc.z, 1);
-                left.y = __shfl_up_sync(0xffffffffu, oc.w, 1);
-                right.x = __shfl_down_sync(0xffffffffu, oc.x, 1);
-                right.y = __shfl_down_sync(0xffffffffu, oc.y, 1);
-                if (tin && lane == 0 && a == 0 && (ca & 1u)) left = x1[HCHK(2 * l - 1, op.N)];
-                if (tin && lane == 31 && a == 1 && (ca & 2u)) right = x1[HCHK(2 * l + 2, op.N)];
-                const float2 ym = (tin && (ca & 4u)) ? pair_node(xin[HCHK(l - sy, NP)], a) : z2;
-                const float2 yp = (tin && (ca & 8u)) ? pair_node(xin[HCHK(l + sy, NP)], a) : z2;
-                sa = six_sum(ca, a ? lo2(oc) : left, a ? right : hi2(oc), ym, yp, pair_node(om, a), pair_node(on, a));
-            }
-            if (tin) {
-                const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, l, a, lc, conj);
-                rc = gs_value(op, ca, pair_node(fc, a), sa, id, pair_node(oc, a), omega, XZERO);
-            }
-        }
-        ring[slot * plane + me] = rc;
-        __syncthreads();
-        // colour 1 - c0 at plane t - 1 (new colour-c0 neighbours)
-        if (inner && t - 1 >= k0 && t - 1 < k1) {
-            const int lmi = l - sz;
-            const int a = (c0 ^ 1) ^ ((j + t - 1) & 1);
-            const unsigned ca = a ? (cm >> 8) : (cm & 0xffu);
-            const float2* P = ring + slot_m * plane;
-            const float2 xm = a ? rm : ((ca & 1u) ? P[me - 1] : z2);
-            const float2 xp = a ? ((ca & 2u) ? P[me + 1] : z2) : rm;
-            const float2 ym = (ca & 4u) ? P[me - TXT] : z2;
-            const float2 yp = (ca & 8u) ? P[me + TXT] : z2;
-            const float2 sb = six_sum(ca, xm, xp, ym, yp, rm2, rc);
-            const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, lmi, a, lm, conj);
-            const float2 b = gs_value(op, ca, pair_node(fm, a), sb, id, pair_node(om, a), omega, false);
-            xout[HCHK(lmi, NP)] = a ? make_float4(rm.x, rm.y, b.x, b.y) : make_float4(b.x, b.y, rm.x, rm.y);
-        }
-        rm2 = rm;
-        rm = rc;
-        om = oc;
-        oc = on;
-        on = onn;
-        fm = fc;
-        fc = fn;
-        cm = cc;
-        cc = cn;
-        lm = lc;
-        lc = ln;
-        slot_m = slot;
-        slot = slot == 2 ? 0 : slot + 1;
-    }
+    return stab[HCHK(m, kMaxLayerCells + 1)];
+}
+
+// dynamic shared memory of k_sweep_c64 for a block of txt x tyt threads
+__host__ __device__ constexpr size_t sweep_smem_bytes(int txt, int tyt, bool xzero) {
+    return (xzero ? 0 : (size_t)kSweepXPlanes * (tyt + 2) * txt * sizeof(float4)) +
+           (size_t)3 * tyt * txt * sizeof(float2) + (size_t)(kMaxLayerCells + 1) * sizeof(float2);
 }
 
 template <bool XZERO>
 __global__ void __launch_bounds__(kSweepMaxThreads, 1)
     k_sweep_c64(Op<float> op, int zc, int c0, const float4* __restrict__ f, const float4* __restrict__ xin,
                 float4* __restrict__ xout, int conj, float omega) {
-    extern __shared__ float2 ring[];                       // [3][blockDim.y][blockDim.x] colour-c0 values
-    sweep_c64_block<XZERO>(op, blockIdx.y, blockIdx.z, zc, c0, f, xin, xout, conj, omega, ring);
+    extern __shared__ float4 sweep_smem[];
+    constexpr unsigned kMM = kMasked | (kMasked << 8);
+    const int n = op.n, h = n >> 1;
+    const int TXT = blockDim.x, TYT = blockDim.y, BYI = TYT - 2;
+    const int i2 = threadIdx.x, ty = threadIdx.y;
+    const int j0 = blockIdx.y * BYI;                       // first inner row of the block
+    const int j = j0 - 1 + ty;                             // this thread's row
+    const int k0 = blockIdx.z * zc, k1 = min(n, k0 + zc);
+    const bool row_ok = i2 < h && j >= 0 && j < n;
+    const bool inner = row_ok && ty >= 1 && ty <= BYI;
+    const int sz = h * n;
+    [[maybe_unused]] const long long NP = op.N >> 1;
+    const int RS = TYT + 2;                                // staged rows j0 - 2 .. j0 + BYI + 1
+    const int PX = RS * TXT, PR = TYT * TXT;
+    float4* xs = sweep_smem;                               // [5][RS][TXT] old pairs (not with XZERO)
+    float2* ring = reinterpret_cast<float2*>(sweep_smem + (XZERO ? 0 : kSweepXPlanes * PX));   // [3][TYT][TXT]
+    float2* stab = ring + 3 * PR;                          // 1/diag by layer index
+    const int me = ty * TXT + i2;                          // this thread in a ring plane
+    const int mx = (ty + 1) * TXT + i2;                    // this thread's row in a staged plane
+    const int im1 = i2 > 0 ? -1 : 0, ip1 = i2 + 1 < TXT ? 1 : 0;
+    const unsigned short* code2 = reinterpret_cast<const unsigned short*>(op.nbm);
+    const unsigned short* lidx2 = reinterpret_cast<const unsigned short*>(op.lidx);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 z2 = make_float2(0.f, 0.f);
+    const int lrow = i2 + h * j;
+    for (int q = ty * TXT + i2; q <= op.L && q <= kMaxLayerCells; q += TXT * TYT) {
+        float2 v = op.invd_tab[q];
+        if (conj) v.y = -v.y;
+        stab[q] = v;
+    }
+    // staged rows of this thread: its own, and the outer row next to a halo row
+    const int jx = ty == 0 ? j0 - 2 : (ty == TYT - 1 ? j0 + BYI + 1 : -1);
+    const int mo = (ty == 0 ? 0 : RS - 1) * TXT + i2;
+    auto slot = [](int p) { return (p + 2 * kSweepXPlanes) % kSweepXPlanes; };
+    // stage plane p (zeros outside the grid)
+    auto stage = [&](int p) {
+        const bool pin = i2 < h && p >= 0 && p < n;
+        const bool v0 = pin && j >= 0 && j < n;
+        cp_async16(xs + slot(p) * PX + mx, xin + HCHK(v0 ? lrow + sz * p : 0, NP), v0);
+        if (jx != -1) {
+            const bool v1 = pin && jx >= 0 && jx < n;
+            cp_async16(xs + slot(p) * PX + mo, xin + HCHK(v1 ? i2 + h * jx + sz * p : 0, NP), v1);
+        }
+    };
+    int t = k0 - 1;
+    auto in_t = [&](int q) { return row_ok && q >= 0 && q < n; };
+    if (!XZERO) {
+        stage(t - 1);
+        stage(t);
+        stage(t + 1);
+        cp_async_commit();
+        stage(t + 2);
+        cp_async_commit();
+        cp_async_wait<1>();
+    }
+    float4 fc = in_t(t) ? f[HCHK(lrow + sz * t, NP)] : z4;
+    unsigned cc = in_t(t) ? (unsigned)code2[HCHK(lrow + sz * t, NP)] : kMM;
+    unsigned lc = in_t(t) ? (unsigned)lidx2[HCHK(lrow + sz * t, NP)] : 0u;
+    float2 rm2 = z2, rm = z2;                              // new colour-c0 values at planes t-2, t-1
+    // the colour-(1 - c0) node of this thread's pair at plane t - 1: f, old value,
+    // code and layer bytes (kept from the previous step)
+    float2 fb = z2, xob = z2;
+    unsigned cb = kMasked, lb = 0u;
+    int rs = 0, rs_m = 2;                                  // ring slots of planes t and t - 1
+    __syncthreads();
+    for (; t <= k1; ++t) {
+        const int l = lrow + sz * t;
+        float4 fn = z4;
+        unsigned cn = kMM, ln = 0u;
+        if (in_t(t + 1)) {
+            fn = f[HCHK(l + sz, NP)];
+            cn = code2[HCHK(l + sz, NP)];
+            ln = lidx2[HCHK(l + sz, NP)];
+        }
+        // colour c0 at plane t (old neighbours from the staged planes)
+        const int ar = c0 ^ ((j + t) & 1);                 // the colour-c0 node of the pair
+        const unsigned ca = ar ? (cc >> 8) : (cc & 0xffu);
+        float2 rc = z2;
+        float4 own = z4;                                   // this thread's old pair at plane t
+        if (!XZERO) own = xs[slot(t) * PX + mx];
+        if (in_t(t)) {
+            float2 sa = z2;
+            if (!XZERO && !(ca & kMasked)) {
+                const float4* P = xs + slot(t) * PX;
+                const float2 xm = ar ? lo2(own) : hi2(P[mx + im1]);
+                const float2 xp = ar ? lo2(P[mx + ip1]) : hi2(own);
+                const float2 ym = pair_node(P[mx - TXT], ar);
+                const float2 yp = pair_node(P[mx + TXT], ar);
+                const float2 zm = pair_node(xs[slot(t - 1) * PX + mx], ar);
+                const float2 zp = pair_node(xs[slot(t + 1) * PX + mx], ar);
+                sa = six_sum(ca, xm, xp, ym, yp, zm, zp);
+            }
+            const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, stab, l, ar, ar ? (lc >> 8) : (lc & 0xffu), conj);
+            rc = gs_value(op, ca, pair_node(fc, ar), sa, id, pair_node(own, ar), omega, XZERO);
+        }
+        ring[rs * PR + me] = rc;
+        if (!XZERO) {
+            // plane t + 3 into the slot of plane t - 2 (last read in the previous step);
+            // plane t + 2 (issued one step ago) must have landed before the barrier
+            stage(t + 3);
+            cp_async_commit();
+            cp_async_wait<1>();
+        }
+        __syncthreads();
+        // colour 1 - c0 at plane t - 1 (new colour-c0 neighbours)
+        if (inner && t - 1 >= k0 && t - 1 < k1) {
+            const int lmi = l - sz;
+            const int a = ar;                              // (c0 ^ 1) ^ ((j + t - 1) & 1)
+            float2 b;
+            if (cb & kMasked) {
+                b = gs_value(op, cb, fb, z2, z2, xob, omega, false);
+            } else {
+                const float2* R = ring + rs_m * PR;
+                const float2 xm = a ? rm : R[me + im1];
+                const float2 xp = a ? R[me + ip1] : rm;
+                const float2 sb = six_sum(cb, xm, xp, R[me - TXT], R[me + TXT], rm2, rc);
+                const float2 id = sweep_invd(op, stab, lmi, a, lb, conj);
+                b = gs_value(op, cb, fb, sb, id, xob, omega, false);
+            }
+            xout[HCHK(lmi, NP)] = a ? make_float4(rm.x, rm.y, b.x, b.y) : make_float4(b.x, b.y, rm.x, rm.y);
+        }
+        rm2 = rm;
+        rm = rc;
+        // the other node of the pair at plane t (element 1 - ar) is swept next step
+        fb = ar ? lo2(fc) : hi2(fc);
+        xob = ar ? lo2(own) : hi2(own);
+        cb = ar ? (cc & 0xffu) : (cc >> 8);
+        lb = ar ? (lc & 0xffu) : (lc >> 8);
+        fc = fn;
+        cc = cn;
+        lc = ln;
+        rs_m = rs;
+        rs = rs == 2 ? 0 : rs + 1;
+    }
+    if (!XZERO) cp_async_wait<0>();
 }
 
 // y = A x, or y = f - A x (resid); two z-planes per thread; optional per-block ||y||^2 partials.
@@ -1572,6 +1684,19 @@ bool launch_red_residual32(const Op<float>& op, const float2* f, const float2* x
     return true;
 }
 
+int launch_apply32_bicg(const Op<float>& op, int mode, const float2* x, float2* y, const float2* w, int conj,
+                        const double2* sc, float* parts, cudaStream_t s) {
+    if (!pair_ok(op, x, y, w) || (mode != 1 && mode != 2)) return 0;
+    int zc;
+    const dim3 g = pair_grid(op.n, &zc), b(BX, BY);
+    const Dot32 d{reinterpret_cast<const float4*>(w), const_cast<double2*>(sc), parts};
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float4* y4 = reinterpret_cast<float4*>(y);
+    if (mode == 1) k_march_c64<0, false, false, 1><<<g, b, 0, s>>>(op, zc, 0.f, x4, nullptr, y4, nullptr, conj, d);
+    else k_march_c64<0, false, false, 2><<<g, b, 0, s>>>(op, zc, 0.f, x4, nullptr, y4, nullptr, conj, d);
+    return (int)(g.x * g.y * g.z);
+}
+
 namespace {
 
 // launch shape of k_sweep_c64 on an n^3 grid: whole rows per block (n/2 pairs, at
@@ -1580,7 +1705,7 @@ namespace {
 struct SweepShape {
     dim3 g, b;
     int zc;
-    size_t smem;
+    size_t smem, smem0;         // dynamic shared memory: from xin, from zero
 };
 
 bool sweep_shape(int n, SweepShape& sh) {
@@ -1590,7 +1715,8 @@ bool sweep_shape(int n, SweepShape& sh) {
     const int tyt = std::max(8, std::min(32, kSweepMaxThreads / txt));
     const int byi = tyt - 2;
     sh.b = dim3(txt, tyt);
-    sh.smem = (size_t)3 * txt * tyt * sizeof(float2);
+    sh.smem = sweep_smem_bytes(txt, tyt, false);
+    sh.smem0 = sweep_smem_bytes(txt, tyt, true);
     static int sms = 0;
     static int occ[5] = {0, 0, 0, 0, 0};
     const int w = txt / 32;
@@ -1598,11 +1724,14 @@ bool sweep_shape(int n, SweepShape& sh) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // the largest block shape (128 x 8 threads) needs about 127 KB
+        cudaFuncSetAttribute(k_sweep_c64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 * 1024);
+        cudaFuncSetAttribute(k_sweep_c64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 * 1024);
     }
     if (occ[w] == 0) {
         int o0 = 0, o1 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_sweep_c64<false>, txt * tyt, sh.smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_sweep_c64<true>, txt * tyt, sh.smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_sweep_c64<true>, txt * tyt, sh.smem0);
         occ[w] = std::max(1, std::min(o0, o1));
     }
     const int gy = (n + byi - 1) / byi;
@@ -1629,7 +1758,7 @@ bool launch_rbgs_sweep32(const Op<float>& op, int c0, const float2* f, const flo
     const float4* x4 = reinterpret_cast<const float4*>(xin);
     float4* y4 = reinterpret_cast<float4*>(xout);
     if (xin) k_sweep_c64<false><<<sh.g, sh.b, sh.smem, s>>>(op, sh.zc, c0, f4, x4, y4, conj, (float)omega);
-    else k_sweep_c64<true><<<sh.g, sh.b, sh.smem, s>>>(op, sh.zc, c0, f4, x4, y4, conj, (float)omega);
+    else k_sweep_c64<true><<<sh.g, sh.b, sh.smem0, s>>>(op, sh.zc, c0, f4, x4, y4, conj, (float)omega);
     return true;
 }
 

@@ -543,21 +543,33 @@ __global__ void __launch_bounds__(64) k_coarse_gemv(const double2* __restrict__ 
 // complex64 partials of the BF16-basis restriction: c_j = sum over blocks (FP64, fixed
 // order), one block per column; then y (complex64) = A_c^-1 c, one block per row --
 // spread over k SMs like the FP64 pair above
-__global__ void __launch_bounds__(64) k_coarse32_reduce(const float2* __restrict__ partials, int nblk, int k,
-                                                        double2* __restrict__ c) {
-    __shared__ double2 red[2];
+// c_j = sum of the nblk partial rows (FP32 partials): one block per column, a
+// strided FP32 sum per thread, an FP32 butterfly per warp, the warps in order
+// (FP64 adds and shuffles run at a small fraction of the FP32 rate on this GPU)
+__global__ void __launch_bounds__(256) k_coarse32_reduce(const float2* __restrict__ partials, int nblk, int k,
+                                                         double2* __restrict__ c) {
+    __shared__ float2 red[8];
     const int j = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double sx = 0, sy = 0;
-    for (int b = threadIdx.x; b < nblk; b += 64) {
+    float sx = 0.f, sy = 0.f;
+    for (int b = threadIdx.x; b < nblk; b += 256) {
         const float2 q = partials[(long long)b * k + j];
         sx += q.x;
         sy += q.y;
     }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) red[w] = make_double2(sx, sy);
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) red[w] = make_float2(sx, sy);
     __syncthreads();
-    if (threadIdx.x == 0) c[j] = make_double2(red[0].x + red[1].x, red[0].y + red[1].y);
+    if (threadIdx.x == 0) {
+        float tx = 0.f, ty = 0.f;
+        for (int q = 0; q < 8; ++q) {
+            tx += red[q].x;
+            ty += red[q].y;
+        }
+        c[j] = make_double2(tx, ty);
+    }
 }
 
 __global__ void __launch_bounds__(64) k_coarse32_gemv(const double2* __restrict__ Ainv, int k, int conj,
@@ -1334,7 +1346,7 @@ void launch_restrict32(const Op<float>& op, const void* Qv, long long ldq, int k
 
 void launch_coarse_apply32(const float2* partials, int nblk, int k, const double2* Ainv, int conj, float2* y,
                            double2* cbuf, cudaStream_t s) {
-    k_coarse32_reduce<<<k, 64, 0, s>>>(partials, nblk, k, cbuf);
+    k_coarse32_reduce<<<k, 256, 0, s>>>(partials, nblk, k, cbuf);
     k_coarse32_gemv<<<k, 64, 0, s>>>(Ainv, k, conj, cbuf, y);
 }
 
