@@ -116,7 +116,13 @@ __device__ __forceinline__ void st2(float2* a, long long q, bool half, float4 v)
 __global__ void __launch_bounds__(kB32Threads) k32_update_p(const float2* __restrict__ r, const float2* __restrict__ v,
                                                             float2* __restrict__ p, const double2* sc, long long N) {
     if (stopped(sc)) return;
-    const float2 beta = tof(sc[S_BETA]), omega = tof(sc[S_OMEGA]);
+    __shared__ float2 s_beta, s_omega;                     // converted once per block
+    if (threadIdx.x == 0) {
+        s_beta = tof(sc[S_BETA]);
+        s_omega = tof(sc[S_OMEGA]);
+    }
+    __syncthreads();
+    const float2 beta = s_beta, omega = s_omega;
     for_pairs(N, [&](long long q, bool half) {
         const float4 rr = ld2(r, q, half), vv = ld2(v, q, half), pp = ld2(p, q, half);
         const float2 a = caddf(lo(rr), cmulf(beta, csubf(lo(pp), cmulf(omega, lo(vv)))));

@@ -655,25 +655,25 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1)
     // staged rows of this thread: its own, and the outer row next to a halo row
     const int jx = ty == 0 ? j0 - 2 : (ty == TYT - 1 ? j0 + BYI + 1 : -1);
     const int mo = (ty == 0 ? 0 : RS - 1) * TXT + i2;
-    auto slot = [](int p) { return (p + 2 * kSweepXPlanes) % kSweepXPlanes; };
-    // stage plane p (zeros outside the grid)
-    auto stage = [&](int p) {
-        const bool pin = i2 < h && p >= 0 && p < n;
-        const bool v0 = pin && j >= 0 && j < n;
-        cp_async16(xs + slot(p) * PX + mx, xin + HCHK(v0 ? lrow + sz * p : 0, NP), v0);
-        if (jx != -1) {
-            const bool v1 = pin && jx >= 0 && jx < n;
-            cp_async16(xs + slot(p) * PX + mo, xin + HCHK(v1 ? i2 + h * jx + sz * p : 0, NP), v1);
-        }
+    // stage plane p (zeros outside the grid) into the staged plane at offset so
+    const bool out_ok = jx != -1 && i2 < h && jx >= 0 && jx < n;
+    const int lout = i2 + h * jx;
+    auto stage = [&](int p, int so) {
+        const bool pin = p >= 0 && p < n;
+        cp_async16(xs + so + mx, xin + HCHK(pin && row_ok ? lrow + sz * p : 0, NP), pin && row_ok);
+        if (jx != -1) cp_async16(xs + so + mo, xin + HCHK(pin && out_ok ? lout + sz * p : 0, NP), pin && out_ok);
     };
     int t = k0 - 1;
     auto in_t = [&](int q) { return row_ok && q >= 0 && q < n; };
+    // offsets of the staged planes t - 1, t, t + 1, t + 2 (in flight) and of the free
+    // slot that plane t + 3 goes to (rotated every step: no index arithmetic per access)
+    int o_m1 = 0, o_0 = PX, o_p1 = 2 * PX, o_p2 = 3 * PX, o_p3 = 4 * PX;
     if (!XZERO) {
-        stage(t - 1);
-        stage(t);
-        stage(t + 1);
+        stage(t - 1, o_m1);
+        stage(t, o_0);
+        stage(t + 1, o_p1);
         cp_async_commit();
-        stage(t + 2);
+        stage(t + 2, o_p2);
         cp_async_commit();
         cp_async_wait<1>();
     }
@@ -701,17 +701,17 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1)
         const unsigned ca = ar ? (cc >> 8) : (cc & 0xffu);
         float2 rc = z2;
         float4 own = z4;                                   // this thread's old pair at plane t
-        if (!XZERO) own = xs[slot(t) * PX + mx];
+        if (!XZERO) own = xs[o_0 + mx];
         if (in_t(t)) {
             float2 sa = z2;
             if (!XZERO && !(ca & kMasked)) {
-                const float4* P = xs + slot(t) * PX;
+                const float4* P = xs + o_0;
                 const float2 xm = ar ? lo2(own) : hi2(P[mx + im1]);
                 const float2 xp = ar ? lo2(P[mx + ip1]) : hi2(own);
                 const float2 ym = pair_node(P[mx - TXT], ar);
                 const float2 yp = pair_node(P[mx + TXT], ar);
-                const float2 zm = pair_node(xs[slot(t - 1) * PX + mx], ar);
-                const float2 zp = pair_node(xs[slot(t + 1) * PX + mx], ar);
+                const float2 zm = pair_node(xs[o_m1 + mx], ar);
+                const float2 zp = pair_node(xs[o_p1 + mx], ar);
                 sa = six_sum(ca, xm, xp, ym, yp, zm, zp);
             }
             const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, stab, l, ar, ar ? (lc >> 8) : (lc & 0xffu), conj);
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1)
         if (!XZERO) {
             // plane t + 3 into the slot of plane t - 2 (last read in the previous step);
             // plane t + 2 (issued one step ago) must have landed before the barrier
-            stage(t + 3);
+            stage(t + 3, o_p3);
             cp_async_commit();
             cp_async_wait<1>();
         }
@@ -755,6 +755,12 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1)
         lc = ln;
         rs_m = rs;
         rs = rs == 2 ? 0 : rs + 1;
+        const int o_free = o_m1;
+        o_m1 = o_0;
+        o_0 = o_p1;
+        o_p1 = o_p2;
+        o_p2 = o_p3;
+        o_p3 = o_free;
     }
     if (!XZERO) cp_async_wait<0>();
 }
