@@ -175,7 +175,11 @@ helm_status helm_set_wait_limit(helm_handle* h, unsigned polls, unsigned extra_a
  * (default 0.1); a recursive residual above runaway times the last true residual
  * (default 1e3) drops the increment and restarts; guard > 0 tries each fold first
  * and takes the increment back out (and restarts) when the true residual would
- * exceed guard times the last true residual (default 0: no guard).
+ * exceed guard times the best true residual so far (default 0: no guard).  After
+ * four such restarts (runaways or rejected folds) the solve continues, for the rest
+ * of maxit, as the FP64 BiCGStab with the same complex64 cycle from the FP64 iterate
+ * (the statistics add both parts).  A solve that ends unconverged keeps its last
+ * increment only if the true residual stays within 100x of the best one seen.
  * HELM_BAD_ARG unless 0 < delta < 1, runaway > 1, guard >= 0. */
 helm_status helm_set_reliable(helm_handle* h, double delta, double runaway, double guard);
 
@@ -354,6 +358,22 @@ helm_status helm_batch_set_tile(helm_batch* b, int tile_rows, int grid);
  * Returns HELM_OK when every problem converged, else the last failing status. */
 helm_status helm_batch_solve(helm_batch* b, const helm_solve_opts* opts, const double* const* f,
                              double* const* x, helm_stats* stats);
+
+/* Many independent solves at once, each stopping at its own convergence: problem i
+ * is solved exactly as helm_solve(hs[i], opts, f[i], x[i], &stats[i], NULL, 0) would
+ * (same kernels, same result bit for bit), but on a private non-blocking stream per
+ * problem, ordered after that handle's stream, from a pool of min(nprob, threads)
+ * host threads (threads <= 0: one per problem), so that the GPU overlaps the
+ * problems' launches instead of running one problem after another, and no problem
+ * waits for the slowest one (unlike helm_batch_solve's lockstep).  The handles must be
+ * distinct HELM_MIXED handles (the complex64 cycles launch no grid-wide barriers, so
+ * any number of them may share the GPU); each keeps its own stream setting, restored
+ * before return.  f[i], x[i] [dev] complex128 as in helm_solve; stats [host] nprob
+ * entries or NULL.  Synchronous.  Returns HELM_OK when every problem converged, else
+ * the status of the first problem (by index) that did not; HELM_BAD_ARG for null or
+ * repeated handles or an FP64 handle. */
+helm_status helm_solve_concurrent(int nprob, helm_handle** hs, const helm_solve_opts* opts, const double* const* f,
+                                  double* const* x, helm_stats* stats, int threads);
 
 /* Residual without allocation (no counterpart in the paper: an interface for
  * callers that cannot allocate device memory -- code running inside a memory

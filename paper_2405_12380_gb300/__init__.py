@@ -3,4 +3,4 @@
 The compute path is libhelm.so (hand-written CUDA for sm_103a behind the C ABI of
 include/helm.h); this package only marshals torch tensors into that ABI.
 """
-from .helm import Batch, Problem, SolveOpts, HelmError, opts  # noqa: F401
+from .helm import Batch, Problem, SolveOpts, HelmError, opts, solve_concurrent  # noqa: F401

@@ -91,6 +91,8 @@ SIGNATURES = {
     "helm_batch_destroy": (i32, [H]),
     "helm_batch_set_tile": (i32, [H, i32, i32]),
     "helm_batch_solve": (i32, [H, C.POINTER(SolveOpts), C.POINTER(vp), C.POINTER(vp), C.POINTER(Stats)]),
+    "helm_solve_concurrent": (i32, [i32, C.POINTER(H), C.POINTER(SolveOpts), C.POINTER(vp), C.POINTER(vp),
+                                    C.POINTER(Stats), i32]),
 }
 
 _lib = None

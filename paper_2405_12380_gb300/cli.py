@@ -42,6 +42,9 @@ def main(argv=None):
     ap.add_argument("--n-r", type=int, default=None, help="experiments: sweeps per preconditioner application")
     ap.add_argument("--method", default=None, help="experiments: fgmres | bicgstab")
     ap.add_argument("--precision", default=None, help="fp64 | mixed (default: the workload's)")
+    ap.add_argument("--form", default="both", choices=["lockstep", "concurrent", "both"],
+                    help="batch: lockstep batched solve (helm_batch_solve), concurrent solves "
+                         "(helm_solve_concurrent), or both")
     a = ap.parse_args(argv)
     if a.stencil:
         return stencil(a.stencil, a.reps)
@@ -49,7 +52,7 @@ def main(argv=None):
     if a.experiment == "mixed":
         return exp_mixed(a.maxit, over)
     if a.experiment == "batch":
-        return exp_batch(a.count, a.maxit, over)
+        return exp_batch(a.count, a.maxit, over, a.form)
     if a.experiment == "adjoint":
         return exp_adjoint(a.fd, a.maxit, over)
     w = dict(scenes.BENCH_WORKLOADS[a.workload])
@@ -155,12 +158,14 @@ def exp_mixed(maxit=None, over=None):
     _emit({"experiment": "mixed", "rel_diff_mixed_vs_fp64_solution": float(d)})
 
 
-def exp_batch(count=64, maxit=None, over=None):
-    """`count` problems on uneven grids 48^3-128^3 (seeded k, scatterers, sources):
-    one batched mixed-precision solve (default DeepONet-FGMRES(30) with Jacobi + trunk
-    basis; --method bicgstab --relax rbgs --n-r 3 for the batched complex64 BiCGStab),
-    to 1e-6, against the same problems solved one after another with the FP64 handle;
-    every batched solution's FP64 residual is recomputed by the library."""
+def exp_batch(count=64, maxit=None, over=None, form="both"):
+    """`count` problems on uneven grids 48^3-128^3 (seeded k, scatterers, sources) on
+    mixed-precision handles, to 1e-6: the lockstep batched solve (default
+    DeepONet-FGMRES(30) with Jacobi + trunk basis; --method bicgstab --relax rbgs
+    --n-r 3 for the batched complex64 BiCGStab) and/or the concurrent solves (each
+    problem's own solve on its own stream, helm_solve_concurrent), against the same
+    problems solved one after another with the FP64 handle; every mixed solution's
+    FP64 residual is recomputed by the library."""
     import torch
 
     import scenes
@@ -176,32 +181,45 @@ def exp_batch(count=64, maxit=None, over=None):
         P.don_load(sc.trunk, sc.p, tau=1e-6)
         probs.append(P)
         fs.append(P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda()))
-    B = hm.Batch(probs)
-    tile, _ = B.autotune(fs, o)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    xb, stb = B.solve(fs, None, o)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
-    ok = sum(1 for s_ in stb if s_["status"] == 0)
-    res_check = []
-    for P, f, x in zip(probs, fs, xb):
-        _, nrm = P.residual(f, x)
-        res_check.append(float(nrm.sqrt().item() / torch.linalg.vector_norm(f).item()))
-    _emit({"experiment": "batch", "form": "batched mixed", "problems": count, "relax": o.relax, "n_r": o.n_r,
-           "nodes": int(sum(P.N for P in probs)), "tile": tile, "wall_s": tb, "converged": ok,
-           "iters_max": max(s_["iters"] for s_ in stb), "rel_res_max": max(s_["rel_res"] for s_ in stb),
-           "fp64_residual_recomputed_max": max(res_check), "method": o.method,
-           "iters_each": [s_["iters"] for s_ in stb]})
-    B.close()
+    results = {}
+    forms = ["lockstep", "concurrent"] if form == "both" else [form]
+    for fm in forms:
+        tile = None
+        if fm == "lockstep":
+            B = hm.Batch(probs)
+            tile, _ = B.autotune(fs, o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if fm == "lockstep":
+            xb, stb = B.solve(fs, None, o)
+        else:
+            xb, stb = hm.solve_concurrent(probs, fs, None, o)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        ok = sum(1 for s_ in stb if s_["status"] == 0)
+        res_check = []
+        for P, f, x in zip(probs, fs, xb):
+            _, nrm = P.residual(f, x)
+            res_check.append(float(nrm.sqrt().item() / torch.linalg.vector_norm(f).item()))
+        _emit({"experiment": "batch", "form": ("batched mixed, lockstep" if fm == "lockstep"
+                                               else "mixed, concurrent solves"),
+               "problems": count, "relax": o.relax, "n_r": o.n_r, "nodes": int(sum(P.N for P in probs)),
+               "tile": tile, "wall_s": tb, "converged": ok, "iters_max": max(s_["iters"] for s_ in stb),
+               "rel_res_max": max(s_["rel_res"] for s_ in stb), "fp64_residual_recomputed_max": max(res_check),
+               "converged_by_fp64_residual": sum(1 for r_ in res_check if r_ <= 1.0001e-6),
+               "method": o.method, "iters_each": [s_["iters"] for s_ in stb]})
+        results[fm] = (tb, xb)
+        if fm == "lockstep":
+            B.close()
+            del B
     for P in probs:
         P.close()
-    del probs, B
+    del probs
     torch.cuda.empty_cache()
     # the same problems, one FP64 handle at a time
     t_seq, ok64, it64 = 0.0, 0, []
-    diffs = []
-    for sc, x in zip(scs, xb):
+    diffs = {fm: [] for fm in results}
+    for i, sc in enumerate(scs):
         P = hm.Problem(3, sc.n, sc.k0, sc.mask, layer_cells=sc.layer_cells)
         f = P.rhs(torch.from_numpy(sc.src).cuda(), torch.from_numpy(sc.g).cuda())
         P.don_load(sc.trunk, sc.p, tau=1e-6)
@@ -212,11 +230,13 @@ def exp_batch(count=64, maxit=None, over=None):
         t_seq += time.perf_counter() - t0
         ok64 += st["status"] == 0
         it64.append(st["iters"])
-        diffs.append(float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64)))
+        for fm, (_, xb) in results.items():
+            diffs[fm].append(float(torch.linalg.vector_norm(xb[i] - x64) / torch.linalg.vector_norm(x64)))
         P.close()
     _emit({"experiment": "batch", "form": "sequential FP64", "problems": count, "wall_s": t_seq,
-           "converged": ok64, "iters_max": max(it64), "rel_diff_batched_vs_fp64_max": max(diffs),
-           "speedup_batched": t_seq / tb})
+           "converged": ok64, "iters_max": max(it64), "iters_each": it64,
+           **{f"rel_diff_{fm}_vs_fp64_max": max(v) for fm, v in diffs.items()},
+           **{f"speedup_{fm}": t_seq / results[fm][0] for fm in results}})
 
 
 def exp_adjoint(n_fd=32, maxit=None, over=None):

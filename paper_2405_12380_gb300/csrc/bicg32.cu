@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kB32Threads) k32_omega(const float2* __restric
 // operator's partial sums (oparts, no blocks), computed by every block with
 // bicg_omega's arithmetic and stored (with its flags) by block 0
 template <bool DOT>
-__global__ void __launch_bounds__(kB32Threads) k32_xr(float2* __restrict__ xl, float2* __restrict__ r,
+__global__ void __launch_bounds__(kB32Threads, 4) k32_xr(float2* __restrict__ xl, float2* __restrict__ r,
                                                       const float2* __restrict__ phat, const float2* __restrict__ shat,
                                                       const float2* __restrict__ s, const float2* __restrict__ t,
                                                       const float2* __restrict__ rhat, double2* sc, long long N,

@@ -6,10 +6,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "helm_internal.cuh"
@@ -859,9 +862,15 @@ helm_status solve_bicgstab(helm_handle* h, const helm_solve_opts* o, const doubl
 // A recursive residual that grows past rel_runaway times the last true one (a
 // runaway of the complex64 recursion) drops the increment and restarts from the
 // FP64 iterate.  With rel_guard > 0 a fold is first tried: if the true residual of
-// x + xl exceeds rel_guard times the last true one the increment is taken back out
-// and the iteration restarts from x.  Convergence is decided on the FP64 true
+// x + xl exceeds rel_guard times the best true one so far the increment is taken back
+// out and the iteration restarts from x.  Convergence is decided on the FP64 true
 // residual only.
+
+// runaway resets and rejected folds after which the complex64 BiCGStab hands the
+// solve to the FP64 BiCGStab (with the same complex64 cycle); the largest factor by
+// which the final fold of an unconverged solve may raise the best true residual
+constexpr int kMixedTroubles = 4;
+constexpr double kFinalGuard = 1e2;
 
 helm_status ensure_b32(helm_handle* h) {
     while (h->b32.size() < 9) {
@@ -875,7 +884,8 @@ helm_status ensure_b32(helm_handle* h) {
 }
 
 helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const double2* f, double2* x,
-                             helm_stats* st, Hist& hist, double bnorm) {
+                             helm_stats* st, Hist& hist, double bnorm, bool* gave_up) {
+    *gave_up = false;
     TRY(ensure_tmp(h, 2));
     TRY(ensure_tmp32(h, 4));
     TRY(ensure_b32(h));
@@ -885,6 +895,7 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
     float2 *r = h->b32[0], *rh = h->b32[1], *p = h->b32[2], *v = h->b32[3], *sv = h->b32[4], *t = h->b32[5],
            *ph = h->b32[6], *sh = h->b32[7], *xl = h->b32[8];
     double* parts = h->b32parts;
+    double2* xtry = h->tmp[0];                   // trial folds (copy of x plus the increment)
     const double tol_abs = o->tol * bnorm;
     TRY(residual_norm(h, f, x, r64, o->conj, S_RN2));
     ++st->matvecs;
@@ -997,21 +1008,24 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
             CKL();
             return poll(h);
         }
-        launch_b32_fold(x, xl, N, s, 2);
-        TRY(residual_norm(h, f, x, r64, o->conj, S_BETA2));
+        // the trial fold goes into a copy of x (taking a large increment back out of x
+        // itself would cancel x's digits); accepted, x += xl gives the same values
+        CK(cudaMemcpyAsync(xtry, x, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        launch_b32_fold(xtry, xl, N, s, 2);
+        TRY(residual_norm(h, f, xtry, r64, o->conj, S_BETA2));
         ++st->matvecs;
         TRY(poll(h));
         const double rt = std::sqrt(hs(h, S_BETA2)) / bnorm;
         if (std::isfinite(rt) && rt <= h->rel_guard * last) {
-            launch_b32_fold(x, xl, N, s, 1);
+            launch_b32_fold(x, xl, N, s, 0);
             launch_b32_replace(r64, r, rh, p, v, restart, h->sc, N, parts, h->counter, s);
-            h->launches += 3;
+            h->launches += 4;
             CKL();
             return poll(h);
         }
-        // the increment made the iterate worse: take it back out and start afresh
+        // the increment made the iterate worse: drop it and start afresh from x
         rejected = true;
-        launch_b32_fold(x, xl, N, s, 3);
+        launch_b32_fold(x, xl, N, s, 1);
         TRY(residual_norm(h, f, x, r64, o->conj, S_BETA2));
         launch_b32_replace(r64, r, rh, p, v, 1, h->sc, N, parts, h->counter, s);
         h->launches += 4;
@@ -1020,8 +1034,8 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
         return poll(h);
     };
     st->status = HELM_NOT_CONVERGED;
-    double maxrr = res, last_true = res;
-    int iters = 0, restarts = 0, inflight = 0, head = 0, since_start = 0;
+    double maxrr = res, last_true = res, best_true = res;
+    int iters = 0, restarts = 0, inflight = 0, head = 0, since_start = 0, troubles = 0;
     while (true) {
         if (inflight == 0) {
             if (iters >= o->maxit) break;
@@ -1064,15 +1078,22 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
             inflight = 0;
         }
         head = 0;
-        TRY(reliable_update(reset ? 1 : 0, reset ? 1 : 0, last_true));
+        TRY(reliable_update(reset ? 1 : 0, reset ? 1 : 0, best_true));
         const double rt = std::sqrt(hs(h, S_BETA2)) / bnorm;
         res = rt;
         if (rt <= o->tol) { st->status = HELM_OK; break; }
         if (!std::isfinite(rt)) { st->status = HELM_DIVERGED; break; }
+        best_true = std::min(best_true, rt);
         if (reset || rejected) {
             ++restarts;
             since_start = 0;
             maxrr = last_true = rt;
+            // the complex64 recursion keeps running away: hand the rest of the solve to
+            // the FP64 BiCGStab (from the FP64 iterate, which the guard kept clean)
+            if (++troubles >= kMixedTroubles) {
+                *gave_up = true;
+                break;
+            }
             continue;
         }
         if (stop && brk != 0.0) {
@@ -1087,9 +1108,23 @@ helm_status solve_bicgstab32(helm_handle* h, const helm_solve_opts* o, const dou
         }
         maxrr = last_true = rt;
     }
-    // fold what is left of the increment and take the final true residual
-    launch_b32_fold(x, xl, N, s);
-    h->launches += 1;
+    // fold what is left of the increment and take the final true residual; without
+    // convergence the fold is tried first and taken back out if it left the iterate
+    // more than kFinalGuard times worse than the best true residual (an increment
+    // that drifted away from its recursive residual)
+    if (st->status != HELM_OK) {
+        CK(cudaMemcpyAsync(xtry, x, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        launch_b32_fold(xtry, xl, N, s, 2);
+        TRY(residual_norm(h, f, xtry, r64, o->conj, S_RN2));
+        TRY(poll(h));
+        const double rt = std::sqrt(hs(h, S_RN2)) / bnorm;
+        launch_b32_fold(x, xl, N, s, (std::isfinite(rt) && rt <= kFinalGuard * best_true) ? 0 : 1);
+        h->launches += 3;
+        ++st->matvecs;
+    } else {
+        launch_b32_fold(x, xl, N, s);
+        h->launches += 1;
+    }
     TRY(residual_norm(h, f, x, r64, o->conj, S_RN2));
     TRY(poll(h));
     st->rel_res = std::sqrt(hs(h, S_RN2)) / bnorm;
@@ -1823,7 +1858,23 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     } else if (o->method == HELM_METHOD_FGMRES) {
         TRY(solve_fgmres(h, o, f, x, &st, hist, bnorm));
     } else if (h->precision == HELM_MIXED) {
-        TRY(solve_bicgstab32(h, o, f, x, &st, hist, bnorm));
+        bool gave_up = false;
+        TRY(solve_bicgstab32(h, o, f, x, &st, hist, bnorm, &gave_up));
+        if (gave_up && st.status != HELM_OK && st.iters < o->maxit) {
+            // the rest of the iteration budget in the FP64 BiCGStab from the current
+            // iterate (complex64 cycle through conversions); the statistics add up
+            helm_solve_opts o2 = *o;
+            o2.maxit = o->maxit - st.iters;
+            helm_stats s2{};
+            s2.status = HELM_NOT_CONVERGED;
+            TRY(solve_bicgstab(h, &o2, f, x, &s2, hist, bnorm));
+            st.status = s2.status;
+            st.rel_res = s2.rel_res;
+            st.iters += s2.iters;
+            st.cycles += s2.cycles + 1;
+            st.precond_applies += s2.precond_applies;
+            st.matvecs += s2.matvecs;
+        }
     } else {
         TRY(solve_bicgstab(h, o, f, x, &st, hist, bnorm));
     }
@@ -1849,6 +1900,67 @@ helm_status helm_solve(helm_handle* h, const helm_solve_opts* o, const void* fv,
     st.apply_ms = h->profile ? ev_sum(h, 3) : 0.0;
     if (stats) *stats = st;
     return (helm_status)st.status;
+}
+
+helm_status helm_solve_concurrent(int nprob, helm_handle** hs, const helm_solve_opts* o, const double* const* f,
+                                  double* const* x, helm_stats* stats, int threads) {
+    NvtxRange nvtx("helm_solve_concurrent");
+    if (nprob < 0 || (nprob > 0 && (!hs || !o || !f || !x))) return HELM_BAD_ARG;
+    std::set<helm_handle*> seen;
+    for (int i = 0; i < nprob; ++i) {
+        if (!hs[i] || !f[i] || !x[i] || hs[i]->precision != HELM_MIXED || !seen.insert(hs[i]).second)
+            return HELM_BAD_ARG;
+    }
+    if (nprob == 0) return HELM_OK;
+    // every problem on a private non-blocking stream, ordered after its handle's stream
+    std::vector<cudaStream_t> own(nprob, nullptr), saved(nprob, nullptr);
+    std::vector<cudaEvent_t> ready(nprob, nullptr);
+    auto release = [&]() {
+        for (int i = 0; i < nprob; ++i) {
+            if (own[i]) {
+                hs[i]->stream = saved[i];
+                cudaStreamSynchronize(own[i]);
+                cudaStreamDestroy(own[i]);
+            }
+            if (ready[i]) cudaEventDestroy(ready[i]);
+        }
+    };
+    for (int i = 0; i < nprob; ++i) {
+        saved[i] = hs[i]->stream;
+        if (cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ready[i], saved[i]) != cudaSuccess || cudaStreamWaitEvent(own[i], ready[i], 0) != cudaSuccess) {
+            release();
+            return HELM_CUDA_ERROR;
+        }
+        hs[i]->stream = own[i];
+    }
+    // a pool of host threads takes the problems in index order; each runs the ordinary
+    // solve of its problem, which waits on its own stream only
+    std::vector<helm_status> st(nprob, HELM_NOT_CONVERGED);
+    std::vector<helm_stats> sv(nprob);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int i = next++; i < nprob; i = next++) st[i] = helm_solve(hs[i], o, f[i], x[i], &sv[i], nullptr, 0);
+    };
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int T = std::max(1, std::min(nprob, threads > 0 ? threads : nprob));
+    std::vector<std::thread> pool;
+    for (int q = 1; q < T; ++q)
+        pool.emplace_back([&, dev]() {
+            cudaSetDevice(dev);
+            work();
+        });
+    work();
+    for (auto& t : pool) t.join();
+    release();
+    helm_status first = HELM_OK;
+    for (int i = 0; i < nprob; ++i) {
+        if (stats) stats[i] = sv[i];
+        if (first == HELM_OK && st[i] != HELM_OK) first = st[i];
+    }
+    return first;
 }
 
 helm_status helm_receivers_setup(helm_handle* h, int nrec, const double* xyz, int* idx, double* w) {

@@ -706,12 +706,15 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1)
             float2 sa = z2;
             if (!XZERO && !(ca & kMasked)) {
                 const float4* P = xs + o_0;
+                // the y and z neighbours: node ar of the neighbouring pairs, read as one
+                // complex64 value each (an offset, not a select)
+                const float2* P2 = reinterpret_cast<const float2*>(xs) + ar;
                 const float2 xm = ar ? lo2(own) : hi2(P[mx + im1]);
                 const float2 xp = ar ? lo2(P[mx + ip1]) : hi2(own);
-                const float2 ym = pair_node(P[mx - TXT], ar);
-                const float2 yp = pair_node(P[mx + TXT], ar);
-                const float2 zm = pair_node(xs[o_m1 + mx], ar);
-                const float2 zp = pair_node(xs[o_p1 + mx], ar);
+                const float2 ym = P2[2 * (o_0 + mx - TXT)];
+                const float2 yp = P2[2 * (o_0 + mx + TXT)];
+                const float2 zm = P2[2 * (o_m1 + mx)];
+                const float2 zp = P2[2 * (o_p1 + mx)];
                 sa = six_sum(ca, xm, xp, ym, yp, zm, zp);
             }
             const float2 id = (ca & kMasked) ? z2 : sweep_invd(op, stab, l, ar, ar ? (lc >> 8) : (lc & 0xffu), conj);

@@ -274,6 +274,29 @@ def _driver_version():
     return v.value
 
 
+def solve_concurrent(problems, fs, xs=None, o: "SolveOpts | None" = None, threads: int = 0):
+    """helm_solve_concurrent: every problem (distinct HELM_MIXED Problems) solved by its
+    own solve on its own stream, overlapped on the GPU, each stopping at its own
+    convergence.  Returns (solutions, per-problem statistics)."""
+    lib = L.lib()
+    o = o or opts("bicgstab", "rbgs", 3, tol=1e-6, maxit=20000)
+    n = len(problems)
+    xs = [torch.zeros_like(f) for f in fs] if xs is None else [x.clone() for x in xs]
+    hs = (C.c_void_p * n)(*[P.h for P in problems])
+    fp = (C.c_void_p * n)(*[f.data_ptr() for f in fs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    stats = (Stats * n)()
+    rc = lib.helm_solve_concurrent(n, hs, C.byref(o), fp, xp, stats, int(threads))
+    if rc in (L.HELM_BAD_ARG, L.HELM_CUDA_ERROR, L.HELM_NOT_READY, L.HELM_OUT_OF_MEMORY):
+        raise HelmError(rc, "helm_solve_concurrent")
+    out = []
+    for s_ in stats:
+        d = s_.as_dict()
+        d["status_name"] = L.STATUS_NAMES.get(d["status"], d["status"])
+        out.append(d)
+    return xs, out
+
+
 class Batch:
     """Many independent problems (HELM_MIXED Problems with a loaded trunk basis)
     solved together by batched FGMRES: one launch per phase over all problems."""

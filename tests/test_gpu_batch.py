@@ -126,3 +126,36 @@ def test_batched_bicgstab_maxit_and_zero_rhs():
         b = assemble.rhs(3, scs[i].n, scs[i].mask, scs[i].src, scs[i].g)
         res = np.linalg.norm(b - A @ xs[i].cpu().numpy()) / np.linalg.norm(b)
         assert abs(res - st[i]["rel_res"]) <= 1e-6 * res
+
+
+def test_concurrent_solves_equal_single_solves_and_reach_tolerance():
+    """helm_solve_concurrent: each problem on its own stream from a thread pool gives
+    the single-problem solve's result bit for bit (same kernels, same order on its
+    stream) and every solution meets the tolerance on the oracle's residual; even-n
+    problems take the fused complex64 sweep, odd-n ones the half-sweeps."""
+    import paper_2405_12380_gb300 as hm
+    scs, probs, fs = _batch(count=6, seed=11)
+    o = hm.opts("bicgstab", "rbgs", 3, tol=1e-6, maxit=3000)
+    for threads in (0, 2):
+        xs, st = hm.solve_concurrent(probs, fs, None, o, threads=threads)
+        for sc, P, f, x, s in zip(scs, probs, fs, xs, st):
+            assert s["status"] == 0, (sc.n, s)
+            x1, s1 = P.solve(f, None, o)
+            assert s1["iters"] == s["iters"], (sc.n, s1["iters"], s["iters"])
+            assert torch.equal(x, x1), sc.n
+            A = assemble.assemble(3, sc.n, assemble.k2_field(3, sc.n, sc.k0, 4, 0.5), sc.mask)
+            b = assemble.rhs(3, sc.n, sc.mask, sc.src, sc.g)
+            res = np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b)
+            assert res <= 1.0001e-6, (sc.n, res)
+
+
+def test_concurrent_solves_reject_fp64_and_repeated_handles():
+    import paper_2405_12380_gb300 as hm
+    from paper_2405_12380_gb300.helm import HelmError
+    scs, probs, fs = _batch(count=2, seed=11)
+    with pytest.raises(HelmError):
+        hm.solve_concurrent([probs[0], probs[0]], [fs[0], fs[0]])
+    sc = scs[0]
+    P64 = hm.Problem(3, sc.n, sc.k0, sc.mask, layer_cells=4)
+    with pytest.raises(HelmError):
+        hm.solve_concurrent([P64], [fs[0]])

@@ -62,3 +62,24 @@ def test_mixed_fgmres_reaches_tolerance(n_r):
     M = otb.hybrid_preconditioner(s["A"], sm, kind, n_r, colours=assemble.colour(3, 37))
     xo, io = krylov.fgmres(s["A"], b, np.zeros_like(b), M, 1e-6, 30, 3000)
     assert abs(st["iters"] - io["iters"]) <= max(5, 0.2 * io["iters"])
+
+
+def test_mixed_bicgstab_hands_over_to_fp64_bicgstab_after_runaways():
+    """A runaway threshold barely above 1 makes the complex64 BiCGStab restart again
+    and again; after four restarts the solve continues as the FP64 BiCGStab with the
+    same complex64 cycle and still reaches the tolerance on the oracle's residual (the
+    restarts and the hand-over show in the cycle count)."""
+    import paper_2405_12380_gb300 as hm
+    s, P, sm, k = _mixed_pair(n=36)
+    b = s["b"]
+    o = hm.opts("bicgstab", "rbgs", 3, tol=1e-6, maxit=3000)
+    x0, st0 = P.solve(to_dev(b), None, o)
+    assert st0["status"] == 0, st0["status_name"]
+    P.set_reliable(delta=0.1, runaway=1.0 + 1e-9, guard=1e2)
+    x, st = P.solve(to_dev(b), None, o)
+    P.set_reliable()
+    assert st["status"] == 0, st["status_name"]
+    assert st["cycles"] >= 5, st
+    res = np.linalg.norm(b - s["A"] @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert res <= 1.0001e-6, res
+    assert rel(x.cpu().numpy(), x0.cpu().numpy()) < 1e-2
