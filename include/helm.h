@@ -68,8 +68,9 @@ enum { HELM_RELAX_NONE = 0, HELM_JACOBI = 1, HELM_RBGS = 2, HELM_SOR = 3, HELM_S
 enum { HELM_CORR_NONE = 0, HELM_CORR_TB = 1, HELM_CORR_NONLINEAR = 2 };
 /* outer methods */
 enum { HELM_METHOD_RELAX = 0, HELM_METHOD_FGMRES = 1, HELM_METHOD_BICGSTAB = 2 };
-/* trunk activations on hidden layers */
-enum { HELM_ACT_TANH = 0 };
+/* trunk activations on hidden layers: tanh, or Leaky ReLU (App. B's trunk; slope
+ * 0.01 for negative arguments) */
+enum { HELM_ACT_TANH = 0, HELM_ACT_LEAKY_RELU = 1 };
 
 /* Options of one solve.  `relax`, `n_r`, `omega` and `correction` define the
  * hybrid cycle M (Eq. 3): n_r relaxation sweeps from zero, then M2 on the new
@@ -232,7 +233,8 @@ helm_status helm_relax(helm_handle* h, int kind, double omega, int sweeps, const
  * span(Q) = span(selected columns); A_c = Q^T A Q (complex, k x k); A_c^-1 by
  * Gauss-Jordan with partial pivoting.
  * weights [host] FP64: per layer W (row-major out x in) then bias; widths[0] = dim,
- * widths[n_layers] >= p; activation on hidden layers only.  p <= 256.
+ * widths[n_layers] >= p; act (HELM_ACT_TANH or HELM_ACT_LEAKY_RELU) on hidden layers
+ * only.  p <= 256.
  * Synchronises.  Returns HELM_SINGULAR_COARSE on a zero pivot. */
 helm_status don_load(helm_handle* h, const double* weights, const int* widths, int n_layers,
                      int act, int p, double tau);
@@ -309,7 +311,8 @@ helm_status helm_set_k2(helm_handle* h, const double* k2);
 /* ---- dense layers for DeepONet training (App. B), FP32, row-major, on `stream` ----
  * nn_gemm: C = alpha op(A) op(B) + beta C; op(A) is M x K (A stored K x M when
  * transA), op(B) is K x N (B stored N x K when transB).
- * nn_bias_act: X = act(X + bias) in place, act 0 = none, 1 = ReLU, 2 = tanh (bias may be NULL).
+ * nn_bias_act: X = act(X + bias) in place, act 0 = none, 1 = ReLU, 2 = tanh, 3 = Leaky
+ *   ReLU (slope 0.01) (bias may be NULL).
  * nn_act_backward: dX *= act'(Y), Y the activation output.
  * nn_bias_grad: db[c] = sum_r dY[r][c].
  * nn_adam: Adam with bias correction, step t >= 1.

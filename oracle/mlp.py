@@ -27,6 +27,18 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+LEAKY_SLOPE = 0.01   # Leaky ReLU slope of the trunk (App. B; PyTorch's default)
+
+
+def leaky_relu(x):
+    return np.where(x > 0, x, LEAKY_SLOPE * x)
+
+
+def leaky_relu_deriv(H):
+    """Derivative from the activation output (same sign as its input)."""
+    return np.where(H > 0, 1.0, LEAKY_SLOPE)
+
+
 def mlp_backward(layers, acts, dout, act_deriv):
     """Gradients (dW, db) per layer given d(loss)/d(output); act_deriv(H) = act'(pre) from the output H."""
     grads = [None] * len(layers)

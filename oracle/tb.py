@@ -21,6 +21,14 @@ import scipy.linalg as sla
 from . import relax
 
 
+LEAKY_SLOPE = 0.01   # Leaky ReLU slope (the paper names the function only; PyTorch's default)
+
+
+def leaky_relu(a):
+    """Leaky ReLU, the trunk's activation in App. B: a for a > 0, LEAKY_SLOPE * a else."""
+    return np.where(a > 0, a, LEAKY_SLOPE * a)
+
+
 def mlp_forward(layers, X, act=np.tanh):
     """Fully connected net: act on hidden layers, linear output (App. B)."""
     a = np.asarray(X, dtype=np.float64)
@@ -43,9 +51,9 @@ class TBSetup:
         return self.Q.shape[1]
 
 
-def trunk_matrix(layers, coords, mask, p: int) -> np.ndarray:
+def trunk_matrix(layers, coords, mask, p: int, act=np.tanh) -> np.ndarray:
     """T with natural-order first p columns and zeroed Dirichlet rows."""
-    T = mlp_forward(layers, coords)[:, :p].copy()
+    T = mlp_forward(layers, coords, act)[:, :p].copy()
     T[np.asarray(mask).reshape(-1) == 1, :] = 0.0
     return T
 
@@ -93,13 +101,14 @@ def bf16_round(Q):
     return rounded.view(np.float32).astype(np.float64)
 
 
-def tb_setup(A, layers, coords, mask, p: int, Q=None, tau: float = 0.0) -> TBSetup:
+def tb_setup(A, layers, coords, mask, p: int, Q=None, tau: float = 0.0, act=np.tanh) -> TBSetup:
     """P = natural-order selection of the first p trunk columns (drop tolerance
     tau), Q orthonormal with span(Q) = span(P), A_c = Q^T A Q, LU with partial
-    pivoting.  A caller may pass its own orthonormal Q (e.g. a rounded copy)."""
+    pivoting.  A caller may pass its own orthonormal Q (e.g. a rounded copy).
+    act: the trunk's hidden-layer activation (tanh, or leaky_relu as in App. B)."""
     kept = None
     if Q is None:
-        T = trunk_matrix(layers, coords, mask, p)
+        T = trunk_matrix(layers, coords, mask, p, act)
         if tau > 0:
             Q, kept = natural_order_select(T, tau)
         else:

@@ -24,6 +24,7 @@ HELM_RELAX_NONE, HELM_JACOBI, HELM_RBGS, HELM_SOR, HELM_SSOR, HELM_MG = 0, 1, 2,
 HELM_CORR_NONE, HELM_CORR_TB, HELM_CORR_NONLINEAR = 0, 1, 2
 HELM_METHOD_RELAX, HELM_METHOD_FGMRES, HELM_METHOD_BICGSTAB = 0, 1, 2
 HELM_ACT_TANH = 0
+HELM_ACT_LEAKY_RELU = 1
 
 
 class SolveOpts(C.Structure):

@@ -1546,7 +1546,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
                      double tau) {
     NvtxRange nvtx("don_load: trunk basis setup");
     if (!h || !weights || !widths) return fail(h, HELM_BAD_ARG, "null argument");
-    if (act != HELM_ACT_TANH) return fail(h, HELM_BAD_ARG, "activation");
+    if (act != HELM_ACT_TANH && act != HELM_ACT_LEAKY_RELU) return fail(h, HELM_BAD_ARG, "activation");
     drop_graphs(h);
     if (n_layers < 1 || n_layers > 7) return fail(h, HELM_BAD_ARG, "n_layers must be 1..7");
     if (widths[0] != h->dim) return fail(h, HELM_BAD_ARG, "widths[0] must equal dim");
@@ -1605,7 +1605,7 @@ helm_status don_load(helm_handle* h, const double* weights, const int* widths, i
     STEP(dalloc(h, &Rinv, (size_t)p * p));
     STEP(dalloc(h, &kept, (size_t)p));
     STEP(dalloc(h, &part, (size_t)2 * 152 * 64 * 64 * 4 + (size_t)p * 2 * p * 16));
-    launch_trunk_eval(h->op64, dW, widths, n_layers, p, T, ldt, s);
+    launch_trunk_eval(h->op64, dW, widths, n_layers, p, act, T, ldt, s);
     dfree(h->Traw);
     STEP(dalloc(h, &h->Traw, (size_t)N * p));
     launch_rm_to_cm_f32(T, ldt, p, h->Traw, N, s);

@@ -254,7 +254,7 @@ void launch_mupdate32(const float2* V, int nv, const double2* coef, double sign,
                       cudaStream_t s);
 
 // tb.cu
-void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p,
+void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p, int act,
                        double* T, int ldt, cudaStream_t s);
 void launch_gram(const double* A, int lda, int p, const double* B, int ldb, int q, long long N,
                  double* partials, double* out, cudaStream_t s);

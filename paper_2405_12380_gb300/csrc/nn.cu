@@ -83,13 +83,14 @@ __global__ void k_scale_matrix(int M, int N, float beta, float* __restrict__ C, 
     }
 }
 
-// X[r][c] = act(X[r][c] + bias[c]); act: 0 none, 1 ReLU, 2 tanh
+// X[r][c] = act(X[r][c] + bias[c]); act: 0 none, 1 ReLU, 2 tanh, 3 Leaky ReLU (slope 0.01)
 __global__ void k_bias_act(int rows, int cols, float* __restrict__ X, const float* __restrict__ bias, int act) {
     const long long total = (long long)rows * cols;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         float v = X[e] + (bias ? bias[e % cols] : 0.f);
         if (act == 1) v = fmaxf(v, 0.f);
         else if (act == 2) v = tanhf(v);
+        else if (act == 3) v = v > 0.f ? v : 0.01f * v;
         X[e] = v;
     }
 }
@@ -100,6 +101,7 @@ __global__ void k_act_backward(long long n, float* __restrict__ dX, const float*
         const float y = Y[e];
         if (act == 1) dX[e] = y > 0.f ? dX[e] : 0.f;
         else if (act == 2) dX[e] *= (1.f - y * y);
+        else if (act == 3) dX[e] = y > 0.f ? dX[e] : 0.01f * dX[e];   // the output keeps the input's sign
     }
 }
 
@@ -201,13 +203,13 @@ helm_status nn_gemm(int transA, int transB, int M, int N, int K, float alpha, co
 }
 
 helm_status nn_bias_act(int rows, int cols, float* X, const float* bias, int act, void* stream) {
-    if (rows < 0 || cols < 0 || !X || act < 0 || act > 2) return HELM_BAD_ARG;
+    if (rows < 0 || cols < 0 || !X || act < 0 || act > 3) return HELM_BAD_ARG;
     k_bias_act<<<grid_for((long long)rows * cols), 256, 0, static_cast<cudaStream_t>(stream)>>>(rows, cols, X, bias, act);
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_CUDA_ERROR;
 }
 
 helm_status nn_act_backward(long long n, float* dX, const float* Y, int act, void* stream) {
-    if (n < 0 || !dX || !Y || act < 0 || act > 2) return HELM_BAD_ARG;
+    if (n < 0 || !dX || !Y || act < 0 || act > 3) return HELM_BAD_ARG;
     k_act_backward<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, dX, Y, act);
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_CUDA_ERROR;
 }

@@ -42,9 +42,11 @@ __device__ __forceinline__ int layer_index(int i, int n, int L) {
 constexpr int TR_NB = 16;        // nodes per block
 constexpr int TR_T = 256;        // threads = max width
 
-// dW: per layer, W^T (in x out, row-major) then bias (out)
+// dW: per layer, W^T (in x out, row-major) then bias (out); act: HELM_ACT_TANH or
+// HELM_ACT_LEAKY_RELU on the hidden layers (slope kLeakySlope for negative arguments)
+constexpr double kLeakySlope = 0.01;
 __global__ void __launch_bounds__(TR_T) k_trunk(Op<double> op, const double* __restrict__ dW, int4 w03, int4 w47,
-                                                int n_layers, int p, double* __restrict__ T, int ldt) {
+                                                int n_layers, int p, double* __restrict__ T, int ldt, int act) {
     extern __shared__ double sm[];
     double* a_in = sm;                       // [TR_NB][TR_T]
     double* a_out = sm + TR_NB * TR_T;       // [TR_NB][TR_T]
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(TR_T) k_trunk(Op<double> op, const double* __r
 #pragma unroll
             for (int nb = 0; nb < TR_NB; ++nb) {
                 double v = acc[nb] + bo;
-                a_out[nb * TR_T + o] = last ? v : tanh(v);
+                a_out[nb * TR_T + o] = last ? v : (act == HELM_ACT_TANH ? tanh(v) : (v > 0.0 ? v : kLeakySlope * v));
             }
         }
         __syncthreads();
@@ -1150,15 +1152,15 @@ __global__ void __launch_bounds__(256) k_prolong32v(const __nv_bfloat16* __restr
 
 }  // namespace
 
-void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p, double* T,
-                       int ldt, cudaStream_t s) {
+void launch_trunk_eval(const Op<double>& op, const double* dW, const int* widths, int n_layers, int p, int act,
+                       double* T, int ldt, cudaStream_t s) {
     int w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = 0; i <= n_layers && i < 8; ++i) w[i] = widths[i];
     size_t smem = 2 * TR_NB * TR_T * sizeof(double);
     cudaFuncSetAttribute(k_trunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     long long blocks = (op.N + TR_NB - 1) / TR_NB;
     k_trunk<<<(unsigned)blocks, TR_T, smem, s>>>(op, dW, make_int4(w[0], w[1], w[2], w[3]),
-                                                 make_int4(w[4], w[5], w[6], w[7]), n_layers, p, T, ldt);
+                                                 make_int4(w[4], w[5], w[6], w[7]), n_layers, p, T, ldt, act);
 }
 
 void launch_gram(const double* A, int lda, int p, const double* B, int ldb, int q, long long N, double* partials,

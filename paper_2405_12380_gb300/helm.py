@@ -144,15 +144,17 @@ class Problem:
                                         _dtype_code(x)), "relax")
         return x
 
-    def don_load(self, layers, p, tau=0.0):
-        """layers: [(W[out, in], b[out])] float64, tanh on hidden layers."""
+    def don_load(self, layers, p, tau=0.0, act="tanh"):
+        """layers: [(W[out, in], b[out])] float64; act on hidden layers: "tanh" or
+        "leaky_relu" (App. B's trunk)."""
         widths = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
         flat = np.ascontiguousarray(np.concatenate(
             [np.concatenate([np.asarray(W, np.float64).reshape(-1), np.asarray(b, np.float64)])
              for W, b in layers]))
         wd = (C.c_int * len(widths))(*widths)
         self._check(self.lib.don_load(self.h, flat.ctypes.data_as(C.c_void_p), wd, len(layers),
-                                      L.HELM_ACT_TANH, int(p), float(tau)), "don_load")
+                                      {"tanh": L.HELM_ACT_TANH, "leaky_relu": L.HELM_ACT_LEAKY_RELU}[act],
+                                      int(p), float(tau)), "don_load")
         k = C.c_int()
         idx = (C.c_int * int(p))()
         self.lib.don_info(self.h, C.byref(k), idx)

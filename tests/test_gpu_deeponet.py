@@ -34,6 +34,30 @@ def test_nn_gemm(ta, tb, M, N, K):
     assert np.max(np.abs(Cd.cpu().numpy() - ref)) <= 2e-6 * np.sqrt(K) * np.max(np.abs(ref)) + 1e-5
 
 
+@pytest.mark.parametrize("act", [1, 2, 3])
+def test_bias_act_and_backward(act):
+    """nn_bias_act / nn_act_backward for ReLU, tanh and the trunk's Leaky ReLU (App. B)
+    against the oracle's activations and their derivatives from the outputs."""
+    from paper_2405_12380_gb300 import _lib as L
+    rng = np.random.default_rng(act)
+    X = rng.standard_normal((37, 53)).astype(np.float32)
+    b = rng.standard_normal(53).astype(np.float32)
+    dY = rng.standard_normal((37, 53)).astype(np.float32)
+    f, df = {1: (mlp.relu, lambda H: (H > 0).astype(np.float64)),
+             2: (np.tanh, lambda H: 1.0 - H * H),
+             3: (mlp.leaky_relu, mlp.leaky_relu_deriv)}[act]
+    ref = f(X.astype(np.float64) + b)
+    Xd, bd, dd = to_dev(X), to_dev(b), to_dev(dY)
+    lib = L.lib()
+    assert lib.nn_bias_act(37, 53, C.c_void_p(Xd.data_ptr()), C.c_void_p(bd.data_ptr()), act, None) == 0
+    torch.cuda.synchronize()
+    Y = Xd.cpu().numpy()
+    assert np.max(np.abs(Y - ref)) <= 1e-6 * (1 + np.max(np.abs(ref)))
+    assert lib.nn_act_backward(Y.size, C.c_void_p(dd.data_ptr()), C.c_void_p(Xd.data_ptr()), act, None) == 0
+    torch.cuda.synchronize()
+    assert np.max(np.abs(dd.cpu().numpy() - dY * df(Y.astype(np.float64)))) <= 1e-6 * np.max(np.abs(dY))
+
+
 def test_training_step_matches_oracle():
     from paper_2405_12380_gb300 import train
     rng = np.random.default_rng(21)

@@ -241,3 +241,22 @@ def test_host_buffer_solve_matches_device_solve():
     st2 = P.solve_host(s["b"].copy(), xh, o)
     assert st2["status"] == 0 and st2["iters"] == st["iters"]
     assert rel(xh, x.cpu().numpy()) < 1e-14
+
+
+@pytest.mark.parametrize("dim,n,widths", [(2, 45, [2, 32, 32, 24]), (3, 37, [3, 64, 64, 40])])
+def test_leaky_relu_trunk_basis_parity(dim, n, widths):
+    """App. B's trunk with Leaky ReLU on the hidden layers: the kept columns exactly,
+    Q and A_c^-1 against the oracle's FP64 setup."""
+    s = small_scene(dim, n)
+    p, tau = widths[-1], 1e-3
+    layers = scenes.glorot_mlp(np.random.default_rng(5), widths)
+    P = problem_for(s)
+    k = P.don_load(layers, p, tau=tau, act="leaky_relu")
+    so = otb.tb_setup(s["A"], layers, scenes.node_coords(dim, n), s["mask"], p, tau=tau, act=otb.leaky_relu)
+    assert P.kept == so.kept and k == len(so.kept)
+    Q = P.basis().cpu().numpy()
+    assert rel(Q, so.Q) < 1e-9
+    assert rel(P.coarse_inverse().cpu().numpy(), np.linalg.inv(so.Ac)) < 1e-9
+    # a different network than the tanh trunk of the same weights
+    st = otb.tb_setup(s["A"], layers, scenes.node_coords(dim, n), s["mask"], p, tau=tau)
+    assert st.kept != so.kept or rel(st.Q, so.Q) > 1e-3

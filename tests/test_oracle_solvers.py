@@ -179,6 +179,33 @@ def test_mlp_forward_matches_torch():
     assert np.max(np.abs(tb.mlp_forward(layers_b, X) - ref)) < 1e-14
 
 
+def test_leaky_relu_trunk_matches_torch():
+    """The trunk of App. B with Leaky ReLU hidden layers (slope 0.01, PyTorch's default)
+    against torch; and the activation's derivative from its output against autograd."""
+    torch = pytest.importorskip("torch")
+    from oracle import mlp
+    rng = np.random.default_rng(8)
+    layers = scenes.glorot_mlp(rng, [3, 12, 9, 6])
+    X = rng.random((17, 3)) * 2 - 1
+    net = []
+    for i, (W, bb) in enumerate(layers):
+        lin = torch.nn.Linear(W.shape[1], W.shape[0]).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(W)); lin.bias.copy_(torch.from_numpy(bb - 0.2 * i))
+        net += [lin, torch.nn.LeakyReLU()]
+    seq = torch.nn.Sequential(*net[:-1])
+    layers_b = [(W, bb - 0.2 * i) for i, (W, bb) in enumerate(layers)]
+    ref = seq(torch.from_numpy(X)).detach().numpy()
+    out = tb.mlp_forward(layers_b, X, tb.leaky_relu)
+    assert np.max(np.abs(out - ref)) < 1e-14
+    assert np.max(np.abs(out - tb.mlp_forward(layers_b, X))) > 1e-3      # not the tanh network
+    a = torch.linspace(-2, 2, 41, dtype=torch.float64, requires_grad=True)
+    y = torch.nn.functional.leaky_relu(a)
+    y.sum().backward()
+    d = mlp.leaky_relu_deriv(mlp.leaky_relu(a.detach().numpy()))
+    assert np.allclose(d[a.detach().numpy() != 0], a.grad.numpy()[a.detach().numpy() != 0], rtol=0, atol=0)
+
+
 # --------------------------------------------------------------------- Krylov
 def test_givens_zeroes_second_component():
     rng = np.random.default_rng(5)
