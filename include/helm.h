@@ -319,6 +319,18 @@ helm_status helm_set_k2(helm_handle* h, const double* k2);
  * nn_rel_l2: per-sample ||pred - target||^2 / ||target||^2 over P2 values and the
  *   gradient of the batch mean with respect to pred.
  * nn_gather: dst[r][c] = src[row_idx[r]][col_idx[c]] (NULL index = identity). */
+/* 3D convolution layer of the CNN branch (App. B: 3 x 3 x 3 kernels), FP32, layout
+ * [batch][channel][z][y][x], W [Co][Ci][3][3][3]:
+ *   Y[b][o][z][y][x] = bias[o] + sum_{i, kz, ky, kx} W[o][i][kz][ky][kx]
+ *                      X[b][i][z s + kz - pad][y s + ky - pad][x s + kx - pad]
+ * (zeros outside X), Y [dev] B x Co x Do^3 with Do = (D + 2 pad - 3) / s + 1; bias may be
+ * NULL.  nn_conv3d_backward writes, for the given dY, dX (B x Ci x D^3), dW and db (Co)
+ * of sum(dY * Y); any of the three may be NULL.  Every value is summed in a fixed
+ * order (no atomics).  stride >= 1, 0 <= pad <= 2; HELM_BAD_ARG otherwise. */
+helm_status nn_conv3d(int B, int Ci, int D, int Co, int stride, int pad, const float* X, const float* W,
+                      const float* bias, float* Y, void* stream);
+helm_status nn_conv3d_backward(int B, int Ci, int D, int Co, int stride, int pad, const float* X, const float* W,
+                               const float* dY, float* dX, float* dW, float* db, void* stream);
 helm_status nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float* A, int lda,
                     const float* B, int ldb, float beta, float* C, int ldc, void* stream);
 helm_status nn_bias_act(int rows, int cols, float* X, const float* bias, int act, void* stream);

@@ -13,6 +13,8 @@ Modules:
   krylov    -- FGMRES(m) with CGS2 + complex Givens, right-preconditioned BiCGStab,
                relaxation meta-solver (hybrid Richardson)
   mlp       -- DeepONet branch/trunk MLP forward/backward, relative-L2 loss, Adam (App. B)
+  cnn       -- 3D convolution layers of the CNN branch, forward and gradients (App. B)
+  bvp, mg   -- the Sommerfeld / Neumann boundary rows (Eq. 1), the multigrid V-cycle (Sec. 4.3)
   adjoint   -- receiver sampling, adjoint solve and k^2 gradient
 
 Parity status: every function is pinned by tests/test_oracle_*.py against closed

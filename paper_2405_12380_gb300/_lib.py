@@ -82,6 +82,8 @@ SIGNATURES = {
     "nn_gemm": (i32, [i32, i32, i32, i32, i32, C.c_float, vp, i32, vp, i32, C.c_float, vp, i32, vp]),
     "nn_gemm_bf16": (i32, [i32, i32, i32, i32, i32, C.c_float, vp, i32, vp, i32, C.c_float, vp, i32, vp]),
     "nn_gemm_bf16_status": (i32, [C.POINTER(i32)]),
+    "nn_conv3d": (i32, [i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]),
+    "nn_conv3d_backward": (i32, [i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "nn_bias_act": (i32, [i32, i32, vp, vp, i32, vp]),
     "nn_act_backward": (i32, [i64, vp, vp, i32, vp]),
     "nn_bias_grad": (i32, [i32, i32, vp, vp, vp]),

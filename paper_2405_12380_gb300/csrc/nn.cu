@@ -179,6 +179,125 @@ int grid_for(long long n) {
     return (int)(b < 8 * 152 ? (b < 1 ? 1 : b) : 8 * 152);
 }
 
+// ---- 3D convolution of the CNN branch (App. B): 3 x 3 x 3 kernels, stride s, zero
+// padding pad, layout [batch][channel][z][y][x], W[out][in][kz][ky][kx].  Every output
+// value is summed by one thread (inputs, then kz, ky, kx) or one block (fixed tree),
+// so the results do not depend on scheduling.
+constexpr int CK = 3;
+
+__device__ __forceinline__ long long vox(int D, int z, int y, int x) { return ((long long)z * D + y) * D + x; }
+
+// Y[b][o][.] = bias[o] + sum_{i,k} W[o][i][k] X[b][i][. s + k - pad]
+__global__ void k_conv3d(int B, int Ci, int D, int Co, int Do, int stride, int pad, const float* __restrict__ X,
+                         const float* __restrict__ W, const float* __restrict__ bias, float* __restrict__ Y) {
+    const long long V = (long long)Do * Do * Do, total = (long long)B * Co * V;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long v = e % V;
+        const int o = (int)((e / V) % Co), b = (int)(e / (V * Co));
+        const int ox = (int)(v % Do), oy = (int)((v / Do) % Do), oz = (int)(v / ((long long)Do * Do));
+        float acc = 0.f;
+        for (int i = 0; i < Ci; ++i) {
+            const float* xi = X + ((long long)b * Ci + i) * D * D * D;
+            const float* wi = W + ((long long)o * Ci + i) * CK * CK * CK;
+            for (int kz = 0; kz < CK; ++kz) {
+                const int z = oz * stride + kz - pad;
+                if (z < 0 || z >= D) continue;
+                for (int ky = 0; ky < CK; ++ky) {
+                    const int y = oy * stride + ky - pad;
+                    if (y < 0 || y >= D) continue;
+                    for (int kx = 0; kx < CK; ++kx) {
+                        const int x = ox * stride + kx - pad;
+                        if (x < 0 || x >= D) continue;
+                        acc = fmaf(wi[(kz * CK + ky) * CK + kx], xi[vox(D, z, y, x)], acc);
+                    }
+                }
+            }
+        }
+        Y[e] = acc + (bias ? bias[o] : 0.f);
+    }
+}
+
+// dX[b][i][p] = sum_{o,k} W[o][i][k] dY[b][o][q] over the outputs q that read p with offset k
+__global__ void k_conv3d_dx(int B, int Ci, int D, int Co, int Do, int stride, int pad, const float* __restrict__ W,
+                            const float* __restrict__ dY, float* __restrict__ dX) {
+    const long long V = (long long)D * D * D, total = (long long)B * Ci * V, Vo = (long long)Do * Do * Do;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long v = e % V;
+        const int i = (int)((e / V) % Ci), b = (int)(e / (V * Ci));
+        const int x = (int)(v % D), y = (int)((v / D) % D), z = (int)(v / ((long long)D * D));
+        float acc = 0.f;
+        for (int o = 0; o < Co; ++o) {
+            const float* dyo = dY + ((long long)b * Co + o) * Vo;
+            const float* wo = W + ((long long)o * Ci + i) * CK * CK * CK;
+            for (int kz = 0; kz < CK; ++kz) {
+                const int tz = z + pad - kz;
+                if (tz < 0 || tz % stride) continue;
+                const int oz = tz / stride;
+                if (oz >= Do) continue;
+                for (int ky = 0; ky < CK; ++ky) {
+                    const int ty = y + pad - ky;
+                    if (ty < 0 || ty % stride) continue;
+                    const int oy = ty / stride;
+                    if (oy >= Do) continue;
+                    for (int kx = 0; kx < CK; ++kx) {
+                        const int tx = x + pad - kx;
+                        if (tx < 0 || tx % stride) continue;
+                        const int ox = tx / stride;
+                        if (ox >= Do) continue;
+                        acc = fmaf(wo[(kz * CK + ky) * CK + kx], dyo[vox(Do, oz, oy, ox)], acc);
+                    }
+                }
+            }
+        }
+        dX[e] = acc;
+    }
+}
+
+// one block per weight (o, i, k) (and per bias o when i == Ci): the sum over the batch
+// and the outputs of dY X at the offset, in a fixed order (strided per thread, then a
+// shared-memory tree)
+__global__ void __launch_bounds__(256) k_conv3d_dw(int B, int Ci, int D, int Co, int Do, int stride, int pad,
+                                                   const float* __restrict__ X, const float* __restrict__ dY,
+                                                   float* __restrict__ dW, float* __restrict__ db) {
+    __shared__ float red[256];
+    const int wid = blockIdx.x;                          // o * (Ci * 27 + 1) + i * 27 + k, k = 27: bias
+    const int per = Ci * CK * CK * CK + 1;
+    const int o = wid / per, r = wid % per;
+    const bool is_bias = r == per - 1;
+    const int i = is_bias ? 0 : r / (CK * CK * CK), k = is_bias ? 0 : r % (CK * CK * CK);
+    const int kz = k / (CK * CK), ky = (k / CK) % CK, kx = k % CK;
+    const long long Vo = (long long)Do * Do * Do, total = (long long)B * Vo;
+    float acc = 0.f;
+    for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+        const int b = (int)(e / Vo);
+        const long long v = e % Vo;
+        const float g = dY[((long long)b * Co + o) * Vo + v];
+        if (is_bias) {
+            acc += g;
+            continue;
+        }
+        const int ox = (int)(v % Do), oy = (int)((v / Do) % Do), oz = (int)(v / ((long long)Do * Do));
+        const int z = oz * stride + kz - pad, y = oy * stride + ky - pad, x = ox * stride + kx - pad;
+        if (z < 0 || z >= D || y < 0 || y >= D || x < 0 || x >= D) continue;
+        acc = fmaf(g, X[((long long)b * Ci + i) * D * D * D + vox(D, z, y, x)], acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (is_bias) {
+            if (db) db[o] = red[0];
+        } else if (dW) {
+            dW[((long long)o * Ci + i) * CK * CK * CK + k] = red[0];
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -239,6 +358,30 @@ helm_status nn_gather(int rows, int cols, const float* src, long long lds, const
 helm_status nn_rel_l2(int B, int P2, const float* pred, const float* target, float* dpred, float* loss, void* stream) {
     if (B < 1 || P2 < 1 || !pred || !target || !dpred || !loss) return HELM_BAD_ARG;
     k_rel_l2<<<B, 256, 0, static_cast<cudaStream_t>(stream)>>>(B, P2, pred, target, dpred, loss);
+    return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_CUDA_ERROR;
+}
+
+helm_status nn_conv3d(int B, int Ci, int D, int Co, int stride, int pad, const float* X, const float* W,
+                      const float* bias, float* Y, void* stream) {
+    if (B < 1 || Ci < 1 || Co < 1 || D < 1 || stride < 1 || pad < 0 || pad > 2 || !X || !W || !Y) return HELM_BAD_ARG;
+    const int Do = (D + 2 * pad - CK) / stride + 1;
+    if (D + 2 * pad < CK || Do < 1) return HELM_BAD_ARG;
+    k_conv3d<<<grid_for((long long)B * Co * Do * Do * Do), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        B, Ci, D, Co, Do, stride, pad, X, W, bias, Y);
+    return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_CUDA_ERROR;
+}
+
+helm_status nn_conv3d_backward(int B, int Ci, int D, int Co, int stride, int pad, const float* X, const float* W,
+                               const float* dY, float* dX, float* dW, float* db, void* stream) {
+    if (B < 1 || Ci < 1 || Co < 1 || D < 1 || stride < 1 || pad < 0 || pad > 2 || !dY) return HELM_BAD_ARG;
+    if ((dX && !W) || ((dW || db) && !X)) return HELM_BAD_ARG;
+    const int Do = (D + 2 * pad - CK) / stride + 1;
+    if (D + 2 * pad < CK || Do < 1) return HELM_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dX)
+        k_conv3d_dx<<<grid_for((long long)B * Ci * D * D * D), 256, 0, s>>>(B, Ci, D, Co, Do, stride, pad, W, dY, dX);
+    if (dW || db)
+        k_conv3d_dw<<<Co * (Ci * CK * CK * CK + 1), 256, 0, s>>>(B, Ci, D, Co, Do, stride, pad, X, dY, dW, db);
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_CUDA_ERROR;
 }
 

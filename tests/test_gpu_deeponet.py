@@ -58,6 +58,38 @@ def test_bias_act_and_backward(act):
     assert np.max(np.abs(dd.cpu().numpy() - dY * df(Y.astype(np.float64)))) <= 1e-6 * np.max(np.abs(dY))
 
 
+@pytest.mark.parametrize("B,Ci,D,Co,stride,pad", [(4, 3, 17, 8, 2, 0), (3, 8, 8, 8, 1, 1), (2, 8, 8, 12, 2, 0)])
+def test_conv3d_layers_match_oracle(B, Ci, D, Co, stride, pad):
+    """The CNN branch's convolution layers (App. B; the three layer shapes of the 3D
+    branch with fewer channels): forward and all three gradients against the FP64
+    oracle (oracle/cnn.py)."""
+    from oracle import cnn
+    from paper_2405_12380_gb300 import _lib as L
+    rng = np.random.default_rng(B + Ci + D)
+    X = rng.standard_normal((B, Ci, D, D, D)).astype(np.float32)
+    W = (rng.standard_normal((Co, Ci, 3, 3, 3)) / np.sqrt(27 * Ci)).astype(np.float32)
+    b = rng.standard_normal(Co).astype(np.float32)
+    Do = cnn.out_size(D, stride, pad)
+    dY = rng.standard_normal((B, Co, Do, Do, Do)).astype(np.float32)
+    Xd, Wd, bd, dYd = to_dev(X), to_dev(W), to_dev(b), to_dev(dY)
+    Yd = torch.empty((B, Co, Do, Do, Do), dtype=torch.float32, device="cuda")
+    dXd, dWd, dbd = torch.empty_like(Xd), torch.empty_like(Wd), torch.empty_like(bd)
+    p = lambda t: C.c_void_p(t.data_ptr())
+    lib = L.lib()
+    assert lib.nn_conv3d(B, Ci, D, Co, stride, pad, p(Xd), p(Wd), p(bd), p(Yd), None) == 0
+    assert lib.nn_conv3d_backward(B, Ci, D, Co, stride, pad, p(Xd), p(Wd), p(dYd), p(dXd), p(dWd), p(dbd), None) == 0
+    torch.cuda.synchronize()
+    Y = cnn.conv3d(X, W, b, stride, pad)
+    dX, dW, db = cnn.conv3d_backward(X, W, dY, stride, pad)
+    # FP32 sums of up to B Do^3 = 2048 products (fixed order)
+    assert rel(Yd.cpu().numpy(), Y) < 1e-5
+    assert rel(dXd.cpu().numpy(), dX) < 1e-5
+    assert rel(dWd.cpu().numpy(), dW) < 1e-5
+    assert rel(dbd.cpu().numpy(), db) < 1e-5
+    # invalid shapes are rejected before any launch
+    assert lib.nn_conv3d(B, Ci, 2, Co, 1, 0, p(Xd), p(Wd), p(bd), p(Yd), None) == L.HELM_BAD_ARG
+
+
 def test_training_step_matches_oracle():
     from paper_2405_12380_gb300 import train
     rng = np.random.default_rng(21)
