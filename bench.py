@@ -147,8 +147,13 @@ def reference_arm(args):
     if rank != 0:
         return
     w = scenes.BENCH_WORKLOADS[args.workload]
-    sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
     iters = reference_iterations(args.workload)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle's own iteration count for "
+                          f"{args.workload} is not stored (python -m oracle.reference_data {args.workload})"}),
+              flush=True)
+        return
+    sc = scenes.make_scene(w["scene"], seed=w["seed"], n=w["n"])
     from oracle import assemble, krylov, tb
     A, b, _ = assemble.problem(sc)
     X = scenes.node_coords(sc.dim, sc.n)
