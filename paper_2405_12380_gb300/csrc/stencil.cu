@@ -5,8 +5,12 @@
 // come from per-layer tables in Op (or the stored field).  Kernel families:
 //   k_apply_z        3D operator/residual marching in z (planes in registers,
 //                    x-neighbours by warp shuffles), complex128 and complex64
-//   k_march_c64      3D complex64 operator and damped Jacobi, two nodes per thread
+//   k_march_c64      3D complex64 operator and damped Jacobi, two nodes per thread; the
+//                    red rows' residual; the operator with the partial sums of a
+//                    BiCGStab scalar (DOT)
 //   k_rbgs_c64       3D complex64 red-black half-sweep, two nodes per thread
+//   k_sweep_c64      3D complex64 full red-black sweep in one launch (old planes
+//                    staged in shared memory by cp.async, halo rows recomputed)
 //   k_apply, k_jacobi, k_rbgs   the general forms (2D, no tables, complex128)
 //   k_apply_bicg(_df)           the BiCGStab operator with its fused reduction
 //   k_cycle_df       the red-black part of the FP64 trunk-basis hybrid cycle in
