@@ -44,6 +44,17 @@ def test_mixed_128_reaches_tolerance_on_oracle_residual():
     res = np.linalg.norm(b - A @ xh) / np.linalg.norm(b)
     assert res <= 1.0001e-6, res
     assert abs(res - st["rel_res"]) <= 1e-9, (res, st["rel_res"])
+    # against the oracle's own solution (tests/golden/solution_submarine3d-128.npz, written
+    # by oracle/reference_data.py: its BiCGStab continued to 1e-10) on the stored node
+    # sample: the error of a solve to 1e-6 is set by the conditioning, so it is compared
+    # with the error the oracle's own iterate at 1e-6 makes
+    gpath = os.path.join(HERE, "golden", "solution_submarine3d-128.npz")
+    if os.path.exists(gpath):
+        gold = np.load(gpath)
+        idx = gold["idx"]
+        err = np.linalg.norm(xh[idx] - gold["x"]) / np.linalg.norm(gold["x"])
+        err_tol = np.linalg.norm(gold["x_tol"] - gold["x"]) / np.linalg.norm(gold["x"])
+        assert err <= max(20 * err_tol, 1e-3), (err, err_tol)
 
 
 def test_adjoint_96_against_oracle_data_and_central_differences():
