@@ -1947,11 +1947,15 @@ helm_status helm_solve_concurrent(int nprob, helm_handle** hs, const helm_solve_
     cudaGetDevice(&dev);
     const int T = std::max(1, std::min(nprob, threads > 0 ? threads : nprob));
     std::vector<std::thread> pool;
-    for (int q = 1; q < T; ++q)
-        pool.emplace_back([&, dev]() {
-            cudaSetDevice(dev);
-            work();
-        });
+    try {
+        for (int q = 1; q < T; ++q)
+            pool.emplace_back([&, dev]() {
+                cudaSetDevice(dev);
+                work();
+            });
+    } catch (...) {
+        // no more threads: the ones started and this one take the remaining problems
+    }
     work();
     for (auto& t : pool) t.join();
     release();
