@@ -63,3 +63,19 @@ def test_checked_build_exports_the_same_boundary():
     lib = ctypes.CDLL(build.LIB_CHECKED)
     for name in _declared():
         assert hasattr(lib, name), name
+
+
+def test_argument_checks_need_no_device(libpath):
+    """Entry points reject bad arguments before touching the GPU: the concurrent solve
+    (negative count, null handles; an empty batch is a no-op) and the convolution layer
+    (a kernel larger than the padded input, a zero stride)."""
+    from paper_2405_12380_gb300 import _lib
+    L = _lib.lib()
+    assert L.helm_solve_concurrent(-1, None, None, None, None, None, 0) == _lib.HELM_BAD_ARG
+    assert L.helm_solve_concurrent(2, None, None, None, None, None, 0) == _lib.HELM_BAD_ARG
+    assert L.helm_solve_concurrent(0, None, None, None, None, None, 0) == _lib.HELM_OK
+    buf = (ctypes.c_float * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.nn_conv3d(1, 1, 2, 1, 1, 0, p, p, None, p, None) == _lib.HELM_BAD_ARG
+    assert L.nn_conv3d(1, 1, 8, 1, 0, 0, p, p, None, p, None) == _lib.HELM_BAD_ARG
+    assert L.nn_conv3d_backward(1, 1, 8, 1, 1, 3, p, p, p, p, p, p, None) == _lib.HELM_BAD_ARG
